@@ -1,0 +1,269 @@
+"""ctypes front end of the FP64 CPU oracle (``lbmd_oracle.c``).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` import this module.  The product library
+(``paper_1610_02733_gb300``) never does.
+
+``build()`` compiles the C oracle with gcc into ``oracle/_build``.  The
+``Oracle`` class mirrors the state machine of the paper's coupled LB/MD
+scheme (Sec. 3): ``md_substep`` m times, then ``lb_step``.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liblbmd_oracle.so")
+_SRC = os.path.join(_HERE, "lbmd_oracle.c")
+
+ORC_OK = 0
+ORC_ERR_SEQUENCE = -4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C99, -O2, no fast-math) and return the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    hdr = os.path.join(_HERE, "lbmd_oracle.h")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrcParams(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32),
+        ("n_sub", ct.c_int32), ("variant", ct.c_int32), ("pad_", ct.c_int32),
+        ("rho0", ct.c_double), ("nu", ct.c_double), ("nu_bulk", ct.c_double),
+        ("gamma_ghost", ct.c_double), ("kT", ct.c_double), ("zeta", ct.c_double),
+        ("body_force", ct.c_double * 3), ("seed", ct.c_uint64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ct.CDLL(build())
+        L = _lib
+        P = ct.c_void_p
+        dp = ct.POINTER(ct.c_double)
+        L.orc_create.restype = P
+        L.orc_create.argtypes = [ct.POINTER(OrcParams)]
+        L.orc_destroy.argtypes = [P]
+        L.orc_add_particles.argtypes = [P, ct.c_int64, dp, dp, dp]
+        L.orc_add_bonds.argtypes = [P, ct.c_int64, ct.POINTER(ct.c_int64), ct.c_double, ct.c_double]
+        L.orc_md_substep.argtypes = [P]
+        L.orc_lb_step.argtypes = [P]
+        L.orc_observables.argtypes = [P, dp]
+        for name in ("orc_get_populations", "orc_set_populations", "orc_get_jacc", "orc_set_jacc",
+                     "orc_get_node_field", "orc_get_coupling_forces"):
+            getattr(L, name).argtypes = [P, dp]
+        L.orc_get_particles.argtypes = [P, dp, dp]
+        L.orc_set_particles.argtypes = [P, dp, dp]
+        L.orc_counters.argtypes = [P, ct.POINTER(ct.c_int64)]
+        L.orc_set_counters.argtypes = [P, ct.c_int64, ct.c_int64]
+        L.orc_num_particles.restype = ct.c_int64
+        L.orc_num_particles.argtypes = [P]
+        u32p = ct.POINTER(ct.c_uint32)
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_uniform_unit.restype = ct.c_double
+        L.orc_uniform_unit.argtypes = [ct.c_uint32]
+        L.orc_d3q19.argtypes = [ct.POINTER(ct.c_int32), dp]
+        L.orc_modes.argtypes = [dp, dp]
+        L.orc_collide_node.argtypes = [P, dp, dp, ct.c_uint32, ct.c_uint32, dp]
+        L.orc_trilinear.argtypes = [P, dp, ct.POINTER(ct.c_int64), dp]
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = (ct.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ct.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ct.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def uniform_unit(x: int) -> float:
+    return lib().orc_uniform_unit(int(x) & 0xFFFFFFFF)
+
+
+def d3q19():
+    c = np.zeros(57, dtype=np.int32)
+    w = np.zeros(19)
+    lib().orc_d3q19(c.ctypes.data_as(ct.POINTER(ct.c_int32)), _dp(w))
+    return c.reshape(19, 3), w
+
+
+def modes():
+    e = np.zeros(19 * 19)
+    b = np.zeros(19)
+    lib().orc_modes(_dp(e), _dp(b))
+    return e.reshape(19, 19), b
+
+
+class Oracle:
+    """The oracle's state: populations, pending momentum transfer, particles.
+
+    Parameters follow the C-ABI of the GPU library: lattice units (a = 1,
+    tau_LB = 1), ``n_sub`` = m MD steps per LB step, ``variant`` 0 = A, 1 = B.
+    """
+
+    def __init__(self, nx, ny, nz, *, n_sub=1, variant=1, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
+                 gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1):
+        p = OrcParams()
+        p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+        p.n_sub, p.variant = int(n_sub), int(variant)
+        p.rho0, p.nu, p.nu_bulk, p.gamma_ghost = float(rho0), float(nu), float(nu_bulk), float(gamma_ghost)
+        p.kT, p.zeta = float(kT), float(zeta)
+        for a in range(3):
+            p.body_force[a] = float(body_force[a])
+        p.seed = int(seed)
+        self.params = p
+        self.shape = (int(nx), int(ny), int(nz))
+        self.n_nodes = int(nx) * int(ny) * int(nz)
+        self.n_sub = int(n_sub)
+        h = lib().orc_create(ct.byref(p))
+        if not h:
+            raise ValueError("orc_create rejected the parameters")
+        self._h = ct.c_void_p(h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state machine ---------------------------------------------------------
+    def add_particles(self, pos, vel, mass=None):
+        pos = _f64(pos).reshape(-1, 3)
+        vel = _f64(vel).reshape(-1, 3)
+        m = None if mass is None else _f64(mass).reshape(-1)
+        rc = lib().orc_add_particles(self._h, pos.shape[0], _dp(pos), _dp(vel),
+                                     None if m is None else _dp(m))
+        if rc != ORC_OK:
+            raise RuntimeError("orc_add_particles: %d" % rc)
+
+    def add_bonds(self, pairs, k, r0):
+        pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+        rc = lib().orc_add_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
+                                 float(k), float(r0))
+        if rc != ORC_OK:
+            raise RuntimeError("orc_add_bonds: %d" % rc)
+
+    def md_substep(self) -> int:
+        return lib().orc_md_substep(self._h)
+
+    def lb_step(self) -> int:
+        return lib().orc_lb_step(self._h)
+
+    def cycle(self, k: int = 1):
+        for _ in range(k):
+            for _ in range(self.n_sub):
+                rc = self.md_substep()
+                assert rc == ORC_OK, rc
+            rc = self.lb_step()
+            assert rc == ORC_OK, rc
+
+    # accessors -------------------------------------------------------------
+    def observables(self) -> dict:
+        o = np.zeros(11)
+        lib().orc_observables(self._h, _dp(o))
+        return {"mass": o[0], "p_fluid": o[1:4].copy(), "p_particles": o[4:7].copy(),
+                "kT_particles": o[7], "e_kin": o[8], "lb_step": int(o[9]), "md_step": int(o[10])}
+
+    def populations(self) -> np.ndarray:
+        out = np.zeros(19 * self.n_nodes)
+        lib().orc_get_populations(self._h, _dp(out))
+        return out.reshape(19, self.n_nodes)
+
+    def set_populations(self, f):
+        f = _f64(f).reshape(-1)
+        assert f.size == 19 * self.n_nodes
+        lib().orc_set_populations(self._h, _dp(f))
+
+    def jacc(self) -> np.ndarray:
+        out = np.zeros(3 * self.n_nodes)
+        lib().orc_get_jacc(self._h, _dp(out))
+        return out.reshape(self.n_nodes, 3)
+
+    def set_jacc(self, j):
+        j = _f64(j).reshape(-1)
+        assert j.size == 3 * self.n_nodes
+        lib().orc_set_jacc(self._h, _dp(j))
+
+    def node_field(self) -> np.ndarray:
+        out = np.zeros(4 * self.n_nodes)
+        lib().orc_get_node_field(self._h, _dp(out))
+        return out.reshape(self.n_nodes, 4)
+
+    @property
+    def n_particles(self) -> int:
+        return int(lib().orc_num_particles(self._h))
+
+    def particles(self):
+        n = self.n_particles
+        pos = np.zeros(3 * max(n, 1))
+        vel = np.zeros(3 * max(n, 1))
+        lib().orc_get_particles(self._h, _dp(pos), _dp(vel))
+        return pos[:3 * n].reshape(n, 3), vel[:3 * n].reshape(n, 3)
+
+    def set_particles(self, pos=None, vel=None):
+        n = self.n_particles
+        p = None if pos is None else _f64(pos).reshape(n, 3)
+        v = None if vel is None else _f64(vel).reshape(n, 3)
+        lib().orc_set_particles(self._h, None if p is None else _dp(p), None if v is None else _dp(v))
+
+    def coupling_forces(self) -> np.ndarray:
+        n = self.n_particles
+        out = np.zeros(3 * max(n, 1))
+        lib().orc_get_coupling_forces(self._h, _dp(out))
+        return out[:3 * n].reshape(n, 3)
+
+    def counters(self):
+        o = (ct.c_int64 * 3)()
+        lib().orc_counters(self._h, o)
+        return int(o[0]), int(o[1]), int(o[2])
+
+    def set_counters(self, lb_step, md_step):
+        lib().orc_set_counters(self._h, int(lb_step), int(md_step))
+
+    # building blocks ---------------------------------------------------------
+    def collide_node(self, f, F, node=0, lb_step=0) -> np.ndarray:
+        f = _f64(f).reshape(19)
+        F = _f64(F).reshape(3)
+        out = np.zeros(19)
+        lib().orc_collide_node(self._h, _dp(f), _dp(F), int(node), int(lb_step), _dp(out))
+        return out
+
+    def trilinear(self, R):
+        R = _f64(R).reshape(3)
+        corner = np.zeros(8, dtype=np.int64)
+        delta = np.zeros(8)
+        lib().orc_trilinear(self._h, _dp(R), corner.ctypes.data_as(ct.POINTER(ct.c_int64)), _dp(delta))
+        return corner, delta

@@ -1,0 +1,69 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module draws initial conditions only; it holds none of the method's
+arithmetic (no lattice weights, no equilibria, no coupling).  Both the GPU
+library and the CPU oracle receive the arrays it returns as plain inputs, so
+initial-condition generation is input data, not shared compute.
+
+The workloads follow the paper's set-up (Sec. 3): ideal or bead-spring point
+particles at uniform-random positions in a periodic box, Maxwellian velocities
+at temperature kT, the fluid initially at rest.  Every generator takes an
+explicit integer seed and uses numpy's Philox bit generator, so the same seed
+gives the same arrays on every machine.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=int(seed) & (2**64 - 1), counter=[0, 0, 0, int(stream)]))
+
+
+def uniform_positions(n: int, shape, seed: int) -> np.ndarray:
+    """n positions uniform in [0, nx) x [0, ny) x [0, nz), float64 (n, 3)."""
+    g = _rng(seed, 1)
+    L = np.asarray(shape, dtype=np.float64)
+    pos = g.random((int(n), 3)) * L
+    # random() is in [0, 1); the product can still round up to L.
+    return np.where(pos >= L, 0.0, pos)
+
+
+def maxwell_velocities(n: int, kT: float, seed: int, mass=1.0) -> np.ndarray:
+    """Gaussian velocities with variance kT / m per component, float64 (n, 3)."""
+    g = _rng(seed, 2)
+    m = np.broadcast_to(np.asarray(mass, dtype=np.float64), (int(n),))
+    return g.standard_normal((int(n), 3)) * np.sqrt(float(kT) / m)[:, None]
+
+
+def bead_spring_chains(n_chains: int, n_beads: int, shape, seed: int, step: float = 1.0):
+    """Random-walk chains: the first bead uniform in the box, each next bead at
+    distance ``step`` in a uniformly random direction (positions wrapped into
+    the box).  Returns (pos (n_chains*n_beads, 3), bonds (n_chains*(n_beads-1), 2))."""
+    g = _rng(seed, 3)
+    L = np.asarray(shape, dtype=np.float64)
+    pos = np.zeros((n_chains, n_beads, 3))
+    pos[:, 0, :] = g.random((n_chains, 3)) * L
+    d = g.standard_normal((n_chains, max(n_beads - 1, 0), 3))
+    d /= np.linalg.norm(d, axis=2, keepdims=True)
+    if n_beads > 1:
+        pos[:, 1:, :] = pos[:, :1, :] + np.cumsum(step * d, axis=1)
+    pos = np.mod(pos, L)
+    pos = np.where(pos >= L, 0.0, pos).reshape(-1, 3)
+    first = (np.arange(n_chains)[:, None] * n_beads + np.arange(n_beads - 1)[None, :]).reshape(-1)
+    bonds = np.stack([first, first + 1], axis=1).astype(np.int64)
+    return pos, bonds
+
+
+def perturbed(base: np.ndarray, amplitude: float, seed: int) -> np.ndarray:
+    """base * (1 + amplitude * U(-1, 1)), elementwise: a random state near a
+    caller-given reference state (e.g. populations of a fluid at rest)."""
+    g = _rng(seed, 4)
+    base = np.asarray(base, dtype=np.float64)
+    return base * (1.0 + float(amplitude) * (2.0 * g.random(base.shape) - 1.0))
+
+
+def uniform(shape, lo: float, hi: float, seed: int, stream: int = 5) -> np.ndarray:
+    """Plain uniform numbers in [lo, hi) (e.g. small momentum transfers)."""
+    g = _rng(seed, stream)
+    return lo + (hi - lo) * g.random(shape)
