@@ -1,0 +1,348 @@
+"""Benchmark of the coupled LB/MD hot path on GB300.
+
+One step = one full LB cycle of the paper's scheme (Sec. 3): m = 10 MD steps
+(interpolation, friction + noise, velocity Verlet, momentum spreading) and one
+LB step (MRT collision with noise and forcing, streaming, node field), variant
+B, FP32 storage and arithmetic, on the workload
+
+    256^3 periodic D3Q19, rho = 1, nu = 1/6, kT = 1e-4,
+    10^6 ideal particles (mass 1, zeta = 1) at uniform-random positions with
+    Maxwellian velocities, dt_MD = tau_LB / 10.
+
+Reported: MLUPS (lattice node updates per second) as ``value`` and
+particle-substeps/s beside it, the roofline of the LB step against the
+measured HBM bandwidth, an end-to-end figure through the C ABI with host
+buffers, and the FP64 CPU oracle timed on a bounded sample of the same
+workload.  Inputs (2.5 GB of populations) are far larger than L2, so no L2
+flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica (the workload
+does not shard); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS + particle-substeps/s (variant B, n=10) and % of HBM roofline vs plain FP32"
+SHAPE = (256, 256, 256)
+N_PARTICLES = 1_000_000
+N_SUB = 10
+KT = 1e-4
+ZETA = 1.0
+SEED = 1
+LB_BYTES_PER_NODE = 2 * 19 * 4  # algorithmic: read and write 19 FP32 populations
+WORKLOAD = "256^3 D3Q19 + 1e6 ideal particles, variant B, n=10, FP32"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "lbmd_clocks_%d_%d.csv" % (os.getpid(), device_index))
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _setup_gpu(torch, lbmd, inputs, seed_offset=0):
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sim = lbmd.LBMD(*SHAPE, variant="B", precision="fp32", n_sub=N_SUB, kT=KT, zeta=ZETA, seed=SEED + seed_offset,
+                    max_particles=N_PARTICLES, stream=stream.cuda_stream)
+    pos = inputs.uniform_positions(N_PARTICLES, SHAPE, SEED + seed_offset)
+    vel = inputs.maxwell_velocities(N_PARTICLES, KT, SEED + seed_offset)
+    sim.add_particles(pos, vel)
+    return sim, stream, pos, vel
+
+
+def _touched_nodes(pos):
+    """Distinct nodes at the corners of the particles' cells (exact)."""
+    import numpy as np
+    base = np.floor(pos).astype(np.int64)
+    L = np.array(SHAPE)
+    ids = []
+    for k in range(8):
+        o = np.array([k & 1, (k >> 1) & 1, (k >> 2) & 1])
+        c = (base + o) % L
+        ids.append(c[:, 0] + L[0] * (c[:, 1] + L[1] * c[:, 2]))
+    return int(np.unique(np.concatenate(ids)).size)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1610_02733_gb300 import inputs, lbmd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+
+    sim, stream, pos0, vel0 = _setup_gpu(torch, lbmd, inputs, seed_offset=rank)
+    n_nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
+
+    for _ in range(args.warmup):
+        sim.cycle(1)
+    stream.synchronize()
+
+    # timed region: K full cycles, device-resident inputs; events around each
+    # LB step give the per-launch duration of the LB kernels
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(args.steps):
+        for _ in range(N_SUB):
+            sim.md_substep()
+        ev[k][0].record(stream)
+        sim.lb_step()
+        ev[k][1].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(stop)
+    lb_ms = [a.elapsed_time(b) for a, b in ev]
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+
+    ms_per_step = total_ms / args.steps
+    mlups = world * n_nodes * args.steps / (total_ms * 1e-3) / 1e6
+    psubsteps = world * N_PARTICLES * N_SUB * args.steps / (total_ms * 1e-3)
+    lb_avg_ms = float(np.mean(lb_ms))
+    md_ms = ms_per_step - lb_avg_ms
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # particle state from pinned host memory, runs the cycle, and reads the
+    # particles and the observables back
+    h_pos = torch.from_numpy(np.ascontiguousarray(pos0, dtype=np.float64).reshape(-1)).pin_memory()
+    h_vel = torch.from_numpy(np.ascontiguousarray(vel0, dtype=np.float64).reshape(-1)).pin_memory()
+    o_pos = torch.empty(3 * N_PARTICLES, dtype=torch.float64).pin_memory()
+    o_vel = torch.empty(3 * N_PARTICLES, dtype=torch.float64).pin_memory()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_steps = max(1, min(args.steps, 50))
+    for k in range(e_steps):
+        sim.set_particles(h_pos, h_vel)
+        sim.cycle(1)
+        lbmd._check(sim.handle, lbmd.load().lbmd_get_particles(sim.handle, o_pos.data_ptr(), o_vel.data_ptr()),
+                    "lbmd_get_particles")
+        sim.observables()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    e2e_s = float(te.item())
+    e2e_mlups = world * n_nodes * e_steps / e2e_s / 1e6
+
+    peak, peak_kind = _peaks()
+    achieved = LB_BYTES_PER_NODE * n_nodes / (lb_avg_ms * 1e-3) / 1e9
+    traffic = _profiled_traffic()
+    touched = _touched_nodes(pos0)
+    cycle_alg_bytes = LB_BYTES_PER_NODE * n_nodes + N_SUB * (N_PARTICLES * 48 + touched * 32)
+    line = {
+        "metric": METRIC,
+        "value": round(mlups, 1),
+        "unit": "MLUPS",
+        "particle_substeps_per_s": float("%.4g" % psubsteps),
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded uniform positions, Maxwellian velocities, fluid at rest)",
+        "config": {"workload": WORKLOAD, "lattice": list(SHAPE), "particles": N_PARTICLES, "n_sub": N_SUB,
+                   "kT": KT, "zeta": ZETA, "variant": "B", "l2": "inputs larger than L2 (2.5 GB populations)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "breakdown_ms": {"lb_step": round(lb_avg_ms, 4), "md_substeps": round(md_ms, 4)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "LB step (lb_collide_push + node_moments)",
+                     "algorithmic_bytes_per_node": LB_BYTES_PER_NODE, "peak_source": peak_kind},
+        "cycle_roofline": {"algorithmic_bytes": cycle_alg_bytes, "touched_nodes": touched,
+                           "frac": round(cycle_alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
+        "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": 2 * 3 * 8 * N_PARTICLES,
+                "d2h_bytes_per_step": 2 * 3 * 8 * N_PARTICLES + 64},
+        "gpu_launches": args.steps * (N_SUB * 2 + 2),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _profiled_traffic():
+    """DRAM bytes per LB step from the committed ncu summary, if it matches the
+    current kernel (see profiles/)."""
+    path = os.path.join(ROOT, "profiles", "lb_step_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("dram_bytes_per_lb_step")
+    except Exception:
+        return None
+
+
+def _oracle_sample(edge: int, cycles: int):
+    """Time the FP64 oracle on a sample of the workload: an edge^3 box at the
+    same particle density (10^6 / 256^3), `cycles` full cycles."""
+    from oracle import oracle as orc
+    from paper_1610_02733_gb300 import inputs
+    shape = (edge, edge, edge)
+    n = max(1, int(round(N_PARTICLES * (edge / SHAPE[0]) ** 3)))
+    o = orc.Oracle(*shape, n_sub=N_SUB, variant=1, kT=KT, zeta=ZETA, seed=SEED)
+    o.add_particles(inputs.uniform_positions(n, shape, SEED), inputs.maxwell_velocities(n, KT, SEED))
+    t0 = time.perf_counter()
+    o.cycle(cycles)
+    dt = time.perf_counter() - t0
+    o.close()
+    return dt, edge ** 3, n
+
+
+def cpu_baseline():
+    edge, cycles = 128, 2
+    dt, nodes, n = _oracle_sample(edge, cycles)
+    return {"value": round(nodes * cycles / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "particle_substeps_per_s": float("%.4g" % (n * N_SUB * cycles / dt)),
+            "sample": "%d cycles of a %d^3 box with %d particles (same density, n=10, variant B), FP64, "
+                      "single thread, %.1f s" % (cycles, edge, n, dt)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm, on the host cores; each step is one
+    cycle of a 64^3 sample of the workload at the same particle density."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    edge = 64
+    for _ in range(args.warmup):
+        _oracle_sample(edge, 1)
+    tot, nodes, n = 0.0, 0, 0
+    for _ in range(args.steps):
+        dt, nodes, n = _oracle_sample(edge, 1)
+        tot += dt
+    mlups = nodes * args.steps / tot / 1e6
+    sample = "1 cycle of a %d^3 box with %d particles per step (same density, n=10, variant B), FP64" % (edge, n)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
+        "particle_substeps_per_s": float("%.4g" % (n * N_SUB * args.steps / tot)), "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--edge", type=int, default=256, help="lattice edge (profiling of smaller cases)")
+    ap.add_argument("--particles", type=int, default=1_000_000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    global SHAPE, N_PARTICLES, WORKLOAD
+    if args.edge != 256 or args.particles != 1_000_000:
+        SHAPE = (args.edge, args.edge, args.edge)
+        N_PARTICLES = args.particles
+        WORKLOAD = "%d^3 D3Q19 + %d ideal particles, variant B, n=10, FP32" % (args.edge, args.particles)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

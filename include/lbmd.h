@@ -1,0 +1,195 @@
+/*
+ * lbmd.h -- C ABI of the GB300 library for the fluctuating D3Q19 lattice
+ * Boltzmann (LB) fluid with dissipative point-particle coupling of
+ * Tretyakov & Duenweg, arXiv:1610.02733 ("An improved dissipative coupling
+ * scheme for a system of Molecular Dynamics particles interacting with a
+ * Lattice Boltzmann fluid"), variants A and B.
+ *
+ * The calls follow the paper's statement of the problem (Sec. 3, Fig. 2):
+ * the fluid is advanced by LB steps of length tau_LB, the particles by m MD
+ * steps of length dt = tau_LB / m per LB step.  A caller therefore issues
+ *     m x lbmd_md_substep(), then 1 x lbmd_lb_step(), and repeats.
+ *
+ * Units: lattice units, lattice spacing a = 1 and tau_LB = 1.
+ * Lattice: nx x ny x nz nodes at integer coordinates, periodic in every axis.
+ * Node index: r = x + nx * (y + ny * z).
+ * Populations in host arrays: f[i * N + r], i = 0..18 in the D3Q19 order
+ *     c_0 = 0; c_1..6 = +x, -x, +y, -y, +z, -z;
+ *     c_7..18 = (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1),
+ *               (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).
+ *
+ * Ownership: the context owns every device buffer it allocates in
+ * lbmd_create; host arrays passed in are read during the call and not kept;
+ * host arrays passed out are written during the call.  The "_device" calls
+ * take device pointers that stay owned by the caller and are used in stream
+ * order on the context's stream.
+ *
+ * Errors: every call returns an lbmd_status; nothing else crosses the ABI
+ * (no exceptions, no exit).  A CUDA failure returns LBMD_ERR_CUDA and keeps
+ * its message for lbmd_last_error().  lbmd_md_substep, lbmd_lb_step and
+ * lbmd_run_cycles only enqueue work on the context's stream: they neither
+ * allocate nor synchronise.  Calls documented as "synchronising" wait for the
+ * stream.
+ *
+ * Randomness: every random number is drawn from Philox4x32-10 (Salmon et al.,
+ * SC'11) keyed by params.seed: fluid noise at node r of LB step t uses the
+ * counters (r, t, 0, q), q = 0..3; the random force on particle p in MD step
+ * s uses (p, s, 1, 0).  Results are therefore reproducible bit for bit.
+ * The step counters are 32 bits wide in these counters: runs longer than
+ * 2^32 LB steps (or MD steps) repeat their noise.
+ */
+#ifndef LBMD_H
+#define LBMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbmd_status {
+    LBMD_OK = 0,
+    LBMD_ERR_ARG = -1,       /* invalid argument or parameter */
+    LBMD_ERR_CUDA = -2,      /* a CUDA call failed; see lbmd_last_error */
+    LBMD_ERR_OOM = -3,       /* device or host allocation failed */
+    LBMD_ERR_SEQUENCE = -4,  /* call out of the m-substeps-then-LB-step order */
+    LBMD_ERR_NONFINITE = -5, /* an observable came out NaN or infinite */
+    LBMD_ERR_CAPACITY = -6   /* more particles or bonds than reserved */
+} lbmd_status;
+
+enum { LBMD_VARIANT_A = 0, LBMD_VARIANT_B = 1 };
+enum { LBMD_FP32 = 0, LBMD_FP64 = 1 };
+
+typedef struct lbmd_params {
+    int32_t nx, ny, nz;    /* lattice nodes per axis (periodic), each >= 2 */
+    int32_t n_sub;         /* m = tau_LB / dt: MD steps per LB step, >= 1 (Sec. 3) */
+    int32_t variant;       /* LBMD_VARIANT_A or LBMD_VARIANT_B (Sec. 3) */
+    int32_t precision;     /* LBMD_FP32 or LBMD_FP64 storage and arithmetic */
+    double rho0;           /* initial fluid density; the fluid starts at rest */
+    double nu;             /* kinematic shear viscosity, > 0 */
+    double nu_bulk;        /* bulk viscosity; < 0 selects relaxation factor 0 */
+    double gamma_ghost;    /* relaxation factor of the 9 ghost modes, |g| < 1 */
+    double kT;             /* temperature; 0 switches all noise off */
+    double zeta;           /* particle friction coefficient of Eq. (4), >= 0 */
+    double body_force[3];  /* uniform force density on the fluid */
+    uint64_t seed;         /* Philox key */
+    int64_t max_particles; /* capacity reserved at creation */
+    int64_t max_bonds;     /* capacity reserved at creation */
+    void *stream;          /* cudaStream_t to enqueue on (borrowed); NULL: the
+                              context creates and owns a stream of its own */
+} lbmd_params;
+
+typedef struct lbmd_ctx lbmd_ctx;
+
+/* Observables, computed with FP64 reductions on the device (Sec. 3: the
+ * particle temperature is the mean kinetic energy). */
+typedef struct lbmd_observables_t {
+    double mass;           /* sum over nodes of rho */
+    double p_fluid[3];     /* fluid momentum incl. transfers not yet collided */
+    double p_particles[3]; /* sum of m v */
+    double kT_particles;   /* sum of m v^2 / (3 N_particles), k_B = 1 */
+    double e_kin;          /* sum of m v^2 / 2 */
+    int64_t lb_step;       /* LB steps done */
+    int64_t md_step;       /* MD steps done */
+} lbmd_observables_t;
+
+/* Create a context: allocates populations (two buffers), the node field, the
+ * momentum-transfer accumulator and particle storage on the current device,
+ * and sets the fluid at rest, f_i = w_i rho0 (Sec. 2).
+ * Errors: LBMD_ERR_ARG for invalid parameters, LBMD_ERR_OOM, LBMD_ERR_CUDA. */
+lbmd_status lbmd_create(const lbmd_params *params, lbmd_ctx **out);
+
+/* Free every resource of the context (synchronising).  NULL is accepted. */
+lbmd_status lbmd_destroy(lbmd_ctx *ctx);
+
+/* Append n particles (synchronising).  pos, vel: host arrays of 3n doubles
+ * (x, y, z per particle; positions are wrapped into the box); mass: n doubles,
+ * or NULL for mass 1.  Particle ids are assigned consecutively; the first is
+ * written to *first_id_out if it is not NULL.
+ * Errors: LBMD_ERR_CAPACITY beyond max_particles, LBMD_ERR_ARG for
+ * non-finite input or mass <= 0. */
+lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, const double *vel, const double *mass,
+                               int64_t *first_id_out);
+
+/* Append nb harmonic bonds U = (k/2)(|r| - r0)^2 between particle ids
+ * pairs[2b], pairs[2b+1] (host array of 2 nb int64, ids must exist; each
+ * particle may take part in at most 8 bonds).  Conservative force of Eq. (4),
+ * synchronising.  Errors: LBMD_ERR_CAPACITY, LBMD_ERR_ARG. */
+lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0);
+
+/* Overwrite positions and velocities of all particles from host arrays of
+ * 3 N doubles each in id order (either may be NULL to keep it).
+ * Enqueues the host-to-device copies; the host arrays must stay valid until
+ * the stream reaches them (pinned memory makes the copy asynchronous;
+ * pageable memory makes it synchronous). */
+lbmd_status lbmd_set_particles(lbmd_ctx *ctx, const double *pos, const double *vel);
+
+/* One MD step of length dt = tau_LB / m (Sec. 3, Eqs. (4)-(8)):
+ *   node velocities at the 8 corners of each particle's cell, trilinear
+ *   interpolation u(R) (Eq. (5)); F = -zeta (v - u(R)) + F_rand (Eq. (4)),
+ *   F_rand with variance 2 zeta kT / dt per component; Delta P = dt F with
+ *   R, v, F_rand of the start of the step (Eq. (6)); velocity Verlet with
+ *   that F held fixed; Delta j_k = -delta_k Delta P / a^3 to the 8 nodes
+ *   (Eqs. (7), (8)).
+ * Variant A reads the node velocities of the last LB update; variant B reads
+ * them updated by every earlier MD step since (Sec. 3).  All particles read
+ * the nodes before any transfer of the same step is applied.
+ * Enqueue only.  LBMD_ERR_SEQUENCE if m MD steps were already done since the
+ * last LB step. */
+lbmd_status lbmd_md_substep(lbmd_ctx *ctx);
+
+/* One LB step (Eq. (3)): at every node the MRT collision with thermal noise
+ * and the forcing term Delta'_i of the force density J_acc / tau_LB + g
+ * (J_acc = the momentum the particles handed over since the last LB step),
+ * then streaming; afterwards the node velocities are those of the new
+ * populations.  Enqueue only.  LBMD_ERR_SEQUENCE unless exactly m MD steps
+ * were done since the last LB step. */
+lbmd_status lbmd_lb_step(lbmd_ctx *ctx);
+
+/* Run n complete cycles (m MD steps + 1 LB step each) by replaying a CUDA
+ * graph of one cycle, captured on first use.  Same results as the separate
+ * calls.  Enqueue only (the first call also captures and instantiates the
+ * graph).  LBMD_ERR_SEQUENCE unless called at a cycle boundary. */
+lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n);
+
+/* FP64 device reductions of the observables; synchronising; copies the
+ * result to *out.  LBMD_ERR_NONFINITE if any of them is NaN or infinite. */
+lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out);
+
+/* Synchronising accessors (host arrays, id order, FP64). */
+/* populations f*_i after the last streaming step: 19 N doubles, [i][r] */
+lbmd_status lbmd_get_populations(lbmd_ctx *ctx, double *out);
+/* replace the populations (19 N doubles, [i][r]); recomputes the node field
+ * and clears the pending transfer; only at a cycle boundary */
+lbmd_status lbmd_set_populations(lbmd_ctx *ctx, const double *in);
+/* node field as the particles see it: 4 N doubles (rho, j_x, j_y, j_z) per
+ * node; variant A: j of the last LB update; variant B: that plus the
+ * transfers since */
+lbmd_status lbmd_get_node_field(lbmd_ctx *ctx, double *out);
+/* momentum handed to the fluid since the last LB step: 3 N doubles */
+lbmd_status lbmd_get_transfer(lbmd_ctx *ctx, double *out);
+/* positions (wrapped into the box) and velocities, 3 N doubles each; either
+ * may be NULL */
+lbmd_status lbmd_get_particles(lbmd_ctx *ctx, double *pos, double *vel);
+
+/* Stream-ordered device-pointer variant of lbmd_get_particles for callers
+ * that keep particle data on the GPU (e.g. PyTorch tensors): pos, vel are
+ * device arrays of 3 N doubles (either may be NULL).  Enqueue only. */
+lbmd_status lbmd_get_particles_device(lbmd_ctx *ctx, double *pos, double *vel);
+
+/* Counters and sizes. */
+lbmd_status lbmd_get_counts(lbmd_ctx *ctx, int64_t *n_particles, int64_t *n_bonds, int64_t *lb_step,
+                            int64_t *md_step, int32_t *substeps_done);
+
+/* The cudaStream_t the context enqueues on. */
+void *lbmd_stream(lbmd_ctx *ctx);
+
+/* Message of the last error of this context (or of lbmd_create when ctx is
+ * NULL); never NULL. */
+const char *lbmd_last_error(lbmd_ctx *ctx);
+const char *lbmd_status_string(lbmd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMD_H */

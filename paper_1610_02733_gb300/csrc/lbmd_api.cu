@@ -1,0 +1,443 @@
+// lbmd_api.cu -- the C ABI declared in include/lbmd.h: context life cycle,
+// the m-MD-steps-then-one-LB-step sequence of Sec. 3, CUDA-graph replay of
+// whole cycles, observables and host accessors.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbmd_ctx.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lbmd_status fail(lbmd_ctx *ctx, lbmd_status s, const std::string &msg) {
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_create_error = msg;
+    return s;
+}
+
+lbmd_status cuda_fail(lbmd_ctx *ctx, cudaError_t e, const char *where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? LBMD_ERR_OOM : LBMD_ERR_CUDA, msg);
+}
+
+#define CK(ctx, call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+size_t real_size(const lbmd_ctx *ctx) { return ctx->p.precision == LBMD_FP64 ? 8 : 4; }
+
+void free_all(lbmd_ctx *ctx) {
+    void *bufs[] = {ctx->f[0],       ctx->f[1],        ctx->node,       ctx->jacc,    ctx->pos4,
+                    ctx->vel4,       ctx->fc4,         ctx->old4,       ctx->fcons4,  ctx->bond_count,
+                    ctx->bond_partner, ctx->bond_k,    ctx->bond_r0,    ctx->staging, ctx->red_partial,
+                    ctx->red_out,    ctx->d_lb_step};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->cycle_graph[i]) cudaGraphExecDestroy(ctx->cycle_graph[i]);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+}
+
+bool is_finite_d(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+extern "C" {
+
+const char *lbmd_status_string(lbmd_status s) {
+    switch (s) {
+    case LBMD_OK: return "ok";
+    case LBMD_ERR_ARG: return "invalid argument";
+    case LBMD_ERR_CUDA: return "CUDA error";
+    case LBMD_ERR_OOM: return "out of memory";
+    case LBMD_ERR_SEQUENCE: return "call out of the MD/LB step sequence";
+    case LBMD_ERR_NONFINITE: return "non-finite observable";
+    case LBMD_ERR_CAPACITY: return "capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char *lbmd_last_error(lbmd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void *lbmd_stream(lbmd_ctx *ctx) { return ctx ? (void *)ctx->stream : nullptr; }
+
+lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
+    if (!p || !out) return fail(nullptr, LBMD_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (p->nx < 2 || p->ny < 2 || p->nz < 2) return fail(nullptr, LBMD_ERR_ARG, "lattice sides must be >= 2");
+    if ((int64_t)p->nx * p->ny * p->nz > (int64_t)0x7fffffff)
+        return fail(nullptr, LBMD_ERR_ARG, "more than 2^31-1 nodes");
+    if (p->n_sub < 1) return fail(nullptr, LBMD_ERR_ARG, "n_sub must be >= 1");
+    if (p->variant != LBMD_VARIANT_A && p->variant != LBMD_VARIANT_B)
+        return fail(nullptr, LBMD_ERR_ARG, "variant must be A (0) or B (1)");
+    if (p->precision != LBMD_FP32 && p->precision != LBMD_FP64)
+        return fail(nullptr, LBMD_ERR_ARG, "precision must be FP32 (0) or FP64 (1)");
+    if (!(p->rho0 > 0) || !(p->nu > 0) || !is_finite_d(p->rho0) || !is_finite_d(p->nu))
+        return fail(nullptr, LBMD_ERR_ARG, "rho0 and nu must be positive");
+    if (!(p->kT >= 0) || !is_finite_d(p->kT)) return fail(nullptr, LBMD_ERR_ARG, "kT must be >= 0");
+    if (!(p->zeta >= 0) || !is_finite_d(p->zeta)) return fail(nullptr, LBMD_ERR_ARG, "zeta must be >= 0");
+    if (!(std::fabs(p->gamma_ghost) < 1.0)) return fail(nullptr, LBMD_ERR_ARG, "|gamma_ghost| must be < 1");
+    if (p->max_particles < 0 || p->max_bonds < 0 || p->max_particles > 0x7fffffffLL)
+        return fail(nullptr, LBMD_ERR_ARG, "bad capacities");
+    for (int d = 0; d < 3; ++d)
+        if (!is_finite_d(p->body_force[d])) return fail(nullptr, LBMD_ERR_ARG, "non-finite body force");
+
+    lbmd_ctx *ctx = new (std::nothrow) lbmd_ctx();
+    if (!ctx) return fail(nullptr, LBMD_ERR_OOM, "host allocation");
+    ctx->p = *p;
+    ctx->N = (int64_t)p->nx * p->ny * p->nz;
+    ctx->dt = 1.0 / (double)p->n_sub;
+    // relaxation factors: nu = (1+g_s)/(6(1-g_s)), nu_b = (1+g_b)/(9(1-g_b))
+    LbCoeffs &co = ctx->co;
+    co.gamma_shear = (6.0 * p->nu - 1.0) / (6.0 * p->nu + 1.0);
+    co.gamma_bulk = p->nu_bulk < 0 ? 0.0 : (9.0 * p->nu_bulk - 1.0) / (9.0 * p->nu_bulk + 1.0);
+    co.gamma_ghost = p->gamma_ghost;
+    static const double bnorm[19] = {1.0,       1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0,
+                                     1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 9.0,
+                                     2.0 / 9.0, 2.0 / 9.0, 2.0,       4.0 / 3.0, 4.0 / 9.0};
+    const double mu = 3.0 * p->kT;  // kT / (a^3 c_s^2)
+    for (int k = 0; k < 19; ++k) {
+        double g = k < 4 ? 1.0 : (k == 4 ? co.gamma_bulk : (k <= 9 ? co.gamma_shear : co.gamma_ghost));
+        co.noise_amp[k] = k < 4 ? 0.0 : std::sqrt(mu * bnorm[k] * (1.0 - g * g));
+    }
+    for (int d = 0; d < 3; ++d) co.body_force[d] = p->body_force[d];
+    co.noisy = p->kT > 0 ? 1 : 0;
+
+    if (p->stream) {
+        ctx->stream = (cudaStream_t)p->stream;
+        ctx->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            lbmd_status s = cuda_fail(nullptr, e, "cudaStreamCreate");
+            delete ctx;
+            return s;
+        }
+        ctx->own_stream = true;
+    }
+
+    const int64_t N = ctx->N;
+    const size_t rs = real_size(ctx);
+    const size_t node_bytes = 4 * rs;  // int4 / longlong4 records
+    const int64_t maxp = p->max_particles > 0 ? p->max_particles : 1;
+    const int64_t chunk = (int64_t)1 << 22;
+    ctx->staging_len = std::max<int64_t>(chunk, 9 * maxp);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ctx->red_blocks = 2 * sms;
+
+    struct Alloc {
+        void **ptr;
+        size_t bytes;
+    } allocs[] = {
+        {&ctx->f[0], (size_t)19 * N * rs},
+        {&ctx->f[1], (size_t)19 * N * rs},
+        {&ctx->node, (size_t)N * node_bytes},
+        {&ctx->jacc, p->variant == LBMD_VARIANT_A ? (size_t)N * node_bytes : 0},
+        {&ctx->pos4, (size_t)maxp * 4 * rs},
+        {&ctx->vel4, (size_t)maxp * 4 * rs},
+        {&ctx->fc4, (size_t)maxp * 4 * rs},
+        {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
+        {&ctx->fcons4, (size_t)maxp * 4 * rs},
+        {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},
+        {(void **)&ctx->bond_partner, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(int32_t)},
+        {(void **)&ctx->bond_k, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
+        {(void **)&ctx->bond_r0, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
+        {(void **)&ctx->staging, (size_t)ctx->staging_len * sizeof(double)},
+        {(void **)&ctx->red_partial, (size_t)ctx->red_blocks * 8 * sizeof(double)},
+        {(void **)&ctx->red_out, 8 * sizeof(double)},
+        {(void **)&ctx->d_lb_step, sizeof(unsigned long long)},
+    };
+    for (auto &a : allocs) {
+        if (a.bytes == 0) continue;
+        cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+        if (e != cudaSuccess) {
+            lbmd_status s = cuda_fail(nullptr, e, "cudaMalloc");
+            free_all(ctx);
+            delete ctx;
+            return s;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_lb_step, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_count, 0, (size_t)maxp * sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fcons4, 0, (size_t)maxp * 4 * rs, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fc4, 0, (size_t)maxp * 4 * rs, ctx->stream);
+    if (e == cudaSuccess && ctx->jacc) e = cudaMemsetAsync(ctx->jacc, 0, (size_t)N * node_bytes, ctx->stream);
+    if (e == cudaSuccess) e = launch_init_equilibrium(ctx);
+    if (e == cudaSuccess) e = launch_node_moments(ctx, false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        lbmd_status s = cuda_fail(nullptr, e, "initialisation");
+        free_all(ctx);
+        delete ctx;
+        return s;
+    }
+    *out = ctx;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_destroy(lbmd_ctx *ctx) {
+    if (!ctx) return LBMD_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, const double *vel, const double *mass,
+                               int64_t *first_id_out) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (n < 0 || (n > 0 && (!pos || !vel))) return fail(ctx, LBMD_ERR_ARG, "bad particle arrays");
+    if (ctx->np + n > ctx->p.max_particles) return fail(ctx, LBMD_ERR_CAPACITY, "max_particles exceeded");
+    for (int64_t q = 0; q < 3 * n; ++q)
+        if (!is_finite_d(pos[q]) || !is_finite_d(vel[q])) return fail(ctx, LBMD_ERR_ARG, "non-finite particle data");
+    if (mass)
+        for (int64_t q = 0; q < n; ++q)
+            if (!(mass[q] > 0) || !is_finite_d(mass[q])) return fail(ctx, LBMD_ERR_ARG, "mass must be positive");
+    if (first_id_out) *first_id_out = ctx->np;
+    if (n == 0) return LBMD_OK;
+    // stage in chunks through the device staging buffer (3 + 3 + 1 doubles each)
+    const int64_t per = ctx->staging_len / 7;
+    for (int64_t s = 0; s < n; s += per) {
+        const int64_t c = std::min(per, n - s);
+        double *dpos = ctx->staging, *dvel = ctx->staging + 3 * c, *dm = ctx->staging + 6 * c;
+        CK(ctx, cudaMemcpyAsync(dpos, pos + 3 * s, 3 * c * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(dvel, vel + 3 * s, 3 * c * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        if (mass) CK(ctx, cudaMemcpyAsync(dm, mass + s, c * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, launch_particles_from_double(ctx, ctx->np + s, c, dpos, dvel, mass ? dm : nullptr, true, true, true));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    const size_t rs = real_size(ctx);
+    CK(ctx, cudaMemsetAsync((char *)ctx->fcons4 + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
+    CK(ctx, cudaMemsetAsync((char *)ctx->fc4 + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
+    ctx->np += n;
+    if (ctx->nb > 0) CK(ctx, launch_bond_forces_only(ctx));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 2; ++i)
+        if (ctx->cycle_graph[i]) {
+            cudaGraphExecDestroy(ctx->cycle_graph[i]);
+            ctx->cycle_graph[i] = nullptr;
+        }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !is_finite_d(r0)) return fail(ctx, LBMD_ERR_ARG, "bad bonds");
+    if (ctx->nb + nb > ctx->p.max_bonds) return fail(ctx, LBMD_ERR_CAPACITY, "max_bonds exceeded");
+    if (nb == 0) return LBMD_OK;
+    const int64_t np = ctx->np;
+    const int M = LBMD_MAX_BONDS_PER_PARTICLE;
+    std::vector<int32_t> count(np), partner((size_t)np * M);
+    std::vector<double> bk((size_t)np * M), br((size_t)np * M);
+    CK(ctx, cudaMemcpy(count.data(), ctx->bond_count, np * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpy(partner.data(), ctx->bond_partner, (size_t)np * M * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpy(bk.data(), ctx->bond_k, (size_t)np * M * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpy(br.data(), ctx->bond_r0, (size_t)np * M * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t i = pairs[2 * b], j = pairs[2 * b + 1];
+        if (i < 0 || j < 0 || i >= np || j >= np || i == j) return fail(ctx, LBMD_ERR_ARG, "bond ids out of range");
+        if (count[i] >= M || count[j] >= M) return fail(ctx, LBMD_ERR_CAPACITY, "more than 8 bonds on a particle");
+        partner[(size_t)i * M + count[i]] = (int32_t)j;
+        bk[(size_t)i * M + count[i]] = k;
+        br[(size_t)i * M + count[i]] = r0;
+        count[i]++;
+        partner[(size_t)j * M + count[j]] = (int32_t)i;
+        bk[(size_t)j * M + count[j]] = k;
+        br[(size_t)j * M + count[j]] = r0;
+        count[j]++;
+    }
+    CK(ctx, cudaMemcpy(ctx->bond_count, count.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->bond_partner, partner.data(), (size_t)np * M * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->bond_k, bk.data(), (size_t)np * M * sizeof(double), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->bond_r0, br.data(), (size_t)np * M * sizeof(double), cudaMemcpyHostToDevice));
+    ctx->nb += nb;
+    CK(ctx, launch_bond_forces_only(ctx));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 2; ++i)
+        if (ctx->cycle_graph[i]) {
+            cudaGraphExecDestroy(ctx->cycle_graph[i]);
+            ctx->cycle_graph[i] = nullptr;
+        }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_particles(lbmd_ctx *ctx, const double *pos, const double *vel) {
+    if (!ctx) return LBMD_ERR_ARG;
+    const int64_t n = ctx->np;
+    if (n == 0 || (!pos && !vel)) return LBMD_OK;
+    if (6 * n > ctx->staging_len) return fail(ctx, LBMD_ERR_CAPACITY, "staging buffer too small");
+    double *dpos = ctx->staging, *dvel = ctx->staging + 3 * n;
+    if (pos) CK(ctx, cudaMemcpyAsync(dpos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (vel) CK(ctx, cudaMemcpyAsync(dvel, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, launch_particles_from_double(ctx, 0, n, dpos, dvel, nullptr, pos != nullptr, vel != nullptr, false));
+    if (pos && ctx->nb > 0) CK(ctx, launch_bond_forces_only(ctx));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_md_substep(lbmd_ctx *ctx) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (ctx->sub_done >= ctx->p.n_sub) return fail(ctx, LBMD_ERR_SEQUENCE, "n_sub MD steps already done");
+    CK(ctx, launch_md_substep(ctx, ctx->sub_done));
+    ctx->sub_done += 1;
+    ctx->md_step += 1;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_lb_step(lbmd_ctx *ctx) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (ctx->sub_done != ctx->p.n_sub) return fail(ctx, LBMD_ERR_SEQUENCE, "LB step before n_sub MD steps");
+    CK(ctx, launch_lb_step(ctx));
+    ctx->sub_done = 0;
+    ctx->lb_step += 1;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
+    if (!ctx || n < 0) return LBMD_ERR_ARG;
+    if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "run_cycles must start at a cycle boundary");
+    for (int64_t c = 0; c < n; ++c) {
+        const int parity = ctx->cur;
+        if (!ctx->cycle_graph[parity]) {
+            // capture one cycle starting from this population buffer
+            cudaGraph_t g = nullptr;
+            CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            const int cur0 = ctx->cur;
+            for (int s = 0; s < ctx->p.n_sub && e == cudaSuccess; ++s) e = launch_md_substep(ctx, s);
+            if (e == cudaSuccess) e = launch_lb_step(ctx);
+            ctx->cur = cur0;  // launch_lb_step flipped it during capture
+            cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(ctx, e, "capture");
+            }
+            if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ctx->cycle_graph[parity], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ctx->cycle_graph[parity] = nullptr;
+                return cuda_fail(ctx, e, "cudaGraphInstantiate");
+            }
+        }
+        CK(ctx, cudaGraphLaunch(ctx->cycle_graph[parity], ctx->stream));
+        ctx->cur ^= 1;
+        ctx->lb_step += 1;
+        ctx->md_step += ctx->p.n_sub;
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
+    if (!ctx || !out) return LBMD_ERR_ARG;
+    double h[8];
+    CK(ctx, launch_observables(ctx));
+    CK(ctx, cudaMemcpyAsync(h, ctx->red_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    out->mass = h[0];
+    for (int d = 0; d < 3; ++d) {
+        out->p_fluid[d] = h[1 + d];
+        out->p_particles[d] = h[4 + d];
+    }
+    out->e_kin = 0.5 * h[7];
+    out->kT_particles = ctx->np > 0 ? h[7] / (3.0 * (double)ctx->np) : 0.0;
+    out->lb_step = ctx->lb_step;
+    out->md_step = ctx->md_step;
+    for (int c = 0; c < 8; ++c)
+        if (!is_finite_d(h[c])) return fail(ctx, LBMD_ERR_NONFINITE, "non-finite observable");
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_populations(lbmd_ctx *ctx, double *out) {
+    if (!ctx || !out) return LBMD_ERR_ARG;
+    const int64_t total = 19 * ctx->N;
+    for (int64_t s = 0; s < total; s += ctx->staging_len) {
+        const int64_t c = std::min(ctx->staging_len, total - s);
+        CK(ctx, launch_populations_to_double(ctx, s, c, ctx->staging));
+        CK(ctx, cudaMemcpyAsync(out + s, ctx->staging, c * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_populations(lbmd_ctx *ctx, const double *in) {
+    if (!ctx || !in) return LBMD_ERR_ARG;
+    if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "set_populations only at a cycle boundary");
+    const int64_t total = 19 * ctx->N;
+    for (int64_t s = 0; s < total; s += ctx->staging_len) {
+        const int64_t c = std::min(ctx->staging_len, total - s);
+        CK(ctx, cudaMemcpyAsync(ctx->staging, in + s, c * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, launch_populations_from_double(ctx, s, c, ctx->staging));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    CK(ctx, launch_node_moments(ctx, false));
+    CK(ctx, launch_clear_transfer(ctx));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBMD_OK;
+}
+
+static lbmd_status node_out(lbmd_ctx *ctx, double *out, bool transfer) {
+    const int w = transfer ? 3 : 4;
+    const int64_t per = ctx->staging_len / w;
+    for (int64_t s = 0; s < ctx->N; s += per) {
+        const int64_t c = std::min(per, ctx->N - s);
+        CK(ctx, launch_node_field_to_double(ctx, s, c, ctx->staging, transfer));
+        CK(ctx, cudaMemcpyAsync(out + w * s, ctx->staging, w * c * sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_node_field(lbmd_ctx *ctx, double *out) {
+    if (!ctx || !out) return LBMD_ERR_ARG;
+    return node_out(ctx, out, false);
+}
+
+lbmd_status lbmd_get_transfer(lbmd_ctx *ctx, double *out) {
+    if (!ctx || !out) return LBMD_ERR_ARG;
+    return node_out(ctx, out, true);
+}
+
+lbmd_status lbmd_get_particles(lbmd_ctx *ctx, double *pos, double *vel) {
+    if (!ctx) return LBMD_ERR_ARG;
+    const int64_t n = ctx->np;
+    if (n == 0 || (!pos && !vel)) return LBMD_OK;
+    if (6 * n > ctx->staging_len) return fail(ctx, LBMD_ERR_CAPACITY, "staging buffer too small");
+    double *dpos = ctx->staging, *dvel = ctx->staging + 3 * n;
+    CK(ctx, launch_particles_to_double(ctx, pos ? dpos : nullptr, vel ? dvel : nullptr));
+    if (pos) CK(ctx, cudaMemcpyAsync(pos, dpos, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (vel) CK(ctx, cudaMemcpyAsync(vel, dvel, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_particles_device(lbmd_ctx *ctx, double *pos, double *vel) {
+    if (!ctx) return LBMD_ERR_ARG;
+    CK(ctx, launch_particles_to_double(ctx, pos, vel));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_counts(lbmd_ctx *ctx, int64_t *n_particles, int64_t *n_bonds, int64_t *lb_step, int64_t *md_step,
+                            int32_t *substeps_done) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (n_particles) *n_particles = ctx->np;
+    if (n_bonds) *n_bonds = ctx->nb;
+    if (lb_step) *lb_step = ctx->lb_step;
+    if (md_step) *md_step = ctx->md_step;
+    if (substeps_done) *substeps_done = ctx->sub_done;
+    return LBMD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// lbmd_ctx.h -- host-side context of the LB/MD library and the launchers the
+// C-ABI layer calls.  Device memory layout (all on one GPU):
+//
+//   f[2]        populations, structure of arrays f[i * N + r], ping-pong:
+//               f[cur] holds the post-stream populations f*.
+//   node        node field, one 16-byte (FP32) / 32-byte (FP64) record per
+//               node: rho* as bits and the momentum density j in fixed point.
+//               Variant A: j* of the last LB update (frozen during the MD
+//               steps).  Variant B: j* plus every transfer since.
+//   jacc        variant A only: the transfers since the last LB step, fixed
+//               point, 4 words per node (x, y, z, unused).
+//   pos4        per particle: fractional position in its cell (x, y, z) and
+//               the linear cell index.
+//   vel4        per particle: velocity (x, y, z) and 1 / mass.
+//   fc4         per particle: coupling force F of the last MD step.
+//   old4        variant B only: pos4 at the start of the current MD step.
+//   fcons4      per particle: bond force at the current positions.
+//   bond_*      per particle up to LBMD_MAX_BONDS_PER_PARTICLE partners.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/lbmd.h"
+
+#define LBMD_MAX_BONDS_PER_PARTICLE 8
+
+struct LbCoeffs {
+    double gamma_bulk, gamma_shear, gamma_ghost;
+    double noise_amp[19];  // sqrt(mu b_k (1 - gamma_k^2)), multiplied by sqrt(rho) per node
+    double body_force[3];
+    int noisy;
+};
+
+struct lbmd_ctx {
+    lbmd_params p;
+    int64_t N;
+    cudaStream_t stream;
+    bool own_stream;
+    int cur;  // index of the population buffer that holds f*
+    void *f[2];
+    void *node;
+    void *jacc;
+    void *pos4, *vel4, *fc4, *old4, *fcons4;
+    int32_t *bond_count, *bond_partner;
+    double *bond_k, *bond_r0;
+    double *staging;   // device staging buffer for host <-> device conversions
+    int64_t staging_len;
+    double *red_partial;  // per-block partial sums of the observables
+    double *red_out;      // final sums
+    int red_blocks;
+    unsigned long long *d_lb_step;  // LB step counter read by the kernels
+    int64_t np, nb;
+    int64_t lb_step, md_step;
+    int sub_done;
+    LbCoeffs co;
+    double dt;
+    cudaGraphExec_t cycle_graph[2];
+    std::string err;
+};
+
+// Launchers, one per kernel family; each enqueues on ctx->stream and returns
+// the launch status.
+cudaError_t launch_lb_step(lbmd_ctx *ctx);
+cudaError_t launch_node_moments(lbmd_ctx *ctx, bool count_step);
+cudaError_t launch_init_equilibrium(lbmd_ctx *ctx);
+cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep);
+cudaError_t launch_bond_forces_only(lbmd_ctx *ctx);
+cudaError_t launch_observables(lbmd_ctx *ctx);
+cudaError_t launch_populations_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst);
+cudaError_t launch_populations_from_double(lbmd_ctx *ctx, int64_t first, int64_t count, const double *src);
+cudaError_t launch_node_field_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst, bool transfer_only);
+cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t count, const double *pos,
+                                         const double *vel, const double *mass, bool set_pos, bool set_vel,
+                                         bool set_mass);
+cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel);
+cudaError_t launch_clear_transfer(lbmd_ctx *ctx);

@@ -1,0 +1,194 @@
+// lbmd_device.cuh -- device building blocks of the GB300 LB/MD library:
+// D3Q19 lattice and mode basis (Sec. 2), Philox4x32-10 counter-based noise,
+// the per-precision storage policy and the fixed-point encoding of the
+// momentum density.
+//
+// Fixed-point momentum.  The node field stores the momentum density j as a
+// signed integer multiple of 2^-30 (FP32 build) or 2^-56 (FP64 build).
+// Particle-to-fluid transfers (Eqs. (7), (8) of the paper) are added with
+// integer atomics, which are associative: the accumulated value does not
+// depend on the order in which particles are processed, so every run is
+// bitwise reproducible without sorting or colouring.  Range: |j| < 2 (FP32)
+// and |j| < 128 (FP64), far above any flow an LB fluid can carry (the
+// lattice Mach number must stay well below one).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbmd {
+
+constexpr int Q = 19;
+
+// D3Q19 velocities c_i (Sec. 2, Fig. 1a): rest, 6 nearest, 12 next-nearest.
+__host__ __device__ constexpr int CX(int i) {
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__host__ __device__ constexpr int CY(int i) {
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int CZ(int i) {
+    constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int C2(int i) { return CX(i) * CX(i) + CY(i) * CY(i) + CZ(i) * CZ(i); }
+
+// Lattice weights: 1/3 (rest), 1/18 (|c|^2 = 1), 1/36 (|c|^2 = 2).
+__host__ __device__ constexpr double WEIGHT(int i) {
+    return C2(i) == 0 ? 1.0 / 3.0 : (C2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Orthogonal mode basis e_k(c_i): 0 mass, 1-3 momentum, 4 bulk stress,
+// 5-9 shear stress, 10-18 ghost modes.  Integer-valued.
+__host__ __device__ constexpr int EMODE(int k, int i) {
+    const int x = CX(i), y = CY(i), z = CZ(i), c2 = C2(i);
+    return k == 0    ? 1
+           : k == 1  ? x
+           : k == 2  ? y
+           : k == 3  ? z
+           : k == 4  ? c2 - 1
+           : k == 5  ? 3 * x * x - c2
+           : k == 6  ? y * y - z * z
+           : k == 7  ? x * y
+           : k == 8  ? x * z
+           : k == 9  ? y * z
+           : k == 10 ? (3 * c2 - 5) * x
+           : k == 11 ? (3 * c2 - 5) * y
+           : k == 12 ? (3 * c2 - 5) * z
+           : k == 13 ? (y * y - z * z) * x
+           : k == 14 ? (z * z - x * x) * y
+           : k == 15 ? (x * x - y * y) * z
+           : k == 16 ? 3 * c2 * c2 - 6 * c2 + 1
+           : k == 17 ? (2 * c2 - 3) * (3 * x * x - c2)
+                     : (2 * c2 - 3) * (y * y - z * z);
+}
+
+// Squared norms b_k = sum_i w_i e_k(c_i)^2, as exact rationals.
+__host__ __device__ constexpr double BNORM(int k) {
+    constexpr double t[Q] = {1.0,       1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0,
+                             1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 9.0,
+                             2.0 / 9.0, 2.0 / 9.0, 2.0,       4.0 / 3.0, 4.0 / 9.0};
+    return t[k];
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor bijection with Weyl-sequence key updates.
+// ---------------------------------------------------------------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 32 random bits -> uniform number with zero mean and unit variance,
+// sqrt(12) ((x + 1/2) 2^-32 - 1/2).  The FP64 form is exact; the FP32 form
+// centres first, (x - 2^31 + 1/2) 2^-32, so only one rounding remains.
+__device__ __forceinline__ double unit_uniform_d(uint32_t x) {
+    return 3.4641016151377544 * (((double)x + 0.5) * 2.3283064365386963e-10 - 0.5);
+}
+__device__ __forceinline__ float unit_uniform_f(uint32_t x) {
+    const float centred = (float)(int32_t)(x ^ 0x80000000u) + 0.5f;
+    return centred * (3.4641016151377544f * 2.3283064365386963e-10f);
+}
+template <typename T>
+__device__ __forceinline__ T unit_uniform(uint32_t x);
+template <>
+__device__ __forceinline__ float unit_uniform<float>(uint32_t x) {
+    return unit_uniform_f(x);
+}
+template <>
+__device__ __forceinline__ double unit_uniform<double>(uint32_t x) {
+    return unit_uniform_d(x);
+}
+
+// ---------------------------------------------------------------------------
+// Storage policy per precision.
+// ---------------------------------------------------------------------------
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+struct __align__(32) L4 {
+    long long x, y, z, w;
+};
+
+template <typename T>
+struct Prec;
+
+template <>
+struct Prec<float> {
+    using real = float;
+    using real4 = float4;
+    using fix = int32_t;
+    using node4 = int4;  // {rho as float bits, j_x, j_y, j_z fixed point}
+    static constexpr float SCALE = 1073741824.0f;             // 2^30
+    static constexpr float INV_SCALE = 9.313225746154785e-10f;  // 2^-30
+    __device__ static __forceinline__ fix to_fix(float v) { return __float2int_rn(v * SCALE); }
+    __device__ static __forceinline__ float from_fix(fix v) { return (float)v * INV_SCALE; }
+    __device__ static __forceinline__ node4 pack(float rho, fix jx, fix jy, fix jz) {
+        return make_int4(__float_as_int(rho), jx, jy, jz);
+    }
+    __device__ static __forceinline__ float rho_of(const node4 &n) { return __int_as_float(n.x); }
+    __device__ static __forceinline__ real4 make4(float a, float b, float c, float d) {
+        return make_float4(a, b, c, d);
+    }
+    // particle position record: frac x, y, z in [0,1) and the cell index
+    __device__ static __forceinline__ int64_t cell_of(const real4 &p) { return (int64_t)(uint32_t)__float_as_int(p.w); }
+    __device__ static __forceinline__ real4 make_pos(float fx, float fy, float fz, int64_t cell) {
+        return make_float4(fx, fy, fz, __int_as_float((int)(uint32_t)cell));
+    }
+    __device__ static __forceinline__ void add_fix(fix *a, fix v) { atomicAdd(a, v); }
+};
+
+template <>
+struct Prec<double> {
+    using real = double;
+    using real4 = D4;
+    using fix = long long;
+    using node4 = L4;  // {rho as double bits, j_x, j_y, j_z fixed point}
+    static constexpr double SCALE = 72057594037927936.0;          // 2^56
+    static constexpr double INV_SCALE = 1.3877787807814457e-17;  // 2^-56
+    __device__ static __forceinline__ fix to_fix(double v) { return __double2ll_rn(v * SCALE); }
+    __device__ static __forceinline__ double from_fix(fix v) { return (double)v * INV_SCALE; }
+    __device__ static __forceinline__ node4 pack(double rho, fix jx, fix jy, fix jz) {
+        return L4{__double_as_longlong(rho), jx, jy, jz};
+    }
+    __device__ static __forceinline__ double rho_of(const node4 &n) { return __longlong_as_double(n.x); }
+    __device__ static __forceinline__ real4 make4(double a, double b, double c, double d) { return D4{a, b, c, d}; }
+    __device__ static __forceinline__ int64_t cell_of(const real4 &p) { return (int64_t)p.w; }
+    __device__ static __forceinline__ real4 make_pos(double fx, double fy, double fz, int64_t cell) {
+        return D4{fx, fy, fz, (double)cell};
+    }
+    __device__ static __forceinline__ void add_fix(fix *a, fix v) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
+    }
+};
+
+// Hydrodynamic moments rho = sum f_i, j = sum f_i c_i (Eqs. (1), (2)).  One
+// fixed summation order, shared by every kernel that needs them, so the
+// values are bitwise identical wherever they are recomputed.
+template <typename T>
+__device__ __forceinline__ void node_moments(const T f[Q], T &rho, T &jx, T &jy, T &jz) {
+    rho = f[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) rho += f[i];
+    jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+    jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) + (f[17] - f[18]);
+    jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) + (f[15] - f[16]) + (f[18] - f[17]);
+}
+
+}  // namespace lbmd

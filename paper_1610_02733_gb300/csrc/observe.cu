@@ -1,0 +1,316 @@
+// observe.cu -- FP64 reductions of the observables and the conversions
+// between the device storage and the FP64 host arrays of the C ABI.
+//
+// Observables (mass, fluid momentum incl. pending transfers, particle
+// momentum, sum of m v^2): every thread accumulates a fixed strided subset in
+// double precision, each block reduces in a fixed tree order into one row of
+// a partial-sum table, and a single block adds the rows in order.  The grid
+// size is fixed per context, so the sums are bitwise reproducible.
+#include "lbmd_ctx.h"
+#include "lbmd_device.cuh"
+
+namespace lbmd {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_COLS = 8;  // mass, pfx, pfy, pfz, ppx, ppy, ppz, sum m v^2
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double v[NV], double *row) {
+    __shared__ double sh[NV][RED_THREADS];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) sh[c][threadIdx.x] = v[c];
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) row[c] = sh[c][0];
+    }
+}
+
+template <typename T, int VARIANT>
+__global__ void __launch_bounds__(RED_THREADS)
+    observe_nodes_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc, int64_t N,
+                         double *partial) {
+    using P = Prec<T>;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
+    for (int64_t r = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; r < N; r += stride) {
+        const typename P::node4 n = node[r];
+        v[0] += (double)P::rho_of(n);
+        v[1] += (double)n.y;
+        v[2] += (double)n.z;
+        v[3] += (double)n.w;
+        if (VARIANT == LBMD_VARIANT_A) {
+            const typename P::node4 J = jacc[r];
+            v[1] += (double)J.y;
+            v[2] += (double)J.z;
+            v[3] += (double)J.w;
+        }
+    }
+    // momenta stay in fixed-point units until the final scaling
+    block_reduce_store<4>(v, partial + (int64_t)blockIdx.x * RED_COLS);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+    observe_particles_kernel(const typename Prec<T>::real4 *vel4, int64_t np, double *partial) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
+    for (int64_t p = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; p < np; p += stride) {
+        const typename Prec<T>::real4 V = vel4[p];
+        const double m = 1.0 / (double)V.w;
+        const double vx = V.x, vy = V.y, vz = V.z;
+        v[0] += m * vx;
+        v[1] += m * vy;
+        v[2] += m * vz;
+        v[3] += m * (vx * vx + vy * vy + vz * vz);
+    }
+    block_reduce_store<4>(v, partial + (int64_t)blockIdx.x * RED_COLS + 4);
+}
+
+template <typename T>
+__global__ void observe_final_kernel(const double *partial, int rows, double *out) {
+    // one thread per column, rows added in order
+    const int c = threadIdx.x;
+    if (c >= RED_COLS) return;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += partial[(int64_t)r * RED_COLS + c];
+    if (c >= 1 && c <= 3) s *= (double)Prec<T>::INV_SCALE;
+    out[c] = s;
+}
+
+template <typename T>
+static cudaError_t observables_t(lbmd_ctx *ctx) {
+    using P = Prec<T>;
+    const int B = ctx->red_blocks;
+    if (ctx->p.variant == LBMD_VARIANT_B)
+        observe_nodes_kernel<T, LBMD_VARIANT_B><<<B, RED_THREADS, 0, ctx->stream>>>(
+            static_cast<const typename P::node4 *>(ctx->node), nullptr, ctx->N, ctx->red_partial);
+    else
+        observe_nodes_kernel<T, LBMD_VARIANT_A><<<B, RED_THREADS, 0, ctx->stream>>>(
+            static_cast<const typename P::node4 *>(ctx->node), static_cast<const typename P::node4 *>(ctx->jacc),
+            ctx->N, ctx->red_partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    observe_particles_kernel<T><<<B, RED_THREADS, 0, ctx->stream>>>(
+        static_cast<const typename P::real4 *>(ctx->vel4), ctx->np, ctx->red_partial);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    observe_final_kernel<T><<<1, 32, 0, ctx->stream>>>(ctx->red_partial, B, ctx->red_out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Conversions for the host accessors.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void pops_to_double_kernel(const T *f, int64_t first, int64_t count, double *dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) dst[t] = (double)f[first + t];
+}
+
+template <typename T>
+__global__ void pops_from_double_kernel(T *f, int64_t first, int64_t count, const double *src) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) f[first + t] = (T)src[t];
+}
+
+// node field (rho, j seen by the particles) or, with transfer_only, the
+// pending transfer J_acc, for nodes [first, first + count)
+template <typename T>
+__global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc,
+                                      const T *f, int64_t N, int64_t first, int64_t count, double *dst,
+                                      int transfer_only, int variant) {
+    using P = Prec<T>;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t r = first + t;
+    const typename P::node4 n = node[r];
+    if (!transfer_only) {
+        dst[4 * t + 0] = (double)P::rho_of(n);
+        dst[4 * t + 1] = (double)P::from_fix(n.y);
+        dst[4 * t + 2] = (double)P::from_fix(n.z);
+        dst[4 * t + 3] = (double)P::from_fix(n.w);
+        return;
+    }
+    if (variant == LBMD_VARIANT_A) {
+        const typename P::node4 J = jacc[r];
+        dst[3 * t + 0] = (double)P::from_fix(J.y);
+        dst[3 * t + 1] = (double)P::from_fix(J.z);
+        dst[3 * t + 2] = (double)P::from_fix(J.w);
+    } else {
+        T fl[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fl[i] = f[(int64_t)i * N + r];
+        T rho, jx, jy, jz;
+        node_moments(fl, rho, jx, jy, jz);
+        dst[3 * t + 0] = (double)P::from_fix(n.y - P::to_fix(jx));
+        dst[3 * t + 1] = (double)P::from_fix(n.z - P::to_fix(jy));
+        dst[3 * t + 2] = (double)P::from_fix(n.w - P::to_fix(jz));
+    }
+}
+
+template <typename T>
+__global__ void clear_transfer_kernel(typename Prec<T>::node4 *jacc, int64_t N) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    typename Prec<T>::node4 z;
+    z.x = z.y = z.z = z.w = 0;
+    jacc[r] = z;
+}
+
+// host FP64 particle arrays -> cell index + fractional offset, velocity, 1/m
+template <typename T>
+__global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, typename Prec<T>::real4 *vel4,
+                                             int64_t first, int64_t count, const double *pos, const double *vel,
+                                             const double *mass, int set_pos, int set_vel, int set_mass, int nx,
+                                             int ny, int nz) {
+    using P = Prec<T>;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t p = first + t;
+    if (set_pos) {
+        const double L[3] = {(double)nx, (double)ny, (double)nz};
+        T fr[3];
+        int64_t cl[3];
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[3 * t + d];
+            x -= L[d] * floor(x / L[d]);
+            if (x >= L[d]) x -= L[d];
+            double b = floor(x);
+            T f = (T)(x - b);
+            if (f >= T(1)) {  // rounding to the storage precision reached the next node
+                f = T(0);
+                b += 1.0;
+                if (b >= L[d]) b = 0.0;
+            }
+            fr[d] = f;
+            cl[d] = (int64_t)b;
+        }
+        pos4[p] = P::make_pos(fr[0], fr[1], fr[2], cl[0] + (int64_t)nx * (cl[1] + (int64_t)ny * cl[2]));
+    }
+    typename P::real4 V = vel4[p];
+    if (set_vel) {
+        V.x = (T)vel[3 * t + 0];
+        V.y = (T)vel[3 * t + 1];
+        V.z = (T)vel[3 * t + 2];
+    }
+    if (set_mass) V.w = (T)(1.0 / (mass ? mass[t] : 1.0));
+    vel4[p] = V;
+}
+
+template <typename T>
+__global__ void particles_to_double_kernel(const typename Prec<T>::real4 *pos4, const typename Prec<T>::real4 *vel4,
+                                           int64_t np, double *pos, double *vel, int nx, int ny) {
+    using P = Prec<T>;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    if (pos) {
+        const typename P::real4 R = pos4[p];
+        const int64_t cell = P::cell_of(R);
+        const int64_t nxy = (int64_t)nx * ny;
+        const int64_t z = cell / nxy, rem = cell - z * nxy, y = rem / nx, x = rem - y * nx;
+        pos[3 * p + 0] = (double)x + (double)R.x;
+        pos[3 * p + 1] = (double)y + (double)R.y;
+        pos[3 * p + 2] = (double)z + (double)R.z;
+    }
+    if (vel) {
+        const typename P::real4 V = vel4[p];
+        vel[3 * p + 0] = (double)V.x;
+        vel[3 * p + 1] = (double)V.y;
+        vel[3 * p + 2] = (double)V.z;
+    }
+}
+
+inline unsigned nblocks(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace lbmd
+
+using namespace lbmd;
+
+cudaError_t launch_observables(lbmd_ctx *ctx) {
+    return ctx->p.precision == LBMD_FP64 ? observables_t<double>(ctx) : observables_t<float>(ctx);
+}
+
+cudaError_t launch_populations_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst) {
+    if (count <= 0) return cudaSuccess;
+    if (ctx->p.precision == LBMD_FP64)
+        pops_to_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<const double *>(ctx->f[ctx->cur]), first, count, dst);
+    else
+        pops_to_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<const float *>(ctx->f[ctx->cur]), first, count, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_populations_from_double(lbmd_ctx *ctx, int64_t first, int64_t count, const double *src) {
+    if (count <= 0) return cudaSuccess;
+    if (ctx->p.precision == LBMD_FP64)
+        pops_from_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<double *>(ctx->f[ctx->cur]), first, count, src);
+    else
+        pops_from_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<float *>(ctx->f[ctx->cur]), first, count, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_field_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst,
+                                        bool transfer_only) {
+    if (count <= 0) return cudaSuccess;
+    if (ctx->p.precision == LBMD_FP64)
+        node_to_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<const Prec<double>::node4 *>(ctx->node), static_cast<const Prec<double>::node4 *>(ctx->jacc),
+            static_cast<const double *>(ctx->f[ctx->cur]), ctx->N, first, count, dst, transfer_only ? 1 : 0,
+            ctx->p.variant);
+    else
+        node_to_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<const Prec<float>::node4 *>(ctx->node), static_cast<const Prec<float>::node4 *>(ctx->jacc),
+            static_cast<const float *>(ctx->f[ctx->cur]), ctx->N, first, count, dst, transfer_only ? 1 : 0,
+            ctx->p.variant);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_transfer(lbmd_ctx *ctx) {
+    if (ctx->p.variant != LBMD_VARIANT_A) return cudaSuccess;
+    if (ctx->p.precision == LBMD_FP64)
+        clear_transfer_kernel<double><<<nblocks(ctx->N), 256, 0, ctx->stream>>>(
+            static_cast<Prec<double>::node4 *>(ctx->jacc), ctx->N);
+    else
+        clear_transfer_kernel<float><<<nblocks(ctx->N), 256, 0, ctx->stream>>>(
+            static_cast<Prec<float>::node4 *>(ctx->jacc), ctx->N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t count, const double *pos,
+                                         const double *vel, const double *mass, bool set_pos, bool set_vel,
+                                         bool set_mass) {
+    if (count <= 0) return cudaSuccess;
+    if (ctx->p.precision == LBMD_FP64)
+        particles_from_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<Prec<double>::real4 *>(ctx->pos4), static_cast<Prec<double>::real4 *>(ctx->vel4), first, count,
+            pos, vel, mass, set_pos, set_vel, set_mass, ctx->p.nx, ctx->p.ny, ctx->p.nz);
+    else
+        particles_from_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
+            static_cast<Prec<float>::real4 *>(ctx->pos4), static_cast<Prec<float>::real4 *>(ctx->vel4), first, count,
+            pos, vel, mass, set_pos, set_vel, set_mass, ctx->p.nx, ctx->p.ny, ctx->p.nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel) {
+    if (ctx->np <= 0) return cudaSuccess;
+    if (ctx->p.precision == LBMD_FP64)
+        particles_to_double_kernel<double><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
+            static_cast<const Prec<double>::real4 *>(ctx->pos4), static_cast<const Prec<double>::real4 *>(ctx->vel4),
+            ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
+    else
+        particles_to_double_kernel<float><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
+            static_cast<const Prec<float>::real4 *>(ctx->pos4), static_cast<const Prec<float>::real4 *>(ctx->vel4),
+            ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
+    return cudaGetLastError();
+}

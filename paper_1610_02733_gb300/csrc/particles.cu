@@ -1,0 +1,310 @@
+// particles.cu -- the dissipative particle-fluid coupling of Sec. 3 on the GPU.
+//
+// couple_kernel (one thread per particle), one MD step of length dt:
+//   * node velocities at the 8 corners of the particle's cell, trilinear
+//     weights delta_k from the fractional position (Eq. (5));
+//   * random force from Philox(p, md_step, 1, 0), friction against the
+//     interpolated fluid velocity (Eq. (4)); Delta P = dt F (Eq. (6));
+//   * velocity Verlet with F held fixed (second half-kick here for ideal
+//     particles, in bond_kick_kernel when bonds exist);
+//   * variant A: the transfer -delta_k Delta P (Eqs. (7), (8)) goes straight
+//     into the accumulator J_acc, which no MD step reads;
+//     variant B: the start-of-step position is kept for spread_kernel, which
+//     runs once every particle has read the node field.
+// Transfers are added as fixed-point integers with atomics, so the sum does
+// not depend on the order of the particles (bitwise reproducible).
+//
+// Particle positions are stored as cell index + fractional offset in [0,1):
+// the offset is exactly the interpolation coordinate, and its precision does
+// not degrade with the box size.
+#include "lbmd_ctx.h"
+#include "lbmd_device.cuh"
+
+namespace lbmd {
+
+template <typename T>
+struct PArgs {
+    using P = Prec<T>;
+    typename P::real4 *pos4, *vel4, *fc4, *old4, *fcons4;
+    typename P::node4 *node, *jacc;
+    const int32_t *bond_count, *bond_partner;
+    const double *bond_k, *bond_r0;
+    int nx, ny, nz;
+    int64_t np;
+    T zeta, dt, half_dt, amp;
+    uint32_t key0, key1;
+    const unsigned long long *lb_step;
+    int n_sub, substep, noisy;
+};
+
+struct CellXYZ {
+    int x, y, z;
+};
+
+__device__ __forceinline__ CellXYZ cell_xyz(int64_t cell, int nx, int ny) {
+    const int64_t nxy = (int64_t)nx * ny;
+    CellXYZ c;
+    c.z = (int)(cell / nxy);
+    const int64_t rem = cell - (int64_t)c.z * nxy;
+    c.y = (int)(rem / nx);
+    c.x = (int)(rem - (int64_t)c.y * nx);
+    return c;
+}
+
+// The 8 corner nodes (k = ox + 2 oy + 4 oz) and trilinear weights of Eq. (5).
+template <typename T>
+__device__ __forceinline__ void corners(const CellXYZ &c, T fx, T fy, T fz, int nx, int ny, int nz, int64_t idx[8],
+                                        T delta[8]) {
+    const int x1 = c.x + 1 == nx ? 0 : c.x + 1;
+    const int y1 = c.y + 1 == ny ? 0 : c.y + 1;
+    const int z1 = c.z + 1 == nz ? 0 : c.z + 1;
+    const int X[2] = {c.x, x1}, Y[2] = {c.y, y1}, Z[2] = {c.z, z1};
+    const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
+        idx[k] = X[ox] + (int64_t)nx * (Y[oy] + (int64_t)ny * Z[oz]);
+        delta[k] = wx[ox] * wy[oy] * wz[oz];
+    }
+}
+
+// Move a fractional coordinate by d and carry whole cells into the index.
+template <typename T>
+__device__ __forceinline__ void advance(T &frac, int &c, T d, int n) {
+    T x = frac + d;
+    T s = floor(x);
+    x -= s;
+    if (x >= T(1)) {  // a tiny negative offset rounded up to the next node
+        x = T(0);
+        s += T(1);
+    }
+    int cn = c + (int)s;
+    cn %= n;
+    if (cn < 0) cn += n;
+    frac = x;
+    c = cn;
+}
+
+template <typename T, int VARIANT, bool BONDS>
+__global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
+    using P = Prec<T>;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const typename P::real4 R = a.pos4[p];
+    typename P::real4 V = a.vel4[p];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
+    int64_t idx[8];
+    T delta[8];
+    corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
+
+    // fluid velocity at the particle, Eq. (5)
+    T ux = T(0), uy = T(0), uz = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const typename P::node4 n = a.node[idx[k]];
+        const T w = delta[k] / P::rho_of(n);
+        ux += w * P::from_fix(n.y);
+        uy += w * P::from_fix(n.z);
+        uz += w * P::from_fix(n.w);
+    }
+    // coupling force, Eq. (4) without the conservative part
+    T Fx = -a.zeta * (V.x - ux), Fy = -a.zeta * (V.y - uy), Fz = -a.zeta * (V.z - uz);
+    if (a.noisy) {
+        const uint32_t md_step = (uint32_t)((*a.lb_step) * (unsigned long long)a.n_sub + (unsigned)a.substep);
+        const U4 r = philox4x32_10(U4{(uint32_t)p, md_step, 1u, 0u}, a.key0, a.key1);
+        Fx += a.amp * unit_uniform<T>(r.x);
+        Fy += a.amp * unit_uniform<T>(r.y);
+        Fz += a.amp * unit_uniform<T>(r.z);
+    }
+    // velocity Verlet with F held fixed over the step
+    const T hm = a.half_dt * V.w;  // V.w = 1 / mass
+    T Gx = Fx, Gy = Fy, Gz = Fz;
+    if (BONDS) {
+        const typename P::real4 Fc = a.fcons4[p];
+        Gx += Fc.x;
+        Gy += Fc.y;
+        Gz += Fc.z;
+    }
+    V.x += hm * Gx;
+    V.y += hm * Gy;
+    V.z += hm * Gz;
+    T fx = R.x, fy = R.y, fz = R.z;
+    int cx = c.x, cy = c.y, cz = c.z;
+    advance(fx, cx, a.dt * V.x, a.nx);
+    advance(fy, cy, a.dt * V.y, a.ny);
+    advance(fz, cz, a.dt * V.z, a.nz);
+    if (!BONDS) {
+        V.x += hm * Fx;
+        V.y += hm * Fy;
+        V.z += hm * Fz;
+    }
+    a.pos4[p] = P::make_pos(fx, fy, fz, cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz));
+    a.vel4[p] = V;
+    a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
+
+    if (VARIANT == LBMD_VARIANT_A) {
+        // Newton's third law, Eqs. (7), (8): straight into J_acc
+        const T dPx = a.dt * Fx, dPy = a.dt * Fy, dPz = a.dt * Fz;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            typename P::fix *j = reinterpret_cast<typename P::fix *>(&a.jacc[idx[k]]);
+            P::add_fix(j + 1, P::to_fix(-delta[k] * dPx));
+            P::add_fix(j + 2, P::to_fix(-delta[k] * dPy));
+            P::add_fix(j + 3, P::to_fix(-delta[k] * dPz));
+        }
+    } else {
+        a.old4[p] = R;
+    }
+}
+
+// Variant B: after every particle has read the node field, add the transfer
+// -delta_k Delta P to the momentum density of the 8 nodes (Eqs. (7), (8)), so
+// the next MD step sees the updated node velocities.
+template <typename T>
+__global__ void __launch_bounds__(256) spread_kernel(PArgs<T> a) {
+    using P = Prec<T>;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const typename P::real4 R = a.old4[p];
+    const typename P::real4 F = a.fc4[p];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
+    int64_t idx[8];
+    T delta[8];
+    corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
+    const T dPx = a.dt * F.x, dPy = a.dt * F.y, dPz = a.dt * F.z;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        typename P::fix *j = reinterpret_cast<typename P::fix *>(&a.node[idx[k]]);
+        P::add_fix(j + 1, P::to_fix(-delta[k] * dPx));
+        P::add_fix(j + 2, P::to_fix(-delta[k] * dPy));
+        P::add_fix(j + 3, P::to_fix(-delta[k] * dPz));
+    }
+}
+
+// Harmonic bond forces at the current positions (minimum image), summed per
+// particle over its partners in a fixed order; with KICK, also the second
+// velocity-Verlet half-kick with the stored coupling force.
+template <typename T, bool KICK>
+__global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
+    using P = Prec<T>;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const typename P::real4 R = a.pos4[p];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
+    T Fx = T(0), Fy = T(0), Fz = T(0);
+    const int nbond = a.bond_count[p];
+    for (int b = 0; b < nbond; ++b) {
+        const int64_t q = a.bond_partner[p * LBMD_MAX_BONDS_PER_PARTICLE + b];
+        const typename P::real4 S = a.pos4[q];
+        const CellXYZ d = cell_xyz(P::cell_of(S), a.nx, a.ny);
+        T dx = T(d.x - c.x) + (S.x - R.x);
+        T dy = T(d.y - c.y) + (S.y - R.y);
+        T dz = T(d.z - c.z) + (S.z - R.z);
+        dx -= T(a.nx) * rint(dx / T(a.nx));
+        dy -= T(a.ny) * rint(dy / T(a.ny));
+        dz -= T(a.nz) * rint(dz / T(a.nz));
+        const T r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r > T(0)) {
+            const T k = (T)a.bond_k[p * LBMD_MAX_BONDS_PER_PARTICLE + b];
+            const T r0 = (T)a.bond_r0[p * LBMD_MAX_BONDS_PER_PARTICLE + b];
+            const T mag = k * (r - r0) / r;
+            Fx += mag * dx;
+            Fy += mag * dy;
+            Fz += mag * dz;
+        }
+    }
+    a.fcons4[p] = P::make4(Fx, Fy, Fz, T(0));
+    if (KICK) {
+        typename P::real4 V = a.vel4[p];
+        const typename P::real4 Fc = a.fc4[p];
+        const T hm = a.half_dt * V.w;
+        V.x += hm * (Fx + Fc.x);
+        V.y += hm * (Fy + Fc.y);
+        V.z += hm * (Fz + Fc.z);
+        a.vel4[p] = V;
+    }
+}
+
+template <typename T>
+static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
+    using P = Prec<T>;
+    PArgs<T> a;
+    a.pos4 = static_cast<typename P::real4 *>(ctx->pos4);
+    a.vel4 = static_cast<typename P::real4 *>(ctx->vel4);
+    a.fc4 = static_cast<typename P::real4 *>(ctx->fc4);
+    a.old4 = static_cast<typename P::real4 *>(ctx->old4);
+    a.fcons4 = static_cast<typename P::real4 *>(ctx->fcons4);
+    a.node = static_cast<typename P::node4 *>(ctx->node);
+    a.jacc = static_cast<typename P::node4 *>(ctx->jacc);
+    a.bond_count = ctx->bond_count;
+    a.bond_partner = ctx->bond_partner;
+    a.bond_k = ctx->bond_k;
+    a.bond_r0 = ctx->bond_r0;
+    a.nx = ctx->p.nx;
+    a.ny = ctx->p.ny;
+    a.nz = ctx->p.nz;
+    a.np = ctx->np;
+    a.zeta = (T)ctx->p.zeta;
+    a.dt = (T)ctx->dt;
+    a.half_dt = (T)(0.5 * ctx->dt);
+    a.amp = (T)sqrt(2.0 * ctx->p.zeta * ctx->p.kT / ctx->dt);
+    a.key0 = (uint32_t)(ctx->p.seed & 0xffffffffu);
+    a.key1 = (uint32_t)(ctx->p.seed >> 32);
+    a.lb_step = ctx->d_lb_step;
+    a.n_sub = ctx->p.n_sub;
+    a.substep = substep;
+    a.noisy = ctx->p.kT > 0.0 ? 1 : 0;
+    return a;
+}
+
+template <typename T>
+static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
+    if (ctx->np == 0) return cudaSuccess;
+    PArgs<T> a = make_pargs<T>(ctx, substep);
+    const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
+    const bool bonds = ctx->nb > 0;
+    const bool B = ctx->p.variant == LBMD_VARIANT_B;
+    if (B) {
+        if (bonds)
+            couple_kernel<T, LBMD_VARIANT_B, true><<<blocks, 256, 0, ctx->stream>>>(a);
+        else
+            couple_kernel<T, LBMD_VARIANT_B, false><<<blocks, 256, 0, ctx->stream>>>(a);
+    } else {
+        if (bonds)
+            couple_kernel<T, LBMD_VARIANT_A, true><<<blocks, 256, 0, ctx->stream>>>(a);
+        else
+            couple_kernel<T, LBMD_VARIANT_A, false><<<blocks, 256, 0, ctx->stream>>>(a);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (bonds) {
+        bond_kick_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (B) {
+        spread_kernel<T><<<blocks, 256, 0, ctx->stream>>>(a);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <typename T>
+static cudaError_t bond_forces_t(lbmd_ctx *ctx) {
+    if (ctx->np == 0) return cudaSuccess;
+    PArgs<T> a = make_pargs<T>(ctx, 0);
+    const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
+    bond_kick_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmd
+
+cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep) {
+    return ctx->p.precision == LBMD_FP64 ? lbmd::md_substep_t<double>(ctx, substep)
+                                         : lbmd::md_substep_t<float>(ctx, substep);
+}
+
+cudaError_t launch_bond_forces_only(lbmd_ctx *ctx) {
+    return ctx->p.precision == LBMD_FP64 ? lbmd::bond_forces_t<double>(ctx) : lbmd::bond_forces_t<float>(ctx);
+}

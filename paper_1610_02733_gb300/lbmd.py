@@ -1,0 +1,307 @@
+"""Thin ctypes binding of the C ABI in ``include/lbmd.h`` (argument
+marshalling only: every step of the LB/MD path runs in the CUDA library).
+
+The functions keep the ABI's names (``lbmd_create``, ``lbmd_md_substep``,
+...).  ``LBMD`` is a small convenience wrapper around one context.  The
+library is loaded from ``_build/liblbmd.so``; if it is missing the import of
+the library fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbmd.so")
+
+LBMD_OK = 0
+LBMD_ERR_ARG = -1
+LBMD_ERR_CUDA = -2
+LBMD_ERR_OOM = -3
+LBMD_ERR_SEQUENCE = -4
+LBMD_ERR_NONFINITE = -5
+LBMD_ERR_CAPACITY = -6
+VARIANT_A, VARIANT_B = 0, 1
+FP32, FP64 = 0, 1
+
+# every symbol include/lbmd.h declares
+EXPORTS = (
+    "lbmd_create", "lbmd_destroy", "lbmd_add_particles", "lbmd_add_bonds", "lbmd_set_particles",
+    "lbmd_md_substep", "lbmd_lb_step", "lbmd_run_cycles", "lbmd_observables", "lbmd_get_populations",
+    "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
+    "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
+)
+
+
+class LbmdParams(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32),
+        ("n_sub", ct.c_int32), ("variant", ct.c_int32), ("precision", ct.c_int32),
+        ("rho0", ct.c_double), ("nu", ct.c_double), ("nu_bulk", ct.c_double),
+        ("gamma_ghost", ct.c_double), ("kT", ct.c_double), ("zeta", ct.c_double),
+        ("body_force", ct.c_double * 3), ("seed", ct.c_uint64),
+        ("max_particles", ct.c_int64), ("max_bonds", ct.c_int64), ("stream", ct.c_void_p),
+    ]
+
+
+class LbmdObservables(ct.Structure):
+    _fields_ = [
+        ("mass", ct.c_double), ("p_fluid", ct.c_double * 3), ("p_particles", ct.c_double * 3),
+        ("kT_particles", ct.c_double), ("e_kin", ct.c_double), ("lb_step", ct.c_int64), ("md_step", ct.c_int64),
+    ]
+
+
+class LbmdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (msg, status, ""))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load liblbmd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbmd.so not built (%s): run __graft_entry__.build()" % LIB_PATH)
+    L = ct.CDLL(LIB_PATH)
+    P = ct.c_void_p
+    dp = ct.POINTER(ct.c_double)
+    i64p = ct.POINTER(ct.c_int64)
+    for name in EXPORTS:
+        getattr(L, name)  # every declared symbol must resolve
+    L.lbmd_create.argtypes = [ct.POINTER(LbmdParams), ct.POINTER(ct.c_void_p)]
+    L.lbmd_destroy.argtypes = [P]
+    L.lbmd_add_particles.argtypes = [P, ct.c_int64, dp, dp, dp, i64p]
+    L.lbmd_add_bonds.argtypes = [P, ct.c_int64, i64p, ct.c_double, ct.c_double]
+    L.lbmd_set_particles.argtypes = [P, ct.c_void_p, ct.c_void_p]
+    L.lbmd_md_substep.argtypes = [P]
+    L.lbmd_lb_step.argtypes = [P]
+    L.lbmd_run_cycles.argtypes = [P, ct.c_int64]
+    L.lbmd_observables.argtypes = [P, ct.POINTER(LbmdObservables)]
+    for name in ("lbmd_get_populations", "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer"):
+        getattr(L, name).argtypes = [P, ct.c_void_p]
+    L.lbmd_get_particles.argtypes = [P, ct.c_void_p, ct.c_void_p]
+    L.lbmd_get_particles_device.argtypes = [P, ct.c_void_p, ct.c_void_p]
+    L.lbmd_get_counts.argtypes = [P, i64p, i64p, i64p, i64p, ct.POINTER(ct.c_int32)]
+    L.lbmd_stream.restype = ct.c_void_p
+    L.lbmd_stream.argtypes = [P]
+    L.lbmd_last_error.restype = ct.c_char_p
+    L.lbmd_last_error.argtypes = [P]
+    L.lbmd_status_string.restype = ct.c_char_p
+    L.lbmd_status_string.argtypes = [ct.c_int]
+    for name in EXPORTS:
+        if name not in ("lbmd_stream", "lbmd_last_error", "lbmd_status_string"):
+            getattr(L, name).restype = ct.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ct.c_void_p)
+
+
+def _f64(a, n=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None:
+        a = a.reshape(n)
+    return a
+
+
+# ---------------------------------------------------------------------------
+# ABI-named functions (handle = ct.c_void_p)
+# ---------------------------------------------------------------------------
+def _check(h, rc, what):
+    if rc != LBMD_OK:
+        L = load()
+        msg = L.lbmd_last_error(h).decode(errors="replace")
+        err = LbmdError(rc, what)
+        err.args = ("%s failed: %s (status %d: %s)" % (what, msg, rc,
+                                                      L.lbmd_status_string(rc).decode()),)
+        raise err
+    return rc
+
+
+def lbmd_create(params: LbmdParams):
+    L = load()
+    h = ct.c_void_p()
+    _check(None, L.lbmd_create(ct.byref(params), ct.byref(h)), "lbmd_create")
+    return h
+
+
+def lbmd_destroy(h):
+    return load().lbmd_destroy(h)
+
+
+def lbmd_md_substep(h):
+    return _check(h, load().lbmd_md_substep(h), "lbmd_md_substep")
+
+
+def lbmd_lb_step(h):
+    return _check(h, load().lbmd_lb_step(h), "lbmd_lb_step")
+
+
+def lbmd_run_cycles(h, n: int):
+    return _check(h, load().lbmd_run_cycles(h, int(n)), "lbmd_run_cycles")
+
+
+def lbmd_observables(h) -> dict:
+    o = LbmdObservables()
+    _check(h, load().lbmd_observables(h, ct.byref(o)), "lbmd_observables")
+    return {"mass": o.mass, "p_fluid": np.array(list(o.p_fluid)), "p_particles": np.array(list(o.p_particles)),
+            "kT_particles": o.kT_particles, "e_kin": o.e_kin, "lb_step": o.lb_step, "md_step": o.md_step}
+
+
+def make_params(nx, ny, nz, *, n_sub=1, variant=VARIANT_B, precision=FP32, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
+                gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1, max_particles=0,
+                max_bonds=0, stream=None) -> LbmdParams:
+    p = LbmdParams()
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    p.n_sub, p.variant, p.precision = int(n_sub), int(variant), int(precision)
+    p.rho0, p.nu, p.nu_bulk, p.gamma_ghost = float(rho0), float(nu), float(nu_bulk), float(gamma_ghost)
+    p.kT, p.zeta = float(kT), float(zeta)
+    for a in range(3):
+        p.body_force[a] = float(body_force[a])
+    p.seed = int(seed)
+    p.max_particles, p.max_bonds = int(max_particles), int(max_bonds)
+    p.stream = stream
+    return p
+
+
+class LBMD:
+    """One simulation context on the current CUDA device.
+
+    Keyword arguments are the fields of ``lbmd_params`` (lattice units,
+    a = tau_LB = 1).  ``precision`` is ``"fp32"`` or ``"fp64"``; ``variant`` is
+    ``"A"`` or ``"B"``.
+    """
+
+    def __init__(self, nx, ny, nz, *, variant="B", precision="fp32", **kw):
+        v = {"A": VARIANT_A, "B": VARIANT_B, 0: VARIANT_A, 1: VARIANT_B}[variant]
+        pr = {"fp32": FP32, "fp64": FP64, 0: FP32, 1: FP64}[precision]
+        self.params = make_params(nx, ny, nz, variant=v, precision=pr, **kw)
+        self.shape = (int(nx), int(ny), int(nz))
+        self.n_nodes = int(nx) * int(ny) * int(nz)
+        self.n_sub = self.params.n_sub
+        self._h = lbmd_create(self.params)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lbmd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # sequence ---------------------------------------------------------------
+    def add_particles(self, pos, vel, mass=None) -> int:
+        pos = _f64(pos).reshape(-1, 3)
+        vel = _f64(vel).reshape(-1, 3)
+        n = pos.shape[0]
+        m = None if mass is None else _f64(mass, n)
+        first = ct.c_int64(0)
+        dp = ct.POINTER(ct.c_double)
+        _check(self._h, load().lbmd_add_particles(
+            self._h, n, pos.ctypes.data_as(dp), vel.ctypes.data_as(dp),
+            None if m is None else m.ctypes.data_as(dp), ct.byref(first)), "lbmd_add_particles")
+        return first.value
+
+    def add_bonds(self, pairs, k, r0):
+        pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+        _check(self._h, load().lbmd_add_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
+                                              float(k), float(r0)), "lbmd_add_bonds")
+
+    def set_particles(self, pos=None, vel=None):
+        """Host arrays (numpy or pinned torch tensors, float64, 3 N each)."""
+        def addr(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return ct.c_void_p(a.data_ptr())
+            return _ptr(a)
+        self._keep = (pos, vel)
+        _check(self._h, load().lbmd_set_particles(self._h, addr(pos), addr(vel)), "lbmd_set_particles")
+
+    def md_substep(self):
+        return lbmd_md_substep(self._h)
+
+    def lb_step(self):
+        return lbmd_lb_step(self._h)
+
+    def cycle(self, k: int = 1):
+        for _ in range(int(k)):
+            for _ in range(self.n_sub):
+                lbmd_md_substep(self._h)
+            lbmd_lb_step(self._h)
+
+    def run_cycles(self, k: int):
+        return lbmd_run_cycles(self._h, k)
+
+    # accessors ----------------------------------------------------------------
+    def observables(self) -> dict:
+        return lbmd_observables(self._h)
+
+    def populations(self) -> np.ndarray:
+        out = np.empty(19 * self.n_nodes)
+        _check(self._h, load().lbmd_get_populations(self._h, _ptr(out)), "lbmd_get_populations")
+        return out.reshape(19, self.n_nodes)
+
+    def set_populations(self, f):
+        f = _f64(f, 19 * self.n_nodes)
+        _check(self._h, load().lbmd_set_populations(self._h, _ptr(f)), "lbmd_set_populations")
+
+    def node_field(self) -> np.ndarray:
+        out = np.empty(4 * self.n_nodes)
+        _check(self._h, load().lbmd_get_node_field(self._h, _ptr(out)), "lbmd_get_node_field")
+        return out.reshape(self.n_nodes, 4)
+
+    def transfer(self) -> np.ndarray:
+        out = np.empty(3 * self.n_nodes)
+        _check(self._h, load().lbmd_get_transfer(self._h, _ptr(out)), "lbmd_get_transfer")
+        return out.reshape(self.n_nodes, 3)
+
+    def counts(self):
+        a, b, c, d = (ct.c_int64() for _ in range(4))
+        e = ct.c_int32()
+        load().lbmd_get_counts(self._h, ct.byref(a), ct.byref(b), ct.byref(c), ct.byref(d), ct.byref(e))
+        return {"n_particles": a.value, "n_bonds": b.value, "lb_step": c.value, "md_step": d.value,
+                "substeps_done": e.value}
+
+    @property
+    def n_particles(self) -> int:
+        return self.counts()["n_particles"]
+
+    def particles(self):
+        n = self.n_particles
+        pos = np.empty(3 * max(n, 1))
+        vel = np.empty(3 * max(n, 1))
+        _check(self._h, load().lbmd_get_particles(self._h, _ptr(pos), _ptr(vel)), "lbmd_get_particles")
+        return pos[:3 * n].reshape(n, 3), vel[:3 * n].reshape(n, 3)
+
+    def particles_device(self, pos, vel):
+        """Stream-ordered copy into caller-owned device tensors (float64, 3 N)."""
+        _check(self._h, load().lbmd_get_particles_device(
+            self._h, None if pos is None else ct.c_void_p(pos.data_ptr()),
+            None if vel is None else ct.c_void_p(vel.data_ptr())), "lbmd_get_particles_device")
+
+    @property
+    def stream(self) -> int:
+        return load().lbmd_stream(self._h) or 0

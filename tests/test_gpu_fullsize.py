@@ -1,0 +1,78 @@
+"""Parity at the benchmark's full size: 256^3 periodic D3Q19, 10^6 ideal
+particles, variant B, m = 10, kT = 1e-4, zeta = 1, FP32, in the launch
+configuration the benchmark times.
+
+The oracle runs the whole MD phase of the first cycle (every particle, every
+node's pending transfer is compared), and then the LB step on a sample of
+nodes, one node at a time: the post-stream populations of node r are the
+post-collision populations of its 19 upstream neighbours r - c_i, which the
+oracle computes from its own state.
+"""
+import numpy as np
+import pytest
+
+from paper_1610_02733_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (256, 256, 256)
+NP = 1_000_000
+N_SUB = 10
+
+
+@pytest.fixture(scope="module")
+def states():
+    from gpu_common import pair
+    o, g = pair(SHAPE, precision="fp32", variant="B", n_sub=N_SUB, kT=1e-4, zeta=1.0, seed=1, max_particles=NP)
+    pos = inputs.uniform_positions(NP, SHAPE, 1)
+    vel = inputs.maxwell_velocities(NP, 1e-4, 1)
+    o.add_particles(pos, vel)
+    g.add_particles(pos, vel)
+    for s in range(N_SUB):
+        o.md_substep()
+        g.md_substep()
+    yield o, g
+    o.close()
+    g.close()
+
+
+def test_md_phase_full_size(states):
+    o, g = states
+    po, vo = o.particles()
+    pg, vg = g.particles()
+    d = pg - po
+    d -= 256.0 * np.round(d / 256.0)
+    assert np.abs(d).max() < 1e-4
+    assert np.abs(vg - vo).max() <= 1e-5 * np.abs(vo).max()
+    Jg, Jo = g.transfer(), o.jacc()
+    assert np.abs(Jg - Jo).max() <= 1e-5 * np.abs(Jo).max()
+    assert np.count_nonzero(np.abs(Jo).sum(axis=1)) > 0.3 * Jo.shape[0]
+
+
+def test_lb_step_full_size_sampled(states):
+    o, g = states
+    c = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 0],
+                  [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1], [-1, 0, 1], [0, 1, 1],
+                  [0, -1, -1], [0, 1, -1], [0, -1, 1]])
+    L = np.array(SHAPE)
+    rng = np.random.default_rng(0)
+    sample = np.vstack([rng.integers(0, 256, size=(200, 3)), [[0, 0, 0], [255, 255, 255], [255, 0, 128]]])
+    f_before = None  # the fluid starts at rest: f*_i = w_i rho0 everywhere
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    J = o.jacc()
+    g.lb_step()
+    fg = g.populations()
+    for r in sample:
+        want = np.zeros(19)
+        for i in range(19):
+            s = (r - c[i]) % L
+            sidx = int(s[0] + 256 * (s[1] + 256 * s[2]))
+            post = o.collide_node(w * 1.0, J[sidx], node=sidx, lb_step=0)
+            want[i] = post[i]
+        ridx = int(r[0] + 256 * (r[1] + 256 * r[2]))
+        got = fg[:, ridx]
+        assert (np.abs(got - want) / w).max() <= 1e-5, (r, np.abs(got - want).max())
+    ob = g.observables()
+    # mass and total momentum after the full cycle (FP32 storage)
+    assert abs(ob["mass"] / 256 ** 3 - 1.0) < 1e-6
+    del f_before
