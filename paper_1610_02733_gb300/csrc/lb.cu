@@ -29,6 +29,7 @@ struct LbArgs {
     uint32_t key0, key1;
     const unsigned long long *lb_step;
     int noisy;
+    int variant;
 };
 
 // Reciprocal norms 1/b_k, exact binary fractions.
@@ -37,6 +38,14 @@ __host__ __device__ constexpr double INV_BNORM(int k) {
                              1.5, 1.5, 1.5, 4.5, 4.5, 4.5, 0.5, 0.75, 2.25};
     return t[k];
 }
+
+// The D3Q19 order pairs every moving velocity with its opposite:
+// c_{2p+2} = -c_{2p+1}, p = 0..8.  Even modes (0, 4-9, 16-18) see only the
+// pair sums s_p = f_{2p+1} + f_{2p+2}, odd modes (1-3, 10-15) only the
+// differences d_p = f_{2p+1} - f_{2p+2}; the back-transform likewise returns
+// an even part E_p and an odd part O_p with f_{2p+1} = w (E_p + O_p) and
+// f_{2p+2} = w (E_p - O_p).  This halves the arithmetic of both transforms.
+__host__ __device__ constexpr bool EVEN_MODE(int k) { return k == 0 || (k >= 4 && k <= 9) || k >= 16; }
 
 // MRT collision with forcing and noise at one node; f holds f* on entry and
 // f' on exit.
@@ -50,14 +59,22 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
     const T uu = ux * ux + uy * uy + uz * uz;
     const T uF = ux * Fx + uy * Fy + uz * Fz;
 
+    T s[9], d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        s[p] = f[2 * p + 1] + f[2 * p + 2];
+        d[p] = f[2 * p + 1] - f[2 * p + 2];
+    }
     // non-conserved moments m_k = sum_i e_k(c_i) f_i, k = 4..18
     T m[Q];
 #pragma unroll
     for (int k = 4; k < Q; ++k) {
         T acc = T(0);
+        if (EVEN_MODE(k) && EMODE(k, 0) != 0) acc = T(EMODE(k, 0)) * f[0];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (EMODE(k, i) != 0) acc += T(EMODE(k, i)) * f[i];
+        for (int p = 0; p < 9; ++p) {
+            const int e = EMODE(k, 2 * p + 1);
+            if (e != 0) acc += T(e) * (EVEN_MODE(k) ? s[p] : d[p]);
         }
         m[k] = acc;
     }
@@ -105,39 +122,60 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
     }
 #pragma unroll
     for (int k = 0; k < Q; ++k) mp[k] *= T(INV_BNORM(k));
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    {
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k < Q; ++k)
-            if (EMODE(k, i) != 0) acc += T(EMODE(k, i)) * mp[k];
-        f[i] = T(WEIGHT(i)) * acc;
+            if (EVEN_MODE(k) && EMODE(k, 0) != 0) acc += T(EMODE(k, 0)) * mp[k];
+        f[0] = T(WEIGHT(0)) * acc;
+    }
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        T ev = T(0), od = T(0);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int e = EMODE(k, 2 * p + 1);
+            if (e == 0) continue;
+            if (EVEN_MODE(k))
+                ev += T(e) * mp[k];
+            else
+                od += T(e) * mp[k];
+        }
+        const T w = T(WEIGHT(2 * p + 1));
+        f[2 * p + 1] = w * (ev + od);
+        f[2 * p + 2] = w * (ev - od);
     }
 }
 
-template <typename T, int VARIANT>
+// One thread per node; grid (ceil(nx / blockDim.x), ny, nz).  The variant is
+// a run-time (warp-uniform) flag rather than a template parameter: both
+// variants then execute one compiled instruction sequence, so at m = 1 they
+// agree bit for bit, as the paper's algorithmic equivalence requires.
+template <typename T>
 __global__ void __launch_bounds__(256) lb_collide_push(LbArgs<T> a) {
     using P = Prec<T>;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= a.N) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const uint32_t r = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     T f[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = a.fin[(int64_t)i * a.N + r];
+    for (int i = 0; i < Q; ++i) f[i] = a.fin[(size_t)i * a.N + r];
     T rho, jx, jy, jz;
     node_moments(f, rho, jx, jy, jz);
     T Fx, Fy, Fz;
-    if (VARIANT == LBMD_VARIANT_B) {
+    if (a.variant == LBMD_VARIANT_B) {
         // node j = fix(j*) + sum of fixed-point transfers: the difference is
         // exactly the accumulated transfer J_acc
         const typename P::node4 n = a.node[r];
-        Fx = P::from_fix(n.y - P::to_fix(jx));
-        Fy = P::from_fix(n.z - P::to_fix(jy));
-        Fz = P::from_fix(n.w - P::to_fix(jz));
+        Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx));
+        Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy));
+        Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz));
     } else {
         const typename P::node4 J = a.jacc[r];
-        Fx = P::from_fix(J.y);
-        Fy = P::from_fix(J.z);
-        Fz = P::from_fix(J.w);
+        Fx = P::from_fix(P::jx_of(J));
+        Fy = P::from_fix(P::jy_of(J));
+        Fz = P::from_fix(P::jz_of(J));
         typename P::node4 zero;
         zero.x = zero.y = zero.z = zero.w = 0;
         a.jacc[r] = zero;
@@ -145,34 +183,32 @@ __global__ void __launch_bounds__(256) lb_collide_push(LbArgs<T> a) {
     Fx += a.g[0];
     Fy += a.g[1];
     Fz += a.g[2];
-    collide(f, rho, jx, jy, jz, Fx, Fy, Fz, a, (uint32_t)r, (uint32_t)(*a.lb_step));
+    collide(f, rho, jx, jy, jz, Fx, Fy, Fz, a, r, (uint32_t)(*a.lb_step));
 
-    const int64_t nxy = (int64_t)a.nx * a.ny;
-    const int z = (int)(r / nxy);
-    const int64_t rem = r - (int64_t)z * nxy;
-    const int y = (int)(rem / a.nx);
-    const int x = (int)(rem - (int64_t)y * a.nx);
+    const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z == a.nz - 1 ? 0 : z + 1;
+    const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        int xn = x + CX(i), yn = y + CY(i), zn = z + CZ(i);
-        xn = xn < 0 ? a.nx - 1 : (xn == a.nx ? 0 : xn);
-        yn = yn < 0 ? a.ny - 1 : (yn == a.ny ? 0 : yn);
-        zn = zn < 0 ? a.nz - 1 : (zn == a.nz ? 0 : zn);
-        a.fout[(int64_t)i * a.N + xn + a.nx * ((int64_t)yn + (int64_t)a.ny * zn)] = f[i];
+        const uint32_t t = (uint32_t)X[CX(i) + 1] +
+                           (uint32_t)a.nx * ((uint32_t)Y[CY(i) + 1] + (uint32_t)a.ny * (uint32_t)Z[CZ(i) + 1]);
+        a.fout[(size_t)i * a.N + t] = f[i];
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    node_moments_kernel(const T *__restrict__ f, typename Prec<T>::node4 *node, int64_t N, unsigned long long *lb_step,
-                        int count_step) {
+    node_moments_kernel(const T *__restrict__ f, typename Prec<T>::node4 *node, int64_t N, int nx, int ny,
+                        unsigned long long *lb_step, int count_step) {
     using P = Prec<T>;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (count_step && r == 0) *lb_step += 1ull;
-    if (r >= N) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (count_step && x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *lb_step += 1ull;
+    if (x >= nx) return;
+    const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)blockIdx.y + (uint32_t)ny * (uint32_t)blockIdx.z);
     T fl[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fl[i] = f[(int64_t)i * N + r];
+    for (int i = 0; i < Q; ++i) fl[i] = f[(size_t)i * N + r];
     T rho, jx, jy, jz;
     node_moments(fl, rho, jx, jy, jz);
     node[r] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
@@ -184,6 +220,15 @@ __global__ void init_equilibrium_kernel(T *f, int64_t N, T rho0) {
     if (r >= N) return;
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[(int64_t)i * N + r] = T(WEIGHT(i)) * rho0;
+}
+
+// Node kernels run one thread per node on a (x-blocks, ny, nz) grid.
+static dim3 node_block(const lbmd_ctx *ctx) {
+    const int bx = ctx->p.nx >= 256 ? 256 : (ctx->p.nx >= 128 ? 128 : (ctx->p.nx >= 64 ? 64 : 32));
+    return dim3(bx, 1, 1);
+}
+static dim3 node_grid(const lbmd_ctx *ctx, dim3 block) {
+    return dim3((ctx->p.nx + block.x - 1) / block.x, ctx->p.ny, ctx->p.nz);
 }
 
 template <typename T>
@@ -206,20 +251,18 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.key1 = (uint32_t)(ctx->p.seed >> 32);
     a.lb_step = ctx->d_lb_step;
     a.noisy = ctx->co.noisy;
-    const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
-    if (ctx->p.variant == LBMD_VARIANT_B)
-        lb_collide_push<T, LBMD_VARIANT_B><<<blocks, 256, 0, ctx->stream>>>(a);
-    else
-        lb_collide_push<T, LBMD_VARIANT_A><<<blocks, 256, 0, ctx->stream>>>(a);
+    a.variant = ctx->p.variant;
+    const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
+    lb_collide_push<T><<<grid, block, 0, ctx->stream>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t node_moments_t(lbmd_ctx *ctx, bool count_step) {
-    const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
-    node_moments_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<const T *>(ctx->f[ctx->cur]),
-                                                             static_cast<typename Prec<T>::node4 *>(ctx->node),
-                                                             ctx->N, ctx->d_lb_step, count_step ? 1 : 0);
+    const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
+    node_moments_kernel<T><<<grid, block, 0, ctx->stream>>>(static_cast<const T *>(ctx->f[ctx->cur]),
+                                                            static_cast<typename Prec<T>::node4 *>(ctx->node), ctx->N,
+                                                            ctx->p.nx, ctx->p.ny, ctx->d_lb_step, count_step ? 1 : 0);
     return cudaGetLastError();
 }
 

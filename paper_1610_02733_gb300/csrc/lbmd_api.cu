@@ -36,10 +36,11 @@ lbmd_status cuda_fail(lbmd_ctx *ctx, cudaError_t e, const char *where) {
 size_t real_size(const lbmd_ctx *ctx) { return ctx->p.precision == LBMD_FP64 ? 8 : 4; }
 
 void free_all(lbmd_ctx *ctx) {
-    void *bufs[] = {ctx->f[0],       ctx->f[1],        ctx->node,       ctx->jacc,    ctx->pos4,
-                    ctx->vel4,       ctx->fc4,         ctx->old4,       ctx->fcons4,  ctx->bond_count,
-                    ctx->bond_partner, ctx->bond_k,    ctx->bond_r0,    ctx->staging, ctx->red_partial,
-                    ctx->red_out,    ctx->d_lb_step};
+    void *bufs[] = {ctx->f[0],      ctx->f[1],       ctx->node,        ctx->jacc,      ctx->pos4[0],
+                    ctx->pos4[1],   ctx->vel4[0],    ctx->vel4[1],     ctx->fcons4[0], ctx->fcons4[1],
+                    ctx->pid[0],    ctx->pid[1],     ctx->slot_of,     ctx->row_count, ctx->sort_rank,
+                    ctx->fc4,       ctx->old4,       ctx->bond_count,  ctx->bond_partner, ctx->bond_k,
+                    ctx->bond_r0,   ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 2; ++i)
@@ -144,11 +145,19 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {&ctx->f[1], (size_t)19 * N * rs},
         {&ctx->node, (size_t)N * node_bytes},
         {&ctx->jacc, p->variant == LBMD_VARIANT_A ? (size_t)N * node_bytes : 0},
-        {&ctx->pos4, (size_t)maxp * 4 * rs},
-        {&ctx->vel4, (size_t)maxp * 4 * rs},
+        {&ctx->pos4[0], (size_t)maxp * 4 * rs},
+        {&ctx->pos4[1], (size_t)maxp * 4 * rs},
+        {&ctx->vel4[0], (size_t)maxp * 4 * rs},
+        {&ctx->vel4[1], (size_t)maxp * 4 * rs},
+        {&ctx->fcons4[0], (size_t)maxp * 4 * rs},
+        {&ctx->fcons4[1], (size_t)maxp * 4 * rs},
+        {(void **)&ctx->pid[0], (size_t)maxp * sizeof(int32_t)},
+        {(void **)&ctx->pid[1], (size_t)maxp * sizeof(int32_t)},
+        {(void **)&ctx->slot_of, (size_t)maxp * sizeof(int32_t)},
+        {(void **)&ctx->row_count, (size_t)p->ny * p->nz * sizeof(int32_t)},
+        {(void **)&ctx->sort_rank, (size_t)maxp * sizeof(int32_t)},
         {&ctx->fc4, (size_t)maxp * 4 * rs},
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
-        {&ctx->fcons4, (size_t)maxp * 4 * rs},
         {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},
         {(void **)&ctx->bond_partner, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(int32_t)},
         {(void **)&ctx->bond_k, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
@@ -171,7 +180,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_lb_step, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_count, 0, (size_t)maxp * sizeof(int32_t), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fcons4, 0, (size_t)maxp * 4 * rs, ctx->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        e = cudaMemsetAsync(ctx->fcons4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fc4, 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess && ctx->jacc) e = cudaMemsetAsync(ctx->jacc, 0, (size_t)N * node_bytes, ctx->stream);
     if (e == cudaSuccess) e = launch_init_equilibrium(ctx);
@@ -219,7 +229,7 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
         CK(ctx, cudaStreamSynchronize(ctx->stream));
     }
     const size_t rs = real_size(ctx);
-    CK(ctx, cudaMemsetAsync((char *)ctx->fcons4 + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
+    CK(ctx, cudaMemsetAsync((char *)ctx->fcons4[ctx->pcur] + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     CK(ctx, cudaMemsetAsync((char *)ctx->fc4 + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     ctx->np += n;
     if (ctx->nb > 0) CK(ctx, launch_bond_forces_only(ctx));
@@ -299,6 +309,7 @@ lbmd_status lbmd_lb_step(lbmd_ctx *ctx) {
     if (!ctx) return LBMD_ERR_ARG;
     if (ctx->sub_done != ctx->p.n_sub) return fail(ctx, LBMD_ERR_SEQUENCE, "LB step before n_sub MD steps");
     CK(ctx, launch_lb_step(ctx));
+    CK(ctx, launch_sort_particles(ctx));
     ctx->sub_done = 0;
     ctx->lb_step += 1;
     return LBMD_OK;
@@ -314,10 +325,12 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
             cudaGraph_t g = nullptr;
             CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
-            const int cur0 = ctx->cur;
+            const int cur0 = ctx->cur, pcur0 = ctx->pcur;
             for (int s = 0; s < ctx->p.n_sub && e == cudaSuccess; ++s) e = launch_md_substep(ctx, s);
             if (e == cudaSuccess) e = launch_lb_step(ctx);
-            ctx->cur = cur0;  // launch_lb_step flipped it during capture
+            if (e == cudaSuccess) e = launch_sort_particles(ctx);
+            ctx->cur = cur0;  // the launchers flipped the buffers during capture
+            ctx->pcur = pcur0;
             cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
             if (e != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -333,6 +346,7 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
         }
         CK(ctx, cudaGraphLaunch(ctx->cycle_graph[parity], ctx->stream));
         ctx->cur ^= 1;
+        ctx->pcur ^= 1;
         ctx->lb_step += 1;
         ctx->md_step += ctx->p.n_sub;
     }

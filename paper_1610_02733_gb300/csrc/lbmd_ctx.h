@@ -9,13 +9,20 @@
 //               steps).  Variant B: j* plus every transfer since.
 //   jacc        variant A only: the transfers since the last LB step, fixed
 //               point, 4 words per node (x, y, z, unused).
-//   pos4        per particle: fractional position in its cell (x, y, z) and
-//               the linear cell index.
-//   vel4        per particle: velocity (x, y, z) and 1 / mass.
-//   fc4         per particle: coupling force F of the last MD step.
+//   Particles live in "slots".  Once per LB step they are re-ordered by
+//   lattice row (y, z) of their cell, so that the particles a warp handles
+//   touch neighbouring nodes (cache locality of the corner reads and
+//   transfers).  Results do not depend on the order: every per-particle
+//   quantity is keyed by the particle id, and transfers are integer sums.
+//   pos4[2]     per slot: fractional position in its cell (x, y, z) and the
+//               linear cell index (two buffers: the re-ordering copies).
+//   vel4[2]     per slot: velocity (x, y, z) and 1 / mass.
+//   fcons4[2]   per slot: bond force at the current positions.
+//   pid[2]      per slot: particle id.   slot_of: per id, its slot.
+//   fc4         per slot: coupling force F of the current MD step.
 //   old4        variant B only: pos4 at the start of the current MD step.
-//   fcons4      per particle: bond force at the current positions.
-//   bond_*      per particle up to LBMD_MAX_BONDS_PER_PARTICLE partners.
+//   bond_*      per particle id: up to LBMD_MAX_BONDS_PER_PARTICLE partner ids.
+//   row_count   per lattice row: particle counts / offsets of the re-ordering.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,7 +49,12 @@ struct lbmd_ctx {
     void *f[2];
     void *node;
     void *jacc;
-    void *pos4, *vel4, *fc4, *old4, *fcons4;
+    int pcur;  // index of the particle buffers in use
+    void *pos4[2], *vel4[2], *fcons4[2];
+    int32_t *pid[2];
+    int32_t *slot_of;
+    void *fc4, *old4;
+    int32_t *row_count, *sort_rank;
     int32_t *bond_count, *bond_partner;
     double *bond_k, *bond_r0;
     double *staging;   // device staging buffer for host <-> device conversions
@@ -76,3 +88,4 @@ cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t c
                                          bool set_mass);
 cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel);
 cudaError_t launch_clear_transfer(lbmd_ctx *ctx);
+cudaError_t launch_sort_particles(lbmd_ctx *ctx);

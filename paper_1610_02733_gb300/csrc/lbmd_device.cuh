@@ -8,7 +8,7 @@
 // Particle-to-fluid transfers (Eqs. (7), (8) of the paper) are added with
 // integer atomics, which are associative: the accumulated value does not
 // depend on the order in which particles are processed, so every run is
-// bitwise reproducible without sorting or colouring.  Range: |j| < 2 (FP32)
+// bitwise reproducible without a fixed particle order or colouring.  Range: |j| < 2 (FP32)
 // and |j| < 128 (FP64), far above any flow an LB fluid can carry (the
 // lattice Mach number must stay well below one).
 #pragma once
@@ -129,20 +129,36 @@ struct __align__(32) L4 {
 template <typename T>
 struct Prec;
 
+// FP32 node record (16 bytes, one int4): word 0 holds rho as float bits,
+// word 1 j_z, words 2-3 one signed 64-bit integer S = j_y 2^32 + j_x (all in
+// units of 2^-30).  The low word of S is j_x itself; the high word is j_y,
+// minus one when j_x is negative.  Because S is an ordinary integer sum, a
+// transfer (dx, dy, dz) is added with two atomics, one 64-bit add of
+// dy 2^32 + dx and one 32-bit add of dz, and the fields stay exact as long as
+// each one stays within its 32-bit range.
 template <>
 struct Prec<float> {
     using real = float;
     using real4 = float4;
     using fix = int32_t;
-    using node4 = int4;  // {rho as float bits, j_x, j_y, j_z fixed point}
+    using node4 = int4;
     static constexpr float SCALE = 1073741824.0f;             // 2^30
     static constexpr float INV_SCALE = 9.313225746154785e-10f;  // 2^-30
     __device__ static __forceinline__ fix to_fix(float v) { return __float2int_rn(v * SCALE); }
     __device__ static __forceinline__ float from_fix(fix v) { return (float)v * INV_SCALE; }
     __device__ static __forceinline__ node4 pack(float rho, fix jx, fix jy, fix jz) {
-        return make_int4(__float_as_int(rho), jx, jy, jz);
+        const long long S = (long long)jy * 4294967296LL + (long long)jx;
+        return make_int4(__float_as_int(rho), jz, (int)(unsigned)(unsigned long long)S, (int)(S >> 32));
     }
     __device__ static __forceinline__ float rho_of(const node4 &n) { return __int_as_float(n.x); }
+    __device__ static __forceinline__ fix jx_of(const node4 &n) { return n.z; }
+    __device__ static __forceinline__ fix jy_of(const node4 &n) { return n.w + (n.z < 0 ? 1 : 0); }
+    __device__ static __forceinline__ fix jz_of(const node4 &n) { return n.y; }
+    __device__ static __forceinline__ void add_transfer(node4 *rec, fix dx, fix dy, fix dz) {
+        const long long S = (long long)dy * 4294967296LL + (long long)dx;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->z), (unsigned long long)S);
+        atomicAdd(&rec->y, dz);
+    }
     __device__ static __forceinline__ real4 make4(float a, float b, float c, float d) {
         return make_float4(a, b, c, d);
     }
@@ -151,15 +167,16 @@ struct Prec<float> {
     __device__ static __forceinline__ real4 make_pos(float fx, float fy, float fz, int64_t cell) {
         return make_float4(fx, fy, fz, __int_as_float((int)(uint32_t)cell));
     }
-    __device__ static __forceinline__ void add_fix(fix *a, fix v) { atomicAdd(a, v); }
 };
 
+// FP64 node record (32 bytes): rho as double bits, then j_x, j_y, j_z as
+// signed 64-bit integers in units of 2^-56; a transfer is three atomics.
 template <>
 struct Prec<double> {
     using real = double;
     using real4 = D4;
     using fix = long long;
-    using node4 = L4;  // {rho as double bits, j_x, j_y, j_z fixed point}
+    using node4 = L4;
     static constexpr double SCALE = 72057594037927936.0;          // 2^56
     static constexpr double INV_SCALE = 1.3877787807814457e-17;  // 2^-56
     __device__ static __forceinline__ fix to_fix(double v) { return __double2ll_rn(v * SCALE); }
@@ -168,13 +185,18 @@ struct Prec<double> {
         return L4{__double_as_longlong(rho), jx, jy, jz};
     }
     __device__ static __forceinline__ double rho_of(const node4 &n) { return __longlong_as_double(n.x); }
+    __device__ static __forceinline__ fix jx_of(const node4 &n) { return n.y; }
+    __device__ static __forceinline__ fix jy_of(const node4 &n) { return n.z; }
+    __device__ static __forceinline__ fix jz_of(const node4 &n) { return n.w; }
+    __device__ static __forceinline__ void add_transfer(node4 *rec, fix dx, fix dy, fix dz) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->y), (unsigned long long)dx);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->z), (unsigned long long)dy);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&rec->w), (unsigned long long)dz);
+    }
     __device__ static __forceinline__ real4 make4(double a, double b, double c, double d) { return D4{a, b, c, d}; }
     __device__ static __forceinline__ int64_t cell_of(const real4 &p) { return (int64_t)p.w; }
     __device__ static __forceinline__ real4 make_pos(double fx, double fy, double fz, int64_t cell) {
         return D4{fx, fy, fz, (double)cell};
-    }
-    __device__ static __forceinline__ void add_fix(fix *a, fix v) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
     }
 };
 

@@ -43,27 +43,30 @@ __global__ void __launch_bounds__(RED_THREADS)
     for (int64_t r = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; r < N; r += stride) {
         const typename P::node4 n = node[r];
         v[0] += (double)P::rho_of(n);
-        v[1] += (double)n.y;
-        v[2] += (double)n.z;
-        v[3] += (double)n.w;
+        v[1] += (double)P::jx_of(n);
+        v[2] += (double)P::jy_of(n);
+        v[3] += (double)P::jz_of(n);
         if (VARIANT == LBMD_VARIANT_A) {
             const typename P::node4 J = jacc[r];
-            v[1] += (double)J.y;
-            v[2] += (double)J.z;
-            v[3] += (double)J.w;
+            v[1] += (double)P::jx_of(J);
+            v[2] += (double)P::jy_of(J);
+            v[3] += (double)P::jz_of(J);
         }
     }
     // momenta stay in fixed-point units until the final scaling
     block_reduce_store<4>(v, partial + (int64_t)blockIdx.x * RED_COLS);
 }
 
+// particles are visited in id order (not slot order), so the sums do not
+// depend on how the particles are currently arranged
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
-    observe_particles_kernel(const typename Prec<T>::real4 *vel4, int64_t np, double *partial) {
+    observe_particles_kernel(const typename Prec<T>::real4 *vel4, const int32_t *slot_of, int64_t np,
+                             double *partial) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-    for (int64_t p = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; p < np; p += stride) {
-        const typename Prec<T>::real4 V = vel4[p];
+    for (int64_t id = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; id < np; id += stride) {
+        const typename Prec<T>::real4 V = vel4[slot_of[id]];
         const double m = 1.0 / (double)V.w;
         const double vx = V.x, vy = V.y, vz = V.z;
         v[0] += m * vx;
@@ -99,7 +102,7 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     observe_particles_kernel<T><<<B, RED_THREADS, 0, ctx->stream>>>(
-        static_cast<const typename P::real4 *>(ctx->vel4), ctx->np, ctx->red_partial);
+        static_cast<const typename P::real4 *>(ctx->vel4[ctx->pcur]), ctx->slot_of, ctx->np, ctx->red_partial);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     observe_final_kernel<T><<<1, 32, 0, ctx->stream>>>(ctx->red_partial, B, ctx->red_out);
@@ -134,25 +137,25 @@ __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const
     const typename P::node4 n = node[r];
     if (!transfer_only) {
         dst[4 * t + 0] = (double)P::rho_of(n);
-        dst[4 * t + 1] = (double)P::from_fix(n.y);
-        dst[4 * t + 2] = (double)P::from_fix(n.z);
-        dst[4 * t + 3] = (double)P::from_fix(n.w);
+        dst[4 * t + 1] = (double)P::from_fix(P::jx_of(n));
+        dst[4 * t + 2] = (double)P::from_fix(P::jy_of(n));
+        dst[4 * t + 3] = (double)P::from_fix(P::jz_of(n));
         return;
     }
     if (variant == LBMD_VARIANT_A) {
         const typename P::node4 J = jacc[r];
-        dst[3 * t + 0] = (double)P::from_fix(J.y);
-        dst[3 * t + 1] = (double)P::from_fix(J.z);
-        dst[3 * t + 2] = (double)P::from_fix(J.w);
+        dst[3 * t + 0] = (double)P::from_fix(P::jx_of(J));
+        dst[3 * t + 1] = (double)P::from_fix(P::jy_of(J));
+        dst[3 * t + 2] = (double)P::from_fix(P::jz_of(J));
     } else {
         T fl[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) fl[i] = f[(int64_t)i * N + r];
         T rho, jx, jy, jz;
         node_moments(fl, rho, jx, jy, jz);
-        dst[3 * t + 0] = (double)P::from_fix(n.y - P::to_fix(jx));
-        dst[3 * t + 1] = (double)P::from_fix(n.z - P::to_fix(jy));
-        dst[3 * t + 2] = (double)P::from_fix(n.w - P::to_fix(jz));
+        dst[3 * t + 0] = (double)P::from_fix(P::jx_of(n) - P::to_fix(jx));
+        dst[3 * t + 1] = (double)P::from_fix(P::jy_of(n) - P::to_fix(jy));
+        dst[3 * t + 2] = (double)P::from_fix(P::jz_of(n) - P::to_fix(jz));
     }
 }
 
@@ -165,22 +168,31 @@ __global__ void clear_transfer_kernel(typename Prec<T>::node4 *jacc, int64_t N) 
     jacc[r] = z;
 }
 
-// host FP64 particle arrays -> cell index + fractional offset, velocity, 1/m
+// host FP64 particle arrays -> cell index + fractional offset, velocity, 1/m,
+// for slots [first, first + count).  assign_ids: new particles, slot = id,
+// source row t; otherwise the source row is the slot's particle id.
 template <typename T>
 __global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, typename Prec<T>::real4 *vel4,
-                                             int64_t first, int64_t count, const double *pos, const double *vel,
-                                             const double *mass, int set_pos, int set_vel, int set_mass, int nx,
-                                             int ny, int nz) {
+                                             int32_t *pid, int32_t *slot_of, int64_t first, int64_t count,
+                                             const double *pos, const double *vel, const double *mass, int set_pos,
+                                             int set_vel, int set_mass, int assign_ids, int nx, int ny, int nz) {
     using P = Prec<T>;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     const int64_t p = first + t;
+    int64_t src = t;
+    if (assign_ids) {
+        pid[p] = (int32_t)p;
+        slot_of[p] = (int32_t)p;
+    } else {
+        src = pid[p];
+    }
     if (set_pos) {
         const double L[3] = {(double)nx, (double)ny, (double)nz};
         T fr[3];
         int64_t cl[3];
         for (int d = 0; d < 3; ++d) {
-            double x = pos[3 * t + d];
+            double x = pos[3 * src + d];
             x -= L[d] * floor(x / L[d]);
             if (x >= L[d]) x -= L[d];
             double b = floor(x);
@@ -197,34 +209,36 @@ __global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, type
     }
     typename P::real4 V = vel4[p];
     if (set_vel) {
-        V.x = (T)vel[3 * t + 0];
-        V.y = (T)vel[3 * t + 1];
-        V.z = (T)vel[3 * t + 2];
+        V.x = (T)vel[3 * src + 0];
+        V.y = (T)vel[3 * src + 1];
+        V.z = (T)vel[3 * src + 2];
     }
-    if (set_mass) V.w = (T)(1.0 / (mass ? mass[t] : 1.0));
+    if (set_mass) V.w = (T)(1.0 / (mass ? mass[src] : 1.0));
     vel4[p] = V;
 }
 
+// device state -> FP64 arrays in id order
 template <typename T>
 __global__ void particles_to_double_kernel(const typename Prec<T>::real4 *pos4, const typename Prec<T>::real4 *vel4,
-                                           int64_t np, double *pos, double *vel, int nx, int ny) {
+                                           const int32_t *pid, int64_t np, double *pos, double *vel, int nx, int ny) {
     using P = Prec<T>;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
+    const int64_t id = pid[p];
     if (pos) {
         const typename P::real4 R = pos4[p];
         const int64_t cell = P::cell_of(R);
         const int64_t nxy = (int64_t)nx * ny;
         const int64_t z = cell / nxy, rem = cell - z * nxy, y = rem / nx, x = rem - y * nx;
-        pos[3 * p + 0] = (double)x + (double)R.x;
-        pos[3 * p + 1] = (double)y + (double)R.y;
-        pos[3 * p + 2] = (double)z + (double)R.z;
+        pos[3 * id + 0] = (double)x + (double)R.x;
+        pos[3 * id + 1] = (double)y + (double)R.y;
+        pos[3 * id + 2] = (double)z + (double)R.z;
     }
     if (vel) {
         const typename P::real4 V = vel4[p];
-        vel[3 * p + 0] = (double)V.x;
-        vel[3 * p + 1] = (double)V.y;
-        vel[3 * p + 2] = (double)V.z;
+        vel[3 * id + 0] = (double)V.x;
+        vel[3 * id + 1] = (double)V.y;
+        vel[3 * id + 2] = (double)V.z;
     }
 }
 
@@ -291,26 +305,32 @@ cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t c
                                          const double *vel, const double *mass, bool set_pos, bool set_vel,
                                          bool set_mass) {
     if (count <= 0) return cudaSuccess;
+    const int b = ctx->pcur;
+    const int assign = set_mass ? 1 : 0;  // only lbmd_add_particles sets masses
     if (ctx->p.precision == LBMD_FP64)
         particles_from_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<Prec<double>::real4 *>(ctx->pos4), static_cast<Prec<double>::real4 *>(ctx->vel4), first, count,
-            pos, vel, mass, set_pos, set_vel, set_mass, ctx->p.nx, ctx->p.ny, ctx->p.nz);
+            static_cast<Prec<double>::real4 *>(ctx->pos4[b]), static_cast<Prec<double>::real4 *>(ctx->vel4[b]),
+            ctx->pid[b], ctx->slot_of, first, count, pos, vel, mass, set_pos, set_vel, set_mass, assign, ctx->p.nx,
+            ctx->p.ny, ctx->p.nz);
     else
         particles_from_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<Prec<float>::real4 *>(ctx->pos4), static_cast<Prec<float>::real4 *>(ctx->vel4), first, count,
-            pos, vel, mass, set_pos, set_vel, set_mass, ctx->p.nx, ctx->p.ny, ctx->p.nz);
+            static_cast<Prec<float>::real4 *>(ctx->pos4[b]), static_cast<Prec<float>::real4 *>(ctx->vel4[b]),
+            ctx->pid[b], ctx->slot_of, first, count, pos, vel, mass, set_pos, set_vel, set_mass, assign, ctx->p.nx,
+            ctx->p.ny, ctx->p.nz);
     return cudaGetLastError();
 }
 
 cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel) {
     if (ctx->np <= 0) return cudaSuccess;
+    const int b = ctx->pcur;
     if (ctx->p.precision == LBMD_FP64)
         particles_to_double_kernel<double><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
-            static_cast<const Prec<double>::real4 *>(ctx->pos4), static_cast<const Prec<double>::real4 *>(ctx->vel4),
-            ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
+            static_cast<const Prec<double>::real4 *>(ctx->pos4[b]),
+            static_cast<const Prec<double>::real4 *>(ctx->vel4[b]), ctx->pid[b], ctx->np, pos, vel, ctx->p.nx,
+            ctx->p.ny);
     else
         particles_to_double_kernel<float><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
-            static_cast<const Prec<float>::real4 *>(ctx->pos4), static_cast<const Prec<float>::real4 *>(ctx->vel4),
-            ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
+            static_cast<const Prec<float>::real4 *>(ctx->pos4[b]), static_cast<const Prec<float>::real4 *>(ctx->vel4[b]),
+            ctx->pid[b], ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
     return cudaGetLastError();
 }

@@ -1,9 +1,9 @@
 // particles.cu -- the dissipative particle-fluid coupling of Sec. 3 on the GPU.
 //
-// couple_kernel (one thread per particle), one MD step of length dt:
+// couple_kernel (one thread per particle slot), one MD step of length dt:
 //   * node velocities at the 8 corners of the particle's cell, trilinear
 //     weights delta_k from the fractional position (Eq. (5));
-//   * random force from Philox(p, md_step, 1, 0), friction against the
+//   * random force from Philox(id, md_step, 1, 0), friction against the
 //     interpolated fluid velocity (Eq. (4)); Delta P = dt F (Eq. (6));
 //   * velocity Verlet with F held fixed (second half-kick here for ideal
 //     particles, in bond_kick_kernel when bonds exist);
@@ -17,6 +17,10 @@
 // Particle positions are stored as cell index + fractional offset in [0,1):
 // the offset is exactly the interpolation coordinate, and its precision does
 // not degrade with the box size.
+//
+// sort_*: once per LB step the particles are re-ordered by the lattice row
+// (y, z) of their cell (counting sort: count, scan, scatter), so that a warp
+// handles particles whose corner nodes lie in a few neighbouring rows.
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
 
@@ -26,6 +30,7 @@ template <typename T>
 struct PArgs {
     using P = Prec<T>;
     typename P::real4 *pos4, *vel4, *fc4, *old4, *fcons4;
+    const int32_t *pid, *slot_of;
     typename P::node4 *node, *jacc;
     const int32_t *bond_count, *bond_partner;
     const double *bond_k, *bond_r0;
@@ -35,6 +40,7 @@ struct PArgs {
     uint32_t key0, key1;
     const unsigned long long *lb_step;
     int n_sub, substep, noisy;
+    int variant;
 };
 
 struct CellXYZ {
@@ -42,18 +48,18 @@ struct CellXYZ {
 };
 
 __device__ __forceinline__ CellXYZ cell_xyz(int64_t cell, int nx, int ny) {
-    const int64_t nxy = (int64_t)nx * ny;
-    CellXYZ c;
-    c.z = (int)(cell / nxy);
-    const int64_t rem = cell - (int64_t)c.z * nxy;
-    c.y = (int)(rem / nx);
-    c.x = (int)(rem - (int64_t)c.y * nx);
-    return c;
+    const uint32_t c = (uint32_t)cell;
+    const uint32_t row = c / (uint32_t)nx;
+    CellXYZ r;
+    r.x = (int)(c - row * (uint32_t)nx);
+    r.z = (int)(row / (uint32_t)ny);
+    r.y = (int)(row - (uint32_t)r.z * (uint32_t)ny);
+    return r;
 }
 
 // The 8 corner nodes (k = ox + 2 oy + 4 oz) and trilinear weights of Eq. (5).
 template <typename T>
-__device__ __forceinline__ void corners(const CellXYZ &c, T fx, T fy, T fz, int nx, int ny, int nz, int64_t idx[8],
+__device__ __forceinline__ void corners(const CellXYZ &c, T fx, T fy, T fz, int nx, int ny, int nz, uint32_t idx[8],
                                         T delta[8]) {
     const int x1 = c.x + 1 == nx ? 0 : c.x + 1;
     const int y1 = c.y + 1 == ny ? 0 : c.y + 1;
@@ -63,7 +69,7 @@ __device__ __forceinline__ void corners(const CellXYZ &c, T fx, T fy, T fz, int 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
-        idx[k] = X[ox] + (int64_t)nx * (Y[oy] + (int64_t)ny * Z[oz]);
+        idx[k] = (uint32_t)X[ox] + (uint32_t)nx * ((uint32_t)Y[oy] + (uint32_t)ny * (uint32_t)Z[oz]);
         delta[k] = wx[ox] * wy[oy] * wz[oz];
     }
 }
@@ -85,7 +91,19 @@ __device__ __forceinline__ void advance(T &frac, int &c, T d, int n) {
     c = cn;
 }
 
-template <typename T, int VARIANT, bool BONDS>
+template <typename T>
+__device__ __forceinline__ void spread_to(typename Prec<T>::node4 *field, const uint32_t idx[8], const T delta[8], T dPx,
+                                          T dPy, T dPz) {
+    using P = Prec<T>;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        P::add_transfer(&field[idx[k]], P::to_fix(-delta[k] * dPx), P::to_fix(-delta[k] * dPy),
+                        P::to_fix(-delta[k] * dPz));
+}
+
+// The variant is a run-time flag (one instruction sequence for both
+// variants, as in the LB kernel).
+template <typename T, bool BONDS>
 __global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
     using P = Prec<T>;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,7 +111,7 @@ __global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
     const typename P::real4 R = a.pos4[p];
     typename P::real4 V = a.vel4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
-    int64_t idx[8];
+    uint32_t idx[8];
     T delta[8];
     corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
 
@@ -103,15 +121,15 @@ __global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
     for (int k = 0; k < 8; ++k) {
         const typename P::node4 n = a.node[idx[k]];
         const T w = delta[k] / P::rho_of(n);
-        ux += w * P::from_fix(n.y);
-        uy += w * P::from_fix(n.z);
-        uz += w * P::from_fix(n.w);
+        ux += w * P::from_fix(P::jx_of(n));
+        uy += w * P::from_fix(P::jy_of(n));
+        uz += w * P::from_fix(P::jz_of(n));
     }
     // coupling force, Eq. (4) without the conservative part
     T Fx = -a.zeta * (V.x - ux), Fy = -a.zeta * (V.y - uy), Fz = -a.zeta * (V.z - uz);
     if (a.noisy) {
         const uint32_t md_step = (uint32_t)((*a.lb_step) * (unsigned long long)a.n_sub + (unsigned)a.substep);
-        const U4 r = philox4x32_10(U4{(uint32_t)p, md_step, 1u, 0u}, a.key0, a.key1);
+        const U4 r = philox4x32_10(U4{(uint32_t)a.pid[p], md_step, 1u, 0u}, a.key0, a.key1);
         Fx += a.amp * unit_uniform<T>(r.x);
         Fy += a.amp * unit_uniform<T>(r.y);
         Fz += a.amp * unit_uniform<T>(r.z);
@@ -140,18 +158,11 @@ __global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
     }
     a.pos4[p] = P::make_pos(fx, fy, fz, cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz));
     a.vel4[p] = V;
-    a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
+    if (BONDS || a.variant == LBMD_VARIANT_B) a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
 
-    if (VARIANT == LBMD_VARIANT_A) {
+    if (a.variant == LBMD_VARIANT_A) {
         // Newton's third law, Eqs. (7), (8): straight into J_acc
-        const T dPx = a.dt * Fx, dPy = a.dt * Fy, dPz = a.dt * Fz;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            typename P::fix *j = reinterpret_cast<typename P::fix *>(&a.jacc[idx[k]]);
-            P::add_fix(j + 1, P::to_fix(-delta[k] * dPx));
-            P::add_fix(j + 2, P::to_fix(-delta[k] * dPy));
-            P::add_fix(j + 3, P::to_fix(-delta[k] * dPz));
-        }
+        spread_to<T>(a.jacc, idx, delta, a.dt * Fx, a.dt * Fy, a.dt * Fz);
     } else {
         a.old4[p] = R;
     }
@@ -168,17 +179,10 @@ __global__ void __launch_bounds__(256) spread_kernel(PArgs<T> a) {
     const typename P::real4 R = a.old4[p];
     const typename P::real4 F = a.fc4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
-    int64_t idx[8];
+    uint32_t idx[8];
     T delta[8];
     corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
-    const T dPx = a.dt * F.x, dPy = a.dt * F.y, dPz = a.dt * F.z;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        typename P::fix *j = reinterpret_cast<typename P::fix *>(&a.node[idx[k]]);
-        P::add_fix(j + 1, P::to_fix(-delta[k] * dPx));
-        P::add_fix(j + 2, P::to_fix(-delta[k] * dPy));
-        P::add_fix(j + 3, P::to_fix(-delta[k] * dPz));
-    }
+    spread_to<T>(a.node, idx, delta, a.dt * F.x, a.dt * F.y, a.dt * F.z);
 }
 
 // Harmonic bond forces at the current positions (minimum image), summed per
@@ -191,10 +195,11 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
     if (p >= a.np) return;
     const typename P::real4 R = a.pos4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
+    const int64_t id = a.pid[p];
     T Fx = T(0), Fy = T(0), Fz = T(0);
-    const int nbond = a.bond_count[p];
+    const int nbond = a.bond_count[id];
     for (int b = 0; b < nbond; ++b) {
-        const int64_t q = a.bond_partner[p * LBMD_MAX_BONDS_PER_PARTICLE + b];
+        const int64_t q = a.slot_of[a.bond_partner[id * LBMD_MAX_BONDS_PER_PARTICLE + b]];
         const typename P::real4 S = a.pos4[q];
         const CellXYZ d = cell_xyz(P::cell_of(S), a.nx, a.ny);
         T dx = T(d.x - c.x) + (S.x - R.x);
@@ -205,8 +210,8 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
         dz -= T(a.nz) * rint(dz / T(a.nz));
         const T r = sqrt(dx * dx + dy * dy + dz * dz);
         if (r > T(0)) {
-            const T k = (T)a.bond_k[p * LBMD_MAX_BONDS_PER_PARTICLE + b];
-            const T r0 = (T)a.bond_r0[p * LBMD_MAX_BONDS_PER_PARTICLE + b];
+            const T k = (T)a.bond_k[id * LBMD_MAX_BONDS_PER_PARTICLE + b];
+            const T r0 = (T)a.bond_r0[id * LBMD_MAX_BONDS_PER_PARTICLE + b];
             const T mag = k * (r - r0) / r;
             Fx += mag * dx;
             Fy += mag * dy;
@@ -225,15 +230,74 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Re-ordering by lattice row.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+    sort_count_kernel(const typename Prec<T>::real4 *pos4, int64_t np, int nx, int32_t *row_count, int32_t *rank) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const uint32_t row = (uint32_t)Prec<T>::cell_of(pos4[p]) / (uint32_t)nx;
+    rank[p] = atomicAdd(&row_count[row], 1);
+}
+
+// exclusive prefix sum of row_count[0..n) in place, one block of 1024 threads
+__global__ void __launch_bounds__(1024) sort_scan_kernel(int32_t *row_count, int64_t n) {
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t lo = t * per, hi = lo + per < n ? lo + per : n;
+    int32_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += row_count[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int32_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t run = part[t] - s;  // exclusive prefix of this thread's chunk
+    for (int64_t i = lo; i < hi; ++i) {
+        const int32_t c = row_count[i];
+        row_count[i] = run;
+        run += c;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    sort_scatter_kernel(const typename Prec<T>::real4 *pos_in, const typename Prec<T>::real4 *vel_in,
+                        const typename Prec<T>::real4 *fcons_in, const int32_t *pid_in, typename Prec<T>::real4 *pos_out,
+                        typename Prec<T>::real4 *vel_out, typename Prec<T>::real4 *fcons_out, int32_t *pid_out,
+                        int32_t *slot_of, const int32_t *row_offset, const int32_t *rank, int64_t np, int nx,
+                        int bonds) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const typename Prec<T>::real4 R = pos_in[p];
+    const uint32_t row = (uint32_t)Prec<T>::cell_of(R) / (uint32_t)nx;
+    const int32_t dst = row_offset[row] + rank[p];
+    pos_out[dst] = R;
+    vel_out[dst] = vel_in[p];
+    if (bonds) fcons_out[dst] = fcons_in[p];
+    const int32_t id = pid_in[p];
+    pid_out[dst] = id;
+    slot_of[id] = dst;
+}
+
 template <typename T>
 static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     using P = Prec<T>;
+    const int b = ctx->pcur;
     PArgs<T> a;
-    a.pos4 = static_cast<typename P::real4 *>(ctx->pos4);
-    a.vel4 = static_cast<typename P::real4 *>(ctx->vel4);
+    a.pos4 = static_cast<typename P::real4 *>(ctx->pos4[b]);
+    a.vel4 = static_cast<typename P::real4 *>(ctx->vel4[b]);
+    a.fcons4 = static_cast<typename P::real4 *>(ctx->fcons4[b]);
+    a.pid = ctx->pid[b];
+    a.slot_of = ctx->slot_of;
     a.fc4 = static_cast<typename P::real4 *>(ctx->fc4);
     a.old4 = static_cast<typename P::real4 *>(ctx->old4);
-    a.fcons4 = static_cast<typename P::real4 *>(ctx->fcons4);
     a.node = static_cast<typename P::node4 *>(ctx->node);
     a.jacc = static_cast<typename P::node4 *>(ctx->jacc);
     a.bond_count = ctx->bond_count;
@@ -254,6 +318,7 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.n_sub = ctx->p.n_sub;
     a.substep = substep;
     a.noisy = ctx->p.kT > 0.0 ? 1 : 0;
+    a.variant = ctx->p.variant;
     return a;
 }
 
@@ -264,17 +329,10 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
     const bool bonds = ctx->nb > 0;
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
-    if (B) {
-        if (bonds)
-            couple_kernel<T, LBMD_VARIANT_B, true><<<blocks, 256, 0, ctx->stream>>>(a);
-        else
-            couple_kernel<T, LBMD_VARIANT_B, false><<<blocks, 256, 0, ctx->stream>>>(a);
-    } else {
-        if (bonds)
-            couple_kernel<T, LBMD_VARIANT_A, true><<<blocks, 256, 0, ctx->stream>>>(a);
-        else
-            couple_kernel<T, LBMD_VARIANT_A, false><<<blocks, 256, 0, ctx->stream>>>(a);
-    }
+    if (bonds)
+        couple_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
+    else
+        couple_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (bonds) {
@@ -298,6 +356,31 @@ static cudaError_t bond_forces_t(lbmd_ctx *ctx) {
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t sort_t(lbmd_ctx *ctx) {
+    using R4 = typename Prec<T>::real4;
+    const int b = ctx->pcur, o = b ^ 1;
+    const int64_t rows = (int64_t)ctx->p.ny * ctx->p.nz;
+    cudaError_t e = cudaMemsetAsync(ctx->row_count, 0, (size_t)rows * sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) return e;
+    if (ctx->np > 0) {
+        const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
+        sort_count_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<const R4 *>(ctx->pos4[b]), ctx->np,
+                                                                ctx->p.nx, ctx->row_count, ctx->sort_rank);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sort_scan_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->row_count, rows);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sort_scatter_kernel<T><<<blocks, 256, 0, ctx->stream>>>(
+            static_cast<const R4 *>(ctx->pos4[b]), static_cast<const R4 *>(ctx->vel4[b]),
+            static_cast<const R4 *>(ctx->fcons4[b]), ctx->pid[b], static_cast<R4 *>(ctx->pos4[o]),
+            static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]), ctx->pid[o], ctx->slot_of,
+            ctx->row_count, ctx->sort_rank, ctx->np, ctx->p.nx, ctx->nb > 0 ? 1 : 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    ctx->pcur = o;
+    return cudaSuccess;
+}
+
 }  // namespace lbmd
 
 cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep) {
@@ -307,4 +390,8 @@ cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep) {
 
 cudaError_t launch_bond_forces_only(lbmd_ctx *ctx) {
     return ctx->p.precision == LBMD_FP64 ? lbmd::bond_forces_t<double>(ctx) : lbmd::bond_forces_t<float>(ctx);
+}
+
+cudaError_t launch_sort_particles(lbmd_ctx *ctx) {
+    return ctx->p.precision == LBMD_FP64 ? lbmd::sort_t<double>(ctx) : lbmd::sort_t<float>(ctx);
 }
