@@ -139,9 +139,18 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 }
 
 /* 32 random bits -> zero-mean, unit-variance uniform number:
- * u = (x + 1/2) 2^-32 in (0,1), xi = sqrt(12) (u - 1/2). */
+ * u = (x + 1/2) 2^-32 in (0,1), xi = sqrt(12) (u - 1/2).  Used for the
+ * random force on the particles. */
 double orc_uniform_unit(uint32_t x) {
     double u = ((double)x + 0.5) * (1.0 / 4294967296.0);
+    return sqrt(12.0) * (u - 0.5);
+}
+
+/* 16 random bits -> zero-mean, unit-variance uniform number on 65536 levels:
+ * u = (h + 1/2) 2^-16, xi = sqrt(12) (u - 1/2).  The fluid noise takes two
+ * such variates from each 32-bit Philox word (low half first). */
+double orc_uniform_unit16(uint32_t h) {
+    double u = ((double)(h & 0xffffu) + 0.5) * (1.0 / 65536.0);
     return sqrt(12.0) * (u - 0.5);
 }
 
@@ -296,10 +305,13 @@ void orc_collide_node(const orc_state *s, const double f[Q], const double F[3],
         uint32_t key[2], ctr[4], out[4];
         double xi[16];
         key_of(s, key);
-        for (uint32_t q = 0; q < 4; ++q) {
+        for (uint32_t q = 0; q < 2; ++q) {
             ctr[0] = node; ctr[1] = lb_step; ctr[2] = 0u; ctr[3] = q;
             orc_philox4x32_10(ctr, key, out);
-            for (int t = 0; t < 4; ++t) xi[4 * q + t] = orc_uniform_unit(out[t]);
+            for (int t = 0; t < 4; ++t) {
+                xi[8 * q + 2 * t] = orc_uniform_unit16(out[t] & 0xffffu);
+                xi[8 * q + 2 * t + 1] = orc_uniform_unit16(out[t] >> 16);
+            }
         }
         double mu = 3.0 * s->p.kT;
         for (int k = 4; k < Q; ++k)

@@ -57,6 +57,7 @@ int64_t orc_num_particles(const orc_state *s);
 /* Building blocks, exposed so the tests can pin each one on its own. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform_unit(uint32_t x);
+double orc_uniform_unit16(uint32_t h);
 void orc_d3q19(int32_t c_out[19 * 3], double w_out[19]);
 void orc_modes(double e_out[19 * 19], double b_out[19]);
 void orc_collide_node(const orc_state *s, const double f[19], const double F[3], uint32_t node, uint32_t lb_step,

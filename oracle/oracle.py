@@ -81,6 +81,8 @@ def lib():
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_uniform_unit.restype = ct.c_double
         L.orc_uniform_unit.argtypes = [ct.c_uint32]
+        L.orc_uniform_unit16.restype = ct.c_double
+        L.orc_uniform_unit16.argtypes = [ct.c_uint32]
         L.orc_d3q19.argtypes = [ct.POINTER(ct.c_int32), dp]
         L.orc_modes.argtypes = [dp, dp]
         L.orc_collide_node.argtypes = [P, dp, dp, ct.c_uint32, ct.c_uint32, dp]
@@ -106,6 +108,10 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def uniform_unit(x: int) -> float:
     return lib().orc_uniform_unit(int(x) & 0xFFFFFFFF)
+
+
+def uniform_unit16(h: int) -> float:
+    return lib().orc_uniform_unit16(int(h) & 0xFFFFFFFF)
 
 
 def d3q19():

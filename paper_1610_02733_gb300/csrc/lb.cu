@@ -108,15 +108,18 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
     mp[9] += fs * T(0.5) * (uy * Fz + uz * Fy);
 
     if (a.noisy) {
+        // 15 variates from two Philox calls: two 16-bit halves per 32-bit
+        // word, low half first, in mode order k = 4..18
         const T sr = sqrt(rho);
 #pragma unroll
-        for (uint32_t q = 0; q < 4; ++q) {
+        for (uint32_t q = 0; q < 2; ++q) {
             const U4 r = philox4x32_10(U4{node, step, 0u, q}, a.key0, a.key1);
             const uint32_t bits[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int k = 4 + 4 * (int)q + t;
-                if (k < Q) mp[k] += a.amp[k] * sr * unit_uniform<T>(bits[t]);
+            for (int t = 0; t < 8; ++t) {
+                const int k = 4 + 8 * (int)q + t;
+                const uint32_t h = (t & 1) ? (bits[t >> 1] >> 16) : (bits[t >> 1] & 0xffffu);
+                if (k < Q) mp[k] += a.amp[k] * sr * unit_uniform16<T>(h);
             }
         }
     }
@@ -205,7 +208,10 @@ __global__ void __launch_bounds__(256)
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (count_step && x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *lb_step += 1ull;
     if (x >= nx) return;
-    const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)blockIdx.y + (uint32_t)ny * (uint32_t)blockIdx.z);
+    // planes in reverse order: the LB kernel wrote the high planes last, so
+    // they are the ones still in L2
+    const uint32_t z = gridDim.z - 1 - blockIdx.z;
+    const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)blockIdx.y + (uint32_t)ny * z);
     T fl[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) fl[i] = f[(size_t)i * N + r];

@@ -38,7 +38,7 @@ size_t real_size(const lbmd_ctx *ctx) { return ctx->p.precision == LBMD_FP64 ? 8
 void free_all(lbmd_ctx *ctx) {
     void *bufs[] = {ctx->f[0],      ctx->f[1],       ctx->node,        ctx->jacc,      ctx->pos4[0],
                     ctx->pos4[1],   ctx->vel4[0],    ctx->vel4[1],     ctx->fcons4[0], ctx->fcons4[1],
-                    ctx->pid[0],    ctx->pid[1],     ctx->slot_of,     ctx->row_count, ctx->sort_rank,
+                    ctx->pid[0],    ctx->pid[1],     ctx->slot_of,     ctx->row_count, ctx->sort_rank, ctx->chunk_total,
                     ctx->fc4,       ctx->old4,       ctx->bond_count,  ctx->bond_partner, ctx->bond_k,
                     ctx->bond_r0,   ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step};
     for (void *b : bufs)
@@ -89,6 +89,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (!(std::fabs(p->gamma_ghost) < 1.0)) return fail(nullptr, LBMD_ERR_ARG, "|gamma_ghost| must be < 1");
     if (p->max_particles < 0 || p->max_bonds < 0 || p->max_particles > 0x7fffffffLL)
         return fail(nullptr, LBMD_ERR_ARG, "bad capacities");
+    if ((int64_t)p->ny * p->nz > (int64_t)1024 * 1024)
+        return fail(nullptr, LBMD_ERR_ARG, "ny * nz must not exceed 2^20 (particle re-ordering by row)");
     for (int d = 0; d < 3; ++d)
         if (!is_finite_d(p->body_force[d])) return fail(nullptr, LBMD_ERR_ARG, "non-finite body force");
 
@@ -156,6 +158,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->slot_of, (size_t)maxp * sizeof(int32_t)},
         {(void **)&ctx->row_count, (size_t)p->ny * p->nz * sizeof(int32_t)},
         {(void **)&ctx->sort_rank, (size_t)maxp * sizeof(int32_t)},
+        {(void **)&ctx->chunk_total, (size_t)1024 * sizeof(int32_t)},
         {&ctx->fc4, (size_t)maxp * 4 * rs},
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
         {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},

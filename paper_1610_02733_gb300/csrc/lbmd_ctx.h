@@ -54,7 +54,7 @@ struct lbmd_ctx {
     int32_t *pid[2];
     int32_t *slot_of;
     void *fc4, *old4;
-    int32_t *row_count, *sort_rank;
+    int32_t *row_count, *sort_rank, *chunk_total;
     int32_t *bond_count, *bond_partner;
     double *bond_k, *bond_r0;
     double *staging;   // device staging buffer for host <-> device conversions

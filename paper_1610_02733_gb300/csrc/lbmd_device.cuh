@@ -105,6 +105,14 @@ __device__ __forceinline__ float unit_uniform_f(uint32_t x) {
     const float centred = (float)(int32_t)(x ^ 0x80000000u) + 0.5f;
     return centred * (3.4641016151377544f * 2.3283064365386963e-10f);
 }
+// 16 random bits -> sqrt(12) ((h + 1/2) 2^-16 - 1/2) on 65536 levels; every
+// step but the final scaling is exact in FP32 and FP64.
+template <typename T>
+__device__ __forceinline__ T unit_uniform16(uint32_t h) {
+    const T u = ((T)(h & 0xffffu) + T(0.5)) * T(1.52587890625e-05);  // 2^-16
+    return T(3.4641016151377544) * (u - T(0.5));
+}
+
 template <typename T>
 __device__ __forceinline__ T unit_uniform(uint32_t x);
 template <>

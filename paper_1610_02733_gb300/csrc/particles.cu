@@ -174,8 +174,11 @@ __global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(256) spread_kernel(PArgs<T> a) {
     using P = Prec<T>;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.np) return;
+    // slots in reverse order: the couple kernel touched the last slots' nodes
+    // most recently, so they are the ones still in L2
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.np) return;
+    const int64_t p = a.np - 1 - t;
     const typename P::real4 R = a.old4[p];
     const typename P::real4 F = a.fc4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
@@ -242,42 +245,64 @@ __global__ void __launch_bounds__(256)
     rank[p] = atomicAdd(&row_count[row], 1);
 }
 
-// exclusive prefix sum of row_count[0..n) in place, one block of 1024 threads
-__global__ void __launch_bounds__(1024) sort_scan_kernel(int32_t *row_count, int64_t n) {
-    __shared__ int32_t part[1024];
-    const int t = threadIdx.x;
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t lo = t * per, hi = lo + per < n ? lo + per : n;
-    int32_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += row_count[i];
-    part[t] = s;
+// Block-wide exclusive scan of one value per thread (1024 threads).
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *total) {
+    __shared__ int32_t warp_sum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sum[w] = x;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int32_t v = t >= off ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    if (w == 0) {
+        int32_t s = warp_sum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        warp_sum[lane] = s;  // inclusive prefix of warp sums
     }
-    int32_t run = part[t] - s;  // exclusive prefix of this thread's chunk
-    for (int64_t i = lo; i < hi; ++i) {
-        const int32_t c = row_count[i];
-        row_count[i] = run;
-        run += c;
-    }
+    __syncthreads();
+    const int32_t before = w > 0 ? warp_sum[w - 1] : 0;
+    if (total) *total = warp_sum[31];
+    __syncthreads();
+    return before + x - v;
 }
 
+// Level 1: each block of 1024 threads turns 1024 row counts into exclusive
+// offsets within its chunk and records the chunk total.
+__global__ void __launch_bounds__(1024) sort_chunk_scan_kernel(int32_t *row_count, int64_t n, int32_t *chunk_total) {
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const int32_t v = i < n ? row_count[i] : 0;
+    int32_t tot;
+    const int32_t ex = block_exclusive_scan(v, &tot);
+    if (i < n) row_count[i] = ex;
+    if (threadIdx.x == 0) chunk_total[blockIdx.x] = tot;
+}
+
+// Level 2 fused into the scatter: every block scans the (at most 1024)
+// chunk totals in shared memory, then moves its particles to
+// chunk offset + offset within the chunk + rank within the row.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
     sort_scatter_kernel(const typename Prec<T>::real4 *pos_in, const typename Prec<T>::real4 *vel_in,
                         const typename Prec<T>::real4 *fcons_in, const int32_t *pid_in, typename Prec<T>::real4 *pos_out,
                         typename Prec<T>::real4 *vel_out, typename Prec<T>::real4 *fcons_out, int32_t *pid_out,
-                        int32_t *slot_of, const int32_t *row_offset, const int32_t *rank, int64_t np, int nx,
-                        int bonds) {
+                        int32_t *slot_of, const int32_t *row_offset, const int32_t *chunk_total, int n_chunks,
+                        const int32_t *rank, int64_t np, int nx, int bonds) {
+    __shared__ int32_t chunk_off[1024];
+    const int32_t v = (int)threadIdx.x < n_chunks ? chunk_total[threadIdx.x] : 0;
+    chunk_off[threadIdx.x] = block_exclusive_scan(v, nullptr);
+    __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const typename Prec<T>::real4 R = pos_in[p];
     const uint32_t row = (uint32_t)Prec<T>::cell_of(R) / (uint32_t)nx;
-    const int32_t dst = row_offset[row] + rank[p];
+    const int32_t dst = chunk_off[row >> 10] + row_offset[row] + rank[p];
     pos_out[dst] = R;
     vel_out[dst] = vel_in[p];
     if (bonds) fcons_out[dst] = fcons_in[p];
@@ -368,13 +393,15 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
         sort_count_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<const R4 *>(ctx->pos4[b]), ctx->np,
                                                                 ctx->p.nx, ctx->row_count, ctx->sort_rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        sort_scan_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->row_count, rows);
+        const int n_chunks = (int)((rows + 1023) / 1024);
+        sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        sort_scatter_kernel<T><<<blocks, 256, 0, ctx->stream>>>(
+        const unsigned sblocks = (unsigned)((ctx->np + 1023) / 1024);
+        sort_scatter_kernel<T><<<sblocks, 1024, 0, ctx->stream>>>(
             static_cast<const R4 *>(ctx->pos4[b]), static_cast<const R4 *>(ctx->vel4[b]),
             static_cast<const R4 *>(ctx->fcons4[b]), ctx->pid[b], static_cast<R4 *>(ctx->pos4[o]),
             static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]), ctx->pid[o], ctx->slot_of,
-            ctx->row_count, ctx->sort_rank, ctx->np, ctx->p.nx, ctx->nb > 0 ? 1 : 0);
+            ctx->row_count, ctx->chunk_total, n_chunks, ctx->sort_rank, ctx->np, ctx->p.nx, ctx->nb > 0 ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ctx->pcur = o;

@@ -79,6 +79,17 @@ def test_uniform_transform(orc):
     assert abs((vals ** 2).mean() - 1.0) < 2e-3
 
 
+def test_uniform16_transform(orc):
+    # 16-bit variates: the 65536 levels (h + 1/2) 2^-16 are symmetric about
+    # 1/2, so the mean over all levels is exactly 0 and the variance is
+    # 1 - 2^-32; only the low 16 bits are used.
+    vals = np.array([orc.uniform_unit16(h) for h in range(65536)])
+    assert abs(vals.mean()) < 1e-15
+    assert abs((vals ** 2).mean() - (1.0 - 2.0 ** -32)) < 1e-12
+    assert orc.uniform_unit16(0x12345) == orc.uniform_unit16(0x2345)
+    assert vals.min() > -np.sqrt(3.0) and vals.max() < np.sqrt(3.0)
+
+
 _TRITON_SCRIPT = r"""
 import json, sys
 import numpy as np
