@@ -39,6 +39,7 @@ void free_all(lbmd_ctx *ctx) {
     void *bufs[] = {ctx->f[0],      ctx->f[1],       ctx->node,        ctx->jacc,      ctx->pos4[0],
                     ctx->pos4[1],   ctx->vel4[0],    ctx->vel4[1],     ctx->fcons4[0], ctx->fcons4[1],
                     ctx->pid[0],    ctx->pid[1],     ctx->slot_of,     ctx->row_count, ctx->sort_rank, ctx->chunk_total,
+                    ctx->row_start, ctx->slot_row, ctx->migrant_slot, ctx->migrant_count,
                     ctx->fc4,       ctx->old4,       ctx->bond_count,  ctx->bond_partner, ctx->bond_k,
                     ctx->bond_r0,   ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step};
     for (void *b : bufs)
@@ -138,6 +139,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     ctx->red_blocks = 2 * sms;
+    ctx->sm_count = sms;
 
     struct Alloc {
         void **ptr;
@@ -159,6 +161,10 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->row_count, (size_t)p->ny * p->nz * sizeof(int32_t)},
         {(void **)&ctx->sort_rank, (size_t)maxp * sizeof(int32_t)},
         {(void **)&ctx->chunk_total, (size_t)1024 * sizeof(int32_t)},
+        {(void **)&ctx->row_start, ((size_t)p->ny * p->nz + 1) * sizeof(int32_t)},
+        {(void **)&ctx->slot_row, (size_t)maxp * sizeof(int32_t)},
+        {(void **)&ctx->migrant_slot, (size_t)maxp * sizeof(int32_t)},
+        {(void **)&ctx->migrant_count, sizeof(int32_t)},
         {&ctx->fc4, (size_t)maxp * 4 * rs},
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
         {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},
@@ -183,6 +189,11 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_lb_step, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_count, 0, (size_t)maxp * sizeof(int32_t), ctx->stream);
+    // no row buckets yet: every particle is spread as a migrant until the
+    // first re-ordering
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctx->row_start, 0, ((size_t)p->ny * p->nz + 1) * sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->slot_row, 0xff, (size_t)maxp * sizeof(int32_t), ctx->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(ctx->fcons4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fc4, 0, (size_t)maxp * 4 * rs, ctx->stream);
@@ -233,6 +244,8 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     }
     const size_t rs = real_size(ctx);
     CK(ctx, cudaMemsetAsync((char *)ctx->fcons4[ctx->pcur] + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
+    // new slots are in no row bucket until the next re-ordering
+    CK(ctx, cudaMemsetAsync(ctx->slot_row + ctx->np, 0xff, n * sizeof(int32_t), ctx->stream));
     CK(ctx, cudaMemsetAsync((char *)ctx->fc4 + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     ctx->np += n;
     if (ctx->nb > 0) CK(ctx, launch_bond_forces_only(ctx));

@@ -23,6 +23,8 @@
 //   old4        variant B only: pos4 at the start of the current MD step.
 //   bond_*      per particle id: up to LBMD_MAX_BONDS_PER_PARTICLE partner ids.
 //   row_count   per lattice row: particle counts / offsets of the re-ordering.
+//   row_start   first slot of every cell row after the re-ordering; slot_row
+//               the row bucket of every slot (-1 for particles added since).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -55,6 +57,11 @@ struct lbmd_ctx {
     int32_t *slot_of;
     void *fc4, *old4;
     int32_t *row_count, *sort_rank, *chunk_total;
+    int32_t *row_start;     // first slot of every cell row (ny*nz + 1 entries)
+    int32_t *slot_row;      // per slot: the row bucket it belongs to, -1 if none
+    int32_t *migrant_slot;  // variant B: slots that left their row bucket
+    int32_t *migrant_count;
+    int sm_count;
     int32_t *bond_count, *bond_partner;
     double *bond_k, *bond_r0;
     double *staging;   // device staging buffer for host <-> device conversions

@@ -167,6 +167,16 @@ struct Prec<float> {
         atomicAdd(reinterpret_cast<unsigned long long *>(&rec->z), (unsigned long long)S);
         atomicAdd(&rec->y, dz);
     }
+    // the same update by a thread that owns the record (no concurrent writer)
+    __device__ static __forceinline__ void add_transfer_plain(node4 *rec, fix dx, fix dy, fix dz) {
+        int4 n = *rec;
+        const long long S = (long long)(((unsigned long long)(unsigned)n.w << 32) | (unsigned)n.z) +
+                            ((long long)dy * 4294967296LL + (long long)dx);
+        n.y += dz;
+        n.z = (int)(unsigned)(unsigned long long)S;
+        n.w = (int)(S >> 32);
+        *rec = n;
+    }
     __device__ static __forceinline__ real4 make4(float a, float b, float c, float d) {
         return make_float4(a, b, c, d);
     }
@@ -200,6 +210,13 @@ struct Prec<double> {
         atomicAdd(reinterpret_cast<unsigned long long *>(&rec->y), (unsigned long long)dx);
         atomicAdd(reinterpret_cast<unsigned long long *>(&rec->z), (unsigned long long)dy);
         atomicAdd(reinterpret_cast<unsigned long long *>(&rec->w), (unsigned long long)dz);
+    }
+    __device__ static __forceinline__ void add_transfer_plain(node4 *rec, fix dx, fix dy, fix dz) {
+        L4 n = *rec;
+        n.y += dx;
+        n.z += dy;
+        n.w += dz;
+        *rec = n;
     }
     __device__ static __forceinline__ real4 make4(double a, double b, double c, double d) { return D4{a, b, c, d}; }
     __device__ static __forceinline__ int64_t cell_of(const real4 &p) { return (int64_t)p.w; }

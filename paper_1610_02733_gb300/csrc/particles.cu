@@ -41,6 +41,10 @@ struct PArgs {
     const unsigned long long *lb_step;
     int n_sub, substep, noisy;
     int variant;
+    // variant B row-gather spreading
+    const int32_t *row_start, *slot_row;
+    int32_t *migrant_slot, *migrant_count;
+    int gather;
 };
 
 struct CellXYZ {
@@ -165,6 +169,10 @@ __global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
         spread_to<T>(a.jacc, idx, delta, a.dt * Fx, a.dt * Fy, a.dt * Fz);
     } else {
         a.old4[p] = R;
+        // a particle whose cell row is no longer the row bucket it was sorted
+        // into is spread separately, after the row gather
+        if (a.gather && (int32_t)((uint32_t)P::cell_of(R) / (uint32_t)a.nx) != a.slot_row[p])
+            a.migrant_slot[atomicAdd(a.migrant_count, 1)] = (int32_t)p;
     }
 }
 
@@ -186,6 +194,102 @@ __global__ void __launch_bounds__(256) spread_kernel(PArgs<T> a) {
     T delta[8];
     corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
     spread_to<T>(a.node, idx, delta, a.dt * F.x, a.dt * F.y, a.dt * F.z);
+}
+
+__device__ __forceinline__ void fix_add(int32_t *a, int32_t v) { atomicAdd(a, v); }
+__device__ __forceinline__ void fix_add(long long *a, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
+}
+
+// Variant B, atomic-free: one warp per node row (y, z), four rows per block,
+// rows in reverse order (the couple kernel touched the high rows last).  The
+// row's nodes get transfers only from particles in the four cell rows
+// (y - oy, z - oz), oy, oz in {0, 1}; with the particles bucketed by cell
+// row, the warp reads those buckets, adds each particle's two contributions
+// to this row (nodes x and x + 1, weight delta_k as in Eq. (5)) as
+// fixed-point integers in shared memory, and then updates only the touched
+// nodes of the row with plain loads and stores: no other warp writes this
+// row.  Particles that left their bucket's row are skipped here and spread
+// by migrant_spread_kernel.
+constexpr int GATHER_WARPS = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * GATHER_WARPS) spread_rows_kernel(PArgs<T> a, int n_rows) {
+    using P = Prec<T>;
+    using fix = typename P::fix;
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    fix *acc = reinterpret_cast<fix *>(smem_raw) + (size_t)warp * 3 * a.nx;  // [nx][3] per warp
+    const int g = blockIdx.x * GATHER_WARPS + warp;
+    if (g >= n_rows) return;
+    const int nrow = n_rows - 1 - g;
+    const int y = nrow % a.ny, z = nrow / a.ny;
+    for (int i = lane; i < 3 * a.nx; i += 32) acc[i] = 0;
+    int32_t lo[4], len[4], crow[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int oy = q & 1, oz = q >> 1;
+        const int cy = y - oy < 0 ? a.ny - 1 : y - oy;
+        const int cz = z - oz < 0 ? a.nz - 1 : z - oz;
+        crow[q] = cy + a.ny * cz;
+        lo[q] = a.row_start[crow[q]];
+        len[q] = a.row_start[crow[q] + 1] - lo[q];
+    }
+    __syncwarp();
+    const int total = len[0] + len[1] + len[2] + len[3];
+    for (int t = lane; t < total; t += 32) {
+        int q = 0, off = t;
+        while (off >= len[q]) {
+            off -= len[q];
+            ++q;
+        }
+        const int64_t p = lo[q] + off;
+        const typename P::real4 R = a.old4[p];
+        const uint32_t cell = (uint32_t)P::cell_of(R);
+        const uint32_t row = cell / (uint32_t)a.nx;
+        if ((int32_t)row != crow[q]) continue;  // migrant
+        const int cx = (int)(cell - row * (uint32_t)a.nx);
+        const int x1 = cx + 1 == a.nx ? 0 : cx + 1;
+        const typename P::real4 F = a.fc4[p];
+        const int oy = q & 1, oz = q >> 1;
+        const T wx[2] = {T(1) - R.x, R.x};
+        const T wy = oy ? R.y : T(1) - R.y;
+        const T wz = oz ? R.z : T(1) - R.z;
+        const T dPx = a.dt * F.x, dPy = a.dt * F.y, dPz = a.dt * F.z;
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+            const T d = wx[ox] * wy * wz;  // the corner weight delta_k of Eq. (5)
+            fix *ak = acc + 3 * (ox ? x1 : cx);
+            fix_add(ak + 0, P::to_fix(-d * dPx));
+            fix_add(ak + 1, P::to_fix(-d * dPy));
+            fix_add(ak + 2, P::to_fix(-d * dPz));
+        }
+    }
+    __syncwarp();
+    typename P::node4 *rowp = a.node + (size_t)a.nx * nrow;
+    for (int x = lane; x < a.nx; x += 32) {
+        const fix dx = acc[3 * x], dy = acc[3 * x + 1], dz = acc[3 * x + 2];
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        P::add_transfer_plain(&rowp[x], dx, dy, dz);
+    }
+}
+
+// Variant B: the migrants of this MD step, spread with atomics once the row
+// gather is done.
+template <typename T>
+__global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a) {
+    using P = Prec<T>;
+    const int n = *a.migrant_count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int64_t p = a.migrant_slot[t];
+        const typename P::real4 R = a.old4[p];
+        const typename P::real4 F = a.fc4[p];
+        const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
+        uint32_t idx[8];
+        T delta[8];
+        corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
+        spread_to<T>(a.node, idx, delta, a.dt * F.x, a.dt * F.y, a.dt * F.z);
+    }
 }
 
 // Harmonic bond forces at the current positions (minimum image), summed per
@@ -284,31 +388,44 @@ __global__ void __launch_bounds__(1024) sort_chunk_scan_kernel(int32_t *row_coun
     if (threadIdx.x == 0) chunk_total[blockIdx.x] = tot;
 }
 
-// Level 2 fused into the scatter: every block scans the (at most 1024)
-// chunk totals in shared memory, then moves its particles to
-// chunk offset + offset within the chunk + rank within the row.
+// Level 2: block c adds the totals of chunks 0..c-1 to its 1024 offsets,
+// giving the first slot of every row; row_start[n] = np closes the table.
+__global__ void __launch_bounds__(1024) sort_finalize_kernel(const int32_t *row_offset, const int32_t *chunk_total,
+                                                             int64_t n, int32_t *row_start, int32_t np) {
+    int32_t before;
+    const int32_t v = (int)threadIdx.x < (int)blockIdx.x ? chunk_total[threadIdx.x] : 0;
+    block_exclusive_scan(v, &before);  // total of the first blockIdx.x chunks
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) row_start[i] = before + row_offset[i];
+    if (i == n - 1) row_start[n] = np;
+}
+
+// Move every particle to row_start[row] + rank within the row.
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
     sort_scatter_kernel(const typename Prec<T>::real4 *pos_in, const typename Prec<T>::real4 *vel_in,
                         const typename Prec<T>::real4 *fcons_in, const int32_t *pid_in, typename Prec<T>::real4 *pos_out,
                         typename Prec<T>::real4 *vel_out, typename Prec<T>::real4 *fcons_out, int32_t *pid_out,
-                        int32_t *slot_of, const int32_t *row_offset, const int32_t *chunk_total, int n_chunks,
-                        const int32_t *rank, int64_t np, int nx, int bonds) {
-    __shared__ int32_t chunk_off[1024];
-    const int32_t v = (int)threadIdx.x < n_chunks ? chunk_total[threadIdx.x] : 0;
-    chunk_off[threadIdx.x] = block_exclusive_scan(v, nullptr);
-    __syncthreads();
+                        int32_t *slot_of, int32_t *slot_row, const int32_t *row_start, const int32_t *rank, int64_t np,
+                        int nx, int bonds) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const typename Prec<T>::real4 R = pos_in[p];
     const uint32_t row = (uint32_t)Prec<T>::cell_of(R) / (uint32_t)nx;
-    const int32_t dst = chunk_off[row >> 10] + row_offset[row] + rank[p];
+    const int32_t dst = row_start[row] + rank[p];
+    slot_row[dst] = (int32_t)row;
     pos_out[dst] = R;
     vel_out[dst] = vel_in[p];
     if (bonds) fcons_out[dst] = fcons_in[p];
     const int32_t id = pid_in[p];
     pid_out[dst] = id;
     slot_of[id] = dst;
+}
+
+// shared memory of the row gather: 3 fixed-point sums per node of a row
+template <typename T>
+static size_t gather_smem_bytes(const lbmd_ctx *ctx) {
+    return (size_t)GATHER_WARPS * 3 * ctx->p.nx * sizeof(typename Prec<T>::fix);
 }
 
 template <typename T>
@@ -344,6 +461,11 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.substep = substep;
     a.noisy = ctx->p.kT > 0.0 ? 1 : 0;
     a.variant = ctx->p.variant;
+    a.row_start = ctx->row_start;
+    a.slot_row = ctx->slot_row;
+    a.migrant_slot = ctx->migrant_slot;
+    a.migrant_count = ctx->migrant_count;
+    a.gather = gather_smem_bytes<T>(ctx) <= 48 * 1024 ? 1 : 0;
     return a;
 }
 
@@ -354,18 +476,28 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
     const bool bonds = ctx->nb > 0;
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
+    cudaError_t e;
+    if (B && a.gather && (e = cudaMemsetAsync(ctx->migrant_count, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess)
+        return e;
     if (bonds)
         couple_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
     else
         couple_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (bonds) {
         bond_kick_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (B) {
+    if (B && a.gather) {
+        const int rows = (int)((int64_t)ctx->p.ny * ctx->p.nz);
+        const unsigned gblocks = (unsigned)((rows + GATHER_WARPS - 1) / GATHER_WARPS);
+        spread_rows_kernel<T><<<gblocks, 32 * GATHER_WARPS, gather_smem_bytes<T>(ctx), ctx->stream>>>(a, rows);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        migrant_spread_kernel<T><<<ctx->sm_count, 256, 0, ctx->stream>>>(a);
+        e = cudaGetLastError();
+    } else if (B) {
         spread_kernel<T><<<blocks, 256, 0, ctx->stream>>>(a);
         e = cudaGetLastError();
     }
@@ -396,12 +528,14 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
         const int n_chunks = (int)((rows + 1023) / 1024);
         sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const unsigned sblocks = (unsigned)((ctx->np + 1023) / 1024);
-        sort_scatter_kernel<T><<<sblocks, 1024, 0, ctx->stream>>>(
+        sort_finalize_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, ctx->chunk_total, rows,
+                                                                 ctx->row_start, (int32_t)ctx->np);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sort_scatter_kernel<T><<<blocks, 256, 0, ctx->stream>>>(
             static_cast<const R4 *>(ctx->pos4[b]), static_cast<const R4 *>(ctx->vel4[b]),
             static_cast<const R4 *>(ctx->fcons4[b]), ctx->pid[b], static_cast<R4 *>(ctx->pos4[o]),
             static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]), ctx->pid[o], ctx->slot_of,
-            ctx->row_count, ctx->chunk_total, n_chunks, ctx->sort_rank, ctx->np, ctx->p.nx, ctx->nb > 0 ? 1 : 0);
+            ctx->slot_row, ctx->row_start, ctx->sort_rank, ctx->np, ctx->p.nx, ctx->nb > 0 ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ctx->pcur = o;
