@@ -9,8 +9,9 @@
 //     particles, in bond_kick_kernel when bonds exist);
 //   * variant A: the transfer -delta_k Delta P (Eqs. (7), (8)) goes straight
 //     into the accumulator J_acc, which no MD step reads;
-//     variant B: the start-of-step position is kept for spread_kernel, which
-//     runs once every particle has read the node field.
+//     variant B: the start-of-step position and F are kept for
+//     spread_rows_kernel, which runs once every particle has read the node
+//     field.
 // Transfers are added as fixed-point integers with atomics, so the sum does
 // not depend on the order of the particles (bitwise reproducible).
 //
@@ -44,7 +45,6 @@ struct PArgs {
     // variant B row-gather spreading
     const int32_t *row_start, *slot_row;
     int32_t *migrant_slot, *migrant_count;
-    int gather;
 };
 
 struct CellXYZ {
@@ -106,9 +106,10 @@ __device__ __forceinline__ void spread_to(typename Prec<T>::node4 *field, const 
 }
 
 // The variant is a run-time flag (one instruction sequence for both
-// variants, as in the LB kernel).
+// variants, as in the LB kernel).  At least 6 blocks of 256 threads per SM:
+// the corner loads are scattered, so latency hiding needs many warps.
 template <typename T, bool BONDS>
-__global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
+__global__ void __launch_bounds__(256, 6) couple_kernel(PArgs<T> a) {
     using P = Prec<T>;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
@@ -171,29 +172,9 @@ __global__ void __launch_bounds__(256) couple_kernel(PArgs<T> a) {
         a.old4[p] = R;
         // a particle whose cell row is no longer the row bucket it was sorted
         // into is spread separately, after the row gather
-        if (a.gather && (int32_t)((uint32_t)P::cell_of(R) / (uint32_t)a.nx) != a.slot_row[p])
+        if ((int32_t)((uint32_t)P::cell_of(R) / (uint32_t)a.nx) != a.slot_row[p])
             a.migrant_slot[atomicAdd(a.migrant_count, 1)] = (int32_t)p;
     }
-}
-
-// Variant B: after every particle has read the node field, add the transfer
-// -delta_k Delta P to the momentum density of the 8 nodes (Eqs. (7), (8)), so
-// the next MD step sees the updated node velocities.
-template <typename T>
-__global__ void __launch_bounds__(256) spread_kernel(PArgs<T> a) {
-    using P = Prec<T>;
-    // slots in reverse order: the couple kernel touched the last slots' nodes
-    // most recently, so they are the ones still in L2
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.np) return;
-    const int64_t p = a.np - 1 - t;
-    const typename P::real4 R = a.old4[p];
-    const typename P::real4 F = a.fc4[p];
-    const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
-    uint32_t idx[8];
-    T delta[8];
-    corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
-    spread_to<T>(a.node, idx, delta, a.dt * F.x, a.dt * F.y, a.dt * F.z);
 }
 
 __device__ __forceinline__ void fix_add(int32_t *a, int32_t v) { atomicAdd(a, v); }
@@ -465,7 +446,6 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.slot_row = ctx->slot_row;
     a.migrant_slot = ctx->migrant_slot;
     a.migrant_count = ctx->migrant_count;
-    a.gather = gather_smem_bytes<T>(ctx) <= 48 * 1024 ? 1 : 0;
     return a;
 }
 
@@ -477,8 +457,7 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     const bool bonds = ctx->nb > 0;
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
     cudaError_t e;
-    if (B && a.gather && (e = cudaMemsetAsync(ctx->migrant_count, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess)
-        return e;
+    if (B && (e = cudaMemsetAsync(ctx->migrant_count, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess) return e;
     if (bonds)
         couple_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
     else
@@ -490,15 +469,12 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (B && a.gather) {
+    if (B) {
         const int rows = (int)((int64_t)ctx->p.ny * ctx->p.nz);
         const unsigned gblocks = (unsigned)((rows + GATHER_WARPS - 1) / GATHER_WARPS);
         spread_rows_kernel<T><<<gblocks, 32 * GATHER_WARPS, gather_smem_bytes<T>(ctx), ctx->stream>>>(a, rows);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         migrant_spread_kernel<T><<<ctx->sm_count, 256, 0, ctx->stream>>>(a);
-        e = cudaGetLastError();
-    } else if (B) {
-        spread_kernel<T><<<blocks, 256, 0, ctx->stream>>>(a);
         e = cudaGetLastError();
     }
     return e;
