@@ -33,8 +33,9 @@
  *
  * Randomness: every random number is drawn from Philox4x32-10 (Salmon et al.,
  * SC'11) keyed by params.seed: fluid noise at node r of LB step t uses the
- * counters (r, t, 0, q), q = 0..3; the random force on particle p in MD step
- * s uses (p, s, 1, 0).  Results are therefore reproducible bit for bit.
+ * counters (r, t, 0, q), q = 0, 1, two 16-bit variates per 32-bit output
+ * word; the random force on particle p in MD step s uses (p, s, 1, 0), one
+ * 32-bit variate per component.  Results are reproducible bit for bit.
  * The step counters are 32 bits wide in these counters: runs longer than
  * 2^32 LB steps (or MD steps) repeat their noise.
  */
@@ -180,6 +181,29 @@ lbmd_status lbmd_get_particles_device(lbmd_ctx *ctx, double *pos, double *vel);
 /* Counters and sizes. */
 lbmd_status lbmd_get_counts(lbmd_ctx *ctx, int64_t *n_particles, int64_t *n_bonds, int64_t *lb_step,
                             int64_t *md_step, int32_t *substeps_done);
+
+/* Particle momentum and kinetic energy of caller-owned device arrays, like the
+ * p_particles / e_kin part of lbmd_observables, but without allocating any
+ * device memory.  The paper has no counterpart: this is a service for callers
+ * that cannot allocate -- code running while a framework captures the stream
+ * into a CUDA graph and forbids allocation during capture, code inside a
+ * framework whose caching allocator owns the device memory budget, or
+ * latency-critical paths where cudaMalloc would be too slow or synchronise.
+ *   vel   device, 3n doubles (v_x, v_y, v_z per particle)
+ *   mass  device, n doubles, or NULL for mass 1
+ *   out   device, 4 doubles: sum m v_x, sum m v_y, sum m v_z, sum m v^2
+ *   stream  cudaStream_t to enqueue on (NULL: the default stream)
+ * Enqueue only; the caller synchronises before reading out.  Scratch: one
+ * fixed 32 KB __device__ array in the library, held by every GPU that loads
+ * it until the process exits; n above 4194304 is rejected with
+ * LBMD_ERR_CAPACITY.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls on one device share that
+ * device's array, and it keeps the last call's partial sums: calls that can
+ * overlap on the GPU (e.g. issued on different streams) race, so the caller
+ * must order them.  Errors: LBMD_ERR_ARG,
+ * LBMD_ERR_CAPACITY, LBMD_ERR_CUDA (message in lbmd_last_error(NULL)). */
+lbmd_status lbmd_particle_sums_static(const double *vel, const double *mass, int64_t n, double *out, void *stream);
 
 /* The cudaStream_t the context enqueues on. */
 void *lbmd_stream(lbmd_ctx *ctx);

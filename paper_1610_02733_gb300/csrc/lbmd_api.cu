@@ -53,6 +53,8 @@ bool is_finite_d(double x) { return std::isfinite(x); }
 
 }  // namespace
 
+void lbmd_set_global_error(const std::string &msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char *lbmd_status_string(lbmd_status s) {

@@ -32,6 +32,7 @@ EXPORTS = (
     "lbmd_md_substep", "lbmd_lb_step", "lbmd_run_cycles", "lbmd_observables", "lbmd_get_populations",
     "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
+    "lbmd_particle_sums_static",
 )
 
 
@@ -89,6 +90,7 @@ def load():
     L.lbmd_get_particles.argtypes = [P, ct.c_void_p, ct.c_void_p]
     L.lbmd_get_particles_device.argtypes = [P, ct.c_void_p, ct.c_void_p]
     L.lbmd_get_counts.argtypes = [P, i64p, i64p, i64p, i64p, ct.POINTER(ct.c_int32)]
+    L.lbmd_particle_sums_static.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p]
     L.lbmd_stream.restype = ct.c_void_p
     L.lbmd_stream.argtypes = [P]
     L.lbmd_last_error.restype = ct.c_char_p
@@ -155,6 +157,14 @@ def lbmd_observables(h) -> dict:
     _check(h, load().lbmd_observables(h, ct.byref(o)), "lbmd_observables")
     return {"mass": o.mass, "p_fluid": np.array(list(o.p_fluid)), "p_particles": np.array(list(o.p_particles)),
             "kT_particles": o.kT_particles, "e_kin": o.e_kin, "lb_step": o.lb_step, "md_step": o.md_step}
+
+
+def lbmd_particle_sums_static(vel_ptr: int, mass_ptr, n: int, out_ptr: int, stream=None):
+    """Device pointers in, 4 device doubles out; allocates nothing (see the
+    header comment of the C function)."""
+    return _check(None, load().lbmd_particle_sums_static(
+        ct.c_void_p(vel_ptr), None if not mass_ptr else ct.c_void_p(mass_ptr), int(n), ct.c_void_p(out_ptr),
+        None if stream is None else ct.c_void_p(stream)), "lbmd_particle_sums_static")
 
 
 def make_params(nx, ny, nz, *, n_sub=1, variant=VARIANT_B, precision=FP32, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
