@@ -42,6 +42,12 @@ KT = 1e-4
 ZETA = 1.0
 SEED = 1
 LB_BYTES_PER_NODE = 2 * 19 * 4  # algorithmic: read and write 19 FP32 populations
+PARTICLE_BYTES = 48              # algorithmic per particle and MD step: R, v read and written (FP32)
+NODE_TOUCH_BYTES = 32            # ... per distinct touched node: node velocity read, transfer written
+# kernels per cycle (variant B, no bonds): per MD step couple + row gather +
+# migrant spread; LB collide + moments; re-ordering count, chunk scan,
+# finalize, scatter
+LAUNCHES_PER_CYCLE = 3 * N_SUB + 2 + 4
 WORKLOAD = "256^3 D3Q19 + 1e6 ideal particles, variant B, n=10, FP32"
 
 
@@ -107,6 +113,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The slowest rank's value (every rank runs an independent replica; the
+    job's time is the longest one)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def _setup_gpu(torch, lbmd, inputs, seed_offset=0):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -149,13 +172,13 @@ def run_gpu(args):
     sim, stream, pos0, vel0 = _setup_gpu(torch, lbmd, inputs, seed_offset=rank)
     n_nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
 
-    for _ in range(args.warmup):
-        sim.cycle(1)
+    # warm-up through the product's cycle replay (captures the CUDA graphs of
+    # both buffer parities on first use)
+    sim.run_cycles(max(args.warmup, 2))
     stream.synchronize()
 
-    # timed region: K full cycles, device-resident inputs; events around each
-    # LB step give the per-launch duration of the LB kernels
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # timed region: K full cycles replayed from the captured CUDA graphs,
+    # device-resident inputs
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(dev)
     clocks.start()
@@ -163,29 +186,35 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     start.record(stream)
-    for k in range(args.steps):
-        for _ in range(N_SUB):
-            sim.md_substep()
-        ev[k][0].record(stream)
-        sim.lb_step()
-        ev[k][1].record(stream)
+    sim.run_cycles(args.steps)
     stop.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = start.elapsed_time(stop)
-    lb_ms = [a.elapsed_time(b) for a, b in ev]
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-
+    total_ms = max_over_ranks(start.elapsed_time(stop), world, "cuda")
     ms_per_step = total_ms / args.steps
-    mlups = world * n_nodes * args.steps / (total_ms * 1e-3) / 1e6
-    psubsteps = world * N_PARTICLES * N_SUB * args.steps / (total_ms * 1e-3)
-    lb_avg_ms = float(np.mean(lb_ms))
-    md_ms = ms_per_step - lb_avg_ms
+    mlups = whole_job_rate(n_nodes * args.steps, world, total_ms * 1e-3) / 1e6
+    psubsteps = whole_job_rate(N_PARTICLES * N_SUB * args.steps, world, total_ms * 1e-3)
+
+    # breakdown: the same cycles issued call by call, with events around every
+    # LB step (its kernels' per-launch duration) on the launching stream
+    nb = max(5, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb)]
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    b0.record(stream)
+    for k in range(nb):
+        for _ in range(N_SUB):
+            sim.md_substep()
+        ev[k][0].record(stream)
+        sim.lb_step()
+        ev[k][1].record(stream)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = b0.elapsed_time(b1) / nb
+    lb_avg_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    md_ms = eager_ms - lb_avg_ms
 
     # end to end through the C ABI with host buffers: every step uploads the
     # particle state from pinned host memory, runs the cycle, and reads the
@@ -201,24 +230,34 @@ def run_gpu(args):
     e_steps = max(1, min(args.steps, 50))
     for k in range(e_steps):
         sim.set_particles(h_pos, h_vel)
-        sim.cycle(1)
+        sim.run_cycles(1)
         lbmd._check(sim.handle, lbmd.load().lbmd_get_particles(sim.handle, o_pos.data_ptr(), o_vel.data_ptr()),
                     "lbmd_get_particles")
         sim.observables()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
     if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
         dist.barrier()
-    e2e_s = float(te.item())
-    e2e_mlups = world * n_nodes * e_steps / e2e_s / 1e6
+    e2e_mlups = whole_job_rate(n_nodes * e_steps, world, e2e_s) / 1e6
 
     peak, peak_kind = _peaks()
-    achieved = LB_BYTES_PER_NODE * n_nodes / (lb_avg_ms * 1e-3) / 1e9
-    traffic = _profiled_traffic()
     touched = _touched_nodes(pos0)
     cycle_alg_bytes = LB_BYTES_PER_NODE * n_nodes + N_SUB * (N_PARTICLES * 48 + touched * 32)
+    # rooflines of the two phases of a cycle; the one that takes longer is
+    # reported as the dominant unit
+    md_alg = N_PARTICLES * PARTICLE_BYTES + touched * NODE_TOUCH_BYTES
+    md_step_ms = md_ms / N_SUB
+    lb_roof = {"bound": "hbm", "achieved": round(LB_BYTES_PER_NODE * n_nodes / (lb_avg_ms * 1e-3) / 1e9, 1),
+               "peak": peak, "unit": "GB/s", "traffic": _profiled_traffic("lb_step"),
+               "kernel": "LB step: lb_collide_push + node_moments_kernel",
+               "algorithmic_bytes": LB_BYTES_PER_NODE * n_nodes, "ms": round(lb_avg_ms, 4), "peak_source": peak_kind}
+    md_roof = {"bound": "hbm", "achieved": round(md_alg / (md_step_ms * 1e-3) / 1e9, 1), "peak": peak,
+               "unit": "GB/s", "traffic": _profiled_traffic("md_substep"),
+               "kernel": "MD step: couple_kernel + spread_rows_kernel + migrant_spread_kernel",
+               "algorithmic_bytes": md_alg, "ms": round(md_step_ms, 4), "peak_source": peak_kind}
+    for r in (lb_roof, md_roof):
+        r["frac"] = round(r["achieved"] / peak, 4)
+    dominant = md_roof if md_ms > lb_avg_ms else lb_roof
     line = {
         "metric": METRIC,
         "value": round(mlups, 1),
@@ -236,16 +275,15 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "lattice": list(SHAPE), "particles": N_PARTICLES, "n_sub": N_SUB,
                    "kT": KT, "zeta": ZETA, "variant": "B", "l2": "inputs larger than L2 (2.5 GB populations)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "breakdown_ms": {"lb_step": round(lb_avg_ms, 4), "md_substeps": round(md_ms, 4)},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "LB step (lb_collide_push + node_moments)",
-                     "algorithmic_bytes_per_node": LB_BYTES_PER_NODE, "peak_source": peak_kind},
+        "breakdown_ms": {"lb_step": round(lb_avg_ms, 4), "md_substeps": round(md_ms, 4),
+                         "eager_cycle": round(eager_ms, 4), "graph_cycle": round(ms_per_step, 4)},
+        "roofline": dominant,
+        "roofline_phases": {"lb_step": lb_roof, "md_substep": md_roof},
         "cycle_roofline": {"algorithmic_bytes": cycle_alg_bytes, "touched_nodes": touched,
                            "frac": round(cycle_alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
         "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS", "h2d_bytes_per_step": 2 * 3 * 8 * N_PARTICLES,
                 "d2h_bytes_per_step": 2 * 3 * 8 * N_PARTICLES + 64},
-        "gpu_launches": args.steps * (N_SUB * 2 + 2),
+        "gpu_launches": args.steps * LAUNCHES_PER_CYCLE,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -257,14 +295,25 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def _profiled_traffic():
-    """DRAM bytes per LB step from the committed ncu summary, if it matches the
-    current kernel (see profiles/)."""
-    path = os.path.join(ROOT, "profiles", "lb_step_traffic.json")
+def _source_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1610_02733_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(unit):
+    """DRAM bytes (read + write) per launch of `unit` from the ncu summary in
+    profiles/traffic.json; None unless the kernel sources still hash to the
+    value recorded with the capture."""
     try:
-        with open(path) as fh:
-            d = json.load(fh)
-        return d.get("dram_bytes_per_lb_step")
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)[unit]
+        if _source_hash(d["sources"]) != d["source_hash"]:
+            return None
+        return d["dram_bytes"]
     except Exception:
         return None
 

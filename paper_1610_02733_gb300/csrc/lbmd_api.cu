@@ -94,6 +94,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         return fail(nullptr, LBMD_ERR_ARG, "bad capacities");
     if ((int64_t)p->ny * p->nz > (int64_t)1024 * 1024)
         return fail(nullptr, LBMD_ERR_ARG, "ny * nz must not exceed 2^20 (particle re-ordering by row)");
+    if (p->nx > (p->precision == LBMD_FP64 ? 2048 : 4096))
+        return fail(nullptr, LBMD_ERR_ARG, "nx must not exceed 4096 (FP32) / 2048 (FP64): row gather shared memory");
     for (int d = 0; d < 3; ++d)
         if (!is_finite_d(p->body_force[d])) return fail(nullptr, LBMD_ERR_ARG, "non-finite body force");
 
@@ -165,8 +167,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->chunk_total, (size_t)1024 * sizeof(int32_t)},
         {(void **)&ctx->row_start, ((size_t)p->ny * p->nz + 1) * sizeof(int32_t)},
         {(void **)&ctx->slot_row, (size_t)maxp * sizeof(int32_t)},
-        {(void **)&ctx->migrant_slot, (size_t)maxp * sizeof(int32_t)},
-        {(void **)&ctx->migrant_count, sizeof(int32_t)},
+        {(void **)&ctx->migrant_slot, (size_t)2 * maxp * sizeof(int32_t)},
+        {(void **)&ctx->migrant_count, 2 * sizeof(int32_t)},
         {&ctx->fc4, (size_t)maxp * 4 * rs},
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
         {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},
@@ -196,10 +198,12 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ctx->row_start, 0, ((size_t)p->ny * p->nz + 1) * sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->slot_row, 0xff, (size_t)maxp * sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->migrant_count, 0, 2 * sizeof(int32_t), ctx->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(ctx->fcons4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fc4, 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess && ctx->jacc) e = cudaMemsetAsync(ctx->jacc, 0, (size_t)N * node_bytes, ctx->stream);
+    if (e == cudaSuccess) e = setup_particle_kernels(ctx);
     if (e == cudaSuccess) e = launch_init_equilibrium(ctx);
     if (e == cudaSuccess) e = launch_node_moments(ctx, false);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

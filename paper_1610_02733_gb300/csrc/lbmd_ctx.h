@@ -96,6 +96,7 @@ cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t c
 cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel);
 cudaError_t launch_clear_transfer(lbmd_ctx *ctx);
 cudaError_t launch_sort_particles(lbmd_ctx *ctx);
+cudaError_t setup_particle_kernels(lbmd_ctx *ctx);
 
 // message returned by lbmd_last_error(NULL) (calls without a context)
 void lbmd_set_global_error(const std::string &msg);

@@ -44,7 +44,8 @@ struct PArgs {
     int variant;
     // variant B row-gather spreading
     const int32_t *row_start, *slot_row;
-    int32_t *migrant_slot, *migrant_count;
+    int32_t *migrant_slot, *migrant_count;  // two lists of np_cap slots, two counters
+    int64_t np_cap;
 };
 
 struct CellXYZ {
@@ -171,9 +172,12 @@ __global__ void __launch_bounds__(256, 6) couple_kernel(PArgs<T> a) {
     } else {
         a.old4[p] = R;
         // a particle whose cell row is no longer the row bucket it was sorted
-        // into is spread separately, after the row gather
-        if ((int32_t)((uint32_t)P::cell_of(R) / (uint32_t)a.nx) != a.slot_row[p])
-            a.migrant_slot[atomicAdd(a.migrant_count, 1)] = (int32_t)p;
+        // into is spread separately, after the row gather; the two lists
+        // alternate with the parity of the MD step
+        if ((int32_t)((uint32_t)P::cell_of(R) / (uint32_t)a.nx) != a.slot_row[p]) {
+            const int par = (int)((*a.lb_step * (unsigned long long)a.n_sub + (unsigned)a.substep) & 1ull);
+            a.migrant_slot[(int64_t)par * a.np_cap + atomicAdd(a.migrant_count + par, 1)] = (int32_t)p;
+        }
     }
 }
 
@@ -260,9 +264,14 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) spread_rows_kernel(PArgs<T>
 template <typename T>
 __global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a) {
     using P = Prec<T>;
-    const int n = *a.migrant_count;
+    const int par = (int)((*a.lb_step * (unsigned long long)a.n_sub + (unsigned)a.substep) & 1ull);
+    const int n = a.migrant_count[par];
+    // the other list serves the next MD step: empty it now (nobody uses it
+    // during this one)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.migrant_count[par ^ 1] = 0;
+    const int32_t *list = a.migrant_slot + (int64_t)par * a.np_cap;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int64_t p = a.migrant_slot[t];
+        const int64_t p = list[t];
         const typename P::real4 R = a.old4[p];
         const typename P::real4 F = a.fc4[p];
         const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
@@ -409,6 +418,15 @@ static size_t gather_smem_bytes(const lbmd_ctx *ctx) {
     return (size_t)GATHER_WARPS * 3 * ctx->p.nx * sizeof(typename Prec<T>::fix);
 }
 
+// The row gather's shared memory grows with nx; allow more than the default
+// 48 KB per block (up to 200 KB: nx <= 4096 in FP32, 2048 in FP64).
+template <typename T>
+static cudaError_t setup_t(lbmd_ctx *ctx) {
+    const size_t smem = gather_smem_bytes<T>(ctx);
+    if (smem > (size_t)200 * 1024) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(spread_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 template <typename T>
 static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     using P = Prec<T>;
@@ -446,6 +464,7 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.slot_row = ctx->slot_row;
     a.migrant_slot = ctx->migrant_slot;
     a.migrant_count = ctx->migrant_count;
+    a.np_cap = ctx->p.max_particles > 0 ? ctx->p.max_particles : 1;
     return a;
 }
 
@@ -457,7 +476,6 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     const bool bonds = ctx->nb > 0;
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
     cudaError_t e;
-    if (B && (e = cudaMemsetAsync(ctx->migrant_count, 0, sizeof(int32_t), ctx->stream)) != cudaSuccess) return e;
     if (bonds)
         couple_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
     else
@@ -527,6 +545,10 @@ cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep) {
 
 cudaError_t launch_bond_forces_only(lbmd_ctx *ctx) {
     return ctx->p.precision == LBMD_FP64 ? lbmd::bond_forces_t<double>(ctx) : lbmd::bond_forces_t<float>(ctx);
+}
+
+cudaError_t setup_particle_kernels(lbmd_ctx *ctx) {
+    return ctx->p.precision == LBMD_FP64 ? lbmd::setup_t<double>(ctx) : lbmd::setup_t<float>(ctx);
 }
 
 cudaError_t launch_sort_particles(lbmd_ctx *ctx) {
