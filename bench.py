@@ -49,6 +49,7 @@ NODE_TOUCH_BYTES = 32            # ... per distinct touched node: node velocity 
 # finalize, scatter
 LAUNCHES_PER_CYCLE = 3 * N_SUB + 2 + 4
 WORKLOAD = "256^3 D3Q19 + 1e6 ideal particles, variant B, n=10, FP32"
+PRECISION = "fp32"
 
 
 def _peaks():
@@ -133,12 +134,38 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 def _setup_gpu(torch, lbmd, inputs, seed_offset=0):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    sim = lbmd.LBMD(*SHAPE, variant="B", precision="fp32", n_sub=N_SUB, kT=KT, zeta=ZETA, seed=SEED + seed_offset,
+    sim = lbmd.LBMD(*SHAPE, variant="B", precision=PRECISION, n_sub=N_SUB, kT=KT, zeta=ZETA, seed=SEED + seed_offset,
                     max_particles=N_PARTICLES, stream=stream.cuda_stream)
     pos = inputs.uniform_positions(N_PARTICLES, SHAPE, SEED + seed_offset)
     vel = inputs.maxwell_velocities(N_PARTICLES, KT, SEED + seed_offset)
     sim.add_particles(pos, vel)
     return sim, stream, pos, vel
+
+
+def _time_form(torch, lbmd, inputs, stream, precision, steps, pos, vel):
+    """Cycle time of the same workload with another population storage form."""
+    sim = lbmd.LBMD(*SHAPE, variant="B", precision=precision, n_sub=N_SUB, kT=KT, zeta=ZETA, seed=SEED,
+                    max_particles=N_PARTICLES, stream=stream.cuda_stream)
+    sim.add_particles(pos, vel)
+    sim.run_cycles(3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    sim.run_cycles(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for e0, e1 in ev:
+        for _ in range(N_SUB):
+            sim.md_substep()
+        e0.record(stream)
+        sim.lb_step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    lb_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+    sim.close()
+    return ms, lb_ms
 
 
 def _touched_nodes(pos):
@@ -286,9 +313,22 @@ def run_gpu(args):
         "gpu_launches": args.steps * LAUNCHES_PER_CYCLE,
         "clocks": clk,
     }
+    sim.close()
+    if not args.no_forms:
+        # the reduced-precision storage forms on the same workload, against
+        # this plain FP32 path (algorithmic LB bytes 2 x 19 x 2 B per node)
+        forms = {}
+        for prec in ("fp16dev", "bf16dev"):
+            ms, lb_ms = _time_form(torch, lbmd, inputs, stream, prec, min(args.steps, 50), pos0, vel0)
+            lb_bytes = 2 * 19 * 2 * n_nodes
+            forms[prec] = {"value": round(whole_job_rate(n_nodes, world, ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                           "ms_per_step": round(ms, 4), "lb_step_ms": round(lb_ms, 4),
+                           "speedup_vs_fp32": round(ms_per_step / ms, 3),
+                           "lb_step_speedup_vs_fp32": round(lb_avg_ms / lb_ms, 3),
+                           "lb_roofline_frac": round(lb_bytes / (lb_ms * 1e-3) / 1e9 / peak, 4)}
+        line["precision_forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-    sim.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -376,12 +416,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--edge", type=int, default=256, help="lattice edge (profiling of smaller cases)")
     ap.add_argument("--particles", type=int, default=1_000_000)
+    ap.add_argument("--kT", type=float, default=1e-4, help="temperature (profiling: 0 switches the noise off)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev"],
+                    help="population storage of the timed workload (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    global SHAPE, N_PARTICLES, WORKLOAD
-    if args.edge != 256 or args.particles != 1_000_000:
+    global SHAPE, N_PARTICLES, WORKLOAD, KT, PRECISION
+    KT = args.kT
+    PRECISION = args.precision
+    if args.edge != 256 or args.particles != 1_000_000 or KT != 1e-4:
         SHAPE = (args.edge, args.edge, args.edge)
         N_PARTICLES = args.particles
         WORKLOAD = "%d^3 D3Q19 + %d ideal particles, variant B, n=10, FP32" % (args.edge, args.particles)

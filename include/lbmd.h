@@ -59,13 +59,18 @@ typedef enum lbmd_status {
 } lbmd_status;
 
 enum { LBMD_VARIANT_A = 0, LBMD_VARIANT_B = 1 };
-enum { LBMD_FP32 = 0, LBMD_FP64 = 1 };
+/* Storage and arithmetic.  FP32 / FP64: populations, node field and particles
+ * in that precision.  FP16_DEV / BF16_DEV: populations stored as deviations
+ * f_i - w_i rho0 in FP16 / BF16 (round to nearest), everything else and all
+ * arithmetic as in FP32; the rounding of the stored deviations breaks exact
+ * mass conservation at the level of their last bit. */
+enum { LBMD_FP32 = 0, LBMD_FP64 = 1, LBMD_FP16_DEV = 2, LBMD_BF16_DEV = 3 };
 
 typedef struct lbmd_params {
     int32_t nx, ny, nz;    /* lattice nodes per axis (periodic), each >= 2 */
     int32_t n_sub;         /* m = tau_LB / dt: MD steps per LB step, >= 1 (Sec. 3) */
     int32_t variant;       /* LBMD_VARIANT_A or LBMD_VARIANT_B (Sec. 3) */
-    int32_t precision;     /* LBMD_FP32 or LBMD_FP64 storage and arithmetic */
+    int32_t precision;     /* LBMD_FP32, LBMD_FP64, LBMD_FP16_DEV or LBMD_BF16_DEV */
     double rho0;           /* initial fluid density; the fluid starts at rest */
     double nu;             /* kinematic shear viscosity, > 0 */
     double nu_bulk;        /* bulk viscosity; < 0 selects relaxation factor 0 */

@@ -15,16 +15,17 @@
 
 namespace lbmd {
 
-template <typename T>
+template <typename T, typename S>
 struct LbArgs {
-    const T *__restrict__ fin;
-    T *__restrict__ fout;
+    const S *__restrict__ fin;
+    S *__restrict__ fout;
+    T rho0;  // reference density of the deviation storage
     typename Prec<T>::node4 *node;
     typename Prec<T>::node4 *jacc;
     int nx, ny, nz;
     int64_t N;
     T gamma_bulk, gamma_shear, gamma_ghost;
-    T amp[Q];
+    T amp16[Q];  // noise amplitude sqrt(mu b_k (1 - g_k^2)) times sqrt(12) 2^-16
     T g[3];
     uint32_t key0, key1;
     const unsigned long long *lb_step;
@@ -49,10 +50,31 @@ __host__ __device__ constexpr bool EVEN_MODE(int k) { return k == 0 || (k >= 4 &
 
 // MRT collision with forcing and noise at one node; f holds f* on entry and
 // f' on exit.
-template <typename T>
-__device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T Fy, T Fz, const LbArgs<T> &a,
+// 1/rho and sqrt(rho): IEEE in FP64; in FP32 both from one reciprocal square
+// root (at most a few ulp, far below the FP32 path's tolerance)
+__device__ __forceinline__ void rho_factors(double rho, double &inv, double &sq) {
+    inv = 1.0 / rho;
+    sq = sqrt(rho);
+}
+__device__ __forceinline__ void rho_factors(float rho, float &inv, float &sq) {
+    const float r = rsqrtf(rho);
+    inv = r * r;
+    sq = rho * r;
+}
+
+// (h - 32767.5) for a 16-bit h, exactly: FP32 builds 2^23 + h from its bit
+// pattern (no int-to-float conversion), removes 2^23 and then 32767.5 (both
+// subtractions exact); FP64 converts.
+__device__ __forceinline__ float centred16(uint32_t h, float) {
+    return (__int_as_float((int)(0x4B000000u | h)) - 8388608.0f) - 32767.5f;
+}
+__device__ __forceinline__ double centred16(uint32_t h, double) { return (double)h - 32767.5; }
+
+template <typename T, typename S>
+__device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T Fy, T Fz, const LbArgs<T, S> &a,
                                         uint32_t node, uint32_t step) {
-    const T inv_rho = T(1) / rho;
+    T inv_rho, sr;
+    rho_factors(rho, inv_rho, sr);
     const T ux = (jx + T(0.5) * Fx) * inv_rho;
     const T uy = (jy + T(0.5) * Fy) * inv_rho;
     const T uz = (jz + T(0.5) * Fz) * inv_rho;
@@ -109,8 +131,9 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
 
     if (a.noisy) {
         // 15 variates from two Philox calls: two 16-bit halves per 32-bit
-        // word, low half first, in mode order k = 4..18
-        const T sr = sqrt(rho);
+        // word, low half first, in mode order k = 4..18.  The variate
+        // sqrt(12) ((h + 1/2) 2^-16 - 1/2) is (h - 32767.5) times
+        // sqrt(12) 2^-16, folded into amp16[k] = amp[k] sqrt(12) 2^-16.
 #pragma unroll
         for (uint32_t q = 0; q < 2; ++q) {
             const U4 r = philox4x32_10(U4{node, step, 0u, q}, a.key0, a.key1);
@@ -119,7 +142,7 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
             for (int t = 0; t < 8; ++t) {
                 const int k = 4 + 8 * (int)q + t;
                 const uint32_t h = (t & 1) ? (bits[t >> 1] >> 16) : (bits[t >> 1] & 0xffffu);
-                if (k < Q) mp[k] += a.amp[k] * sr * unit_uniform16<T>(h);
+                if (k < Q) mp[k] += (a.amp16[k] * sr) * centred16(h, T(0));
             }
         }
     }
@@ -154,16 +177,17 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
 // a run-time (warp-uniform) flag rather than a template parameter: both
 // variants then execute one compiled instruction sequence, so at m = 1 they
 // agree bit for bit, as the paper's algorithmic equivalence requires.
-template <typename T>
-__global__ void __launch_bounds__(256) lb_collide_push(LbArgs<T> a) {
+template <typename T, typename S>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(LbArgs<T, S> a) {
     using P = Prec<T>;
+    using St = PopStore<S, T>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.nx) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const uint32_t r = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     T f[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = a.fin[(size_t)i * a.N + r];
+    for (int i = 0; i < Q; ++i) f[i] = St::load(a.fin + (size_t)i * a.N + r, T(WEIGHT(i)) * a.rho0);
     T rho, jx, jy, jz;
     node_moments(f, rho, jx, jy, jz);
     T Fx, Fy, Fz;
@@ -196,15 +220,16 @@ __global__ void __launch_bounds__(256) lb_collide_push(LbArgs<T> a) {
     for (int i = 0; i < Q; ++i) {
         const uint32_t t = (uint32_t)X[CX(i) + 1] +
                            (uint32_t)a.nx * ((uint32_t)Y[CY(i) + 1] + (uint32_t)a.ny * (uint32_t)Z[CZ(i) + 1]);
-        a.fout[(size_t)i * a.N + t] = f[i];
+        St::store(a.fout + (size_t)i * a.N + t, f[i], T(WEIGHT(i)) * a.rho0);
     }
 }
 
-template <typename T>
+template <typename T, typename S>
 __global__ void __launch_bounds__(256)
-    node_moments_kernel(const T *__restrict__ f, typename Prec<T>::node4 *node, int64_t N, int nx, int ny,
+    node_moments_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, int64_t N, int nx, int ny, T rho0,
                         unsigned long long *lb_step, int count_step) {
     using P = Prec<T>;
+    using St = PopStore<S, T>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (count_step && x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *lb_step += 1ull;
     if (x >= nx) return;
@@ -214,18 +239,18 @@ __global__ void __launch_bounds__(256)
     const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)blockIdx.y + (uint32_t)ny * z);
     T fl[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fl[i] = f[(size_t)i * N + r];
+    for (int i = 0; i < Q; ++i) fl[i] = St::load(f + (size_t)i * N + r, T(WEIGHT(i)) * rho0);
     T rho, jx, jy, jz;
     node_moments(fl, rho, jx, jy, jz);
     node[r] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
 }
 
-template <typename T>
-__global__ void init_equilibrium_kernel(T *f, int64_t N, T rho0) {
+template <typename T, typename S>
+__global__ void init_equilibrium_kernel(S *f, int64_t N, T rho0) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[(int64_t)i * N + r] = T(WEIGHT(i)) * rho0;
+    for (int i = 0; i < Q; ++i) PopStore<S, T>::store(f + (int64_t)i * N + r, T(WEIGHT(i)) * rho0, T(WEIGHT(i)) * rho0);
 }
 
 // Node kernels run one thread per node on a (x-blocks, ny, nz) grid.
@@ -237,11 +262,12 @@ static dim3 node_grid(const lbmd_ctx *ctx, dim3 block) {
     return dim3((ctx->p.nx + block.x - 1) / block.x, ctx->p.ny, ctx->p.nz);
 }
 
-template <typename T>
+template <typename T, typename S>
 static cudaError_t lb_step_t(lbmd_ctx *ctx) {
-    LbArgs<T> a;
-    a.fin = static_cast<const T *>(ctx->f[ctx->cur]);
-    a.fout = static_cast<T *>(ctx->f[ctx->cur ^ 1]);
+    LbArgs<T, S> a;
+    a.fin = static_cast<const S *>(ctx->f[ctx->cur]);
+    a.fout = static_cast<S *>(ctx->f[ctx->cur ^ 1]);
+    a.rho0 = (T)ctx->p.rho0;
     a.node = static_cast<typename Prec<T>::node4 *>(ctx->node);
     a.jacc = static_cast<typename Prec<T>::node4 *>(ctx->jacc);
     a.nx = ctx->p.nx;
@@ -251,7 +277,7 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.gamma_bulk = (T)ctx->co.gamma_bulk;
     a.gamma_shear = (T)ctx->co.gamma_shear;
     a.gamma_ghost = (T)ctx->co.gamma_ghost;
-    for (int k = 0; k < Q; ++k) a.amp[k] = (T)ctx->co.noise_amp[k];
+    for (int k = 0; k < Q; ++k) a.amp16[k] = (T)(ctx->co.noise_amp[k] * 3.4641016151377544 * 1.52587890625e-05);
     for (int d = 0; d < 3; ++d) a.g[d] = (T)ctx->co.body_force[d];
     a.key0 = (uint32_t)(ctx->p.seed & 0xffffffffu);
     a.key1 = (uint32_t)(ctx->p.seed >> 32);
@@ -259,42 +285,46 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.noisy = ctx->co.noisy;
     a.variant = ctx->p.variant;
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
-    lb_collide_push<T><<<grid, block, 0, ctx->stream>>>(a);
+    lb_collide_push<T, S><<<grid, block, 0, ctx->stream>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename S>
 static cudaError_t node_moments_t(lbmd_ctx *ctx, bool count_step) {
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
-    node_moments_kernel<T><<<grid, block, 0, ctx->stream>>>(static_cast<const T *>(ctx->f[ctx->cur]),
-                                                            static_cast<typename Prec<T>::node4 *>(ctx->node), ctx->N,
-                                                            ctx->p.nx, ctx->p.ny, ctx->d_lb_step, count_step ? 1 : 0);
+    node_moments_kernel<T, S><<<grid, block, 0, ctx->stream>>>(
+        static_cast<const S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node), ctx->N, ctx->p.nx,
+        ctx->p.ny, (T)ctx->p.rho0, ctx->d_lb_step, count_step ? 1 : 0);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename S>
 static cudaError_t init_equilibrium_t(lbmd_ctx *ctx) {
     const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
-    init_equilibrium_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<T *>(ctx->f[ctx->cur]), ctx->N,
-                                                                 (T)ctx->p.rho0);
+    init_equilibrium_kernel<T, S><<<blocks, 256, 0, ctx->stream>>>(static_cast<S *>(ctx->f[ctx->cur]), ctx->N,
+                                                                    (T)ctx->p.rho0);
     return cudaGetLastError();
 }
 
 }  // namespace lbmd
 
+// population storage per precision: FP32 and FP64 plain, FP16 / BF16 as
+// deviations with FP32 arithmetic
+#define LBMD_DISPATCH_POPS(ctx, FN, ...)                                                   \
+    ((ctx)->p.precision == LBMD_FP64       ? FN<double, double>(__VA_ARGS__)               \
+     : (ctx)->p.precision == LBMD_FP16_DEV ? FN<float, __half>(__VA_ARGS__)                \
+     : (ctx)->p.precision == LBMD_BF16_DEV ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
+                                           : FN<float, float>(__VA_ARGS__))
+
 cudaError_t launch_lb_step(lbmd_ctx *ctx) {
-    cudaError_t e = ctx->p.precision == LBMD_FP64 ? lbmd::lb_step_t<double>(ctx) : lbmd::lb_step_t<float>(ctx);
+    cudaError_t e = LBMD_DISPATCH_POPS(ctx, lbmd::lb_step_t, ctx);
     if (e != cudaSuccess) return e;
     ctx->cur ^= 1;
     return launch_node_moments(ctx, true);
 }
 
 cudaError_t launch_node_moments(lbmd_ctx *ctx, bool count_step) {
-    return ctx->p.precision == LBMD_FP64 ? lbmd::node_moments_t<double>(ctx, count_step)
-                                         : lbmd::node_moments_t<float>(ctx, count_step);
+    return LBMD_DISPATCH_POPS(ctx, lbmd::node_moments_t, ctx, count_step);
 }
 
-cudaError_t launch_init_equilibrium(lbmd_ctx *ctx) {
-    return ctx->p.precision == LBMD_FP64 ? lbmd::init_equilibrium_t<double>(ctx)
-                                         : lbmd::init_equilibrium_t<float>(ctx);
-}
+cudaError_t launch_init_equilibrium(lbmd_ctx *ctx) { return LBMD_DISPATCH_POPS(ctx, lbmd::init_equilibrium_t, ctx); }

@@ -33,7 +33,14 @@ lbmd_status cuda_fail(lbmd_ctx *ctx, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
     } while (0)
 
+// bytes of one real of the node field and particle records (FP32 for the
+// reduced-precision population forms)
 size_t real_size(const lbmd_ctx *ctx) { return ctx->p.precision == LBMD_FP64 ? 8 : 4; }
+
+// bytes of one stored population
+size_t pop_size(const lbmd_ctx *ctx) {
+    return ctx->p.precision == LBMD_FP64 ? 8 : (ctx->p.precision == LBMD_FP32 ? 4 : 2);
+}
 
 void free_all(lbmd_ctx *ctx) {
     void *bufs[] = {ctx->f[0],      ctx->f[1],       ctx->node,        ctx->jacc,      ctx->pos4[0],
@@ -83,8 +90,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (p->n_sub < 1) return fail(nullptr, LBMD_ERR_ARG, "n_sub must be >= 1");
     if (p->variant != LBMD_VARIANT_A && p->variant != LBMD_VARIANT_B)
         return fail(nullptr, LBMD_ERR_ARG, "variant must be A (0) or B (1)");
-    if (p->precision != LBMD_FP32 && p->precision != LBMD_FP64)
-        return fail(nullptr, LBMD_ERR_ARG, "precision must be FP32 (0) or FP64 (1)");
+    if (p->precision < LBMD_FP32 || p->precision > LBMD_BF16_DEV)
+        return fail(nullptr, LBMD_ERR_ARG, "precision must be FP32, FP64, FP16_DEV or BF16_DEV");
     if (!(p->rho0 > 0) || !(p->nu > 0) || !is_finite_d(p->rho0) || !is_finite_d(p->nu))
         return fail(nullptr, LBMD_ERR_ARG, "rho0 and nu must be positive");
     if (!(p->kT >= 0) || !is_finite_d(p->kT)) return fail(nullptr, LBMD_ERR_ARG, "kT must be >= 0");
@@ -149,8 +156,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         void **ptr;
         size_t bytes;
     } allocs[] = {
-        {&ctx->f[0], (size_t)19 * N * rs},
-        {&ctx->f[1], (size_t)19 * N * rs},
+        {&ctx->f[0], (size_t)19 * N * pop_size(ctx)},
+        {&ctx->f[1], (size_t)19 * N * pop_size(ctx)},
         {&ctx->node, (size_t)N * node_bytes},
         {&ctx->jacc, p->variant == LBMD_VARIANT_A ? (size_t)N * node_bytes : 0},
         {&ctx->pos4[0], (size_t)maxp * 4 * rs},

@@ -14,6 +14,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbmd {
@@ -105,14 +107,6 @@ __device__ __forceinline__ float unit_uniform_f(uint32_t x) {
     const float centred = (float)(int32_t)(x ^ 0x80000000u) + 0.5f;
     return centred * (3.4641016151377544f * 2.3283064365386963e-10f);
 }
-// 16 random bits -> sqrt(12) ((h + 1/2) 2^-16 - 1/2) on 65536 levels; every
-// step but the final scaling is exact in FP32 and FP64.
-template <typename T>
-__device__ __forceinline__ T unit_uniform16(uint32_t h) {
-    const T u = ((T)(h & 0xffffu) + T(0.5)) * T(1.52587890625e-05);  // 2^-16
-    return T(3.4641016151377544) * (u - T(0.5));
-}
-
 template <typename T>
 __device__ __forceinline__ T unit_uniform(uint32_t x);
 template <>
@@ -223,6 +217,36 @@ struct Prec<double> {
     __device__ static __forceinline__ real4 make_pos(double fx, double fy, double fz, int64_t cell) {
         return D4{fx, fy, fz, (double)cell};
     }
+};
+
+// ---------------------------------------------------------------------------
+// Population storage.  FP32 / FP64 store f_i itself.  The reduced-precision
+// forms store the deviation from the rest equilibrium, f_i - w_i rho0, as FP16
+// or BF16 (rounded to nearest) and do all arithmetic in FP32: the deviations
+// are small (thermal and flow perturbations), so the 11- or 8-bit significand
+// is spent on them rather than on the constant w_i rho0.
+// ---------------------------------------------------------------------------
+template <typename S, typename T>
+struct PopStore {  // plain storage: S == T
+    __device__ static __forceinline__ T load(const S *p, T /*base*/) { return *p; }
+    __device__ static __forceinline__ void store(S *p, T v, T /*base*/) { *p = v; }
+    static constexpr bool deviation = false;
+};
+template <>
+struct PopStore<__half, float> {
+    __device__ static __forceinline__ float load(const __half *p, float base) { return base + __half2float(*p); }
+    __device__ static __forceinline__ void store(__half *p, float v, float base) { *p = __float2half_rn(v - base); }
+    static constexpr bool deviation = true;
+};
+template <>
+struct PopStore<__nv_bfloat16, float> {
+    __device__ static __forceinline__ float load(const __nv_bfloat16 *p, float base) {
+        return base + __bfloat162float(*p);
+    }
+    __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v, float base) {
+        *p = __float2bfloat16_rn(v - base);
+    }
+    static constexpr bool deviation = true;
 };
 
 // Hydrodynamic moments rho = sum f_i, j = sum f_i c_i (Eqs. (1), (2)).  One

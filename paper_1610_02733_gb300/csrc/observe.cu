@@ -112,23 +112,38 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
 // ---------------------------------------------------------------------------
 // Conversions for the host accessors.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void pops_to_double_kernel(const T *f, int64_t first, int64_t count, double *dst) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < count) dst[t] = (double)f[first + t];
+// populations [first, first + count) of the flat array f[i * N + r]
+__device__ __forceinline__ double pop_base(int64_t flat, int64_t N, double rho0) {
+    const int i = (int)(flat / N);
+    double w = 1.0 / 36.0;
+    if (i == 0) w = 1.0 / 3.0;
+    else if (i <= 6) w = 1.0 / 18.0;
+    return w * rho0;
 }
 
-template <typename T>
-__global__ void pops_from_double_kernel(T *f, int64_t first, int64_t count, const double *src) {
+template <typename T, typename S>
+__global__ void pops_to_double_kernel(const S *f, int64_t first, int64_t count, int64_t N, double rho0,
+                                      double *dst) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < count) f[first + t] = (T)src[t];
+    if (t >= count) return;
+    const int64_t k = first + t;
+    dst[t] = (double)PopStore<S, T>::load(f + k, (T)pop_base(k, N, rho0));
+}
+
+template <typename T, typename S>
+__global__ void pops_from_double_kernel(S *f, int64_t first, int64_t count, int64_t N, double rho0,
+                                        const double *src) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t k = first + t;
+    PopStore<S, T>::store(f + k, (T)src[t], (T)pop_base(k, N, rho0));
 }
 
 // node field (rho, j seen by the particles) or, with transfer_only, the
 // pending transfer J_acc, for nodes [first, first + count)
-template <typename T>
+template <typename T, typename S>
 __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc,
-                                      const T *f, int64_t N, int64_t first, int64_t count, double *dst,
+                                      const S *f, int64_t N, T rho0, int64_t first, int64_t count, double *dst,
                                       int transfer_only, int variant) {
     using P = Prec<T>;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,7 +165,7 @@ __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const
     } else {
         T fl[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) fl[i] = f[(int64_t)i * N + r];
+        for (int i = 0; i < Q; ++i) fl[i] = PopStore<S, T>::load(f + (int64_t)i * N + r, T(WEIGHT(i)) * rho0);
         T rho, jx, jy, jz;
         node_moments(fl, rho, jx, jy, jz);
         dst[3 * t + 0] = (double)P::from_fix(P::jx_of(n) - P::to_fix(jx));
@@ -252,42 +267,49 @@ cudaError_t launch_observables(lbmd_ctx *ctx) {
     return ctx->p.precision == LBMD_FP64 ? observables_t<double>(ctx) : observables_t<float>(ctx);
 }
 
+template <typename T, typename S>
+static cudaError_t pops_to_double_t(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst) {
+    pops_to_double_kernel<T, S><<<nblocks(count), 256, 0, ctx->stream>>>(
+        static_cast<const S *>(ctx->f[ctx->cur]), first, count, ctx->N, ctx->p.rho0, dst);
+    return cudaGetLastError();
+}
+
+template <typename T, typename S>
+static cudaError_t pops_from_double_t(lbmd_ctx *ctx, int64_t first, int64_t count, const double *src) {
+    pops_from_double_kernel<T, S><<<nblocks(count), 256, 0, ctx->stream>>>(static_cast<S *>(ctx->f[ctx->cur]),
+                                                                            first, count, ctx->N, ctx->p.rho0, src);
+    return cudaGetLastError();
+}
+
+template <typename T, typename S>
+static cudaError_t node_to_double_t(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst, bool transfer_only) {
+    using N4 = typename Prec<T>::node4;
+    node_to_double_kernel<T, S><<<nblocks(count), 256, 0, ctx->stream>>>(
+        static_cast<const N4 *>(ctx->node), static_cast<const N4 *>(ctx->jacc), static_cast<const S *>(ctx->f[ctx->cur]),
+        ctx->N, (T)ctx->p.rho0, first, count, dst, transfer_only ? 1 : 0, ctx->p.variant);
+    return cudaGetLastError();
+}
+
+#define LBMD_DISPATCH_POPS(ctx, FN, ...)                                                   \
+    ((ctx)->p.precision == LBMD_FP64       ? FN<double, double>(__VA_ARGS__)               \
+     : (ctx)->p.precision == LBMD_FP16_DEV ? FN<float, __half>(__VA_ARGS__)                \
+     : (ctx)->p.precision == LBMD_BF16_DEV ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
+                                           : FN<float, float>(__VA_ARGS__))
+
 cudaError_t launch_populations_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst) {
     if (count <= 0) return cudaSuccess;
-    if (ctx->p.precision == LBMD_FP64)
-        pops_to_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<const double *>(ctx->f[ctx->cur]), first, count, dst);
-    else
-        pops_to_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<const float *>(ctx->f[ctx->cur]), first, count, dst);
-    return cudaGetLastError();
+    return LBMD_DISPATCH_POPS(ctx, pops_to_double_t, ctx, first, count, dst);
 }
 
 cudaError_t launch_populations_from_double(lbmd_ctx *ctx, int64_t first, int64_t count, const double *src) {
     if (count <= 0) return cudaSuccess;
-    if (ctx->p.precision == LBMD_FP64)
-        pops_from_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<double *>(ctx->f[ctx->cur]), first, count, src);
-    else
-        pops_from_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<float *>(ctx->f[ctx->cur]), first, count, src);
-    return cudaGetLastError();
+    return LBMD_DISPATCH_POPS(ctx, pops_from_double_t, ctx, first, count, src);
 }
 
 cudaError_t launch_node_field_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst,
                                         bool transfer_only) {
     if (count <= 0) return cudaSuccess;
-    if (ctx->p.precision == LBMD_FP64)
-        node_to_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<const Prec<double>::node4 *>(ctx->node), static_cast<const Prec<double>::node4 *>(ctx->jacc),
-            static_cast<const double *>(ctx->f[ctx->cur]), ctx->N, first, count, dst, transfer_only ? 1 : 0,
-            ctx->p.variant);
-    else
-        node_to_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<const Prec<float>::node4 *>(ctx->node), static_cast<const Prec<float>::node4 *>(ctx->jacc),
-            static_cast<const float *>(ctx->f[ctx->cur]), ctx->N, first, count, dst, transfer_only ? 1 : 0,
-            ctx->p.variant);
-    return cudaGetLastError();
+    return LBMD_DISPATCH_POPS(ctx, node_to_double_t, ctx, first, count, dst, transfer_only);
 }
 
 cudaError_t launch_clear_transfer(lbmd_ctx *ctx) {

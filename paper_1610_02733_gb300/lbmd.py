@@ -24,7 +24,8 @@ LBMD_ERR_SEQUENCE = -4
 LBMD_ERR_NONFINITE = -5
 LBMD_ERR_CAPACITY = -6
 VARIANT_A, VARIANT_B = 0, 1
-FP32, FP64 = 0, 1
+FP32, FP64, FP16_DEV, BF16_DEV = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_DEV}
 
 # every symbol include/lbmd.h declares
 EXPORTS = (
@@ -187,13 +188,14 @@ class LBMD:
     """One simulation context on the current CUDA device.
 
     Keyword arguments are the fields of ``lbmd_params`` (lattice units,
-    a = tau_LB = 1).  ``precision`` is ``"fp32"`` or ``"fp64"``; ``variant`` is
-    ``"A"`` or ``"B"``.
+    a = tau_LB = 1).  ``precision`` is ``"fp32"``, ``"fp64"``, ``"fp16dev"`` or
+    ``"bf16dev"`` (populations stored as FP16 / BF16 deviations from the rest
+    state, FP32 arithmetic); ``variant`` is ``"A"`` or ``"B"``.
     """
 
     def __init__(self, nx, ny, nz, *, variant="B", precision="fp32", **kw):
         v = {"A": VARIANT_A, "B": VARIANT_B, 0: VARIANT_A, 1: VARIANT_B}[variant]
-        pr = {"fp32": FP32, "fp64": FP64, 0: FP32, 1: FP64}[precision]
+        pr = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.params = make_params(nx, ny, nz, variant=v, precision=pr, **kw)
         self.shape = (int(nx), int(ny), int(nz))
         self.n_nodes = int(nx) * int(ny) * int(nz)
