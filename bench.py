@@ -364,7 +364,7 @@ def _oracle_sample(edge: int, cycles: int):
     from oracle import oracle as orc
     from paper_1610_02733_gb300 import inputs
     shape = (edge, edge, edge)
-    n = max(1, int(round(N_PARTICLES * (edge / SHAPE[0]) ** 3)))
+    n = max(1, int(round(N_PARTICLES * edge ** 3 / (SHAPE[0] * SHAPE[1] * SHAPE[2]))))
     o = orc.Oracle(*shape, n_sub=N_SUB, variant=1, kT=KT, zeta=ZETA, seed=SEED)
     o.add_particles(inputs.uniform_positions(n, shape, SEED), inputs.maxwell_velocities(n, KT, SEED))
     t0 = time.perf_counter()
@@ -418,6 +418,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--edge", type=int, default=256, help="lattice edge (profiling of smaller cases)")
+    ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
+                    help="non-cubic lattice (profiling of smaller cases with 256-node rows)")
     ap.add_argument("--particles", type=int, default=1_000_000)
     ap.add_argument("--kT", type=float, default=1e-4, help="temperature (profiling: 0 switches the noise off)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev"],
@@ -427,10 +429,12 @@ def main():
     global SHAPE, N_PARTICLES, WORKLOAD, KT, PRECISION
     KT = args.kT
     PRECISION = args.precision
-    if args.edge != 256 or args.particles != 1_000_000 or KT != 1e-4:
-        SHAPE = (args.edge, args.edge, args.edge)
+    shape = tuple(args.lattice) if args.lattice else (args.edge, args.edge, args.edge)
+    if shape != (256, 256, 256) or args.particles != 1_000_000 or KT != 1e-4 or PRECISION != "fp32":
+        SHAPE = shape
         N_PARTICLES = args.particles
-        WORKLOAD = "%d^3 D3Q19 + %d ideal particles, variant B, n=10, FP32" % (args.edge, args.particles)
+        WORKLOAD = "%dx%dx%d D3Q19 + %d ideal particles, variant B, n=10, %s storage, kT=%g" % (
+            shape + (args.particles, PRECISION, KT))
     if args.impl == "reference":
         run_reference(args)
         return

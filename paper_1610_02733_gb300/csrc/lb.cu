@@ -9,7 +9,8 @@
 //
 // node_moments_kernel: one thread per node.  Recomputes rho* and j* of the
 // freshly streamed populations and writes the node field that the MD steps of
-// the next LB cycle read (and, in variant B, update).
+// the next LB cycle read (and, in variant B, update); in variant B also the
+// compact record of every active node.
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
 
@@ -22,6 +23,9 @@ struct LbArgs {
     T rho0;  // reference density of the deviation storage
     typename Prec<T>::node4 *node;
     typename Prec<T>::node4 *jacc;
+    const uint2 *occw;                     // variant B: active nodes
+    const typename Prec<T>::node4 *cact;   // variant B: their compact records
+    int occ_words;
     int nx, ny, nz;
     int64_t N;
     T gamma_bulk, gamma_shear, gamma_ghost;
@@ -193,8 +197,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
     T Fx, Fy, Fz;
     if (a.variant == LBMD_VARIANT_B) {
         // node j = fix(j*) + sum of fixed-point transfers: the difference is
-        // exactly the accumulated transfer J_acc
-        const typename P::node4 n = a.node[r];
+        // exactly the accumulated transfer J_acc (an active node's current
+        // record is its compact one)
+        const int sl = active_slot(a.occw[((size_t)y + (size_t)a.ny * z) * a.occ_words + (x >> 5)], x);
+        const typename P::node4 n = sl >= 0 ? a.cact[sl] : a.node[r];
         Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx));
         Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy));
         Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz));
@@ -226,7 +232,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(256)
-    node_moments_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, int64_t N, int nx, int ny, T rho0,
+    node_moments_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
+                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, T rho0,
                         unsigned long long *lb_step, int count_step) {
     using P = Prec<T>;
     using St = PopStore<S, T>;
@@ -242,7 +249,12 @@ __global__ void __launch_bounds__(256)
     for (int i = 0; i < Q; ++i) fl[i] = St::load(f + (size_t)i * N + r, T(WEIGHT(i)) * rho0);
     T rho, jx, jy, jz;
     node_moments(fl, rho, jx, jy, jz);
-    node[r] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    const typename P::node4 rec = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    node[r] = rec;
+    if (occw) {
+        const int sl = active_slot(occw[((size_t)blockIdx.y + (size_t)ny * z) * occ_words + (x >> 5)], x);
+        if (sl >= 0) cact[sl] = rec;
+    }
 }
 
 template <typename T, typename S>
@@ -270,6 +282,9 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.rho0 = (T)ctx->p.rho0;
     a.node = static_cast<typename Prec<T>::node4 *>(ctx->node);
     a.jacc = static_cast<typename Prec<T>::node4 *>(ctx->jacc);
+    a.occw = ctx->occw;
+    a.cact = static_cast<const typename Prec<T>::node4 *>(ctx->cact);
+    a.occ_words = active_words(ctx->p.nx);
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
@@ -292,9 +307,11 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
 template <typename T, typename S>
 static cudaError_t node_moments_t(lbmd_ctx *ctx, bool count_step) {
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
+    const bool B = ctx->p.variant == LBMD_VARIANT_B;
     node_moments_kernel<T, S><<<grid, block, 0, ctx->stream>>>(
-        static_cast<const S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node), ctx->N, ctx->p.nx,
-        ctx->p.ny, (T)ctx->p.rho0, ctx->d_lb_step, count_step ? 1 : 0);
+        static_cast<const S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
+        B ? ctx->occw : nullptr, static_cast<typename Prec<T>::node4 *>(ctx->cact), active_words(ctx->p.nx), ctx->N,
+        ctx->p.nx, ctx->p.ny, (T)ctx->p.rho0, ctx->d_lb_step, count_step ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -316,10 +333,15 @@ static cudaError_t init_equilibrium_t(lbmd_ctx *ctx) {
      : (ctx)->p.precision == LBMD_BF16_DEV ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
                                            : FN<float, float>(__VA_ARGS__))
 
+// One LB update: collide and stream, re-order the particles by row, rebuild
+// the active nodes (variant B) and recompute the node field (and the active
+// nodes' compact records) from the new populations.
 cudaError_t launch_lb_step(lbmd_ctx *ctx) {
     cudaError_t e = LBMD_DISPATCH_POPS(ctx, lbmd::lb_step_t, ctx);
     if (e != cudaSuccess) return e;
     ctx->cur ^= 1;
+    if ((e = launch_sort_particles(ctx)) != cudaSuccess) return e;
+    if ((e = launch_active_set(ctx)) != cudaSuccess) return e;
     return launch_node_moments(ctx, true);
 }
 

@@ -48,10 +48,11 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->pid[0],    ctx->pid[1],     ctx->slot_of,     ctx->row_count, ctx->sort_rank, ctx->chunk_total,
                     ctx->row_start, ctx->slot_row, ctx->migrant_slot, ctx->migrant_count,
                     ctx->fc4,       ctx->old4,       ctx->bond_count,  ctx->bond_partner, ctx->bond_k,
-                    ctx->bond_r0,   ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step};
+                    ctx->bond_r0,   ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step,
+                    ctx->occw,      ctx->cact};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (ctx->cycle_graph[i]) cudaGraphExecDestroy(ctx->cycle_graph[i]);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
 }
@@ -151,6 +152,10 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     ctx->red_blocks = 2 * sms;
     ctx->sm_count = sms;
+    // active nodes: every particle makes at most the 8 corners of its cell
+    // active
+    ctx->cact_cap = std::min<int64_t>(N, 8 * maxp);
+    const size_t occ_bytes = (size_t)p->ny * p->nz * (size_t)((p->nx + 31) / 32) * sizeof(uint2);
 
     struct Alloc {
         void **ptr;
@@ -178,6 +183,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->migrant_count, 2 * sizeof(int32_t)},
         {&ctx->fc4, (size_t)maxp * 4 * rs},
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
+        {(void **)&ctx->occw, p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
+        {&ctx->cact, p->variant == LBMD_VARIANT_B ? (size_t)ctx->cact_cap * node_bytes : 0},
         {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},
         {(void **)&ctx->bond_partner, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(int32_t)},
         {(void **)&ctx->bond_k, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
@@ -206,6 +213,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         e = cudaMemsetAsync(ctx->row_start, 0, ((size_t)p->ny * p->nz + 1) * sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->slot_row, 0xff, (size_t)maxp * sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->migrant_count, 0, 2 * sizeof(int32_t), ctx->stream);
+    // no active nodes until the first re-ordering
+    if (e == cudaSuccess && ctx->occw) e = cudaMemsetAsync(ctx->occw, 0, occ_bytes, ctx->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(ctx->fcons4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fc4, 0, (size_t)maxp * 4 * rs, ctx->stream);
@@ -263,7 +272,7 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     ctx->np += n;
     if (ctx->nb > 0) CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (ctx->cycle_graph[i]) {
             cudaGraphExecDestroy(ctx->cycle_graph[i]);
             ctx->cycle_graph[i] = nullptr;
@@ -304,7 +313,7 @@ lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, doub
     ctx->nb += nb;
     CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (ctx->cycle_graph[i]) {
             cudaGraphExecDestroy(ctx->cycle_graph[i]);
             ctx->cycle_graph[i] = nullptr;
@@ -338,7 +347,6 @@ lbmd_status lbmd_lb_step(lbmd_ctx *ctx) {
     if (!ctx) return LBMD_ERR_ARG;
     if (ctx->sub_done != ctx->p.n_sub) return fail(ctx, LBMD_ERR_SEQUENCE, "LB step before n_sub MD steps");
     CK(ctx, launch_lb_step(ctx));
-    CK(ctx, launch_sort_particles(ctx));
     ctx->sub_done = 0;
     ctx->lb_step += 1;
     return LBMD_OK;
@@ -348,7 +356,7 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
     if (!ctx || n < 0) return LBMD_ERR_ARG;
     if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "run_cycles must start at a cycle boundary");
     for (int64_t c = 0; c < n; ++c) {
-        const int parity = ctx->cur;
+        const int parity = ctx->cur | (int)((ctx->lb_step & 1) << 1);
         if (!ctx->cycle_graph[parity]) {
             // capture one cycle starting from this population buffer
             cudaGraph_t g = nullptr;
@@ -357,7 +365,6 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
             const int cur0 = ctx->cur, pcur0 = ctx->pcur;
             for (int s = 0; s < ctx->p.n_sub && e == cudaSuccess; ++s) e = launch_md_substep(ctx, s);
             if (e == cudaSuccess) e = launch_lb_step(ctx);
-            if (e == cudaSuccess) e = launch_sort_particles(ctx);
             ctx->cur = cur0;  // the launchers flipped the buffers during capture
             ctx->pcur = pcur0;
             cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
@@ -385,6 +392,7 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
 lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
     if (!ctx || !out) return LBMD_ERR_ARG;
     double h[8];
+    CK(ctx, launch_active_sync(ctx));
     CK(ctx, launch_observables(ctx));
     CK(ctx, cudaMemcpyAsync(h, ctx->red_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -432,6 +440,7 @@ lbmd_status lbmd_set_populations(lbmd_ctx *ctx, const double *in) {
 
 static lbmd_status node_out(lbmd_ctx *ctx, double *out, bool transfer) {
     const int w = transfer ? 3 : 4;
+    CK(ctx, launch_active_sync(ctx));
     const int64_t per = ctx->staging_len / w;
     for (int64_t s = 0; s < ctx->N; s += per) {
         const int64_t c = std::min(per, ctx->N - s);

@@ -25,6 +25,13 @@
 //   row_count   per lattice row: particle counts / offsets of the re-ordering.
 //   row_start   first slot of every cell row after the re-ordering; slot_row
 //               the row bucket of every slot (-1 for particles added since).
+//   occw        variant B: the active nodes (corners of the particles' cells
+//               at the last re-ordering), per row and 32-node word the bits
+//               and the compact slot of the word's first active node.
+//   cact        variant B: compact node records of the active nodes.  For an
+//               active node the compact record, not `node`, is current
+//               between LB updates; `node` is brought up to date from it only
+//               for the observables and the host accessors.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -61,7 +68,11 @@ struct lbmd_ctx {
     int32_t *slot_row;      // per slot: the row bucket it belongs to, -1 if none
     int32_t *migrant_slot;  // variant B: slots that left their row bucket
     int32_t *migrant_count;
+    uint2 *occw;         // variant B: (ny * nz) x active_words(nx) words
+    void *cact;          // variant B: compact node records, cact_cap of them
+    int64_t cact_cap;
     int sm_count;
+    int gather_warps;  // warps per block of the variant B row gather
     int32_t *bond_count, *bond_partner;
     double *bond_k, *bond_r0;
     double *staging;   // device staging buffer for host <-> device conversions
@@ -75,7 +86,9 @@ struct lbmd_ctx {
     int sub_done;
     LbCoeffs co;
     double dt;
-    cudaGraphExec_t cycle_graph[2];
+    // one captured cycle per (population buffer, LB step parity); the two
+    // flip together, so two of the four are used
+    cudaGraphExec_t cycle_graph[4];
     std::string err;
 };
 
@@ -96,6 +109,8 @@ cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t c
 cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel);
 cudaError_t launch_clear_transfer(lbmd_ctx *ctx);
 cudaError_t launch_sort_particles(lbmd_ctx *ctx);
+cudaError_t launch_active_set(lbmd_ctx *ctx);
+cudaError_t launch_active_sync(lbmd_ctx *ctx);
 cudaError_t setup_particle_kernels(lbmd_ctx *ctx);
 
 // message returned by lbmd_last_error(NULL) (calls without a context)

@@ -147,6 +147,10 @@ struct Prec<float> {
     static constexpr float SCALE = 1073741824.0f;             // 2^30
     static constexpr float INV_SCALE = 9.313225746154785e-10f;  // 2^-30
     __device__ static __forceinline__ fix to_fix(float v) { return __float2int_rn(v * SCALE); }
+    // to_fix(-d * dp) for ps = neg_scaled(dp): the power-of-two scale and the
+    // sign move onto dp, which is exact, so the two are bitwise equal
+    __device__ static __forceinline__ float neg_scaled(float dp) { return dp * -SCALE; }
+    __device__ static __forceinline__ fix to_fix_neg(float d, float ps) { return __float2int_rn(d * ps); }
     __device__ static __forceinline__ float from_fix(fix v) { return (float)v * INV_SCALE; }
     __device__ static __forceinline__ node4 pack(float rho, fix jx, fix jy, fix jz) {
         const long long S = (long long)jy * 4294967296LL + (long long)jx;
@@ -162,13 +166,16 @@ struct Prec<float> {
         atomicAdd(&rec->y, dz);
     }
     // the same update by a thread that owns the record (no concurrent writer)
-    __device__ static __forceinline__ void add_transfer_plain(node4 *rec, fix dx, fix dy, fix dz) {
-        int4 n = *rec;
+    __device__ static __forceinline__ void add_transfer_reg(node4 &n, fix dx, fix dy, fix dz) {
         const long long S = (long long)(((unsigned long long)(unsigned)n.w << 32) | (unsigned)n.z) +
                             ((long long)dy * 4294967296LL + (long long)dx);
         n.y += dz;
         n.z = (int)(unsigned)(unsigned long long)S;
         n.w = (int)(S >> 32);
+    }
+    __device__ static __forceinline__ void add_transfer_plain(node4 *rec, fix dx, fix dy, fix dz) {
+        int4 n = *rec;
+        add_transfer_reg(n, dx, dy, dz);
         *rec = n;
     }
     __device__ static __forceinline__ real4 make4(float a, float b, float c, float d) {
@@ -192,6 +199,8 @@ struct Prec<double> {
     static constexpr double SCALE = 72057594037927936.0;          // 2^56
     static constexpr double INV_SCALE = 1.3877787807814457e-17;  // 2^-56
     __device__ static __forceinline__ fix to_fix(double v) { return __double2ll_rn(v * SCALE); }
+    __device__ static __forceinline__ double neg_scaled(double dp) { return dp * -SCALE; }
+    __device__ static __forceinline__ fix to_fix_neg(double d, double ps) { return __double2ll_rn(d * ps); }
     __device__ static __forceinline__ double from_fix(fix v) { return (double)v * INV_SCALE; }
     __device__ static __forceinline__ node4 pack(double rho, fix jx, fix jy, fix jz) {
         return L4{__double_as_longlong(rho), jx, jy, jz};
@@ -205,11 +214,14 @@ struct Prec<double> {
         atomicAdd(reinterpret_cast<unsigned long long *>(&rec->z), (unsigned long long)dy);
         atomicAdd(reinterpret_cast<unsigned long long *>(&rec->w), (unsigned long long)dz);
     }
-    __device__ static __forceinline__ void add_transfer_plain(node4 *rec, fix dx, fix dy, fix dz) {
-        L4 n = *rec;
+    __device__ static __forceinline__ void add_transfer_reg(node4 &n, fix dx, fix dy, fix dz) {
         n.y += dx;
         n.z += dy;
         n.w += dz;
+    }
+    __device__ static __forceinline__ void add_transfer_plain(node4 *rec, fix dx, fix dy, fix dz) {
+        L4 n = *rec;
+        add_transfer_reg(n, dx, dy, dz);
         *rec = n;
     }
     __device__ static __forceinline__ real4 make4(double a, double b, double c, double d) { return D4{a, b, c, d}; }
@@ -260,6 +272,49 @@ __device__ __forceinline__ void node_moments(const T f[Q], T &rho, T &jx, T &jy,
     jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
     jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) + (f[17] - f[18]);
     jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) + (f[15] - f[16]) + (f[18] - f[17]);
+}
+
+// ---------------------------------------------------------------------------
+// Unsigned division by a run-time invariant d, 1 <= d < 2^31, with one
+// multiply-high, a subtract, an add and two shifts (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Fig. 4.1):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n),
+// exact for every 32-bit n.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1ull);
+    f.s1 = l < 1 ? l : 1u;
+    f.s2 = l > 1 ? l - 1u : 0u;
+    return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+    const uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// ---------------------------------------------------------------------------
+// Active nodes of variant B.  Once per LB step, after the particles are
+// re-ordered, every node that is a corner of some particle's cell is marked
+// active and given a slot in a compact array of node records; during the MD
+// steps that compact record, not the node field entry, holds the node's
+// (rho, j).  The set is described per lattice row (y, z) and 32-node word:
+// uint2 {bits, base}, bit b set if node x = 32 w + b is active, base the slot
+// of the word's first active node (slots run in row-major node order).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int active_words(int nx) { return (nx + 31) / 32; }
+
+// compact slot of node x of a row whose word (x / 32) is w, or -1 if inactive
+__device__ __forceinline__ int active_slot(uint2 w, int x) {
+    const uint32_t b = 1u << (x & 31);
+    return (w.x & b) ? (int)w.y + __popc(w.x & (b - 1u)) : -1;
 }
 
 }  // namespace lbmd

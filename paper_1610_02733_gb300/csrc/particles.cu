@@ -22,6 +22,14 @@
 // sort_*: once per LB step the particles are re-ordered by the lattice row
 // (y, z) of their cell (counting sort: count, scan, scatter), so that a warp
 // handles particles whose corner nodes lie in a few neighbouring rows.
+//
+// active_*: variant B, after each re-ordering: the corners of the particles'
+// cells become the active nodes, numbered row by row into a compact array of
+// node records (filled by the LB moments kernel).  Between LB updates the MD
+// kernels read and update an active node through its compact record, which
+// is about as large as the touched part of the lattice rather than the whole
+// node field, and a node that is not active (one a particle reaches only
+// after moving to another cell) through the node field, as before.
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
 
@@ -36,14 +44,20 @@ struct PArgs {
     const int32_t *bond_count, *bond_partner;
     const double *bond_k, *bond_r0;
     int nx, ny, nz;
+    FastDiv fd_nx, fd_ny;  // division by nx and ny
     int64_t np;
     T zeta, dt, half_dt, amp;
+    T neg_scale_dt;  // -dt times the fixed-point scale: neg_scaled(dt F) = F neg_scale_dt exactly
     uint32_t key0, key1;
     const unsigned long long *lb_step;
     int n_sub, substep, noisy;
+    int mig_par;  // parity of the MD step (lb_step n_sub + substep): which migrant list is filled
     int variant;
-    // variant B row-gather spreading
+    // variant B row-gather spreading and active nodes
     const int32_t *row_start, *slot_row;
+    const uint2 *occw;
+    typename P::node4 *cact;
+    int occ_words;
     int32_t *migrant_slot, *migrant_count;  // two lists of np_cap slots, two counters
     int64_t np_cap;
 };
@@ -52,13 +66,13 @@ struct CellXYZ {
     int x, y, z;
 };
 
-__device__ __forceinline__ CellXYZ cell_xyz(int64_t cell, int nx, int ny) {
+__device__ __forceinline__ CellXYZ cell_xyz(int64_t cell, const FastDiv &fnx, const FastDiv &fny) {
     const uint32_t c = (uint32_t)cell;
-    const uint32_t row = c / (uint32_t)nx;
+    const uint32_t row = fdiv(c, fnx);
     CellXYZ r;
-    r.x = (int)(c - row * (uint32_t)nx);
-    r.z = (int)(row / (uint32_t)ny);
-    r.y = (int)(row - (uint32_t)r.z * (uint32_t)ny);
+    r.x = (int)(c - row * fnx.d);
+    r.z = (int)fdiv(row, fny);
+    r.y = (int)(row - (uint32_t)r.z * fny.d);
     return r;
 }
 
@@ -79,6 +93,30 @@ __device__ __forceinline__ void corners(const CellXYZ &c, T fx, T fy, T fz, int 
     }
 }
 
+// The 4 lattice rows (y, z) of the corners, q = oy + 2 oz (corners 2q, 2q+1).
+__device__ __forceinline__ void corner_rows(const CellXYZ &c, int ny, int nz, uint32_t rows[4]) {
+    const int y1 = c.y + 1 == ny ? 0 : c.y + 1;
+    const int z1 = c.z + 1 == nz ? 0 : c.z + 1;
+    rows[0] = (uint32_t)c.y + (uint32_t)ny * (uint32_t)c.z;
+    rows[1] = (uint32_t)y1 + (uint32_t)ny * (uint32_t)c.z;
+    rows[2] = (uint32_t)c.y + (uint32_t)ny * (uint32_t)z1;
+    rows[3] = (uint32_t)y1 + (uint32_t)ny * (uint32_t)z1;
+}
+
+// Variant B: the records of corners 2q, 2q+1 (nodes x0 and x0 + 1 of row
+// `row`): compact record of an active node, node field entry otherwise.
+template <typename T>
+__device__ __forceinline__ void corner_pair(const PArgs<T> &a, uint32_t row, int x0, int x1,
+                                            typename Prec<T>::node4 &n0, typename Prec<T>::node4 &n1) {
+    const uint2 *wr = a.occw + (size_t)row * (uint32_t)a.occ_words;
+    const uint2 w0 = wr[x0 >> 5];
+    const uint2 w1 = (x1 >> 5) == (x0 >> 5) ? w0 : wr[x1 >> 5];
+    const int s0 = active_slot(w0, x0), s1 = active_slot(w1, x1);
+    const size_t r0 = (size_t)row * (uint32_t)a.nx;
+    n0 = s0 >= 0 ? a.cact[s0] : a.node[r0 + x0];
+    n1 = s1 >= 0 ? a.cact[s1] : a.node[r0 + x1];
+}
+
 // Move a fractional coordinate by d and carry whole cells into the index.
 template <typename T>
 __device__ __forceinline__ void advance(T &frac, int &c, T d, int n) {
@@ -90,46 +128,66 @@ __device__ __forceinline__ void advance(T &frac, int &c, T d, int n) {
         s += T(1);
     }
     int cn = c + (int)s;
-    cn %= n;
-    if (cn < 0) cn += n;
+    if (cn < 0 || cn >= n) {  // crossed the periodic boundary
+        cn %= n;
+        if (cn < 0) cn += n;
+    }
     frac = x;
     c = cn;
 }
 
+// The transfer -delta_k Delta P of Eqs. (7), (8) in fixed point; every
+// spreading path computes it this way (sx = F_x neg_scale_dt etc., equal to
+// neg_scaled(dt F_x) because the scale is a power of two).
 template <typename T>
-__device__ __forceinline__ void spread_to(typename Prec<T>::node4 *field, const uint32_t idx[8], const T delta[8], T dPx,
-                                          T dPy, T dPz) {
+__device__ __forceinline__ void spread_to(typename Prec<T>::node4 *field, const uint32_t idx[8], const T delta[8], T sx,
+                                          T sy, T sz) {
     using P = Prec<T>;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-        P::add_transfer(&field[idx[k]], P::to_fix(-delta[k] * dPx), P::to_fix(-delta[k] * dPy),
-                        P::to_fix(-delta[k] * dPz));
+        P::add_transfer(&field[idx[k]], P::to_fix_neg(delta[k], sx), P::to_fix_neg(delta[k], sy),
+                        P::to_fix_neg(delta[k], sz));
 }
 
 // The variant is a run-time flag (one instruction sequence for both
-// variants, as in the LB kernel).  At least 6 blocks of 256 threads per SM:
-// the corner loads are scattered, so latency hiding needs many warps.
+// variants, as in the LB kernel).  At least 5 blocks of 256 threads per SM
+// (3 in FP64): the corner loads are scattered, so latency hiding needs many
+// warps.
 template <typename T, bool BONDS>
-__global__ void __launch_bounds__(256, 6) couple_kernel(PArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PArgs<T> a) {
     using P = Prec<T>;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
     const typename P::real4 R = a.pos4[p];
     typename P::real4 V = a.vel4[p];
-    const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
-    uint32_t idx[8];
-    T delta[8];
-    corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
 
-    // fluid velocity at the particle, Eq. (5)
+    // fluid velocity at the particle, Eq. (5), corners in the order
+    // k = ox + 2 oy + 4 oz = 0..7 with weights delta_k = wx wy wz
     T ux = T(0), uy = T(0), uz = T(0);
+    {
+        uint32_t rows[4];
+        corner_rows(c, a.ny, a.nz, rows);
+        const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
+        const T wx[2] = {T(1) - R.x, R.x}, wy[2] = {T(1) - R.y, R.y}, wz[2] = {T(1) - R.z, R.z};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const typename P::node4 n = a.node[idx[k]];
-        const T w = delta[k] / P::rho_of(n);
-        ux += w * P::from_fix(P::jx_of(n));
-        uy += w * P::from_fix(P::jy_of(n));
-        uz += w * P::from_fix(P::jz_of(n));
+        for (int q = 0; q < 4; ++q) {
+            typename P::node4 n[2];
+            if (a.variant == LBMD_VARIANT_B) {
+                corner_pair(a, rows[q], c.x, x1, n[0], n[1]);
+            } else {
+                const size_t r0 = (size_t)rows[q] * (uint32_t)a.nx;
+                n[0] = a.node[r0 + c.x];
+                n[1] = a.node[r0 + x1];
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const T w = (wx[h] * wy[q & 1] * wz[q >> 1]) / P::rho_of(n[h]);
+                ux += w * P::from_fix(P::jx_of(n[h]));
+                uy += w * P::from_fix(P::jy_of(n[h]));
+                uz += w * P::from_fix(P::jz_of(n[h]));
+            }
+        }
     }
     // coupling force, Eq. (4) without the conservative part
     T Fx = -a.zeta * (V.x - ux), Fy = -a.zeta * (V.y - uy), Fz = -a.zeta * (V.z - uz);
@@ -168,15 +226,18 @@ __global__ void __launch_bounds__(256, 6) couple_kernel(PArgs<T> a) {
 
     if (a.variant == LBMD_VARIANT_A) {
         // Newton's third law, Eqs. (7), (8): straight into J_acc
-        spread_to<T>(a.jacc, idx, delta, a.dt * Fx, a.dt * Fy, a.dt * Fz);
+        uint32_t idx[8];
+        T delta[8];
+        corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
+        spread_to<T>(a.jacc, idx, delta, Fx * a.neg_scale_dt, Fy * a.neg_scale_dt, Fz * a.neg_scale_dt);
     } else {
         a.old4[p] = R;
         // a particle whose cell row is no longer the row bucket it was sorted
         // into is spread separately, after the row gather; the two lists
         // alternate with the parity of the MD step
-        if ((int32_t)((uint32_t)P::cell_of(R) / (uint32_t)a.nx) != a.slot_row[p]) {
-            const int par = (int)((*a.lb_step * (unsigned long long)a.n_sub + (unsigned)a.substep) & 1ull);
-            a.migrant_slot[(int64_t)par * a.np_cap + atomicAdd(a.migrant_count + par, 1)] = (int32_t)p;
+        const int32_t srow = a.slot_row[p];
+        if (srow < 0 || (uint32_t)P::cell_of(R) - (uint32_t)srow * (uint32_t)a.nx >= (uint32_t)a.nx) {
+            a.migrant_slot[(int64_t)a.mig_par * a.np_cap + atomicAdd(a.migrant_count + a.mig_par, 1)] = (int32_t)p;
         }
     }
 }
@@ -190,81 +251,151 @@ __device__ __forceinline__ void fix_add(long long *a, long long v) {
 // rows in reverse order (the couple kernel touched the high rows last).  The
 // row's nodes get transfers only from particles in the four cell rows
 // (y - oy, z - oz), oy, oz in {0, 1}; with the particles bucketed by cell
-// row, the warp reads those buckets, adds each particle's two contributions
-// to this row (nodes x and x + 1, weight delta_k as in Eq. (5)) as
-// fixed-point integers in shared memory, and then updates only the touched
-// nodes of the row with plain loads and stores: no other warp writes this
-// row.  Particles that left their bucket's row are skipped here and spread
-// by migrant_spread_kernel.
-constexpr int GATHER_WARPS = 4;
+// row, the warp reads those buckets and adds each particle's two
+// contributions to this row (nodes x and x + 1, weight delta_k as in
+// Eq. (5)) as fixed-point integers in shared memory, one entry per active
+// node of the row; then it updates the row's compact records with plain
+// loads and stores (no other warp writes them).  A contribution to an
+// inactive node goes to the node field with atomics.  Particles that left
+// their bucket's row are skipped here and spread by migrant_spread_kernel.
+constexpr int GATHER_WARPS = 4;  // warps per block (fewer for very long rows)
+
+// Shared-memory sums of the row gather: 3 per active node (odd stride, so
+// the lanes' atomics spread over the banks), cleared with 16-byte stores; the
+// per-warp area has room for 3 nx + 4 sums.
+template <typename fix>
+__host__ __device__ constexpr size_t acc_words(int nx) {
+    return ((size_t)3 * nx + 4 + (16 / sizeof(fix)) - 1) / (16 / sizeof(fix)) * (16 / sizeof(fix));
+}
+template <typename fix>
+__device__ __forceinline__ void acc_clear(fix *acc, int cnt, int lane) {
+    constexpr int per = 16 / sizeof(fix);
+    const int n4 = (3 * cnt + per - 1) / per;
+    int4 *a4 = reinterpret_cast<int4 *>(acc);
+    for (int k = lane; k < n4; k += 32) a4[k] = make_int4(0, 0, 0, 0);
+}
+
+// bytes of the active-word area of one block (rounded to 16)
+__host__ __device__ inline size_t gather_occ_bytes(int warps, int W) {
+    return ((size_t)warps * W * sizeof(uint2) + 15) & ~(size_t)15;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(32 * GATHER_WARPS) spread_rows_kernel(PArgs<T> a, int n_rows) {
     using P = Prec<T>;
     using fix = typename P::fix;
-    extern __shared__ unsigned char smem_raw[];
+    using N4 = typename P::node4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    fix *acc = reinterpret_cast<fix *>(smem_raw) + (size_t)warp * 3 * a.nx;  // [nx][3] per warp
-    const int g = blockIdx.x * GATHER_WARPS + warp;
+    const int W = a.occ_words;
+    // per warp: the row's active words (slots relative to the row's first),
+    // then the sums of the active nodes
+    uint2 *occ = reinterpret_cast<uint2 *>(smem_raw) + (size_t)warp * W;
+    fix *acc = reinterpret_cast<fix *>(smem_raw + gather_occ_bytes(warps, W)) + (size_t)warp * acc_words<fix>(a.nx);
+    const int g = blockIdx.x * warps + warp;
     if (g >= n_rows) return;
     const int nrow = n_rows - 1 - g;
-    const int y = nrow % a.ny, z = nrow / a.ny;
-    for (int i = lane; i < 3 * a.nx; i += 32) acc[i] = 0;
-    int32_t lo[4], len[4], crow[4];
+    const int z = (int)fdiv((uint32_t)nrow, a.fd_ny), y = nrow - z * a.ny;
+    // the four cell rows (y - oy, z - oz), q = oy + 2 oz, as one run of
+    // total = e[4] particle entries: entry t belongs to row q with
+    // e[q] <= t < e[q + 1], at slot lo[q] + t - e[q]
+    const int ym = y == 0 ? a.ny - 1 : y - 1, zm = z == 0 ? a.nz - 1 : z - 1;
+    const int c0 = y + a.ny * z, c1 = ym + a.ny * z, c2 = y + a.ny * zm, c3 = ym + a.ny * zm;
+    const int lo0 = a.row_start[c0], lo1 = a.row_start[c1], lo2 = a.row_start[c2], lo3 = a.row_start[c3];
+    const int e1 = a.row_start[c0 + 1] - lo0;
+    const int e2 = e1 + a.row_start[c1 + 1] - lo1;
+    const int e3 = e2 + a.row_start[c2 + 1] - lo2;
+    const int total = e3 + a.row_start[c3 + 1] - lo3;
+    const uint2 *wrow = a.occw + (size_t)nrow * W;
+    const int base = (int)wrow[0].y;
+    for (int w = lane; w < W; w += 32) {
+        uint2 v = wrow[w];
+        v.y -= (uint32_t)base;
+        occ[w] = v;
+    }
+    const uint2 last = wrow[W - 1];
+    const int cnt = (int)last.y - base + __popc(last.x);
+    acc_clear(acc, cnt, lane);
+    __syncwarp();
+    N4 *rowp = a.node + (size_t)a.nx * nrow;
+    // entries in passes of 64, two per lane, both loaded before either is used
+    for (int t0 = 0; t0 < total; t0 += 64) {
+        typename P::real4 Rv[2], Fv[2];
+        int crow[2];
+        bool oyv[2], ozv[2], live[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int oy = q & 1, oz = q >> 1;
-        const int cy = y - oy < 0 ? a.ny - 1 : y - oy;
-        const int cz = z - oz < 0 ? a.nz - 1 : z - oz;
-        crow[q] = cy + a.ny * cz;
-        lo[q] = a.row_start[crow[q]];
-        len[q] = a.row_start[crow[q] + 1] - lo[q];
+        for (int h = 0; h < 2; ++h) {
+            const int t = t0 + 32 * h + lane;
+            live[h] = t < total;
+            const bool b1 = t >= e1, b2 = t >= e2, b3 = t >= e3;
+            const int slot0 = b3 ? lo3 - e3 : b2 ? lo2 - e2 : b1 ? lo1 - e1 : lo0;
+            crow[h] = b3 ? c3 : b2 ? c2 : b1 ? c1 : c0;
+            oyv[h] = b1 != b2 || b3;  // q = 1 or 3
+            ozv[h] = b2;              // q = 2 or 3
+            if (live[h]) {
+                Rv[h] = a.old4[slot0 + t];
+                Fv[h] = a.fc4[slot0 + t];
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!live[h]) continue;
+            const typename P::real4 R = Rv[h], F = Fv[h];
+            // cell x within the bucket's row; anything else is a migrant
+            const int cx = (int)((uint32_t)P::cell_of(R) - (uint32_t)crow[h] * (uint32_t)a.nx);
+            if ((uint32_t)cx >= (uint32_t)a.nx) continue;
+            const int x1 = cx + 1 == a.nx ? 0 : cx + 1;
+            const T wx[2] = {T(1) - R.x, R.x};
+            const T wy = oyv[h] ? R.y : T(1) - R.y;
+            const T wz = ozv[h] ? R.z : T(1) - R.z;
+            const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
+#pragma unroll
+            for (int ox = 0; ox < 2; ++ox) {
+                const T d = wx[ox] * wy * wz;  // the corner weight delta_k of Eq. (5)
+                const int xn = ox ? x1 : cx;
+                const fix vx = P::to_fix_neg(d, sx), vy = P::to_fix_neg(d, sy), vz = P::to_fix_neg(d, sz);
+                const int sl = active_slot(occ[xn >> 5], xn);
+                if (sl >= 0) {
+                    fix *ak = acc + 3 * sl;
+                    fix_add(ak + 0, vx);
+                    fix_add(ak + 1, vy);
+                    fix_add(ak + 2, vz);
+                } else {
+                    P::add_transfer(&rowp[xn], vx, vy, vz);
+                }
+            }
+        }
     }
     __syncwarp();
-    const int total = len[0] + len[1] + len[2] + len[3];
-    for (int t = lane; t < total; t += 32) {
-        int q = 0, off = t;
-        while (off >= len[q]) {
-            off -= len[q];
-            ++q;
-        }
-        const int64_t p = lo[q] + off;
-        const typename P::real4 R = a.old4[p];
-        const uint32_t cell = (uint32_t)P::cell_of(R);
-        const uint32_t row = cell / (uint32_t)a.nx;
-        if ((int32_t)row != crow[q]) continue;  // migrant
-        const int cx = (int)(cell - row * (uint32_t)a.nx);
-        const int x1 = cx + 1 == a.nx ? 0 : cx + 1;
-        const typename P::real4 F = a.fc4[p];
-        const int oy = q & 1, oz = q >> 1;
-        const T wx[2] = {T(1) - R.x, R.x};
-        const T wy = oy ? R.y : T(1) - R.y;
-        const T wz = oz ? R.z : T(1) - R.z;
-        const T dPx = a.dt * F.x, dPy = a.dt * F.y, dPz = a.dt * F.z;
+    // write-back in passes of 128 nodes, the four records loaded together
+    N4 *crec = a.cact + base;
+    for (int k0 = 0; k0 < cnt; k0 += 128) {
+        N4 rec[4];
 #pragma unroll
-        for (int ox = 0; ox < 2; ++ox) {
-            const T d = wx[ox] * wy * wz;  // the corner weight delta_k of Eq. (5)
-            fix *ak = acc + 3 * (ox ? x1 : cx);
-            fix_add(ak + 0, P::to_fix(-d * dPx));
-            fix_add(ak + 1, P::to_fix(-d * dPy));
-            fix_add(ak + 2, P::to_fix(-d * dPz));
+        for (int h = 0; h < 4; ++h) {
+            const int k = k0 + 32 * h + lane;
+            if (k < cnt) rec[h] = crec[k];
         }
-    }
-    __syncwarp();
-    typename P::node4 *rowp = a.node + (size_t)a.nx * nrow;
-    for (int x = lane; x < a.nx; x += 32) {
-        const fix dx = acc[3 * x], dy = acc[3 * x + 1], dz = acc[3 * x + 2];
-        if (dx == 0 && dy == 0 && dz == 0) continue;
-        P::add_transfer_plain(&rowp[x], dx, dy, dz);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int k = k0 + 32 * h + lane;
+            if (k >= cnt) continue;
+            const fix dx = acc[3 * k], dy = acc[3 * k + 1], dz = acc[3 * k + 2];
+            if (dx == 0 && dy == 0 && dz == 0) continue;
+            P::add_transfer_reg(rec[h], dx, dy, dz);
+            crec[k] = rec[h];
+        }
     }
 }
 
 // Variant B: the migrants of this MD step, spread with atomics once the row
-// gather is done.
+// gather is done (into the compact record of an active corner, the node
+// field entry of an inactive one).
 template <typename T>
 __global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a) {
     using P = Prec<T>;
-    const int par = (int)((*a.lb_step * (unsigned long long)a.n_sub + (unsigned)a.substep) & 1ull);
+    const int par = a.mig_par;
     const int n = a.migrant_count[par];
     // the other list serves the next MD step: empty it now (nobody uses it
     // during this one)
@@ -274,11 +405,20 @@ __global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a) {
         const int64_t p = list[t];
         const typename P::real4 R = a.old4[p];
         const typename P::real4 F = a.fc4[p];
-        const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
-        uint32_t idx[8];
+        const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
+        uint32_t idx[8], rows[4];
         T delta[8];
         corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
-        spread_to<T>(a.node, idx, delta, a.dt * F.x, a.dt * F.y, a.dt * F.z);
+        corner_rows(c, a.ny, a.nz, rows);
+        const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
+        const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int xn = (k & 1) ? x1 : c.x;
+            const int sl = active_slot(a.occw[(size_t)rows[k >> 1] * (uint32_t)a.occ_words + (xn >> 5)], xn);
+            typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[idx[k]];
+            P::add_transfer(rec, P::to_fix_neg(delta[k], sx), P::to_fix_neg(delta[k], sy), P::to_fix_neg(delta[k], sz));
+        }
     }
 }
 
@@ -291,14 +431,14 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
     const typename P::real4 R = a.pos4[p];
-    const CellXYZ c = cell_xyz(P::cell_of(R), a.nx, a.ny);
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
     const int64_t id = a.pid[p];
     T Fx = T(0), Fy = T(0), Fz = T(0);
     const int nbond = a.bond_count[id];
     for (int b = 0; b < nbond; ++b) {
         const int64_t q = a.slot_of[a.bond_partner[id * LBMD_MAX_BONDS_PER_PARTICLE + b]];
         const typename P::real4 S = a.pos4[q];
-        const CellXYZ d = cell_xyz(P::cell_of(S), a.nx, a.ny);
+        const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
         T dx = T(d.x - c.x) + (S.x - R.x);
         T dy = T(d.y - c.y) + (S.y - R.y);
         T dz = T(d.z - c.z) + (S.z - R.z);
@@ -332,10 +472,10 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
-    sort_count_kernel(const typename Prec<T>::real4 *pos4, int64_t np, int nx, int32_t *row_count, int32_t *rank) {
+    sort_count_kernel(const typename Prec<T>::real4 *pos4, int64_t np, FastDiv fnx, int32_t *row_count, int32_t *rank) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
-    const uint32_t row = (uint32_t)Prec<T>::cell_of(pos4[p]) / (uint32_t)nx;
+    const uint32_t row = fdiv((uint32_t)Prec<T>::cell_of(pos4[p]), fnx);
     rank[p] = atomicAdd(&row_count[row], 1);
 }
 
@@ -397,11 +537,11 @@ __global__ void __launch_bounds__(256)
                         const typename Prec<T>::real4 *fcons_in, const int32_t *pid_in, typename Prec<T>::real4 *pos_out,
                         typename Prec<T>::real4 *vel_out, typename Prec<T>::real4 *fcons_out, int32_t *pid_out,
                         int32_t *slot_of, int32_t *slot_row, const int32_t *row_start, const int32_t *rank, int64_t np,
-                        int nx, int bonds) {
+                        FastDiv fnx, int bonds) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const typename Prec<T>::real4 R = pos_in[p];
-    const uint32_t row = (uint32_t)Prec<T>::cell_of(R) / (uint32_t)nx;
+    const uint32_t row = fdiv((uint32_t)Prec<T>::cell_of(R), fnx);
     const int32_t dst = row_start[row] + rank[p];
     slot_row[dst] = (int32_t)row;
     pos_out[dst] = R;
@@ -412,18 +552,108 @@ __global__ void __launch_bounds__(256)
     slot_of[id] = dst;
 }
 
-// shared memory of the row gather: 3 fixed-point sums per node of a row
+// ---------------------------------------------------------------------------
+// Active nodes (variant B), rebuilt after each re-ordering.
+// ---------------------------------------------------------------------------
+// Level 0: one warp per node row marks nodes x and x + 1 of every particle in
+// the four cell rows with corners in this row, then stores the row's words
+// with the in-row slot of each word's first active node, and the row's count.
 template <typename T>
-static size_t gather_smem_bytes(const lbmd_ctx *ctx) {
-    return (size_t)GATHER_WARPS * 3 * ctx->p.nx * sizeof(typename Prec<T>::fix);
+__global__ void __launch_bounds__(32 * GATHER_WARPS)
+    active_rows_kernel(const typename Prec<T>::real4 *pos4, const int32_t *row_start, int nx, FastDiv fny, int nz, int W,
+                       uint2 *occw, int32_t *row_count, int n_rows) {
+    extern __shared__ uint32_t bits_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *bits = bits_smem + (size_t)warp * W;
+    const int nrow = blockIdx.x * GATHER_WARPS + warp;
+    if (nrow >= n_rows) return;
+    const int ny = (int)fny.d;
+    const int z = (int)fdiv((uint32_t)nrow, fny), y = nrow - z * ny;
+    for (int w = lane; w < W; w += 32) bits[w] = 0u;
+    // the four cell rows (y - oy, z - oz) as one run of entries, as in
+    // spread_rows_kernel
+    const int ym = y == 0 ? ny - 1 : y - 1, zm = z == 0 ? nz - 1 : z - 1;
+    const int c0 = y + ny * z, c1 = ym + ny * z, c2 = y + ny * zm, c3 = ym + ny * zm;
+    const int lo0 = row_start[c0], lo1 = row_start[c1], lo2 = row_start[c2], lo3 = row_start[c3];
+    const int e1 = row_start[c0 + 1] - lo0;
+    const int e2 = e1 + row_start[c1 + 1] - lo1;
+    const int e3 = e2 + row_start[c2 + 1] - lo2;
+    const int total = e3 + row_start[c3 + 1] - lo3;
+    __syncwarp();
+    for (int t = lane; t < total; t += 32) {
+        const bool b1 = t >= e1, b2 = t >= e2, b3 = t >= e3;
+        const int slot0 = b3 ? lo3 - e3 : b2 ? lo2 - e2 : b1 ? lo1 - e1 : lo0;
+        const int crow = b3 ? c3 : b2 ? c2 : b1 ? c1 : c0;
+        // freshly re-ordered: every particle's cell lies in its bucket's row
+        const int cx = (int)((uint32_t)Prec<T>::cell_of(pos4[slot0 + t]) - (uint32_t)crow * (uint32_t)nx);
+        const int x1 = cx + 1 == nx ? 0 : cx + 1;
+        atomicOr(&bits[cx >> 5], 1u << (cx & 31));
+        atomicOr(&bits[x1 >> 5], 1u << (x1 & 31));
+    }
+    __syncwarp();
+    int carry = 0;
+    for (int w0 = 0; w0 < W; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t b = w < W ? bits[w] : 0u;
+        const int c = __popc(b);
+        int incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (w < W) occw[(size_t)nrow * W + w] = make_uint2(b, (uint32_t)(carry + incl - c));
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) row_count[nrow] = carry;
 }
 
-// The row gather's shared memory grows with nx; allow more than the default
-// 48 KB per block (up to 200 KB: nx <= 4096 in FP32, 2048 in FP64).
+// Level 2 (after sort_chunk_scan_kernel turned the row counts into offsets
+// within chunks of 1024 rows): the first slot of every row, added to the
+// in-row slots of its words.
+__global__ void __launch_bounds__(1024) active_finalize_kernel(const int32_t *row_offset, const int32_t *chunk_total,
+                                                               int64_t n_rows, uint2 *occw, int W) {
+    int32_t before;
+    const int32_t v = (int)threadIdx.x < (int)blockIdx.x ? chunk_total[threadIdx.x] : 0;
+    block_exclusive_scan(v, &before);  // total of the first blockIdx.x chunks
+    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    if (i >= n_rows) return;
+    const uint32_t b = (uint32_t)(before + row_offset[i]);
+    uint2 *wr = occw + (size_t)i * W;
+    for (int w = 0; w < W; ++w) wr[w].y += b;
+}
+
+// Node field entries of the active nodes brought up to date from their
+// compact records (for the observables and the host accessors).
+template <typename T>
+__global__ void __launch_bounds__(256) active_sync_kernel(const uint2 *occw, const typename Prec<T>::node4 *cact,
+                                                          typename Prec<T>::node4 *node, int64_t N, int nx, int W) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const int64_t row = r / nx;
+    const int x = (int)(r - row * nx);
+    const int sl = active_slot(occw[(size_t)row * W + (x >> 5)], x);
+    if (sl >= 0) node[r] = cact[sl];
+}
+
+// shared memory of the row gather with `warps` warps per block: the rows'
+// active words and the sums of up to nx active nodes per row
+template <typename T>
+static size_t gather_smem_bytes(const lbmd_ctx *ctx, int warps) {
+    using fix = typename Prec<T>::fix;
+    return gather_occ_bytes(warps, active_words(ctx->p.nx)) + (size_t)warps * acc_words<fix>(ctx->p.nx) * sizeof(fix);
+}
+
+// The row gather's shared memory grows with nx: as many warps per block (at
+// most GATHER_WARPS) as fit in 200 KB, and the opt-in above the default
+// 48 KB per block.
 template <typename T>
 static cudaError_t setup_t(lbmd_ctx *ctx) {
-    const size_t smem = gather_smem_bytes<T>(ctx);
+    int warps = GATHER_WARPS;
+    while (warps > 1 && gather_smem_bytes<T>(ctx, warps) > (size_t)200 * 1024) --warps;
+    const size_t smem = gather_smem_bytes<T>(ctx, warps);
     if (smem > (size_t)200 * 1024) return cudaErrorInvalidValue;
+    ctx->gather_warps = warps;
     return cudaFuncSetAttribute(spread_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -448,16 +678,20 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
+    a.fd_nx = make_fastdiv((uint32_t)ctx->p.nx);
+    a.fd_ny = make_fastdiv((uint32_t)ctx->p.ny);
     a.np = ctx->np;
     a.zeta = (T)ctx->p.zeta;
     a.dt = (T)ctx->dt;
     a.half_dt = (T)(0.5 * ctx->dt);
     a.amp = (T)sqrt(2.0 * ctx->p.zeta * ctx->p.kT / ctx->dt);
+    a.neg_scale_dt = (T)ctx->dt * -P::SCALE;
     a.key0 = (uint32_t)(ctx->p.seed & 0xffffffffu);
     a.key1 = (uint32_t)(ctx->p.seed >> 32);
     a.lb_step = ctx->d_lb_step;
     a.n_sub = ctx->p.n_sub;
     a.substep = substep;
+    a.mig_par = (int)((ctx->lb_step * ctx->p.n_sub + substep) & 1);
     a.noisy = ctx->p.kT > 0.0 ? 1 : 0;
     a.variant = ctx->p.variant;
     a.row_start = ctx->row_start;
@@ -465,6 +699,9 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.migrant_slot = ctx->migrant_slot;
     a.migrant_count = ctx->migrant_count;
     a.np_cap = ctx->p.max_particles > 0 ? ctx->p.max_particles : 1;
+    a.occw = ctx->occw;
+    a.cact = static_cast<typename P::node4 *>(ctx->cact);
+    a.occ_words = active_words(ctx->p.nx);
     return a;
 }
 
@@ -489,8 +726,9 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     }
     if (B) {
         const int rows = (int)((int64_t)ctx->p.ny * ctx->p.nz);
-        const unsigned gblocks = (unsigned)((rows + GATHER_WARPS - 1) / GATHER_WARPS);
-        spread_rows_kernel<T><<<gblocks, 32 * GATHER_WARPS, gather_smem_bytes<T>(ctx), ctx->stream>>>(a, rows);
+        const int gw = ctx->gather_warps;
+        const unsigned gblocks = (unsigned)((rows + gw - 1) / gw);
+        spread_rows_kernel<T><<<gblocks, 32 * gw, gather_smem_bytes<T>(ctx, gw), ctx->stream>>>(a, rows);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         migrant_spread_kernel<T><<<ctx->sm_count, 256, 0, ctx->stream>>>(a);
         e = cudaGetLastError();
@@ -517,7 +755,8 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
     if (ctx->np > 0) {
         const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
         sort_count_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<const R4 *>(ctx->pos4[b]), ctx->np,
-                                                                ctx->p.nx, ctx->row_count, ctx->sort_rank);
+                                                                make_fastdiv((uint32_t)ctx->p.nx), ctx->row_count,
+                                                                ctx->sort_rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int n_chunks = (int)((rows + 1023) / 1024);
         sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
@@ -529,14 +768,53 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
             static_cast<const R4 *>(ctx->pos4[b]), static_cast<const R4 *>(ctx->vel4[b]),
             static_cast<const R4 *>(ctx->fcons4[b]), ctx->pid[b], static_cast<R4 *>(ctx->pos4[o]),
             static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]), ctx->pid[o], ctx->slot_of,
-            ctx->slot_row, ctx->row_start, ctx->sort_rank, ctx->np, ctx->p.nx, ctx->nb > 0 ? 1 : 0);
+            ctx->slot_row, ctx->row_start, ctx->sort_rank, ctx->np, make_fastdiv((uint32_t)ctx->p.nx),
+            ctx->nb > 0 ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ctx->pcur = o;
     return cudaSuccess;
 }
 
+template <typename T>
+static cudaError_t active_set_t(lbmd_ctx *ctx) {
+    const int64_t rows = (int64_t)ctx->p.ny * ctx->p.nz;
+    const int W = active_words(ctx->p.nx);
+    if (ctx->np == 0) return cudaMemsetAsync(ctx->occw, 0, (size_t)rows * W * sizeof(uint2), ctx->stream);
+    const unsigned blocks = (unsigned)((rows + GATHER_WARPS - 1) / GATHER_WARPS);
+    active_rows_kernel<T><<<blocks, 32 * GATHER_WARPS, GATHER_WARPS * W * sizeof(uint32_t), ctx->stream>>>(
+        static_cast<const typename Prec<T>::real4 *>(ctx->pos4[ctx->pcur]), ctx->row_start, ctx->p.nx,
+        make_fastdiv((uint32_t)ctx->p.ny), ctx->p.nz, W, ctx->occw, ctx->row_count, (int)rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int n_chunks = (int)((rows + 1023) / 1024);
+    sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    active_finalize_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, ctx->chunk_total, rows, ctx->occw, W);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t active_sync_t(lbmd_ctx *ctx) {
+    using N4 = typename Prec<T>::node4;
+    const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
+    active_sync_kernel<T><<<blocks, 256, 0, ctx->stream>>>(ctx->occw, static_cast<const N4 *>(ctx->cact),
+                                                           static_cast<N4 *>(ctx->node), ctx->N, ctx->p.nx,
+                                                           active_words(ctx->p.nx));
+    return cudaGetLastError();
+}
+
 }  // namespace lbmd
+
+cudaError_t launch_active_set(lbmd_ctx *ctx) {
+    if (ctx->p.variant != LBMD_VARIANT_B) return cudaSuccess;
+    return ctx->p.precision == LBMD_FP64 ? lbmd::active_set_t<double>(ctx) : lbmd::active_set_t<float>(ctx);
+}
+
+cudaError_t launch_active_sync(lbmd_ctx *ctx) {
+    if (ctx->p.variant != LBMD_VARIANT_B) return cudaSuccess;
+    return ctx->p.precision == LBMD_FP64 ? lbmd::active_sync_t<double>(ctx) : lbmd::active_sync_t<float>(ctx);
+}
 
 cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep) {
     return ctx->p.precision == LBMD_FP64 ? lbmd::md_substep_t<double>(ctx, substep)
