@@ -74,7 +74,10 @@ __device__ __forceinline__ float centred16(uint32_t h, float) {
 }
 __device__ __forceinline__ double centred16(uint32_t h, double) { return (double)h - 32767.5; }
 
-template <typename T, typename S>
+// RELAX_FULL: gamma_bulk = gamma_ghost = 0 (the default reading), so the
+// bulk and ghost modes relax fully, m'_k = m^eq_k exactly, and their moments
+// m_k need not be computed (gamma (m - m^eq) is +-0 for finite m).
+template <typename T, typename S, bool RELAX_FULL>
 __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T Fy, T Fz, const LbArgs<T, S> &a,
                                         uint32_t node, uint32_t step) {
     T inv_rho, sr;
@@ -122,6 +125,10 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
     mp[3] = jz + Fz;
 #pragma unroll
     for (int k = 4; k < Q; ++k) {
+        if (RELAX_FULL && (k == 4 || k >= 10)) {
+            mp[k] = meq[k];
+            continue;
+        }
         const T gk = k == 4 ? a.gamma_bulk : (k <= 9 ? a.gamma_shear : a.gamma_ghost);
         mp[k] = meq[k] + gk * (m[k] - meq[k]);
     }
@@ -181,7 +188,7 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
 // a run-time (warp-uniform) flag rather than a template parameter: both
 // variants then execute one compiled instruction sequence, so at m = 1 they
 // agree bit for bit, as the paper's algorithmic equivalence requires.
-template <typename T, typename S>
+template <typename T, typename S, bool RELAX_FULL>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(LbArgs<T, S> a) {
     using P = Prec<T>;
     using St = PopStore<S, T>;
@@ -216,7 +223,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
     Fx += a.g[0];
     Fy += a.g[1];
     Fz += a.g[2];
-    collide(f, rho, jx, jy, jz, Fx, Fy, Fz, a, r, (uint32_t)(*a.lb_step));
+    collide<T, S, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, r, (uint32_t)(*a.lb_step));
 
     const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
@@ -300,7 +307,10 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.noisy = ctx->co.noisy;
     a.variant = ctx->p.variant;
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
-    lb_collide_push<T, S><<<grid, block, 0, ctx->stream>>>(a);
+    if (ctx->co.gamma_bulk == 0.0 && ctx->co.gamma_ghost == 0.0)
+        lb_collide_push<T, S, true><<<grid, block, 0, ctx->stream>>>(a);
+    else
+        lb_collide_push<T, S, false><<<grid, block, 0, ctx->stream>>>(a);
     return cudaGetLastError();
 }
 
