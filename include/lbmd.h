@@ -210,6 +210,73 @@ lbmd_status lbmd_get_counts(lbmd_ctx *ctx, int64_t *n_particles, int64_t *n_bond
  * LBMD_ERR_CAPACITY, LBMD_ERR_CUDA (message in lbmd_last_error(NULL)). */
 lbmd_status lbmd_particle_sums_static(const double *vel, const double *mass, int64_t n, double *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched replicas.  Many independent periodic boxes advanced together: each
+ * replica r is a complete problem of its own (lattice dims, particles,
+ * friction zeta_r, m_r MD steps per LB step, variant, Philox key seed_r) and
+ * evolves exactly as a context created by lbmd_create with those parameters
+ * (shared: rho0, nu, nu_bulk, gamma_ghost, kT; no body force, no bonds).  The
+ * paper's temperature experiment (Sec. 4: particle temperature against zeta,
+ * m and dt in variants A and B) needs many such boxes.  Every replica makes
+ * one MD step per "tick" and its LB step after every m_r-th tick; the
+ * P = lcm(m_r) ticks of a period are captured once into a CUDA graph and
+ * replayed.  Block sizes are chosen by timing candidates on the batch
+ * (lbmd_batch_tuning).  Explicit friction is unstable for zeta dt / m >~ 2:
+ * a replica whose particle speed exceeds 1 (lattice units) or stops being
+ * finite is flagged unstable and frozen rather than clamped
+ * (lbmd_batch_unstable).
+ * ------------------------------------------------------------------------- */
+typedef struct lbmd_batch_params {
+    int32_t n_replicas;            /* R >= 1 */
+    const int32_t *dims;           /* 3R: nx, ny, nz of every replica, each in [2, 512] */
+    const int32_t *n_sub;          /* R: m_r >= 1; lcm over replicas <= 256 */
+    const int32_t *variant;        /* R: LBMD_VARIANT_A or LBMD_VARIANT_B */
+    const double *zeta;            /* R: friction coefficient, >= 0 */
+    const uint64_t *seed;          /* R: Philox key of the replica */
+    const int32_t *max_particles;  /* R: particle capacity of the replica */
+    int32_t precision;             /* LBMD_FP32 or LBMD_FP64 */
+    double rho0, nu, nu_bulk, gamma_ghost, kT; /* as in lbmd_params, shared */
+    void *stream;                  /* cudaStream_t (borrowed) or NULL: own stream */
+} lbmd_batch_params;
+
+typedef struct lbmd_batch lbmd_batch;
+
+/* Create the batch (arrays of the params are read during the call); fluid at
+ * rest in every replica; tunes the node kernels' block size (synchronising).
+ * Errors: LBMD_ERR_ARG, LBMD_ERR_OOM, LBMD_ERR_CUDA. */
+lbmd_status lbmd_batch_create(const lbmd_batch_params *params, lbmd_batch **out);
+lbmd_status lbmd_batch_destroy(lbmd_batch *b);
+/* Append n particles to replica r (ids continue from the replica's count;
+ * host arrays pos, vel of 3n doubles, mass of n or NULL for 1; synchronising).
+ * LBMD_ERR_CAPACITY beyond max_particles[r]. */
+lbmd_status lbmd_batch_add_particles(lbmd_batch *b, int32_t replica, int64_t n, const double *pos,
+                                     const double *vel, const double *mass);
+/* Advance every replica by md_steps MD steps (each makes its LB step after
+ * every m_r-th).  Enqueues only, except that the first call after particles
+ * were added tunes the particle kernels (synchronising). */
+lbmd_status lbmd_batch_run(lbmd_batch *b, int64_t md_steps);
+/* Per replica, 5 doubles: sum m v^2, sum m v (x, y, z), particle count
+ * (FP64 device reductions in a fixed order; synchronising). */
+lbmd_status lbmd_batch_kinetic(lbmd_batch *b, double *out);
+/* Per replica: 1 if flagged unstable (frozen since), else 0 (synchronising). */
+lbmd_status lbmd_batch_unstable(lbmd_batch *b, int32_t *out);
+/* Replica accessors, as the single-box ones (synchronising, FP64 host arrays,
+ * populations [i][r] of 19 N_r doubles, particles in id order). */
+lbmd_status lbmd_batch_get_populations(lbmd_batch *b, int32_t replica, double *out);
+/* only at the replica's cycle boundary (LBMD_ERR_SEQUENCE otherwise); recomputes
+ * its node field and clears its pending transfers */
+lbmd_status lbmd_batch_set_populations(lbmd_batch *b, int32_t replica, const double *in);
+lbmd_status lbmd_batch_get_particles(lbmd_batch *b, int32_t replica, double *pos, double *vel);
+lbmd_status lbmd_batch_get_counts(lbmd_batch *b, int32_t replica, int64_t *n_particles, int64_t *lb_step,
+                                  int64_t *md_step);
+/* The autotuner's choice and its timings of the 3 candidates (64, 128, 256):
+ * nodes per block of the LB kernels, threads per block of the particle
+ * kernels; lb_ms and particle_ms take 3 doubles each or NULL. */
+lbmd_status lbmd_batch_tuning(lbmd_batch *b, int32_t *nodes_per_block, int32_t *particle_block, double *lb_ms,
+                              double *particle_ms);
+void *lbmd_batch_stream(lbmd_batch *b);
+const char *lbmd_batch_last_error(lbmd_batch *b);
+
 /* The cudaStream_t the context enqueues on. */
 void *lbmd_stream(lbmd_ctx *ctx);
 

@@ -8,6 +8,7 @@
 // size is fixed per context, so the sums are bitwise reproducible.
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
+#include "particle_core.cuh"
 
 namespace lbmd {
 
@@ -202,26 +203,7 @@ __global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, type
     } else {
         src = pid[p];
     }
-    if (set_pos) {
-        const double L[3] = {(double)nx, (double)ny, (double)nz};
-        T fr[3];
-        int64_t cl[3];
-        for (int d = 0; d < 3; ++d) {
-            double x = pos[3 * src + d];
-            x -= L[d] * floor(x / L[d]);
-            if (x >= L[d]) x -= L[d];
-            double b = floor(x);
-            T f = (T)(x - b);
-            if (f >= T(1)) {  // rounding to the storage precision reached the next node
-                f = T(0);
-                b += 1.0;
-                if (b >= L[d]) b = 0.0;
-            }
-            fr[d] = f;
-            cl[d] = (int64_t)b;
-        }
-        pos4[p] = P::make_pos(fr[0], fr[1], fr[2], cl[0] + (int64_t)nx * (cl[1] + (int64_t)ny * cl[2]));
-    }
+    if (set_pos) pos4[p] = pos_from_double<T>(pos + 3 * src, nx, ny, nz);
     typename P::real4 V = vel4[p];
     if (set_vel) {
         V.x = (T)vel[3 * src + 0];

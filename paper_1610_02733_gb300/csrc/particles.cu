@@ -32,6 +32,7 @@
 // after moving to another cell) through the node field, as before.
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
+#include "particle_core.cuh"
 
 namespace lbmd {
 
@@ -62,47 +63,6 @@ struct PArgs {
     int64_t np_cap;
 };
 
-struct CellXYZ {
-    int x, y, z;
-};
-
-__device__ __forceinline__ CellXYZ cell_xyz(int64_t cell, const FastDiv &fnx, const FastDiv &fny) {
-    const uint32_t c = (uint32_t)cell;
-    const uint32_t row = fdiv(c, fnx);
-    CellXYZ r;
-    r.x = (int)(c - row * fnx.d);
-    r.z = (int)fdiv(row, fny);
-    r.y = (int)(row - (uint32_t)r.z * fny.d);
-    return r;
-}
-
-// The 8 corner nodes (k = ox + 2 oy + 4 oz) and trilinear weights of Eq. (5).
-template <typename T>
-__device__ __forceinline__ void corners(const CellXYZ &c, T fx, T fy, T fz, int nx, int ny, int nz, uint32_t idx[8],
-                                        T delta[8]) {
-    const int x1 = c.x + 1 == nx ? 0 : c.x + 1;
-    const int y1 = c.y + 1 == ny ? 0 : c.y + 1;
-    const int z1 = c.z + 1 == nz ? 0 : c.z + 1;
-    const int X[2] = {c.x, x1}, Y[2] = {c.y, y1}, Z[2] = {c.z, z1};
-    const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
-        idx[k] = (uint32_t)X[ox] + (uint32_t)nx * ((uint32_t)Y[oy] + (uint32_t)ny * (uint32_t)Z[oz]);
-        delta[k] = wx[ox] * wy[oy] * wz[oz];
-    }
-}
-
-// The 4 lattice rows (y, z) of the corners, q = oy + 2 oz (corners 2q, 2q+1).
-__device__ __forceinline__ void corner_rows(const CellXYZ &c, int ny, int nz, uint32_t rows[4]) {
-    const int y1 = c.y + 1 == ny ? 0 : c.y + 1;
-    const int z1 = c.z + 1 == nz ? 0 : c.z + 1;
-    rows[0] = (uint32_t)c.y + (uint32_t)ny * (uint32_t)c.z;
-    rows[1] = (uint32_t)y1 + (uint32_t)ny * (uint32_t)c.z;
-    rows[2] = (uint32_t)c.y + (uint32_t)ny * (uint32_t)z1;
-    rows[3] = (uint32_t)y1 + (uint32_t)ny * (uint32_t)z1;
-}
-
 // Variant B: the records of corners 2q, 2q+1 (nodes x0 and x0 + 1 of row
 // `row`): compact record of an active node, node field entry otherwise.
 template <typename T>
@@ -115,38 +75,6 @@ __device__ __forceinline__ void corner_pair(const PArgs<T> &a, uint32_t row, int
     const size_t r0 = (size_t)row * (uint32_t)a.nx;
     n0 = s0 >= 0 ? a.cact[s0] : a.node[r0 + x0];
     n1 = s1 >= 0 ? a.cact[s1] : a.node[r0 + x1];
-}
-
-// Move a fractional coordinate by d and carry whole cells into the index.
-template <typename T>
-__device__ __forceinline__ void advance(T &frac, int &c, T d, int n) {
-    T x = frac + d;
-    T s = floor(x);
-    x -= s;
-    if (x >= T(1)) {  // a tiny negative offset rounded up to the next node
-        x = T(0);
-        s += T(1);
-    }
-    int cn = c + (int)s;
-    if (cn < 0 || cn >= n) {  // crossed the periodic boundary
-        cn %= n;
-        if (cn < 0) cn += n;
-    }
-    frac = x;
-    c = cn;
-}
-
-// The transfer -delta_k Delta P of Eqs. (7), (8) in fixed point; every
-// spreading path computes it this way (sx = F_x neg_scale_dt etc., equal to
-// neg_scaled(dt F_x) because the scale is a power of two).
-template <typename T>
-__device__ __forceinline__ void spread_to(typename Prec<T>::node4 *field, const uint32_t idx[8], const T delta[8], T sx,
-                                          T sy, T sz) {
-    using P = Prec<T>;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        P::add_transfer(&field[idx[k]], P::to_fix_neg(delta[k], sx), P::to_fix_neg(delta[k], sy),
-                        P::to_fix_neg(delta[k], sz));
 }
 
 // The variant is a run-time flag (one instruction sequence for both
@@ -242,10 +170,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PAr
     }
 }
 
-__device__ __forceinline__ void fix_add(int32_t *a, int32_t v) { atomicAdd(a, v); }
-__device__ __forceinline__ void fix_add(long long *a, long long v) {
-    atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
-}
 
 // Variant B, atomic-free: one warp per node row (y, z), four rows per block,
 // rows in reverse order (the couple kernel touched the high rows last).  The

@@ -34,6 +34,9 @@ EXPORTS = (
     "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
     "lbmd_particle_sums_static",
+    "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add_particles", "lbmd_batch_run", "lbmd_batch_kinetic",
+    "lbmd_batch_unstable", "lbmd_batch_get_populations", "lbmd_batch_set_populations", "lbmd_batch_get_particles",
+    "lbmd_batch_get_counts", "lbmd_batch_tuning", "lbmd_batch_stream", "lbmd_batch_last_error",
 )
 
 
@@ -45,6 +48,15 @@ class LbmdParams(ct.Structure):
         ("gamma_ghost", ct.c_double), ("kT", ct.c_double), ("zeta", ct.c_double),
         ("body_force", ct.c_double * 3), ("seed", ct.c_uint64),
         ("max_particles", ct.c_int64), ("max_bonds", ct.c_int64), ("stream", ct.c_void_p),
+    ]
+
+
+class LbmdBatchParams(ct.Structure):
+    _fields_ = [
+        ("n_replicas", ct.c_int32), ("dims", ct.c_void_p), ("n_sub", ct.c_void_p), ("variant", ct.c_void_p),
+        ("zeta", ct.c_void_p), ("seed", ct.c_void_p), ("max_particles", ct.c_void_p), ("precision", ct.c_int32),
+        ("rho0", ct.c_double), ("nu", ct.c_double), ("nu_bulk", ct.c_double), ("gamma_ghost", ct.c_double),
+        ("kT", ct.c_double), ("stream", ct.c_void_p),
     ]
 
 
@@ -98,8 +110,25 @@ def load():
     L.lbmd_last_error.argtypes = [P]
     L.lbmd_status_string.restype = ct.c_char_p
     L.lbmd_status_string.argtypes = [ct.c_int]
+    i32 = ct.c_int32
+    L.lbmd_batch_create.argtypes = [ct.POINTER(LbmdBatchParams), ct.POINTER(ct.c_void_p)]
+    L.lbmd_batch_destroy.argtypes = [P]
+    L.lbmd_batch_add_particles.argtypes = [P, i32, ct.c_int64, P, P, P]
+    L.lbmd_batch_run.argtypes = [P, ct.c_int64]
+    L.lbmd_batch_kinetic.argtypes = [P, P]
+    L.lbmd_batch_unstable.argtypes = [P, P]
+    L.lbmd_batch_get_populations.argtypes = [P, i32, P]
+    L.lbmd_batch_set_populations.argtypes = [P, i32, P]
+    L.lbmd_batch_get_particles.argtypes = [P, i32, P, P]
+    L.lbmd_batch_get_counts.argtypes = [P, i32, i64p, i64p, i64p]
+    L.lbmd_batch_tuning.argtypes = [P, ct.POINTER(i32), ct.POINTER(i32), P, P]
+    L.lbmd_batch_stream.restype = ct.c_void_p
+    L.lbmd_batch_stream.argtypes = [P]
+    L.lbmd_batch_last_error.restype = ct.c_char_p
+    L.lbmd_batch_last_error.argtypes = [P]
     for name in EXPORTS:
-        if name not in ("lbmd_stream", "lbmd_last_error", "lbmd_status_string"):
+        if name not in ("lbmd_stream", "lbmd_last_error", "lbmd_status_string", "lbmd_batch_stream",
+                        "lbmd_batch_last_error"):
             getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -317,3 +346,129 @@ class LBMD:
     @property
     def stream(self) -> int:
         return load().lbmd_stream(self._h) or 0
+
+
+# ---------------------------------------------------------------------------
+# Batched replicas
+# ---------------------------------------------------------------------------
+def _bcheck(h, rc, what):
+    if rc != LBMD_OK:
+        L = load()
+        msg = L.lbmd_batch_last_error(h).decode(errors="replace")
+        err = LbmdError(rc, what)
+        err.args = ("%s failed: %s (status %d: %s)" % (what, msg, rc, L.lbmd_status_string(rc).decode()),)
+        raise err
+    return rc
+
+
+class Batch:
+    """Many independent replica boxes advanced together (``lbmd_batch_*``).
+
+    ``dims``: R x 3 lattice sizes; ``n_sub``, ``variant`` ("A"/"B" or 0/1),
+    ``zeta``, ``seed``, ``max_particles``: one per replica (scalars are
+    broadcast).  ``rho0``, ``nu``, ``nu_bulk``, ``gamma_ghost``, ``kT`` are
+    shared.  Replica r evolves as ``LBMD(*dims[r], n_sub=n_sub[r], ...,
+    seed=seed[r])`` would.
+    """
+
+    def __init__(self, dims, *, n_sub=1, variant="B", zeta=1.0, seed=1, max_particles=0, precision="fp32",
+                 rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0, gamma_ghost=0.0, kT=0.0, stream=None):
+        dims = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+        R = dims.shape[0]
+
+        def per(x, dtype):
+            a = np.asarray(x)
+            if a.ndim == 0:
+                a = np.full(R, a)
+            return np.ascontiguousarray(a, dtype=dtype).reshape(R)
+
+        vmap = {"A": VARIANT_A, "B": VARIANT_B, 0: VARIANT_A, 1: VARIANT_B}
+        if isinstance(variant, str) or np.asarray(variant).ndim == 0:
+            variant = [variant] * R
+        self.dims = dims
+        self.n_sub = per(n_sub, np.int32)
+        self.variant = np.array([vmap[v] for v in variant], dtype=np.int32)
+        self.zeta = per(zeta, np.float64)
+        self.seed = per(seed, np.uint64)
+        self.max_particles = per(max_particles, np.int32)
+        self.R = R
+        p = LbmdBatchParams()
+        p.n_replicas = R
+        p.dims, p.n_sub, p.variant = _ptr(self.dims), _ptr(self.n_sub), _ptr(self.variant)
+        p.zeta, p.seed, p.max_particles = _ptr(self.zeta), _ptr(self.seed), _ptr(self.max_particles)
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.rho0, p.nu, p.nu_bulk, p.gamma_ghost, p.kT = float(rho0), float(nu), float(nu_bulk), float(gamma_ghost), \
+            float(kT)
+        p.stream = stream
+        self._h = ct.c_void_p()
+        _bcheck(None, load().lbmd_batch_create(ct.byref(p), ct.byref(self._h)), "lbmd_batch_create")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lbmd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_nodes(self, r: int) -> int:
+        return int(np.prod(self.dims[r]))
+
+    def add_particles(self, r: int, pos, vel, mass=None):
+        pos = _f64(pos).reshape(-1, 3)
+        vel = _f64(vel).reshape(-1, 3)
+        m = None if mass is None else _f64(mass, pos.shape[0])
+        _bcheck(self._h, load().lbmd_batch_add_particles(self._h, int(r), pos.shape[0], _ptr(pos), _ptr(vel),
+                                                         None if m is None else _ptr(m)), "lbmd_batch_add_particles")
+
+    def run(self, md_steps: int):
+        _bcheck(self._h, load().lbmd_batch_run(self._h, int(md_steps)), "lbmd_batch_run")
+
+    def kinetic(self) -> np.ndarray:
+        """R x 5: sum m v^2, sum m v (3), particle count."""
+        out = np.empty(5 * self.R)
+        _bcheck(self._h, load().lbmd_batch_kinetic(self._h, _ptr(out)), "lbmd_batch_kinetic")
+        return out.reshape(self.R, 5)
+
+    def unstable(self) -> np.ndarray:
+        out = np.empty(self.R, dtype=np.int32)
+        _bcheck(self._h, load().lbmd_batch_unstable(self._h, _ptr(out)), "lbmd_batch_unstable")
+        return out
+
+    def populations(self, r: int) -> np.ndarray:
+        out = np.empty(19 * self.n_nodes(r))
+        _bcheck(self._h, load().lbmd_batch_get_populations(self._h, int(r), _ptr(out)), "lbmd_batch_get_populations")
+        return out.reshape(19, -1)
+
+    def set_populations(self, r: int, f):
+        f = _f64(f, 19 * self.n_nodes(r))
+        _bcheck(self._h, load().lbmd_batch_set_populations(self._h, int(r), _ptr(f)), "lbmd_batch_set_populations")
+
+    def counts(self, r: int) -> dict:
+        a, b, c = ct.c_int64(), ct.c_int64(), ct.c_int64()
+        _bcheck(self._h, load().lbmd_batch_get_counts(self._h, int(r), ct.byref(a), ct.byref(b), ct.byref(c)),
+                "lbmd_batch_get_counts")
+        return {"n_particles": a.value, "lb_step": b.value, "md_step": c.value}
+
+    def particles(self, r: int):
+        n = self.counts(r)["n_particles"]
+        pos, vel = np.empty(3 * max(n, 1)), np.empty(3 * max(n, 1))
+        if n:
+            _bcheck(self._h, load().lbmd_batch_get_particles(self._h, int(r), _ptr(pos), _ptr(vel)),
+                    "lbmd_batch_get_particles")
+        return pos[:3 * n].reshape(n, 3), vel[:3 * n].reshape(n, 3)
+
+    def tuning(self) -> dict:
+        nb, pb = ct.c_int32(), ct.c_int32()
+        lb, pt = np.zeros(3), np.zeros(3)
+        _bcheck(self._h, load().lbmd_batch_tuning(self._h, ct.byref(nb), ct.byref(pb), _ptr(lb), _ptr(pt)),
+                "lbmd_batch_tuning")
+        return {"nodes_per_block": nb.value, "particle_block": pb.value, "candidates": [64, 128, 256],
+                "lb_ms": lb.tolist(), "particle_ms": pt.tolist()}
+
+    @property
+    def stream(self) -> int:
+        return load().lbmd_batch_stream(self._h) or 0
