@@ -168,6 +168,92 @@ def _time_form(torch, lbmd, inputs, stream, precision, steps, pos, vel):
     return ms, lb_ms
 
 
+BATCH_REPLICAS, BATCH_MD_STEPS, BATCH_SAMPLE = 512, 2000, 10
+
+
+def _batched_replicas(torch, lbmd, inputs, stream, peak):
+    """The batched form: 512 independent replica boxes (cubic edges from
+    {12, 16, 24, 32}, 1-400 ideal particles, zeta in [0.5, 5], m in {1, 5,
+    10}, variants alternating A and B, kT = 1e-4, FP32), 2000 MD steps
+    replayed from the captured period graph, with every replica's particle
+    kinetic energy recorded on the device every 10 MD steps.  Reports the
+    throughput and the per-replica temperature drift (stable replicas), and
+    the replicas flagged unstable (explicit friction, zeta dt / m >~ 2)."""
+    import numpy as np
+
+    cfg = inputs.replica_configs(BATCH_REPLICAS, SEED)
+    R = BATCH_REPLICAS
+    b = lbmd.Batch(cfg["dims"], n_sub=cfg["n_sub"], variant=cfg["variant"], zeta=cfg["zeta"],
+                   seed=np.arange(R, dtype=np.uint64) + np.uint64(SEED * 1000), max_particles=cfg["n_particles"],
+                   precision="fp32", kT=KT, stream=stream.cuda_stream)
+    for r in range(R):
+        n = int(cfg["n_particles"][r])
+        b.add_particles(r, inputs.uniform_positions(n, cfg["dims"][r], SEED + r),
+                        inputs.maxwell_velocities(n, KT, SEED + r))
+    b.run(10)  # tunes the particle kernels and captures the period graph
+    n_samples = BATCH_MD_STEPS // BATCH_SAMPLE + 1
+    kin = torch.empty((n_samples, R, 5), dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.kinetic_device(kin[0].data_ptr())
+    for s in range(1, n_samples):
+        b.run(BATCH_SAMPLE)
+        b.kinetic_device(kin[s].data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    unstable = b.unstable().astype(bool)
+    k = kin.cpu().numpy()
+    stable = ~unstable
+    nodes = cfg["dims"].prod(axis=1).astype(np.float64)
+    node_updates = float((nodes * (BATCH_MD_STEPS // cfg["n_sub"]))[stable].sum())
+    psteps = float(cfg["n_particles"][stable].sum()) * BATCH_MD_STEPS
+    alg_bytes = LB_BYTES_PER_NODE * node_updates + PARTICLE_BYTES * psteps
+    # per-replica temperature T / kT over the run; excess = mean over the
+    # second half - 1, drift = least-squares slope over the second half per
+    # 1000 MD steps
+    T = k[:, :, 0] / (3.0 * np.maximum(k[:, :, 4], 1.0) * KT)
+    half = n_samples // 2
+    t = np.arange(n_samples)[half:] * BATCH_SAMPLE / 1000.0
+    excess = T[half:].mean(axis=0) - 1.0
+    slope = np.zeros(R)
+    if stable.any():
+        slope[stable] = np.polyfit(t, T[half:][:, stable], 1)[0]
+    zdt = cfg["zeta"] / cfg["n_sub"]
+    var = np.array(cfg["variant"])
+    bins = [(0.0, 0.25), (0.25, 0.5), (0.5, 1.0), (1.0, 2.0), (2.0, 10.0)]
+    temp = {}
+    for v in ("A", "B"):
+        sel = stable & (var == v)
+        w = cfg["n_particles"].astype(np.float64)
+        byb = {}
+        for lo, hi in bins:
+            m = sel & (zdt >= lo) & (zdt < hi)
+            if m.any():
+                byb["%g-%g" % (lo, hi)] = {"replicas": int(m.sum()),
+                                           "excess_T": round(float((excess[m] * w[m]).sum() / w[m].sum()), 4)}
+        temp[v] = {"replicas": int(sel.sum()),
+                   "excess_T_weighted": round(float((excess[sel] * w[sel]).sum() / w[sel].sum()), 4),
+                   "median_drift_per_1000_steps": round(float(np.median(slope[sel])), 4),
+                   "by_zeta_dt": byb}
+    tune = b.tuning()
+    b.close()
+    return {
+        "workload": "512 replica boxes, edges {12,16,24,32}, 1-400 ideal particles, zeta in [0.5, 5], "
+                    "m in {1,5,10}, variants A/B alternating, kT=1e-4, FP32, 2000 MD steps",
+        "value": round(node_updates / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+        "particle_substeps_per_s": float("%.4g" % (psteps / (ms * 1e-3))),
+        "ms_total": round(ms, 2), "lb_node_updates": node_updates,
+        "roofline_frac": round(alg_bytes / (ms * 1e-3) / 1e9 / peak, 4),
+        "graph_launches": BATCH_MD_STEPS // 10, "tuning": tune,
+        "unstable": {"count": int(unstable.sum()), "min_zeta_dt_unstable":
+                     round(float(zdt[unstable].min()), 3) if unstable.any() else None,
+                     "max_zeta_dt_stable": round(float(zdt[stable].max()), 3)},
+        "temperature": temp,
+    }
+
+
 def _touched_nodes(pos):
     """Distinct nodes at the corners of the particles' cells (exact)."""
     import numpy as np
@@ -327,6 +413,7 @@ def run_gpu(args):
                            "lb_step_speedup_vs_fp32": round(lb_avg_ms / lb_ms, 3),
                            "lb_roofline_frac": round(lb_bytes / (lb_ms * 1e-3) / 1e9 / peak, 4)}
         line["precision_forms"] = forms
+        line["batched_replicas"] = _batched_replicas(torch, lbmd, inputs, stream, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -416,7 +503,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the reduced-precision storage forms and the batched replicas")
     ap.add_argument("--edge", type=int, default=256, help="lattice edge (profiling of smaller cases)")
     ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="non-cubic lattice (profiling of smaller cases with 256-node rows)")

@@ -258,6 +258,9 @@ lbmd_status lbmd_batch_run(lbmd_batch *b, int64_t md_steps);
 /* Per replica, 5 doubles: sum m v^2, sum m v (x, y, z), particle count
  * (FP64 device reductions in a fixed order; synchronising). */
 lbmd_status lbmd_batch_kinetic(lbmd_batch *b, double *out);
+/* The same 5 R doubles written to caller-owned device memory in stream order
+ * on the batch's stream (no synchronisation; for sampling during a run). */
+lbmd_status lbmd_batch_kinetic_device(lbmd_batch *b, double *out);
 /* Per replica: 1 if flagged unstable (frozen since), else 0 (synchronising). */
 lbmd_status lbmd_batch_unstable(lbmd_batch *b, int32_t *out);
 /* Replica accessors, as the single-box ones (synchronising, FP64 host arrays,

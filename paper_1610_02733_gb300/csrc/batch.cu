@@ -937,15 +937,22 @@ lbmd_status lbmd_batch_run(lbmd_batch *b, int64_t md_steps) {
     return LBMD_OK;
 }
 
-lbmd_status lbmd_batch_kinetic(lbmd_batch *b, double *out) {
+lbmd_status lbmd_batch_kinetic_device(lbmd_batch *b, double *out) {
     if (!b || !out) return LBMD_ERR_ARG;
     if (b->precision == LBMD_FP64)
         batch_kinetic_kernel<double><<<b->R, 256, 0, b->stream>>>(static_cast<BRep<double> *>(b->rep),
-                                                                   static_cast<D4 *>(b->vel4), b->kin);
+                                                                   static_cast<D4 *>(b->vel4), out);
     else
         batch_kinetic_kernel<float><<<b->R, 256, 0, b->stream>>>(static_cast<BRep<float> *>(b->rep),
-                                                                  static_cast<float4 *>(b->vel4), b->kin);
+                                                                  static_cast<float4 *>(b->vel4), out);
     BCK(b, cudaGetLastError());
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_batch_kinetic(lbmd_batch *b, double *out) {
+    if (!b || !out) return LBMD_ERR_ARG;
+    lbmd_status s = lbmd_batch_kinetic_device(b, b->kin);
+    if (s != LBMD_OK) return s;
     BCK(b, cudaMemcpyAsync(out, b->kin, (size_t)b->R * 5 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     return LBMD_OK;

@@ -67,3 +67,20 @@ def uniform(shape, lo: float, hi: float, seed: int, stream: int = 5) -> np.ndarr
     """Plain uniform numbers in [lo, hi) (e.g. small momentum transfers)."""
     g = _rng(seed, stream)
     return lo + (hi - lo) * g.random(shape)
+
+
+def replica_configs(n_replicas: int, seed: int, edges=(12, 16, 24, 32), max_particles: int = 400,
+                    zeta_range=(0.5, 5.0), n_subs=(1, 5, 10)):
+    """Parameters of a batch of independent replica boxes: cubic edge drawn
+    uniformly from ``edges``, particle count uniform in [1, max_particles],
+    friction uniform in ``zeta_range``, MD steps per LB step drawn from
+    ``n_subs``; variants alternate A, B.  Returns a dict of per-replica arrays."""
+    g = _rng(seed, 11)
+    edge = np.asarray(edges)[g.integers(0, len(edges), n_replicas)]
+    return {
+        "dims": np.stack([edge, edge, edge], axis=1).astype(np.int32),
+        "n_particles": g.integers(1, max_particles + 1, n_replicas).astype(np.int32),
+        "zeta": g.uniform(zeta_range[0], zeta_range[1], n_replicas),
+        "n_sub": np.asarray(n_subs)[g.integers(0, len(n_subs), n_replicas)].astype(np.int32),
+        "variant": ["A" if r % 2 == 0 else "B" for r in range(n_replicas)],
+    }

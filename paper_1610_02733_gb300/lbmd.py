@@ -35,6 +35,7 @@ EXPORTS = (
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
     "lbmd_particle_sums_static",
     "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add_particles", "lbmd_batch_run", "lbmd_batch_kinetic",
+    "lbmd_batch_kinetic_device",
     "lbmd_batch_unstable", "lbmd_batch_get_populations", "lbmd_batch_set_populations", "lbmd_batch_get_particles",
     "lbmd_batch_get_counts", "lbmd_batch_tuning", "lbmd_batch_stream", "lbmd_batch_last_error",
 )
@@ -116,6 +117,7 @@ def load():
     L.lbmd_batch_add_particles.argtypes = [P, i32, ct.c_int64, P, P, P]
     L.lbmd_batch_run.argtypes = [P, ct.c_int64]
     L.lbmd_batch_kinetic.argtypes = [P, P]
+    L.lbmd_batch_kinetic_device.argtypes = [P, P]
     L.lbmd_batch_unstable.argtypes = [P, P]
     L.lbmd_batch_get_populations.argtypes = [P, i32, P]
     L.lbmd_batch_set_populations.argtypes = [P, i32, P]
@@ -432,6 +434,11 @@ class Batch:
         out = np.empty(5 * self.R)
         _bcheck(self._h, load().lbmd_batch_kinetic(self._h, _ptr(out)), "lbmd_batch_kinetic")
         return out.reshape(self.R, 5)
+
+    def kinetic_device(self, out_ptr: int):
+        """Stream-ordered: 5 R doubles into caller-owned device memory."""
+        _bcheck(self._h, load().lbmd_batch_kinetic_device(self._h, ct.c_void_p(out_ptr)),
+                "lbmd_batch_kinetic_device")
 
     def unstable(self) -> np.ndarray:
         out = np.empty(self.R, dtype=np.int32)
