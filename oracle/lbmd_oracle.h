@@ -64,6 +64,19 @@ void orc_collide_node(const orc_state *s, const double f[19], const double F[3],
                       double fout[19]);
 void orc_trilinear(const orc_state *s, const double R[3], int64_t corner[8], double delta[8]);
 
+/* Forward-mode derivative (tangent) of the oracle's step for the mean
+ * particle drag along x, ideal particles of mass 1 (lbmd_tangent.c). */
+typedef struct tan_state tan_state;
+tan_state *tan_create(const orc_params *p);
+void tan_destroy(tan_state *t);
+int tan_set_particles(tan_state *t, int64_t np, const double *pos, const double *vel, const double *dpos,
+                      double dzeta);
+int tan_md_substep(tan_state *t);
+int tan_lb_step(tan_state *t);
+void tan_drag(const tan_state *t, double out[2]);
+void tan_get_populations(const tan_state *t, double *val, double *der);
+void tan_get_particles(const tan_state *t, double *pos, double *vel, double *dpos, double *dvel);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbmd_oracle.so")
 _SRC = os.path.join(_HERE, "lbmd_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lbmd_tangent.c")]
 
 ORC_OK = 0
 ORC_ERR_SEQUENCE = -4
@@ -30,11 +31,11 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     hdr = os.path.join(_HERE, "lbmd_oracle.h")
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+            and os.path.getmtime(_LIB_PATH) >= max([os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(hdr)])):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp] + _SRCS + ["-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -87,6 +88,15 @@ def lib():
         L.orc_modes.argtypes = [dp, dp]
         L.orc_collide_node.argtypes = [P, dp, dp, ct.c_uint32, ct.c_uint32, dp]
         L.orc_trilinear.argtypes = [P, dp, ct.POINTER(ct.c_int64), dp]
+        L.tan_create.restype = P
+        L.tan_create.argtypes = [ct.POINTER(OrcParams)]
+        L.tan_destroy.argtypes = [P]
+        L.tan_set_particles.argtypes = [P, ct.c_int64, dp, dp, dp, ct.c_double]
+        L.tan_md_substep.argtypes = [P]
+        L.tan_lb_step.argtypes = [P]
+        L.tan_drag.argtypes = [P, dp]
+        L.tan_get_populations.argtypes = [P, dp, dp]
+        L.tan_get_particles.argtypes = [P, dp, dp, dp, dp]
     return _lib
 
 
@@ -273,3 +283,71 @@ class Oracle:
         delta = np.zeros(8)
         lib().orc_trilinear(self._h, _dp(R), corner.ctypes.data_as(ct.POINTER(ct.c_int64)), _dp(delta))
         return corner, delta
+
+
+class Tangent:
+    """Forward-mode derivative of the oracle's step (``lbmd_tangent.c``):
+    the same state as ``Oracle`` carried as (value, derivative along one
+    direction of zeta and the initial positions).  Ideal particles, mass 1.
+    ``drag()`` returns (S, dS) with S the sum of the coupling force F_x over
+    the MD steps done and the particles."""
+
+    def __init__(self, nx, ny, nz, *, n_sub=1, variant=1, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
+                 gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1):
+        p = OrcParams()
+        p.nx, p.ny, p.nz, p.n_sub, p.variant = nx, ny, nz, n_sub, variant
+        p.rho0, p.nu, p.nu_bulk, p.gamma_ghost, p.kT, p.zeta = rho0, nu, nu_bulk, gamma_ghost, kT, zeta
+        for a in range(3):
+            p.body_force[a] = body_force[a]
+        p.seed = seed
+        self.n_sub = n_sub
+        self.n_nodes = nx * ny * nz
+        self.np = 0
+        self._h = lib().tan_create(ct.byref(p))
+        if not self._h:
+            raise ValueError("bad tangent parameters")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_particles(self, pos, vel, dpos=None, dzeta=0.0):
+        pos = _f64(pos).reshape(-1)
+        vel = _f64(vel).reshape(-1)
+        self.np = pos.size // 3
+        d = None if dpos is None else _f64(dpos).reshape(-1)
+        lib().tan_set_particles(self._h, self.np, _dp(pos), _dp(vel), None if d is None else _dp(d), float(dzeta))
+
+    def md_substep(self):
+        lib().tan_md_substep(self._h)
+
+    def lb_step(self):
+        lib().tan_lb_step(self._h)
+
+    def cycle(self, k: int = 1):
+        for _ in range(int(k)):
+            for _ in range(self.n_sub):
+                self.md_substep()
+            self.lb_step()
+
+    def drag(self):
+        out = np.zeros(2)
+        lib().tan_drag(self._h, _dp(out))
+        return float(out[0]), float(out[1])
+
+    def populations(self):
+        v = np.empty(19 * self.n_nodes)
+        d = np.empty(19 * self.n_nodes)
+        lib().tan_get_populations(self._h, _dp(v), _dp(d))
+        return v.reshape(19, -1), d.reshape(19, -1)
+
+    def particles(self):
+        n = max(self.np, 1)
+        a, b, c, e = (np.empty(3 * n) for _ in range(4))
+        lib().tan_get_particles(self._h, _dp(a), _dp(b), _dp(c), _dp(e))
+        k = 3 * self.np
+        return a[:k].reshape(-1, 3), b[:k].reshape(-1, 3), c[:k].reshape(-1, 3), e[:k].reshape(-1, 3)
