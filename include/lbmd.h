@@ -280,6 +280,46 @@ lbmd_status lbmd_batch_tuning(lbmd_batch *b, int32_t *nodes_per_block, int32_t *
 void *lbmd_batch_stream(lbmd_batch *b);
 const char *lbmd_batch_last_error(lbmd_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Adjoint (reverse-mode derivative) of the coupled step, variant B, for the
+ * mean particle drag along x:
+ *     L = (1 / (K m N_p)) sum over K cycles of m MD steps and N_p particles of
+ *         the coupling force F_x of Eq. (4),
+ * with respect to zeta and the initial particle positions.  The random
+ * numbers are fixed by their Philox counters (kT = 0 or kT > 0), so the map
+ * is deterministic; it is piecewise smooth (kinks where a particle crosses a
+ * cell face).  The forward pass starts from the fluid at rest (f_i = w_i rho0)
+ * and keeps the populations and particles of every LB step; the backward pass
+ * recomputes each cycle's m MD steps from its checkpoint and runs the
+ * hand-written adjoint kernels (transposed collision and streaming, moments,
+ * interpolation, friction, velocity Verlet and transfers).  Ideal particles
+ * of mass 1.
+ * ------------------------------------------------------------------------- */
+typedef struct lbmd_adjoint_params {
+    int32_t nx, ny, nz;     /* periodic lattice, each >= 2 */
+    int32_t n_sub;          /* m MD steps per LB step, >= 1 */
+    int32_t n_particles;    /* N_p */
+    int32_t n_cycles;       /* K LB steps of the forward pass */
+    int32_t precision;      /* LBMD_FP32 or LBMD_FP64 */
+    int32_t pad_;
+    double rho0, nu, nu_bulk, gamma_ghost, kT; /* as in lbmd_params */
+    double body_force[3];   /* uniform force density on the fluid */
+    uint64_t seed;          /* Philox key */
+    void *stream;           /* cudaStream_t (borrowed) or NULL: own stream */
+} lbmd_adjoint_params;
+
+typedef struct lbmd_adjoint lbmd_adjoint;
+
+lbmd_status lbmd_adjoint_create(const lbmd_adjoint_params *params, lbmd_adjoint **out);
+lbmd_status lbmd_adjoint_destroy(lbmd_adjoint *a);
+/* Forward pass with friction zeta from N_p initial positions and velocities
+ * (host arrays of 3 N_p doubles); writes L.  Synchronising. */
+lbmd_status lbmd_adjoint_forward(lbmd_adjoint *a, double zeta, const double *pos0, const double *vel0, double *loss);
+/* dL/dzeta and dL/dR0 (host array of 3 N_p doubles) of the last forward pass;
+ * LBMD_ERR_SEQUENCE before any forward pass.  Synchronising. */
+lbmd_status lbmd_adjoint_backward(lbmd_adjoint *a, double *dloss_dzeta, double *dloss_dpos0);
+const char *lbmd_adjoint_last_error(lbmd_adjoint *a);
+
 /* The cudaStream_t the context enqueues on. */
 void *lbmd_stream(lbmd_ctx *ctx);
 

@@ -38,6 +38,8 @@ EXPORTS = (
     "lbmd_batch_kinetic_device",
     "lbmd_batch_unstable", "lbmd_batch_get_populations", "lbmd_batch_set_populations", "lbmd_batch_get_particles",
     "lbmd_batch_get_counts", "lbmd_batch_tuning", "lbmd_batch_stream", "lbmd_batch_last_error",
+    "lbmd_adjoint_create", "lbmd_adjoint_destroy", "lbmd_adjoint_forward", "lbmd_adjoint_backward",
+    "lbmd_adjoint_last_error",
 )
 
 
@@ -58,6 +60,15 @@ class LbmdBatchParams(ct.Structure):
         ("zeta", ct.c_void_p), ("seed", ct.c_void_p), ("max_particles", ct.c_void_p), ("precision", ct.c_int32),
         ("rho0", ct.c_double), ("nu", ct.c_double), ("nu_bulk", ct.c_double), ("gamma_ghost", ct.c_double),
         ("kT", ct.c_double), ("stream", ct.c_void_p),
+    ]
+
+
+class LbmdAdjointParams(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("n_sub", ct.c_int32),
+        ("n_particles", ct.c_int32), ("n_cycles", ct.c_int32), ("precision", ct.c_int32), ("pad_", ct.c_int32),
+        ("rho0", ct.c_double), ("nu", ct.c_double), ("nu_bulk", ct.c_double), ("gamma_ghost", ct.c_double),
+        ("kT", ct.c_double), ("body_force", ct.c_double * 3), ("seed", ct.c_uint64), ("stream", ct.c_void_p),
     ]
 
 
@@ -128,9 +139,15 @@ def load():
     L.lbmd_batch_stream.argtypes = [P]
     L.lbmd_batch_last_error.restype = ct.c_char_p
     L.lbmd_batch_last_error.argtypes = [P]
+    L.lbmd_adjoint_create.argtypes = [ct.POINTER(LbmdAdjointParams), ct.POINTER(ct.c_void_p)]
+    L.lbmd_adjoint_destroy.argtypes = [P]
+    L.lbmd_adjoint_forward.argtypes = [P, ct.c_double, P, P, dp]
+    L.lbmd_adjoint_backward.argtypes = [P, dp, P]
+    L.lbmd_adjoint_last_error.restype = ct.c_char_p
+    L.lbmd_adjoint_last_error.argtypes = [P]
     for name in EXPORTS:
         if name not in ("lbmd_stream", "lbmd_last_error", "lbmd_status_string", "lbmd_batch_stream",
-                        "lbmd_batch_last_error"):
+                        "lbmd_batch_last_error", "lbmd_adjoint_last_error"):
             getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -479,3 +496,88 @@ class Batch:
     @property
     def stream(self) -> int:
         return load().lbmd_batch_stream(self._h) or 0
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the coupled step (mean particle drag along x)
+# ---------------------------------------------------------------------------
+def _acheck(h, rc, what):
+    if rc != LBMD_OK:
+        L = load()
+        msg = L.lbmd_adjoint_last_error(h).decode(errors="replace")
+        err = LbmdError(rc, what)
+        err.args = ("%s failed: %s (status %d: %s)" % (what, msg, rc, L.lbmd_status_string(rc).decode()),)
+        raise err
+    return rc
+
+
+class Adjoint:
+    """``lbmd_adjoint_*``: L(zeta, R0) = mean particle drag F_x over K cycles
+    of m MD steps (variant B, fluid starting at rest, ideal particles of mass
+    1), its value (``forward``) and its gradient (``backward``) from the
+    hand-written adjoint kernels."""
+
+    def __init__(self, nx, ny, nz, *, n_particles, n_cycles, n_sub=10, precision="fp64", rho0=1.0, nu=1.0 / 6.0,
+                 nu_bulk=-1.0, gamma_ghost=0.0, kT=0.0, body_force=(0.0, 0.0, 0.0), seed=1, stream=None):
+        p = LbmdAdjointParams()
+        p.nx, p.ny, p.nz, p.n_sub = int(nx), int(ny), int(nz), int(n_sub)
+        p.n_particles, p.n_cycles = int(n_particles), int(n_cycles)
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.rho0, p.nu, p.nu_bulk, p.gamma_ghost, p.kT = float(rho0), float(nu), float(nu_bulk), float(gamma_ghost), \
+            float(kT)
+        for a in range(3):
+            p.body_force[a] = float(body_force[a])
+        p.seed = int(seed)
+        p.stream = stream
+        self.n_particles = int(n_particles)
+        self._h = ct.c_void_p()
+        _acheck(None, load().lbmd_adjoint_create(ct.byref(p), ct.byref(self._h)), "lbmd_adjoint_create")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lbmd_adjoint_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, zeta: float, pos0, vel0) -> float:
+        pos0 = _f64(pos0, 3 * self.n_particles)
+        vel0 = _f64(vel0, 3 * self.n_particles)
+        out = ct.c_double()
+        _acheck(self._h, load().lbmd_adjoint_forward(self._h, float(zeta), _ptr(pos0), _ptr(vel0), ct.byref(out)),
+                "lbmd_adjoint_forward")
+        return out.value
+
+    def backward(self):
+        """(dL/dzeta, dL/dR0 as an N_p x 3 array) of the last forward pass."""
+        dz = ct.c_double()
+        dpos = np.zeros(3 * max(self.n_particles, 1))
+        _acheck(self._h, load().lbmd_adjoint_backward(self._h, ct.byref(dz), _ptr(dpos)), "lbmd_adjoint_backward")
+        return dz.value, dpos[:3 * self.n_particles].reshape(-1, 3)
+
+
+def drag_function(adjoint: Adjoint, vel0):
+    """A ``torch.autograd.Function`` L(zeta, R0) backed by ``adjoint``: its
+    forward runs the forward pass, its backward the adjoint kernels.  zeta is
+    a 0-d tensor, R0 an N_p x 3 tensor (float64, CPU); vel0 is fixed."""
+    import torch
+
+    vel0 = np.ascontiguousarray(vel0, dtype=np.float64)
+
+    class _Drag(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, zeta, pos0):
+            loss = adjoint.forward(float(zeta), pos0.detach().cpu().numpy(), vel0)
+            return torch.tensor(loss, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            dz, dpos = adjoint.backward()
+            g = float(grad)
+            return torch.tensor(g * dz, dtype=torch.float64), torch.from_numpy(g * dpos)
+
+    return _Drag.apply
