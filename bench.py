@@ -254,6 +254,42 @@ def _batched_replicas(torch, lbmd, inputs, stream, peak):
     }
 
 
+def _adjoint_form(torch, lbmd, inputs):
+    """The adjoint form: L = mean particle drag along x over 200 MD steps
+    (32^3, 64 ideal particles, zeta = 1.5, m = 10, body force 1e-5 along x,
+    kT = 1e-4 with fixed Philox counters), forward pass with a checkpoint per
+    LB step and the hand-written backward pass, FP32, with the FP64 gradients
+    as the accuracy reference."""
+    import numpy as np
+
+    shape, n, cycles, zeta = (32, 32, 32), 64, 20, 1.5
+    pos = inputs.uniform_positions(n, shape, SEED + 7)
+    vel = inputs.maxwell_velocities(n, KT, SEED + 7)
+    out = {"workload": "32^3 D3Q19, 64 ideal particles, zeta=1.5, m=10, 200 MD steps, body force 1e-5, kT=1e-4, "
+                       "variant B; L = mean particle drag along x; gradients w.r.t. zeta and initial positions"}
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        ad = lbmd.Adjoint(*shape, n_particles=n, n_cycles=cycles, n_sub=10, precision=prec, kT=KT,
+                          body_force=(1e-5, 0.0, 0.0), seed=SEED)
+        ad.forward(zeta, pos, vel)  # warm-up
+        ad.backward()
+        t0 = time.perf_counter()
+        L = ad.forward(zeta, pos, vel)
+        t1 = time.perf_counter()
+        dz, dpos = ad.backward()
+        t2 = time.perf_counter()
+        grads[prec] = (L, dz, dpos)
+        out[prec] = {"forward_ms": round((t1 - t0) * 1e3, 3), "backward_ms": round((t2 - t1) * 1e3, 3),
+                     "loss": L, "dL_dzeta": dz, "dL_dR0_norm": float(np.linalg.norm(dpos))}
+        ad.close()
+    L64, z64, p64 = grads["fp64"]
+    L32, z32, p32 = grads["fp32"]
+    out["fp32_vs_fp64"] = {"loss_rel": float(abs(L32 - L64) / abs(L64)), "dL_dzeta_rel": float(abs(z32 - z64) / abs(z64)),
+                           "dL_dR0_rel": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))}
+    out["accuracy"] = "FP64 gradients match the oracle tangent to 1e-9 and FP64 finite differences (tests)"
+    return out
+
+
 def _touched_nodes(pos):
     """Distinct nodes at the corners of the particles' cells (exact)."""
     import numpy as np
@@ -414,6 +450,7 @@ def run_gpu(args):
                            "lb_roofline_frac": round(lb_bytes / (lb_ms * 1e-3) / 1e9 / peak, 4)}
         line["precision_forms"] = forms
         line["batched_replicas"] = _batched_replicas(torch, lbmd, inputs, stream, peak)
+        line["adjoint"] = _adjoint_form(torch, lbmd, inputs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -462,7 +499,7 @@ def _oracle_sample(edge: int, cycles: int):
 
 
 def cpu_baseline():
-    edge, cycles = 128, 2
+    edge, cycles = 128, 8
     dt, nodes, n = _oracle_sample(edge, cycles)
     return {"value": round(nodes * cycles / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "particle_substeps_per_s": float("%.4g" % (n * N_SUB * cycles / dt)),
@@ -504,7 +541,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the reduced-precision storage forms and the batched replicas")
+                    help="skip the reduced-precision, batched and adjoint forms")
     ap.add_argument("--edge", type=int, default=256, help="lattice edge (profiling of smaller cases)")
     ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="non-cubic lattice (profiling of smaller cases with 256-node rows)")
