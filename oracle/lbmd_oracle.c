@@ -1,6 +1,6 @@
 /*
  * lbmd_oracle.c -- plain FP64 CPU oracle for the fluctuating D3Q19 lattice
- * Boltzmann fluid with dissipative point-particle coupling, variants A and B,
+ * Boltzmann fluid with dissipative point-particle coupling, variants A, B and C,
  * of Tretyakov & Duenweg, "An improved dissipative coupling scheme for a
  * system of Molecular Dynamics particles interacting with a Lattice Boltzmann
  * fluid" (arXiv:1610.02733).
@@ -200,7 +200,7 @@ static void compute_moments(orc_state *s) {
 
 orc_state *orc_create(const orc_params *p) {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->n_sub < 1) return NULL;
-    if (p->variant != 0 && p->variant != 1) return NULL;
+    if (p->variant < 0 || p->variant > 2) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     if (!s) return NULL;
     s->p = *p;
@@ -391,7 +391,9 @@ void orc_trilinear(const orc_state *s, const double R[3], int64_t corner[8], dou
 
 /* Momentum density at node r as seen by the particles.  Variant A: the value
  * of the last LB update (Sec. 3, "variant A").  Variant B: that value plus
- * every transfer made since, so the node velocities follow each MD step. */
+ * every transfer made since, so the node velocities follow each MD step.
+ * Variant C: the momentum of the populations, which every MD step updates
+ * (orc_forcing_update). */
 static void node_momentum_seen(const orc_state *s, int64_t r, double jout[3]) {
     for (int a = 0; a < 3; ++a) {
         jout[a] = s->jst[3 * r + a];
@@ -420,6 +422,48 @@ static void compute_bond_forces(orc_state *s) {
         }
     }
     s->fcons_valid = 1;
+}
+
+/* Variant C (Sec. 4): after every MD step the populations themselves take
+ * the momentum transfer F = J_acc of that step through the forcing part
+ * Delta'_i of the collision operator alone -- no relaxation, no noise, no
+ * streaming.  In moment space (the forcing of orc_collide_node): mass
+ * unchanged, momentum + F, stress modes + (1 + gamma) times the symmetric
+ * products of u and F with the local streaming velocity u = (j + F/2)/rho of
+ * the current populations, ghost modes unchanged.  The node moments are then
+ * recomputed from the populations and J_acc restarts from zero. */
+static void orc_forcing_update(orc_state *s) {
+    int64_t n = s->n_nodes;
+    double gb = s->gam[4], gs = s->gam[5];
+    for (int64_t r = 0; r < n; ++r) {
+        const double *F = s->jacc + 3 * r;
+        if (F[0] == 0.0 && F[1] == 0.0 && F[2] == 0.0) continue;
+        double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < Q; ++i) {
+            double fi = s->f[i * n + r];
+            rho += fi;
+            for (int a = 0; a < 3; ++a) j[a] += fi * C[i][a];
+        }
+        double u[3];
+        for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
+        double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+        double dm[Q];
+        for (int k = 0; k < Q; ++k) dm[k] = 0.0;
+        for (int a = 0; a < 3; ++a) dm[1 + a] = F[a];
+        dm[4] = (1.0 + gb) * uF;
+        dm[5] = (1.0 + gs) * (3.0 * u[0] * F[0] - uF);
+        dm[6] = (1.0 + gs) * (u[1] * F[1] - u[2] * F[2]);
+        dm[7] = (1.0 + gs) * 0.5 * (u[0] * F[1] + u[1] * F[0]);
+        dm[8] = (1.0 + gs) * 0.5 * (u[0] * F[2] + u[2] * F[0]);
+        dm[9] = (1.0 + gs) * 0.5 * (u[1] * F[2] + u[2] * F[1]);
+        for (int i = 0; i < Q; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < Q; ++k) acc += s->e[k][i] * dm[k] / s->b[k];
+            s->f[i * n + r] += s->w[i] * acc;
+        }
+    }
+    compute_moments(s);
+    memset(s->jacc, 0, sizeof(double) * 3 * n);
 }
 
 /* One MD step of length dt = tau_LB / m for every particle (Sec. 3).
@@ -487,6 +531,7 @@ int orc_md_substep(orc_state *s) {
                     s->jacc[3 * corner[8 * p + k] + a] -= delta[8 * p + k] * dP[3 * p + a];
         free(corner); free(delta); free(dP);
     }
+    if (s->p.variant == 2) orc_forcing_update(s);
     s->md_step += 1;
     s->sub_done += 1;
     return ORC_OK;

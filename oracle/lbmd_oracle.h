@@ -19,7 +19,7 @@ enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_OOM = -3, ORC_ERR_SEQUENCE = -4 };
 typedef struct orc_params {
     int32_t nx, ny, nz;   /* periodic lattice, nodes per axis, a = 1 */
     int32_t n_sub;        /* m = tau_LB / dt, MD steps per LB step */
-    int32_t variant;      /* 0 = variant A, 1 = variant B (Sec. 3) */
+    int32_t variant;      /* 0 = variant A, 1 = variant B (Sec. 3), 2 = variant C (Sec. 4) */
     int32_t pad_;
     double rho0;          /* initial fluid density */
     double nu;            /* kinematic shear viscosity */

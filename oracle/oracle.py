@@ -142,7 +142,7 @@ class Oracle:
     """The oracle's state: populations, pending momentum transfer, particles.
 
     Parameters follow the C-ABI of the GPU library: lattice units (a = 1,
-    tau_LB = 1), ``n_sub`` = m MD steps per LB step, ``variant`` 0 = A, 1 = B.
+    tau_LB = 1), ``n_sub`` = m MD steps per LB step, ``variant`` 0 = A, 1 = B, 2 = C.
     """
 
     def __init__(self, nx, ny, nz, *, n_sub=1, variant=1, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
