@@ -58,7 +58,11 @@ typedef enum lbmd_status {
     LBMD_ERR_CAPACITY = -6   /* more particles or bonds than reserved */
 } lbmd_status;
 
-enum { LBMD_VARIANT_A = 0, LBMD_VARIANT_B = 1 };
+/* Variants of the coupling: A and B (Sec. 3); C (Sec. 4): after every MD step
+ * the populations at the touched nodes take that step's momentum transfer
+ * through the forcing part of the collision (local streaming velocity
+ * u = (j + F/2)/rho, no relaxation, noise or streaming). */
+enum { LBMD_VARIANT_A = 0, LBMD_VARIANT_B = 1, LBMD_VARIANT_C = 2 };
 /* Storage and arithmetic.  FP32 / FP64: populations, node field and particles
  * in that precision.  FP16_DEV / BF16_DEV: populations stored as deviations
  * f_i - w_i rho0 in FP16 / BF16 (round to nearest), everything else and all
@@ -69,7 +73,7 @@ enum { LBMD_FP32 = 0, LBMD_FP64 = 1, LBMD_FP16_DEV = 2, LBMD_BF16_DEV = 3 };
 typedef struct lbmd_params {
     int32_t nx, ny, nz;    /* lattice nodes per axis (periodic), each >= 2 */
     int32_t n_sub;         /* m = tau_LB / dt: MD steps per LB step, >= 1 (Sec. 3) */
-    int32_t variant;       /* LBMD_VARIANT_A or LBMD_VARIANT_B (Sec. 3) */
+    int32_t variant;       /* LBMD_VARIANT_A, _B (Sec. 3) or _C (Sec. 4) */
     int32_t precision;     /* LBMD_FP32, LBMD_FP64, LBMD_FP16_DEV or LBMD_BF16_DEV */
     double rho0;           /* initial fluid density; the fluid starts at rest */
     double nu;             /* kinematic shear viscosity, > 0 */

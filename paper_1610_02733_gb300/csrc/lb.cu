@@ -7,6 +7,9 @@
 // force density F = J_acc / tau_LB + g; the post-collision populations are
 // pushed to the neighbours r + c_i in the other buffer.
 //
+// forcing_update_kernel (variant C): after every MD step, the transfer of
+// that step enters the populations through the forcing part of the collision.
+//
 // node_moments_kernel: one thread per node.  Recomputes rho* and j* of the
 // freshly streamed populations and writes the node field that the MD steps of
 // the next LB cycle read (and, in variant B, update); in variant B also the
@@ -118,6 +121,62 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Variant C (Sec. 4): the momentum transfer F = J_acc of the MD step just
+// done enters the populations through the forcing part of the collision
+// alone: mass unchanged, momentum + F, stress modes + (1 + gamma) times the
+// symmetric products of u = (j + F/2)/rho and F (as in collide()), ghost
+// modes unchanged; then the node record is recomputed from the populations
+// and J_acc is cleared.  Nodes without a transfer are left as they are.
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) forcing_update_kernel(S *__restrict__ f, typename Prec<T>::node4 *node,
+                                                             typename Prec<T>::node4 *jacc, int64_t N, T rho0,
+                                                             T gamma_bulk, T gamma_shear) {
+    using P = Prec<T>;
+    using St = PopStore<S, T>;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const typename P::node4 J = jacc[r];
+    if (P::jx_of(J) == 0 && P::jy_of(J) == 0 && P::jz_of(J) == 0) return;
+    const T Fx = P::from_fix(P::jx_of(J)), Fy = P::from_fix(P::jy_of(J)), Fz = P::from_fix(P::jz_of(J));
+    T fl[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fl[i] = St::load(f + (int64_t)i * N + r, T(WEIGHT(i)) * rho0);
+    T rho, jx, jy, jz;
+    node_moments(fl, rho, jx, jy, jz);
+    const T ir = T(1) / rho;
+    const T ux = (jx + T(0.5) * Fx) * ir, uy = (jy + T(0.5) * Fy) * ir, uz = (jz + T(0.5) * Fz) * ir;
+    const T uF = ux * Fx + uy * Fy + uz * Fz;
+    T dm[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) dm[k] = T(0);
+    dm[1] = Fx;
+    dm[2] = Fy;
+    dm[3] = Fz;
+    const T fb = T(1) + gamma_bulk, fs = T(1) + gamma_shear;
+    dm[4] = fb * uF;
+    dm[5] = fs * (T(3) * ux * Fx - uF);
+    dm[6] = fs * (uy * Fy - uz * Fz);
+    dm[7] = fs * T(0.5) * (ux * Fy + uy * Fx);
+    dm[8] = fs * T(0.5) * (ux * Fz + uz * Fx);
+    dm[9] = fs * T(0.5) * (uy * Fz + uz * Fy);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 1; k <= 9; ++k) {
+            const int e = EMODE(k, i);
+            if (e != 0) acc += T(e) * dm[k] * T(INV_BNORM(k));
+        }
+        fl[i] += T(WEIGHT(i)) * acc;
+        St::store(f + (int64_t)i * N + r, fl[i], T(WEIGHT(i)) * rho0);
+    }
+    node_moments(fl, rho, jx, jy, jz);
+    node[r] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    typename P::node4 zero;
+    zero.x = zero.y = zero.z = zero.w = 0;
+    jacc[r] = zero;
+}
+
 template <typename T, typename S>
 __global__ void init_equilibrium_kernel(S *f, int64_t N, T rho0) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,6 +239,16 @@ static cudaError_t node_moments_t(lbmd_ctx *ctx, bool count_step) {
 }
 
 template <typename T, typename S>
+static cudaError_t forcing_update_t(lbmd_ctx *ctx) {
+    const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
+    forcing_update_kernel<T, S><<<blocks, 256, 0, ctx->stream>>>(
+        static_cast<S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
+        static_cast<typename Prec<T>::node4 *>(ctx->jacc), ctx->N, (T)ctx->p.rho0, (T)ctx->co.gamma_bulk,
+        (T)ctx->co.gamma_shear);
+    return cudaGetLastError();
+}
+
+template <typename T, typename S>
 static cudaError_t init_equilibrium_t(lbmd_ctx *ctx) {
     const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
     init_equilibrium_kernel<T, S><<<blocks, 256, 0, ctx->stream>>>(static_cast<S *>(ctx->f[ctx->cur]), ctx->N,
@@ -214,3 +283,5 @@ cudaError_t launch_node_moments(lbmd_ctx *ctx, bool count_step) {
 }
 
 cudaError_t launch_init_equilibrium(lbmd_ctx *ctx) { return LBMD_DISPATCH_POPS(ctx, lbmd::init_equilibrium_t, ctx); }
+
+cudaError_t launch_forcing_update(lbmd_ctx *ctx) { return LBMD_DISPATCH_POPS(ctx, lbmd::forcing_update_t, ctx); }

@@ -89,8 +89,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if ((int64_t)p->nx * p->ny * p->nz > (int64_t)0x7fffffff)
         return fail(nullptr, LBMD_ERR_ARG, "more than 2^31-1 nodes");
     if (p->n_sub < 1) return fail(nullptr, LBMD_ERR_ARG, "n_sub must be >= 1");
-    if (p->variant != LBMD_VARIANT_A && p->variant != LBMD_VARIANT_B)
-        return fail(nullptr, LBMD_ERR_ARG, "variant must be A (0) or B (1)");
+    if (p->variant != LBMD_VARIANT_A && p->variant != LBMD_VARIANT_B && p->variant != LBMD_VARIANT_C)
+        return fail(nullptr, LBMD_ERR_ARG, "variant must be A (0), B (1) or C (2)");
     if (p->precision < LBMD_FP32 || p->precision > LBMD_BF16_DEV)
         return fail(nullptr, LBMD_ERR_ARG, "precision must be FP32, FP64, FP16_DEV or BF16_DEV");
     if (!(p->rho0 > 0) || !(p->nu > 0) || !is_finite_d(p->rho0) || !is_finite_d(p->nu))
@@ -164,7 +164,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {&ctx->f[0], (size_t)19 * N * pop_size(ctx)},
         {&ctx->f[1], (size_t)19 * N * pop_size(ctx)},
         {&ctx->node, (size_t)N * node_bytes},
-        {&ctx->jacc, p->variant == LBMD_VARIANT_A ? (size_t)N * node_bytes : 0},
+        {&ctx->jacc, p->variant != LBMD_VARIANT_B ? (size_t)N * node_bytes : 0},
         {&ctx->pos4[0], (size_t)maxp * 4 * rs},
         {&ctx->pos4[1], (size_t)maxp * 4 * rs},
         {&ctx->vel4[0], (size_t)maxp * 4 * rs},

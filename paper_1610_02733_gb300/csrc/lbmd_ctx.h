@@ -7,8 +7,8 @@
 //               node: rho* as bits and the momentum density j in fixed point.
 //               Variant A: j* of the last LB update (frozen during the MD
 //               steps).  Variant B: j* plus every transfer since.
-//   jacc        variant A only: the transfers since the last LB step, fixed
-//               point, 4 words per node (x, y, z, unused).
+//   jacc        variants A and C: the transfers since the last LB step (C:
+//               since the last MD step), fixed point, 4 words per node.
 //   Particles live in "slots".  Once per LB step they are re-ordered by
 //   lattice row (y, z) of their cell, so that the particles a warp handles
 //   touch neighbouring nodes (cache locality of the corner reads and
@@ -96,6 +96,7 @@ struct lbmd_ctx {
 // the launch status.
 cudaError_t launch_lb_step(lbmd_ctx *ctx);
 cudaError_t launch_node_moments(lbmd_ctx *ctx, bool count_step);
+cudaError_t launch_forcing_update(lbmd_ctx *ctx);
 cudaError_t launch_init_equilibrium(lbmd_ctx *ctx);
 cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep);
 cudaError_t launch_bond_forces_only(lbmd_ctx *ctx);

@@ -158,7 +158,7 @@ __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const
         dst[4 * t + 3] = (double)P::from_fix(P::jz_of(n));
         return;
     }
-    if (variant == LBMD_VARIANT_A) {
+    if (variant != LBMD_VARIANT_B) {
         const typename P::node4 J = jacc[r];
         dst[3 * t + 0] = (double)P::from_fix(P::jx_of(J));
         dst[3 * t + 1] = (double)P::from_fix(P::jy_of(J));
@@ -295,7 +295,7 @@ cudaError_t launch_node_field_to_double(lbmd_ctx *ctx, int64_t first, int64_t co
 }
 
 cudaError_t launch_clear_transfer(lbmd_ctx *ctx) {
-    if (ctx->p.variant != LBMD_VARIANT_A) return cudaSuccess;
+    if (ctx->p.variant == LBMD_VARIANT_B) return cudaSuccess;
     if (ctx->p.precision == LBMD_FP64)
         clear_transfer_kernel<double><<<nblocks(ctx->N), 256, 0, ctx->stream>>>(
             static_cast<Prec<double>::node4 *>(ctx->jacc), ctx->N);

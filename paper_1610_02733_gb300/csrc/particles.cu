@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PAr
     a.vel4[p] = V;
     if (BONDS || a.variant == LBMD_VARIANT_B) a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
 
-    if (a.variant == LBMD_VARIANT_A) {
-        // Newton's third law, Eqs. (7), (8): straight into J_acc
+    if (a.variant != LBMD_VARIANT_B) {
+        // Newton's third law, Eqs. (7), (8): straight into J_acc (variant C
+        // then moves it into the populations, forcing_update_kernel)
         uint32_t idx[8];
         T delta[8];
         corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
@@ -648,6 +649,7 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (ctx->p.variant == LBMD_VARIANT_C) return launch_forcing_update(ctx);
     if (B) {
         const int rows = (int)((int64_t)ctx->p.ny * ctx->p.nz);
         const int gw = ctx->gather_warps;

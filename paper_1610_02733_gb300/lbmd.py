@@ -23,7 +23,7 @@ LBMD_ERR_OOM = -3
 LBMD_ERR_SEQUENCE = -4
 LBMD_ERR_NONFINITE = -5
 LBMD_ERR_CAPACITY = -6
-VARIANT_A, VARIANT_B = 0, 1
+VARIANT_A, VARIANT_B, VARIANT_C = 0, 1, 2
 FP32, FP64, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_DEV}
 
@@ -242,7 +242,7 @@ class LBMD:
     """
 
     def __init__(self, nx, ny, nz, *, variant="B", precision="fp32", **kw):
-        v = {"A": VARIANT_A, "B": VARIANT_B, 0: VARIANT_A, 1: VARIANT_B}[variant]
+        v = {"A": VARIANT_A, "B": VARIANT_B, "C": VARIANT_C, 0: VARIANT_A, 1: VARIANT_B, 2: VARIANT_C}[variant]
         pr = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.params = make_params(nx, ny, nz, variant=v, precision=pr, **kw)
         self.shape = (int(nx), int(ny), int(nz))

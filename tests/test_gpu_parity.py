@@ -9,7 +9,7 @@ m = 1, repeated runs, graph replay) must match bit for bit.
 import numpy as np
 import pytest
 
-from gpu_common import assert_pops_close, assert_vec_close, pair, random_state
+from gpu_common import W, assert_pops_close, assert_vec_close, pair, random_state
 from paper_1610_02733_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -45,7 +45,7 @@ def test_one_lb_step(precision, shape, kT):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("variant", ["A", "B"])
+@pytest.mark.parametrize("variant", ["A", "B", "C"])
 @pytest.mark.parametrize("shape", [(8, 8, 8), (10, 6, 14)])
 def test_md_substeps_then_lb_step(precision, variant, shape):
     n_sub, n = 4, 40
@@ -145,7 +145,7 @@ def test_repeat_runs_and_graph_replay_are_bitwise_identical():
         np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("variant", ["A", "B"])
+@pytest.mark.parametrize("variant", ["A", "B", "C"])
 def test_momentum_conservation_every_md_step_fp64(variant):
     shape, n = (8, 8, 8), 30
     o, g = pair(shape, precision="fp64", variant=variant, n_sub=5, kT=1e-3, zeta=2.0, seed=5, max_particles=n)
@@ -205,3 +205,22 @@ def test_temperature_statistics_match_oracle():
             To.append(o.observables()["kT_particles"])
             Tg.append(g.observables()["kT_particles"])
     assert abs(np.mean(Tg) / np.mean(To) - 1.0) < 0.005
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev"])
+def test_variant_c_several_cycles(precision):
+    # variant C over several cycles, with thermal noise, in the plain and a
+    # reduced-precision storage form (populations updated after every MD step)
+    shape, n_sub, n = (12, 10, 8), 5, 30
+    o, g = pair(shape, precision=precision, variant="C", n_sub=n_sub, kT=1e-4, zeta=1.0, seed=21, max_particles=n)
+    pos, vel = inputs.uniform_positions(n, shape, 8), inputs.maxwell_velocities(n, 1e-4, 8)
+    o.add_particles(pos, vel)
+    g.add_particles(pos, vel)
+    o.cycle(3)
+    g.run_cycles(3)
+    err = np.abs(g.populations() - o.populations()) / W[:, None]
+    assert float(err.max()) <= {"fp32": 1e-5, "fp16dev": 2e-4}[precision]
+    if precision == "fp32":
+        _, vg = g.particles()
+        _, vo = o.particles()
+        assert_vec_close(vg, vo, "fp32", "velocities")
