@@ -254,6 +254,31 @@ def _batched_replicas(torch, lbmd, inputs, stream, peak):
     }
 
 
+def _variant_costs(torch, lbmd, inputs, stream, pos, vel, steps, ms_b):
+    """Cycle time of variants A and C on the same workload against B (the
+    paper's comparison of the extra effort of B and C over A, Sec. 4)."""
+    out = {}
+    for v in ("A", "C"):
+        sim = lbmd.LBMD(*SHAPE, variant=v, precision="fp32", n_sub=N_SUB, kT=KT, zeta=ZETA, seed=SEED,
+                        max_particles=N_PARTICLES, stream=stream.cuda_stream)
+        sim.add_particles(pos, vel)
+        sim.run_cycles(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        sim.run_cycles(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[v] = {"ms_per_cycle": round(ms, 4),
+                  "value": round(SHAPE[0] * SHAPE[1] * SHAPE[2] / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS"}
+        sim.close()
+    out["B"] = {"ms_per_cycle": round(ms_b, 4)}
+    ma = out["A"]["ms_per_cycle"]
+    out["extra_vs_A"] = {"B": round(ms_b / ma - 1.0, 4), "C": round(out["C"]["ms_per_cycle"] / ma - 1.0, 4)}
+    return out
+
+
 def _adjoint_form(torch, lbmd, inputs):
     """The adjoint form: L = mean particle drag along x over 200 MD steps
     (32^3, 64 ideal particles, zeta = 1.5, m = 10, body force 1e-5 along x,
@@ -449,6 +474,7 @@ def run_gpu(args):
                            "lb_step_speedup_vs_fp32": round(lb_avg_ms / lb_ms, 3),
                            "lb_roofline_frac": round(lb_bytes / (lb_ms * 1e-3) / 1e9 / peak, 4)}
         line["precision_forms"] = forms
+        line["variants"] = _variant_costs(torch, lbmd, inputs, stream, pos0, vel0, min(args.steps, 30), ms_per_step)
         line["batched_replicas"] = _batched_replicas(torch, lbmd, inputs, stream, peak)
         line["adjoint"] = _adjoint_form(torch, lbmd, inputs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -541,7 +567,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the reduced-precision, batched and adjoint forms")
+                    help="skip the reduced-precision, variant A/C, batched and adjoint forms")
     ap.add_argument("--edge", type=int, default=256, help="lattice edge (profiling of smaller cases)")
     ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="non-cubic lattice (profiling of smaller cases with 256-node rows)")

@@ -10,10 +10,14 @@
 // forcing_update_kernel (variant C): after every MD step, the transfer of
 // that step enters the populations through the forcing part of the collision.
 //
-// node_moments_kernel: one thread per node.  Recomputes rho* and j* of the
-// freshly streamed populations and writes the node field that the MD steps of
-// the next LB cycle read (and, in variant B, update); in variant B also the
-// compact record of every active node.
+// The post-stream moments rho* and j* of the freshly streamed populations
+// (the node field the MD steps of the next LB cycle read and, in variant B,
+// update, plus the compact record of every active node) are fused into
+// lb_collide_push: a block computes them for the node row two planes back,
+// once the 27 blocks around that row have pushed (per-block flags tagged with
+// the LB step); moments_rest_kernel covers the rows the dataflow cannot
+// reach.  node_moments_kernel computes them on their own (creation, replaced
+// populations).
 #include "lb_core.cuh"
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
@@ -27,9 +31,14 @@ struct LbArgs {
     T rho0;  // reference density of the deviation storage
     typename Prec<T>::node4 *node;
     typename Prec<T>::node4 *jacc;
-    const uint2 *occw;                     // variant B: active nodes
+    const uint2 *occw;                     // variant B: active nodes of this cycle
     const typename Prec<T>::node4 *cact;   // variant B: their compact records
+    const uint2 *occw_new;                 // variant B: active nodes of the next cycle
+    typename Prec<T>::node4 *cact_new;     // ... whose records the fused moments write
     int occ_words;
+    // fused post-stream moments (dataflow between collide blocks)
+    uint32_t *blk_done;
+    int32_t *missed, *missed_list;
     int nx, ny, nz;
     int64_t N;
     T gamma_bulk, gamma_shear, gamma_ghost;
@@ -41,17 +50,49 @@ struct LbArgs {
     int variant;
 };
 
+// Post-stream moments rho*, j* (Eqs. (1), (2)) of node (x, y, t): the node
+// record and, for an active node of the coming cycle (variant B), its
+// compact record.  The populations are read through L2 (ld.global.cg): they
+// were written by other blocks of the same kernel.
+template <typename T, typename S>
+__device__ __forceinline__ void node_moments_at(const S *f, typename Prec<T>::node4 *node, const uint2 *occw,
+                                                typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx,
+                                                int ny, T rho0, int x, int y, int t) {
+    using P = Prec<T>;
+    using St = PopStore<S, T>;
+    const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)t);
+    T fl[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fl[i] = St::load_cg(f + (size_t)i * N + r, T(WEIGHT(i)) * rho0);
+    T rho, jx, jy, jz;
+    node_moments(fl, rho, jx, jy, jz);
+    const typename P::node4 rec = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    node[r] = rec;
+    if (occw) {
+        const int sl = active_slot(occw[((size_t)y + (size_t)ny * t) * occ_words + (x >> 5)], x);
+        if (sl >= 0) cact[sl] = rec;
+    }
+}
+
+// The moments of node row (block) b of the collide grid are computed, once
+// its 27 neighbouring blocks (planes t - 1..t + 1) have pushed, by the block
+// FUSE_LAG planes further on; rows of the first plane and of the last
+// FUSE_LAG planes (whose neighbourhood wraps to later planes), and any row
+// whose wait ran out, are left to moments_rest_kernel.
+constexpr int FUSE_LAG = 2;
+constexpr int FUSE_SPIN = 1 << 20;  // polls of 64 ns at most, then the row is left to the fallback
+
 // One thread per node; grid (ceil(nx / blockDim.x), ny, nz).  The variant is
 // a run-time (warp-uniform) flag rather than a template parameter: both
 // variants then execute one compiled instruction sequence, so at m = 1 they
 // agree bit for bit, as the paper's algorithmic equivalence requires.
+// Collide node (x, y, z) and push its post-collision populations to the
+// neighbours r + c_i in the other buffer.
 template <typename T, typename S, bool RELAX_FULL>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(LbArgs<T, S> a) {
+__device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, int y, int z,
+                                                  unsigned long long step) {
     using P = Prec<T>;
     using St = PopStore<S, T>;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.nx) return;
-    const int y = blockIdx.y, z = blockIdx.z;
     const uint32_t r = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     T f[Q];
 #pragma unroll
@@ -80,7 +121,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
     Fx += a.g[0];
     Fy += a.g[1];
     Fz += a.g[2];
-    collide<T, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, r, (uint32_t)(*a.lb_step));
+    collide<T, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, r, (uint32_t)step);
 
     const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
@@ -94,31 +135,96 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
     }
 }
 
+template <typename T, typename S, bool RELAX_FULL>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(LbArgs<T, S> a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    // the step counter, read before the fallback kernel advances it; it also
+    // tags the blocks that have pushed
+    const unsigned long long step = *a.lb_step;
+    if (x < a.nx) collide_push_node<T, S, RELAX_FULL>(a, x, y, z, step);
+
+    // fused post-stream moments: publish this block, then compute the
+    // moments of the block FUSE_LAG planes back once its neighbourhood is in
+    const uint32_t gx = gridDim.x, gy = gridDim.y;
+    const uint32_t epoch = (uint32_t)step + 1u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&a.blk_done[blockIdx.x + gx * (blockIdx.y + gy * blockIdx.z)], epoch);
+    }
+    const int t = z - FUSE_LAG;
+    if (t < 1) return;
+    __shared__ int s_ok;
+    if (threadIdx.x < 32) {
+        bool ok = true;
+        if (threadIdx.x < 27) {
+            const int dx = (int)threadIdx.x % 3 - 1, dy = ((int)threadIdx.x / 3) % 3 - 1;
+            const int dz = (int)threadIdx.x / 9 - 1;
+            const uint32_t xb = (blockIdx.x + gx + dx) % gx, yb = (uint32_t)((y + a.ny + dy) % a.ny);
+            const volatile uint32_t *flag = a.blk_done + xb + gx * (yb + gy * (uint32_t)(t + dz));
+            int polls = 0;
+            while (*flag != epoch) {
+                if (++polls > FUSE_SPIN) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_ok = ok ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (threadIdx.x == 0) a.missed_list[atomicAdd(a.missed, 1)] = (int32_t)(blockIdx.x + gx * (y + gy * t));
+        return;
+    }
+    if (x < a.nx)
+        node_moments_at<T, S>(a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, a.N, a.nx, a.ny, a.rho0, x, y, t);
+}
+
+// The moments the collide kernel left: node rows of plane 0 and of the last
+// FUSE_LAG planes, and the rows whose wait ran out; then the LB step counter
+// advances.
+template <typename T, typename S>
+__global__ void __launch_bounds__(256)
+    moments_rest_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
+                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, int nz, T rho0,
+                        const int32_t *missed, const int32_t *missed_list, unsigned long long *lb_step) {
+    const int gx = (nx + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int rows = gx * ny;
+    // boundary planes: 0 and max(1, nz - FUSE_LAG) .. nz - 1
+    const int first_tail = nz - FUSE_LAG > 1 ? nz - FUSE_LAG : 1;
+    const int n_planes = 1 + (nz - first_tail);
+    const int n_boundary = n_planes * rows;
+    const int total = n_boundary + *missed;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        int b;
+        if (i < n_boundary) {
+            const int k = i / rows;
+            const int plane = k == 0 ? 0 : first_tail + (k - 1);
+            b = i - k * rows + plane * rows;
+        } else {
+            b = missed_list[i - n_boundary];
+        }
+        const int xb = b % gx, rest = b / gx, y = rest % ny, t = rest / ny;
+        const int x = xb * (int)blockDim.x + (int)threadIdx.x;
+        if (x < nx) node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, x, y, t);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *lb_step += 1ull;
+}
+
 template <typename T, typename S>
 __global__ void __launch_bounds__(256)
     node_moments_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
-                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, T rho0,
-                        unsigned long long *lb_step, int count_step) {
-    using P = Prec<T>;
-    using St = PopStore<S, T>;
+                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, T rho0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (count_step && x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *lb_step += 1ull;
     if (x >= nx) return;
-    // planes in reverse order: the LB kernel wrote the high planes last, so
-    // they are the ones still in L2
-    const uint32_t z = gridDim.z - 1 - blockIdx.z;
-    const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)blockIdx.y + (uint32_t)ny * z);
-    T fl[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fl[i] = St::load(f + (size_t)i * N + r, T(WEIGHT(i)) * rho0);
-    T rho, jx, jy, jz;
-    node_moments(fl, rho, jx, jy, jz);
-    const typename P::node4 rec = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
-    node[r] = rec;
-    if (occw) {
-        const int sl = active_slot(occw[((size_t)blockIdx.y + (size_t)ny * z) * occ_words + (x >> 5)], x);
-        if (sl >= 0) cact[sl] = rec;
-    }
+    node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, x, blockIdx.y, blockIdx.z);
 }
 
 // Variant C (Sec. 4): the momentum transfer F = J_acc of the MD step just
@@ -202,9 +308,15 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.rho0 = (T)ctx->p.rho0;
     a.node = static_cast<typename Prec<T>::node4 *>(ctx->node);
     a.jacc = static_cast<typename Prec<T>::node4 *>(ctx->jacc);
-    a.occw = ctx->occw;
-    a.cact = static_cast<const typename Prec<T>::node4 *>(ctx->cact);
+    const bool B = ctx->p.variant == LBMD_VARIANT_B;
+    a.occw = B ? active_words_now(ctx) : nullptr;
+    a.cact = static_cast<const typename Prec<T>::node4 *>(B ? active_records_now(ctx) : nullptr);
+    a.occw_new = B ? active_words_next(ctx) : nullptr;
+    a.cact_new = static_cast<typename Prec<T>::node4 *>(B ? active_records_next(ctx) : nullptr);
     a.occ_words = active_words(ctx->p.nx);
+    a.blk_done = ctx->blk_done;
+    a.missed = ctx->lb_missed;
+    a.missed_list = ctx->missed_list;
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
@@ -220,21 +332,31 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.noisy = ctx->co.noisy;
     a.variant = ctx->p.variant;
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
+    cudaError_t e = cudaMemsetAsync(ctx->lb_missed, 0, sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) return e;
     if (ctx->co.gamma_bulk == 0.0 && ctx->co.gamma_ghost == 0.0)
         lb_collide_push<T, S, true><<<grid, block, 0, ctx->stream>>>(a);
     else
         lb_collide_push<T, S, false><<<grid, block, 0, ctx->stream>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the moments the collide kernel left, on the new populations
+    moments_rest_kernel<T, S><<<2 * ctx->sm_count, block, 0, ctx->stream>>>(
+        a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, ctx->N, ctx->p.nx, ctx->p.ny, ctx->p.nz, a.rho0,
+        ctx->lb_missed, ctx->missed_list, ctx->d_lb_step);
     return cudaGetLastError();
 }
 
+// node field (and the current active nodes' records) of the current
+// populations, outside the LB step (creation, replaced populations)
 template <typename T, typename S>
-static cudaError_t node_moments_t(lbmd_ctx *ctx, bool count_step) {
+static cudaError_t node_moments_t(lbmd_ctx *ctx) {
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
     node_moments_kernel<T, S><<<grid, block, 0, ctx->stream>>>(
         static_cast<const S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
-        B ? ctx->occw : nullptr, static_cast<typename Prec<T>::node4 *>(ctx->cact), active_words(ctx->p.nx), ctx->N,
-        ctx->p.nx, ctx->p.ny, (T)ctx->p.rho0, ctx->d_lb_step, count_step ? 1 : 0);
+        B ? active_words_now(ctx) : nullptr,
+        static_cast<typename Prec<T>::node4 *>(B ? active_records_now(ctx) : nullptr),
+        active_words(ctx->p.nx), ctx->N, ctx->p.nx, ctx->p.ny, (T)ctx->p.rho0);
     return cudaGetLastError();
 }
 
@@ -266,21 +388,20 @@ static cudaError_t init_equilibrium_t(lbmd_ctx *ctx) {
      : (ctx)->p.precision == LBMD_BF16_DEV ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
                                            : FN<float, float>(__VA_ARGS__))
 
-// One LB update: collide and stream, re-order the particles by row, rebuild
-// the active nodes (variant B) and recompute the node field (and the active
-// nodes' compact records) from the new populations.
+// One LB update: re-order the particles by row and build the active nodes of
+// the coming cycle (variant B; the particles do not move during the LB
+// step), then collide and stream with the post-stream moments fused in
+// (node field and the new active nodes' compact records).
 cudaError_t launch_lb_step(lbmd_ctx *ctx) {
-    cudaError_t e = LBMD_DISPATCH_POPS(ctx, lbmd::lb_step_t, ctx);
+    cudaError_t e = launch_sort_particles(ctx);
     if (e != cudaSuccess) return e;
-    ctx->cur ^= 1;
-    if ((e = launch_sort_particles(ctx)) != cudaSuccess) return e;
     if ((e = launch_active_set(ctx)) != cudaSuccess) return e;
-    return launch_node_moments(ctx, true);
+    if ((e = LBMD_DISPATCH_POPS(ctx, lbmd::lb_step_t, ctx)) != cudaSuccess) return e;
+    ctx->cur ^= 1;
+    return cudaSuccess;
 }
 
-cudaError_t launch_node_moments(lbmd_ctx *ctx, bool count_step) {
-    return LBMD_DISPATCH_POPS(ctx, lbmd::node_moments_t, ctx, count_step);
-}
+cudaError_t launch_node_moments(lbmd_ctx *ctx, bool) { return LBMD_DISPATCH_POPS(ctx, lbmd::node_moments_t, ctx); }
 
 cudaError_t launch_init_equilibrium(lbmd_ctx *ctx) { return LBMD_DISPATCH_POPS(ctx, lbmd::init_equilibrium_t, ctx); }
 

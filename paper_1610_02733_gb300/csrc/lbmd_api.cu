@@ -49,7 +49,8 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->row_start, ctx->slot_row, ctx->migrant_slot, ctx->migrant_count,
                     ctx->fc4,       ctx->old4,       ctx->bond_count,  ctx->bond_partner, ctx->bond_k,
                     ctx->bond_r0,   ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step,
-                    ctx->occw,      ctx->cact};
+                    ctx->occw[0],   ctx->occw[1],    ctx->cact[0],     ctx->cact[1],   ctx->blk_done,
+                    ctx->lb_missed, ctx->missed_list};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 4; ++i)
@@ -156,6 +157,9 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     // active
     ctx->cact_cap = std::min<int64_t>(N, 8 * maxp);
     const size_t occ_bytes = (size_t)p->ny * p->nz * (size_t)((p->nx + 31) / 32) * sizeof(uint2);
+    // blocks of the LB collide (node kernels: rows of up to 256 nodes)
+    const int bx = p->nx >= 256 ? 256 : (p->nx >= 128 ? 128 : (p->nx >= 64 ? 64 : 32));
+    const int64_t n_lb_blocks = (int64_t)((p->nx + bx - 1) / bx) * p->ny * p->nz;
 
     struct Alloc {
         void **ptr;
@@ -183,8 +187,13 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->migrant_count, 2 * sizeof(int32_t)},
         {&ctx->fc4, (size_t)maxp * 4 * rs},
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
-        {(void **)&ctx->occw, p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
-        {&ctx->cact, p->variant == LBMD_VARIANT_B ? (size_t)ctx->cact_cap * node_bytes : 0},
+        {(void **)&ctx->occw[0], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
+        {(void **)&ctx->occw[1], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
+        {&ctx->cact[0], p->variant == LBMD_VARIANT_B ? (size_t)ctx->cact_cap * node_bytes : 0},
+        {&ctx->cact[1], p->variant == LBMD_VARIANT_B ? (size_t)ctx->cact_cap * node_bytes : 0},
+        {(void **)&ctx->blk_done, (size_t)n_lb_blocks * sizeof(uint32_t)},
+        {(void **)&ctx->lb_missed, sizeof(int32_t)},
+        {(void **)&ctx->missed_list, (size_t)n_lb_blocks * sizeof(int32_t)},
         {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},
         {(void **)&ctx->bond_partner, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(int32_t)},
         {(void **)&ctx->bond_k, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
@@ -214,7 +223,9 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->slot_row, 0xff, (size_t)maxp * sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->migrant_count, 0, 2 * sizeof(int32_t), ctx->stream);
     // no active nodes until the first re-ordering
-    if (e == cudaSuccess && ctx->occw) e = cudaMemsetAsync(ctx->occw, 0, occ_bytes, ctx->stream);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+        if (ctx->occw[s]) e = cudaMemsetAsync(ctx->occw[s], 0, occ_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->blk_done, 0, (size_t)n_lb_blocks * sizeof(uint32_t), ctx->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(ctx->fcons4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fc4, 0, (size_t)maxp * 4 * rs, ctx->stream);

@@ -68,9 +68,17 @@ struct lbmd_ctx {
     int32_t *slot_row;      // per slot: the row bucket it belongs to, -1 if none
     int32_t *migrant_slot;  // variant B: slots that left their row bucket
     int32_t *migrant_count;
-    uint2 *occw;         // variant B: (ny * nz) x active_words(nx) words
-    void *cact;          // variant B: compact node records, cact_cap of them
+    // variant B, two sets by LB-step parity: the MD steps of LB cycle s use set
+    // s & 1 (built at the end of cycle s - 1); the LB step of cycle s reads
+    // set s & 1 and writes the new moments into set (s + 1) & 1
+    uint2 *occw[2];      // (ny * nz) x active_words(nx) words
+    void *cact[2];       // compact node records, cact_cap of them
     int64_t cact_cap;
+    // LB collide with fused post-stream moments: per collide block the LB step
+    // (+1) it last pushed, and the rows whose moments the fallback computes
+    uint32_t *blk_done;
+    int32_t *lb_missed;    // count
+    int32_t *missed_list;  // collide-block ids
     int sm_count;
     int gather_warps;  // warps per block of the variant B row gather
     int32_t *bond_count, *bond_partner;
@@ -91,6 +99,13 @@ struct lbmd_ctx {
     cudaGraphExec_t cycle_graph[4];
     std::string err;
 };
+
+// The active-node set the MD steps of the current LB cycle use, and the one
+// the coming LB step fills.
+inline uint2 *active_words_now(const lbmd_ctx *c) { return c->occw[c->lb_step & 1]; }
+inline void *active_records_now(const lbmd_ctx *c) { return c->cact[c->lb_step & 1]; }
+inline uint2 *active_words_next(const lbmd_ctx *c) { return c->occw[(c->lb_step + 1) & 1]; }
+inline void *active_records_next(const lbmd_ctx *c) { return c->cact[(c->lb_step + 1) & 1]; }
 
 // Launchers, one per kernel family; each enqueues on ctx->stream and returns
 // the launch status.

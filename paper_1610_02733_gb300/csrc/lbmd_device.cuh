@@ -241,12 +241,16 @@ struct Prec<double> {
 template <typename S, typename T>
 struct PopStore {  // plain storage: S == T
     __device__ static __forceinline__ T load(const S *p, T /*base*/) { return *p; }
+    __device__ static __forceinline__ T load_cg(const S *p, T /*base*/) { return __ldcg(p); }
     __device__ static __forceinline__ void store(S *p, T v, T /*base*/) { *p = v; }
     static constexpr bool deviation = false;
 };
 template <>
 struct PopStore<__half, float> {
     __device__ static __forceinline__ float load(const __half *p, float base) { return base + __half2float(*p); }
+    __device__ static __forceinline__ float load_cg(const __half *p, float base) {
+        return base + __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
     __device__ static __forceinline__ void store(__half *p, float v, float base) { *p = __float2half_rn(v - base); }
     static constexpr bool deviation = true;
 };
@@ -254,6 +258,9 @@ template <>
 struct PopStore<__nv_bfloat16, float> {
     __device__ static __forceinline__ float load(const __nv_bfloat16 *p, float base) {
         return base + __bfloat162float(*p);
+    }
+    __device__ static __forceinline__ float load_cg(const __nv_bfloat16 *p, float base) {
+        return base + __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p))));
     }
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v, float base) {
         *p = __float2bfloat16_rn(v - base);

@@ -624,8 +624,8 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.migrant_slot = ctx->migrant_slot;
     a.migrant_count = ctx->migrant_count;
     a.np_cap = ctx->p.max_particles > 0 ? ctx->p.max_particles : 1;
-    a.occw = ctx->occw;
-    a.cact = static_cast<typename P::node4 *>(ctx->cact);
+    a.occw = active_words_now(ctx);
+    a.cact = static_cast<typename P::node4 *>(active_records_now(ctx));
     a.occ_words = active_words(ctx->p.nx);
     return a;
 }
@@ -706,17 +706,18 @@ template <typename T>
 static cudaError_t active_set_t(lbmd_ctx *ctx) {
     const int64_t rows = (int64_t)ctx->p.ny * ctx->p.nz;
     const int W = active_words(ctx->p.nx);
-    if (ctx->np == 0) return cudaMemsetAsync(ctx->occw, 0, (size_t)rows * W * sizeof(uint2), ctx->stream);
+    uint2 *occw = active_words_next(ctx);  // built for the coming LB cycle
+    if (ctx->np == 0) return cudaMemsetAsync(occw, 0, (size_t)rows * W * sizeof(uint2), ctx->stream);
     const unsigned blocks = (unsigned)((rows + GATHER_WARPS - 1) / GATHER_WARPS);
     active_rows_kernel<T><<<blocks, 32 * GATHER_WARPS, GATHER_WARPS * W * sizeof(uint32_t), ctx->stream>>>(
         static_cast<const typename Prec<T>::real4 *>(ctx->pos4[ctx->pcur]), ctx->row_start, ctx->p.nx,
-        make_fastdiv((uint32_t)ctx->p.ny), ctx->p.nz, W, ctx->occw, ctx->row_count, (int)rows);
+        make_fastdiv((uint32_t)ctx->p.ny), ctx->p.nz, W, occw, ctx->row_count, (int)rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int n_chunks = (int)((rows + 1023) / 1024);
     sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    active_finalize_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, ctx->chunk_total, rows, ctx->occw, W);
+    active_finalize_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, ctx->chunk_total, rows, occw, W);
     return cudaGetLastError();
 }
 
@@ -724,7 +725,8 @@ template <typename T>
 static cudaError_t active_sync_t(lbmd_ctx *ctx) {
     using N4 = typename Prec<T>::node4;
     const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
-    active_sync_kernel<T><<<blocks, 256, 0, ctx->stream>>>(ctx->occw, static_cast<const N4 *>(ctx->cact),
+    active_sync_kernel<T><<<blocks, 256, 0, ctx->stream>>>(active_words_now(ctx),
+                                                           static_cast<const N4 *>(active_records_now(ctx)),
                                                            static_cast<N4 *>(ctx->node), ctx->N, ctx->p.nx,
                                                            active_words(ctx->p.nx));
     return cudaGetLastError();
