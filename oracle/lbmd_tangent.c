@@ -275,7 +275,8 @@ int tan_md_substep(tan_state *t) {
                 dual wk = cst(1.0);
                 for (int a = 0; a < 3; ++a) wk = mul(wk, o[a] ? d[a] : sub(cst(1.0), d[a]));
                 delta[8 * p + k] = wk;
-                corner[8 * p + k] = node_at(t, (int64_t)base[0] + o[0], (int64_t)base[1] + o[1], (int64_t)base[2] + o[2]);
+                corner[8 * p + k] =
+                    node_at(t, (int64_t)base[0] + o[0], (int64_t)base[1] + o[1], (int64_t)base[2] + o[2]);
             }
             dual uR[3] = {cst(0.0), cst(0.0), cst(0.0)};
             for (int k = 0; k < 8; ++k) {
@@ -307,7 +308,8 @@ int tan_md_substep(tan_state *t) {
                 t->pos[3 * p + a] = mk(xv, x.d);
             }
         for (int64_t p = 0; p < np; ++p)
-            for (int a = 0; a < 3; ++a) t->vel[3 * p + a] = add(t->vel[3 * p + a], scl(hm, add(cst(0.0), fc[3 * p + a])));
+            for (int a = 0; a < 3; ++a)
+                t->vel[3 * p + a] = add(t->vel[3 * p + a], scl(hm, add(cst(0.0), fc[3 * p + a])));
         /* Eqs. (7), (8): transfers in particle id order */
         for (int64_t p = 0; p < np; ++p)
             for (int k = 0; k < 8; ++k)

@@ -612,7 +612,8 @@ cudaError_t forward_t(lbmd_adjoint *ad, const double *pos0, const double *vel0, 
         if ((e = run_md<T>(ad, c, false)) != cudaSuccess) return e;
         if (np > 0) {
             R4 *nx = pchk_at<T>(ad, c + 1);
-            if ((e = cudaMemcpyAsync(nx, ad->pos, np * sizeof(R4), cudaMemcpyDeviceToDevice, ad->stream)) != cudaSuccess)
+            if ((e = cudaMemcpyAsync(nx, ad->pos, np * sizeof(R4), cudaMemcpyDeviceToDevice, ad->stream)) !=
+                cudaSuccess)
                 return e;
             if ((e = cudaMemcpyAsync(nx + np, ad->vel, np * sizeof(R4), cudaMemcpyDeviceToDevice, ad->stream)) !=
                 cudaSuccess)

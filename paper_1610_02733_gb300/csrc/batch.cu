@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
     }
     T Fx = -rp.zeta * (V.x - ux), Fy = -rp.zeta * (V.y - uy), Fz = -rp.zeta * (V.z - uz);
     if (rp.amp != T(0)) {
-        const uint32_t md_step = (uint32_t)(a.lb_step[r] * (unsigned long long)rp.n_sub + (unsigned)(a.tick % rp.n_sub));
+        const uint32_t md_step =
+            (uint32_t)(a.lb_step[r] * (unsigned long long)rp.n_sub + (unsigned)(a.tick % rp.n_sub));
         const U4 rnd = philox4x32_10(U4{(uint32_t)local, md_step, 1u, 0u}, rp.key0, rp.key1);
         Fx += rp.amp * unit_uniform<T>(rnd.x);
         Fy += rp.amp * unit_uniform<T>(rnd.y);
@@ -658,7 +659,8 @@ cudaError_t tune_particles(lbmd_batch *b) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(vel, b->vel4, pbytes, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(node, b->node, nbytes, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(jacc, b->jacc, nbytes, cudaMemcpyDeviceToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(unst, b->unstable, b->R * sizeof(int), cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(unst, b->unstable, b->R * sizeof(int), cudaMemcpyDeviceToDevice, b->stream);
     const int cand[3] = {64, 128, 256};
     if (e == cudaSuccess) {
         BArgs<T> a = make_bargs<T>(b, 0);

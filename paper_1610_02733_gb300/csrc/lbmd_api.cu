@@ -293,7 +293,8 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
 
 lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0) {
     if (!ctx) return LBMD_ERR_ARG;
-    if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !is_finite_d(r0)) return fail(ctx, LBMD_ERR_ARG, "bad bonds");
+    if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !is_finite_d(r0))
+        return fail(ctx, LBMD_ERR_ARG, "bad bonds");
     if (ctx->nb + nb > ctx->p.max_bonds) return fail(ctx, LBMD_ERR_CAPACITY, "max_bonds exceeded");
     if (nb == 0) return LBMD_OK;
     const int64_t np = ctx->np;

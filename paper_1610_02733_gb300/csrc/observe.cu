@@ -267,7 +267,8 @@ template <typename T, typename S>
 static cudaError_t node_to_double_t(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst, bool transfer_only) {
     using N4 = typename Prec<T>::node4;
     node_to_double_kernel<T, S><<<nblocks(count), 256, 0, ctx->stream>>>(
-        static_cast<const N4 *>(ctx->node), static_cast<const N4 *>(ctx->jacc), static_cast<const S *>(ctx->f[ctx->cur]),
+        static_cast<const N4 *>(ctx->node), static_cast<const N4 *>(ctx->jacc),
+        static_cast<const S *>(ctx->f[ctx->cur]),
         ctx->N, (T)ctx->p.rho0, first, count, dst, transfer_only ? 1 : 0, ctx->p.variant);
     return cudaGetLastError();
 }
@@ -334,7 +335,8 @@ cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel) 
             ctx->p.ny);
     else
         particles_to_double_kernel<float><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
-            static_cast<const Prec<float>::real4 *>(ctx->pos4[b]), static_cast<const Prec<float>::real4 *>(ctx->vel4[b]),
+            static_cast<const Prec<float>::real4 *>(ctx->pos4[b]),
+            static_cast<const Prec<float>::real4 *>(ctx->vel4[b]),
             ctx->pid[b], ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
     return cudaGetLastError();
 }

@@ -459,7 +459,8 @@ __global__ void __launch_bounds__(1024) sort_finalize_kernel(const int32_t *row_
 template <typename T>
 __global__ void __launch_bounds__(256)
     sort_scatter_kernel(const typename Prec<T>::real4 *pos_in, const typename Prec<T>::real4 *vel_in,
-                        const typename Prec<T>::real4 *fcons_in, const int32_t *pid_in, typename Prec<T>::real4 *pos_out,
+                        const typename Prec<T>::real4 *fcons_in, const int32_t *pid_in,
+                        typename Prec<T>::real4 *pos_out,
                         typename Prec<T>::real4 *vel_out, typename Prec<T>::real4 *fcons_out, int32_t *pid_out,
                         int32_t *slot_of, int32_t *slot_row, const int32_t *row_start, const int32_t *rank, int64_t np,
                         FastDiv fnx, int bonds) {
@@ -485,8 +486,8 @@ __global__ void __launch_bounds__(256)
 // with the in-row slot of each word's first active node, and the row's count.
 template <typename T>
 __global__ void __launch_bounds__(32 * GATHER_WARPS)
-    active_rows_kernel(const typename Prec<T>::real4 *pos4, const int32_t *row_start, int nx, FastDiv fny, int nz, int W,
-                       uint2 *occw, int32_t *row_count, int n_rows) {
+    active_rows_kernel(const typename Prec<T>::real4 *pos4, const int32_t *row_start, int nx, FastDiv fny, int nz,
+                       int W, uint2 *occw, int32_t *row_count, int n_rows) {
     extern __shared__ uint32_t bits_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *bits = bits_smem + (size_t)warp * W;
