@@ -101,6 +101,8 @@ struct orc_state {
     int64_t nb, cap_b;
     int64_t *bond;
     double *bond_k, *bond_r0;
+    int *bond_kind;       /* ORC_BOND_HARMONIC or ORC_BOND_FENE per bond */
+    double lj_eps, lj_sigma, lj_rc; /* Lennard-Jones between all particles; off when lj_rc = 0 */
     int fcons_valid;
     uint64_t lb_step, md_step;
     int sub_done;
@@ -245,7 +247,7 @@ void orc_destroy(orc_state *s) {
     if (!s) return;
     free(s->f); free(s->f_tmp); free(s->rho); free(s->jst); free(s->jacc);
     free(s->pos); free(s->vel); free(s->mass); free(s->fcons); free(s->fc);
-    free(s->bond); free(s->bond_k); free(s->bond_r0);
+    free(s->bond); free(s->bond_k); free(s->bond_r0); free(s->bond_kind);
     free(s);
 }
 
@@ -401,25 +403,88 @@ static void node_momentum_seen(const orc_state *s, int64_t r, double jout[3]) {
     }
 }
 
-static void compute_bond_forces(orc_state *s) {
+/* Minimum-image separation d = R_j - R_i and its length squared. */
+static double separation(const orc_state *s, int64_t i, int64_t j, double d[3]) {
+    double L[3] = {s->p.nx, s->p.ny, s->p.nz}, r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = s->pos[3 * j + a] - s->pos[3 * i + a];
+        d[a] -= L[a] * round(d[a] / L[a]);
+        r2 += d[a] * d[a];
+    }
+    return r2;
+}
+
+/* Bond b of length r: magnitude g with force g d on the first particle and
+ * -g d on the second (d from the first to the second), and the energy.
+ *   harmonic  U = (k/2)(r - r0)^2,                 g = k (r - r0) / r
+ *   FENE      U = -(k/2) R0^2 ln(1 - (r/R0)^2),     g = k / (1 - (r/R0)^2)
+ * (the finitely extensible springs of the Kremer-Grest chains, Sec. 4; R0 is
+ * stored in bond_r0).  A FENE bond stretched to r >= R0 has infinite energy:
+ * NaN force. */
+static double bond_force(const orc_state *s, int64_t b, double r2, double *energy) {
+    double k = s->bond_k[b], r0 = s->bond_r0[b];
+    if (s->bond_kind[b] == ORC_BOND_FENE) {
+        double x = r2 / (r0 * r0);
+        if (!(x < 1.0)) {
+            if (energy) *energy = INFINITY;
+            return NAN;
+        }
+        if (energy) *energy = -0.5 * k * r0 * r0 * log(1.0 - x);
+        return k / (1.0 - x);
+    }
+    double r = sqrt(r2);
+    if (energy) *energy = 0.5 * k * (r - r0) * (r - r0);
+    if (r == 0.0) return 0.0;
+    return k * (r - r0) / r;
+}
+
+/* Lennard-Jones pair at distance^2 r2 < rc^2 (Sec. 4: the Kremer-Grest
+ * monomers, cut off at rc): U = 4 eps ((sigma/r)^12 - (sigma/r)^6) - U_c with
+ * the shift U_c making U(rc) = 0; magnitude g with force g d on the first
+ * particle (d from the first to the second), g = -24 eps (2 t^2 - t) / r^2,
+ * t = (sigma/r)^6. */
+static double lj_force(const orc_state *s, double r2, double *energy) {
+    double t = pow(s->lj_sigma * s->lj_sigma / r2, 3.0);
+    if (energy) {
+        double tc = pow(s->lj_sigma * s->lj_sigma / (s->lj_rc * s->lj_rc), 3.0);
+        *energy = 4.0 * s->lj_eps * (t * t - t) - 4.0 * s->lj_eps * (tc * tc - tc);
+    }
+    return -24.0 * s->lj_eps * (2.0 * t * t - t) / r2;
+}
+
+/* Conservative force F^cons of Eq. (4) on every particle at the current
+ * positions: bonds (harmonic or FENE) in bond order, then Lennard-Jones over
+ * every pair i < j within the cut-off (bonded pairs included: all monomers
+ * interact, Sec. 4).  Each pair's force is added to both particles with
+ * opposite signs, so the total is zero up to rounding.  energy (if not NULL)
+ * receives the harmonic, FENE and LJ potential energies. */
+static void compute_conservative_forces(orc_state *s, double energy[3]) {
     for (int64_t q = 0; q < 3 * s->np; ++q) s->fcons[q] = 0.0;
-    double L[3] = {s->p.nx, s->p.ny, s->p.nz};
+    if (energy) energy[0] = energy[1] = energy[2] = 0.0;
     for (int64_t b = 0; b < s->nb; ++b) {
         int64_t i = s->bond[2 * b], j = s->bond[2 * b + 1];
-        double d[3], r2 = 0.0;
+        double d[3], u;
+        double g = bond_force(s, b, separation(s, i, j, d), &u);
         for (int a = 0; a < 3; ++a) {
-            d[a] = s->pos[3 * j + a] - s->pos[3 * i + a];
-            d[a] -= L[a] * round(d[a] / L[a]); /* minimum image */
-            r2 += d[a] * d[a];
+            s->fcons[3 * i + a] += g * d[a];
+            s->fcons[3 * j + a] -= g * d[a];
         }
-        double r = sqrt(r2);
-        if (r == 0.0) continue;
-        /* Harmonic bond U = (k/2)(r - r0)^2: force on i along +d. */
-        double mag = s->bond_k[b] * (r - s->bond_r0[b]) / r;
-        for (int a = 0; a < 3; ++a) {
-            s->fcons[3 * i + a] += mag * d[a];
-            s->fcons[3 * j + a] -= mag * d[a];
-        }
+        if (energy) energy[s->bond_kind[b] == ORC_BOND_FENE ? 1 : 0] += u;
+    }
+    if (s->lj_rc > 0.0) {
+        double rc2 = s->lj_rc * s->lj_rc;
+        for (int64_t i = 0; i < s->np; ++i)
+            for (int64_t j = i + 1; j < s->np; ++j) {
+                double d[3], u;
+                double r2 = separation(s, i, j, d);
+                if (!(r2 < rc2)) continue;
+                double g = lj_force(s, r2, &u);
+                for (int a = 0; a < 3; ++a) {
+                    s->fcons[3 * i + a] += g * d[a];
+                    s->fcons[3 * j + a] -= g * d[a];
+                }
+                if (energy) energy[2] += u;
+            }
     }
     s->fcons_valid = 1;
 }
@@ -479,7 +544,7 @@ int orc_md_substep(orc_state *s) {
     int64_t np = s->np;
     double dt = 1.0 / (double)s->p.n_sub;
     if (np > 0) {
-        if (!s->fcons_valid) compute_bond_forces(s);
+        if (!s->fcons_valid) compute_conservative_forces(s, NULL);
         int64_t *corner = (int64_t *)malloc(sizeof(int64_t) * 8 * np);
         double *delta = (double *)malloc(sizeof(double) * 8 * np);
         double *dP = (double *)malloc(sizeof(double) * 3 * np);
@@ -519,7 +584,7 @@ int orc_md_substep(orc_state *s) {
                 s->pos[3 * p + a] = wrap_pos(s->pos[3 * p + a] + dt * s->vel[3 * p + a], L[a]);
             }
         }
-        compute_bond_forces(s);
+        compute_conservative_forces(s, NULL);
         for (int64_t p = 0; p < np; ++p) {
             double hm = 0.5 * dt / s->mass[p];
             for (int a = 0; a < 3; ++a) s->vel[3 * p + a] += hm * (s->fcons[3 * p + a] + s->fc[3 * p + a]);
@@ -567,7 +632,7 @@ int orc_add_particles(orc_state *s, int64_t n, const double *pos, const double *
     return ORC_OK;
 }
 
-int orc_add_bonds(orc_state *s, int64_t nb, const int64_t *pairs, double k, double r0) {
+static int add_bonds_of_kind(orc_state *s, int64_t nb, const int64_t *pairs, double k, double r0, int kind) {
     if (nb < 0) return ORC_ERR_ARG;
     for (int64_t q = 0; q < 2 * nb; ++q)
         if (pairs[q] < 0 || pairs[q] >= s->np) return ORC_ERR_ARG;
@@ -583,6 +648,9 @@ int orc_add_bonds(orc_state *s, int64_t nb, const int64_t *pairs, double k, doub
         double *nr = (double *)realloc(s->bond_r0, sizeof(double) * cap);
         if (!nr) return ORC_ERR_OOM;
         s->bond_r0 = nr;
+        int *nkind = (int *)realloc(s->bond_kind, sizeof(int) * cap);
+        if (!nkind) return ORC_ERR_OOM;
+        s->bond_kind = nkind;
         s->cap_b = cap;
     }
     for (int64_t q = 0; q < nb; ++q) {
@@ -590,10 +658,36 @@ int orc_add_bonds(orc_state *s, int64_t nb, const int64_t *pairs, double k, doub
         s->bond[2 * (s->nb + q) + 1] = pairs[2 * q + 1];
         s->bond_k[s->nb + q] = k;
         s->bond_r0[s->nb + q] = r0;
+        s->bond_kind[s->nb + q] = kind;
     }
     s->nb = need;
     s->fcons_valid = 0;
     return ORC_OK;
+}
+
+int orc_add_bonds(orc_state *s, int64_t nb, const int64_t *pairs, double k, double r0) {
+    return add_bonds_of_kind(s, nb, pairs, k, r0, ORC_BOND_HARMONIC);
+}
+
+int orc_add_fene_bonds(orc_state *s, int64_t nb, const int64_t *pairs, double k, double R0) {
+    if (!(R0 > 0.0)) return ORC_ERR_ARG;
+    return add_bonds_of_kind(s, nb, pairs, k, R0, ORC_BOND_FENE);
+}
+
+int orc_set_lj(orc_state *s, double eps, double sigma, double rc) {
+    if (!(eps >= 0.0) || !(sigma > 0.0) || !(rc >= 0.0)) return ORC_ERR_ARG;
+    s->lj_eps = eps;
+    s->lj_sigma = sigma;
+    s->lj_rc = rc;
+    s->fcons_valid = 0;
+    return ORC_OK;
+}
+
+/* Conservative forces (3 np) at the current positions and the potential
+ * energies [harmonic, FENE, LJ]. */
+void orc_conservative_forces(orc_state *s, double *forces, double energy[3]) {
+    compute_conservative_forces(s, energy);
+    if (forces) memcpy(forces, s->fcons, sizeof(double) * 3 * s->np);
 }
 
 /* ------------------------------------------------------------------------ */

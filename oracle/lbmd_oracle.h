@@ -15,6 +15,7 @@ extern "C" {
 #endif
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_OOM = -3, ORC_ERR_SEQUENCE = -4 };
+enum { ORC_BOND_HARMONIC = 0, ORC_BOND_FENE = 1 };
 
 typedef struct orc_params {
     int32_t nx, ny, nz;   /* periodic lattice, nodes per axis, a = 1 */
@@ -38,6 +39,9 @@ void orc_destroy(orc_state *s);
 
 int orc_add_particles(orc_state *s, int64_t n, const double *pos, const double *vel, const double *mass);
 int orc_add_bonds(orc_state *s, int64_t nb, const int64_t *pairs, double k, double r0);
+int orc_add_fene_bonds(orc_state *s, int64_t nb, const int64_t *pairs, double k, double R0);
+int orc_set_lj(orc_state *s, double eps, double sigma, double rc);
+void orc_conservative_forces(orc_state *s, double *forces, double energy[3]);
 int orc_md_substep(orc_state *s);
 int orc_lb_step(orc_state *s);
 void orc_observables(const orc_state *s, double out[11]);

@@ -66,6 +66,9 @@ def lib():
         L.orc_destroy.argtypes = [P]
         L.orc_add_particles.argtypes = [P, ct.c_int64, dp, dp, dp]
         L.orc_add_bonds.argtypes = [P, ct.c_int64, ct.POINTER(ct.c_int64), ct.c_double, ct.c_double]
+        L.orc_add_fene_bonds.argtypes = [P, ct.c_int64, ct.POINTER(ct.c_int64), ct.c_double, ct.c_double]
+        L.orc_set_lj.argtypes = [P, ct.c_double, ct.c_double, ct.c_double]
+        L.orc_conservative_forces.argtypes = [P, dp, dp]
         L.orc_md_substep.argtypes = [P]
         L.orc_lb_step.argtypes = [P]
         L.orc_observables.argtypes = [P, dp]
@@ -191,6 +194,28 @@ class Oracle:
                                  float(k), float(r0))
         if rc != ORC_OK:
             raise RuntimeError("orc_add_bonds: %d" % rc)
+
+    def add_fene_bonds(self, pairs, k, R0):
+        """FENE springs U = -(k/2) R0^2 ln(1 - (r/R0)^2) (Sec. 4)."""
+        pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+        rc = lib().orc_add_fene_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
+                                      float(k), float(R0))
+        if rc != ORC_OK:
+            raise RuntimeError("orc_add_fene_bonds: %d" % rc)
+
+    def set_lj(self, eps, sigma, rc):
+        """Lennard-Jones between all particles, cut off (and shifted to 0) at rc (Sec. 4)."""
+        r = lib().orc_set_lj(self._h, float(eps), float(sigma), float(rc))
+        if r != ORC_OK:
+            raise RuntimeError("orc_set_lj: %d" % r)
+
+    def conservative_forces(self):
+        """(forces (np, 3), energies {harmonic, fene, lj}) at the current positions."""
+        n = self.n_particles
+        out = np.zeros((max(n, 1), 3))
+        e = np.zeros(3)
+        lib().orc_conservative_forces(self._h, _dp(out), _dp(e))
+        return out[:n], {"harmonic": float(e[0]), "fene": float(e[1]), "lj": float(e[2])}
 
     def md_substep(self) -> int:
         return lib().orc_md_substep(self._h)

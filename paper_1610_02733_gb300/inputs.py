@@ -55,6 +55,71 @@ def bead_spring_chains(n_chains: int, n_beads: int, shape, seed: int, step: floa
     return pos, bonds
 
 
+def self_avoiding_chains(n_chains: int, n_beads: int, shape, seed: int, bond: float = 0.97, d_min: float = 0.9,
+                         tries: int = 64):
+    """Bead-spring chains with no two beads closer than ``d_min`` (minimum
+    image): each chain starts at a uniform point, each next bead at distance
+    ``bond`` from the previous one in a uniformly random direction, a trial
+    that comes closer than ``d_min`` to any placed bead is redrawn (a chain
+    that gets stuck is started again).  A stand-in for a relaxed
+    Kremer-Grest melt: no overlaps, so Lennard-Jones forces start finite.
+    Returns (pos (n_chains*n_beads, 3), bonds (n_chains*(n_beads-1), 2))."""
+    g = _rng(seed, 6)
+    L = np.asarray(shape, dtype=np.float64)
+    nc = np.maximum((L // d_min).astype(int), 1)  # hash cells of edge >= d_min
+    csz = L / nc
+    grid = {}
+
+    def key(x):
+        return tuple(int(v) % int(c) for v, c in zip(np.floor(x / csz), nc))
+
+    def free(x):
+        k = key(x)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for y in grid.get(((k[0] + dx) % nc[0], (k[1] + dy) % nc[1], (k[2] + dz) % nc[2]), ()):
+                        d = y - x
+                        d -= L * np.round(d / L)
+                        if float(d @ d) < d_min * d_min:
+                            return False
+        return True
+
+    out = np.zeros((n_chains, n_beads, 3))
+    for c in range(n_chains):
+        for _attempt in range(1000):
+            placed = []
+            x = g.random(3) * L
+            ok = free(x)
+            while ok and len(placed) < n_beads:
+                placed.append(x)
+                grid.setdefault(key(x), []).append(x)
+                if len(placed) == n_beads:
+                    break
+                ok = False
+                for _ in range(tries):
+                    d = g.standard_normal(3)
+                    y = np.mod(placed[-1] + bond * d / np.linalg.norm(d), L)
+                    y = np.where(y >= L, 0.0, y)
+                    if free(y):
+                        x, ok = y, True
+                        break
+            if len(placed) == n_beads:
+                out[c] = np.asarray(placed)
+                break
+            for x in placed:  # stuck: take the chain out and start again
+                lst = grid[key(x)]
+                for i, y in enumerate(lst):
+                    if y is x:
+                        del lst[i]
+                        break
+        else:
+            raise RuntimeError("self_avoiding_chains: could not place chain %d" % c)
+    first = (np.arange(n_chains)[:, None] * n_beads + np.arange(n_beads - 1)[None, :]).reshape(-1)
+    bonds = np.stack([first, first + 1], axis=1).astype(np.int64)
+    return out.reshape(-1, 3), bonds
+
+
 def perturbed(base: np.ndarray, amplitude: float, seed: int) -> np.ndarray:
     """base * (1 + amplitude * U(-1, 1)), elementwise: a random state near a
     caller-given reference state (e.g. populations of a fluid at rest)."""
