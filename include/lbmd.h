@@ -3,7 +3,8 @@
  * Boltzmann (LB) fluid with dissipative point-particle coupling of
  * Tretyakov & Duenweg, arXiv:1610.02733 ("An improved dissipative coupling
  * scheme for a system of Molecular Dynamics particles interacting with a
- * Lattice Boltzmann fluid"), variants A and B.
+ * Lattice Boltzmann fluid"), variants A, B and C, with the Kremer-Grest
+ * interactions of the paper's test system.
  *
  * The calls follow the paper's statement of the problem (Sec. 3, Fig. 2):
  * the fluid is advanced by LB steps of length tau_LB, the particles by m MD
@@ -126,6 +127,39 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
  * particle may take part in at most 8 bonds).  Conservative force of Eq. (4),
  * synchronising.  Errors: LBMD_ERR_CAPACITY, LBMD_ERR_ARG. */
 lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0);
+
+/* Kinds of bonds (per bond, fixed when it is added). */
+enum { LBMD_BOND_HARMONIC = 0, LBMD_BOND_FENE = 1 };
+
+/* Append nb FENE springs U = -(k/2) R0^2 ln(1 - (r/R0)^2), the finitely
+ * extensible bonds of the Kremer-Grest chains of Sec. 4 (standard model:
+ * k = 30 epsilon / sigma^2, R0 = 1.5 sigma), between particle ids
+ * pairs[2b], pairs[2b+1]; same storage, limits and behaviour as
+ * lbmd_add_bonds (at most 8 bonds of any kind per particle, max_bonds in
+ * total).  A spring stretched to r >= R0 has infinite energy: its force is
+ * NaN, the particles' velocities become NaN and lbmd_observables reports
+ * LBMD_ERR_NONFINITE.  Synchronising.  Errors: LBMD_ERR_ARG (ids, k < 0,
+ * R0 <= 0), LBMD_ERR_CAPACITY. */
+lbmd_status lbmd_add_fene_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double R0);
+
+/* Largest max_particles with which Lennard-Jones forces can be switched on:
+ * every particle interacts with every other one (all pairs, minimum image),
+ * which costs O(N^2) per MD step. */
+#define LBMD_MAX_LJ_PARTICLES 131072
+
+/* Lennard-Jones forces between all particles (bonded ones included), the
+ * monomer interaction of the Kremer-Grest model of Sec. 4:
+ *     U(r) = 4 eps ((sigma/r)^12 - (sigma/r)^6) - U(r_cut)   for r < r_cut,
+ *     0 beyond (the paper cuts at r_cut = 2^(7/6) sigma).
+ * Part of the conservative force of Eq. (4), evaluated at the current
+ * positions with the minimum image; velocity Verlet as for bonds.
+ * r_cut = 0 switches the forces off.  Each box edge must be at least
+ * 2 r_cut + 2 lattice spacings, and max_particles at most
+ * LBMD_MAX_LJ_PARTICLES.  The per-particle sums run over particle ids in a
+ * fixed order, so results are reproducible bit for bit.  Synchronising;
+ * recomputes the conservative forces.  Errors: LBMD_ERR_ARG (eps < 0,
+ * sigma <= 0, r_cut < 0, box too small), LBMD_ERR_CAPACITY. */
+lbmd_status lbmd_set_lj(lbmd_ctx *ctx, double eps, double sigma, double r_cut);
 
 /* Overwrite positions and velocities of all particles from host arrays of
  * 3 N doubles each in id order (either may be NULL to keep it).

@@ -48,7 +48,7 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->pid[0],    ctx->pid[1],     ctx->slot_of,     ctx->row_count, ctx->sort_rank, ctx->chunk_total,
                     ctx->row_start, ctx->slot_row, ctx->migrant_slot, ctx->migrant_count,
                     ctx->fc4,       ctx->old4,       ctx->bond_count,  ctx->bond_partner, ctx->bond_k,
-                    ctx->bond_r0,   ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step,
+                    ctx->bond_r0,   ctx->bond_kind, ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step,
                     ctx->occw[0],   ctx->occw[1],    ctx->cact[0],     ctx->cact[1],   ctx->blk_done,
                     ctx->lb_missed, ctx->missed_list};
     for (void *b : bufs)
@@ -198,6 +198,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->bond_partner, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(int32_t)},
         {(void **)&ctx->bond_k, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
         {(void **)&ctx->bond_r0, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
+        {(void **)&ctx->bond_kind, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE},
         {(void **)&ctx->staging, (size_t)ctx->staging_len * sizeof(double)},
         {(void **)&ctx->red_partial, (size_t)ctx->red_blocks * 8 * sizeof(double)},
         {(void **)&ctx->red_out, 8 * sizeof(double)},
@@ -216,6 +217,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_lb_step, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_count, 0, (size_t)maxp * sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_kind, 0, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE, ctx->stream);
     // no row buckets yet: every particle is spread as a migrant until the
     // first re-ordering
     if (e == cudaSuccess)
@@ -281,7 +283,7 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     CK(ctx, cudaMemsetAsync(ctx->slot_row + ctx->np, 0xff, n * sizeof(int32_t), ctx->stream));
     CK(ctx, cudaMemsetAsync((char *)ctx->fc4 + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     ctx->np += n;
-    if (ctx->nb > 0) CK(ctx, launch_bond_forces_only(ctx));
+    if (has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     for (int i = 0; i < 4; ++i)
         if (ctx->cycle_graph[i]) {
@@ -291,45 +293,90 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     return LBMD_OK;
 }
 
-lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0) {
-    if (!ctx) return LBMD_ERR_ARG;
-    if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !is_finite_d(r0))
-        return fail(ctx, LBMD_ERR_ARG, "bad bonds");
+static void drop_cycle_graphs(lbmd_ctx *ctx) {
+    for (int i = 0; i < 4; ++i)
+        if (ctx->cycle_graph[i]) {
+            cudaGraphExecDestroy(ctx->cycle_graph[i]);
+            ctx->cycle_graph[i] = nullptr;
+        }
+}
+
+static lbmd_status add_bonds_of_kind(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0,
+                                     uint8_t kind) {
     if (ctx->nb + nb > ctx->p.max_bonds) return fail(ctx, LBMD_ERR_CAPACITY, "max_bonds exceeded");
     if (nb == 0) return LBMD_OK;
     const int64_t np = ctx->np;
     const int M = LBMD_MAX_BONDS_PER_PARTICLE;
     std::vector<int32_t> count(np), partner((size_t)np * M);
     std::vector<double> bk((size_t)np * M), br((size_t)np * M);
+    std::vector<uint8_t> kd((size_t)np * M);
     CK(ctx, cudaMemcpy(count.data(), ctx->bond_count, np * sizeof(int32_t), cudaMemcpyDeviceToHost));
     CK(ctx, cudaMemcpy(partner.data(), ctx->bond_partner, (size_t)np * M * sizeof(int32_t), cudaMemcpyDeviceToHost));
     CK(ctx, cudaMemcpy(bk.data(), ctx->bond_k, (size_t)np * M * sizeof(double), cudaMemcpyDeviceToHost));
     CK(ctx, cudaMemcpy(br.data(), ctx->bond_r0, (size_t)np * M * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpy(kd.data(), ctx->bond_kind, (size_t)np * M, cudaMemcpyDeviceToHost));
     for (int64_t b = 0; b < nb; ++b) {
         const int64_t i = pairs[2 * b], j = pairs[2 * b + 1];
         if (i < 0 || j < 0 || i >= np || j >= np || i == j) return fail(ctx, LBMD_ERR_ARG, "bond ids out of range");
         if (count[i] >= M || count[j] >= M) return fail(ctx, LBMD_ERR_CAPACITY, "more than 8 bonds on a particle");
-        partner[(size_t)i * M + count[i]] = (int32_t)j;
-        bk[(size_t)i * M + count[i]] = k;
-        br[(size_t)i * M + count[i]] = r0;
-        count[i]++;
-        partner[(size_t)j * M + count[j]] = (int32_t)i;
-        bk[(size_t)j * M + count[j]] = k;
-        br[(size_t)j * M + count[j]] = r0;
-        count[j]++;
+        for (const int64_t e : {i, j}) {
+            const size_t s = (size_t)e * M + count[e];
+            partner[s] = (int32_t)(e == i ? j : i);
+            bk[s] = k;
+            br[s] = r0;
+            kd[s] = kind;
+            count[e]++;
+        }
     }
     CK(ctx, cudaMemcpy(ctx->bond_count, count.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(ctx, cudaMemcpy(ctx->bond_partner, partner.data(), (size_t)np * M * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(ctx, cudaMemcpy(ctx->bond_k, bk.data(), (size_t)np * M * sizeof(double), cudaMemcpyHostToDevice));
     CK(ctx, cudaMemcpy(ctx->bond_r0, br.data(), (size_t)np * M * sizeof(double), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->bond_kind, kd.data(), (size_t)np * M, cudaMemcpyHostToDevice));
     ctx->nb += nb;
     CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 4; ++i)
-        if (ctx->cycle_graph[i]) {
-            cudaGraphExecDestroy(ctx->cycle_graph[i]);
-            ctx->cycle_graph[i] = nullptr;
-        }
+    drop_cycle_graphs(ctx);
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !is_finite_d(r0))
+        return fail(ctx, LBMD_ERR_ARG, "bad bonds");
+    return add_bonds_of_kind(ctx, nb, pairs, k, r0, LBMD_BOND_HARMONIC);
+}
+
+lbmd_status lbmd_add_fene_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double R0) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !(k >= 0) || !is_finite_d(R0) || !(R0 > 0))
+        return fail(ctx, LBMD_ERR_ARG, "bad FENE bonds");
+    return add_bonds_of_kind(ctx, nb, pairs, k, R0, LBMD_BOND_FENE);
+}
+
+lbmd_status lbmd_set_lj(lbmd_ctx *ctx, double eps, double sigma, double r_cut) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (!is_finite_d(eps) || !(eps >= 0) || !is_finite_d(sigma) || !(sigma > 0) || !is_finite_d(r_cut) ||
+        !(r_cut >= 0))
+        return fail(ctx, LBMD_ERR_ARG, "bad Lennard-Jones parameters");
+    if (r_cut > 0) {
+        if (ctx->p.max_particles > LBMD_MAX_LJ_PARTICLES)
+            return fail(ctx, LBMD_ERR_CAPACITY, "Lennard-Jones: max_particles above LBMD_MAX_LJ_PARTICLES");
+        const int dims[3] = {ctx->p.nx, ctx->p.ny, ctx->p.nz};
+        for (int d : dims)
+            if ((double)d < 2.0 * r_cut + 2.0)
+                return fail(ctx, LBMD_ERR_ARG, "Lennard-Jones: every box edge must be at least 2 r_cut + 2");
+    }
+    ctx->lj_eps = eps;
+    ctx->lj_sigma = sigma;
+    ctx->lj_rc = r_cut;
+    if (ctx->np > 0 && has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
+    if (ctx->np > 0 && !has_cons(ctx)) {
+        const size_t rs = real_size(ctx);
+        CK(ctx, cudaMemsetAsync(ctx->fcons4[ctx->pcur], 0, (size_t)ctx->np * 4 * rs, ctx->stream));
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    drop_cycle_graphs(ctx);
     return LBMD_OK;
 }
 
@@ -342,7 +389,7 @@ lbmd_status lbmd_set_particles(lbmd_ctx *ctx, const double *pos, const double *v
     if (pos) CK(ctx, cudaMemcpyAsync(dpos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     if (vel) CK(ctx, cudaMemcpyAsync(dvel, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, launch_particles_from_double(ctx, 0, n, dpos, dvel, nullptr, pos != nullptr, vel != nullptr, false));
-    if (pos && ctx->nb > 0) CK(ctx, launch_bond_forces_only(ctx));
+    if (pos && has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
     return LBMD_OK;
 }
 

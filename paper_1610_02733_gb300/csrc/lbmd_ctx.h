@@ -83,6 +83,10 @@ struct lbmd_ctx {
     int gather_warps;  // warps per block of the variant B row gather
     int32_t *bond_count, *bond_partner;
     double *bond_k, *bond_r0;
+    uint8_t *bond_kind;  // LBMD_BOND_HARMONIC or LBMD_BOND_FENE per (id, bond)
+    // Lennard-Jones between all particles (Kremer-Grest monomers); off while
+    // lj_rc == 0
+    double lj_eps, lj_sigma, lj_rc;
     double *staging;   // device staging buffer for host <-> device conversions
     int64_t staging_len;
     double *red_partial;  // per-block partial sums of the observables
@@ -115,6 +119,8 @@ cudaError_t launch_forcing_update(lbmd_ctx *ctx);
 cudaError_t launch_init_equilibrium(lbmd_ctx *ctx);
 cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep);
 cudaError_t launch_bond_forces_only(lbmd_ctx *ctx);
+// conservative forces present (bonds or Lennard-Jones)
+inline bool has_cons(const lbmd_ctx *ctx) { return ctx->nb > 0 || ctx->lj_rc > 0.0; }
 cudaError_t launch_observables(lbmd_ctx *ctx);
 cudaError_t launch_populations_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst);
 cudaError_t launch_populations_from_double(lbmd_ctx *ctx, int64_t first, int64_t count, const double *src);

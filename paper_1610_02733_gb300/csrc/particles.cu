@@ -44,6 +44,8 @@ struct PArgs {
     typename P::node4 *node, *jacc;
     const int32_t *bond_count, *bond_partner;
     const double *bond_k, *bond_r0;
+    const uint8_t *bond_kind;
+    T lj_eps24, lj_sig2, lj_rc2;  // Lennard-Jones: 24 eps, sigma^2, r_cut^2
     int nx, ny, nz;
     FastDiv fd_nx, fd_ny;  // division by nx and ny
     int64_t np;
@@ -347,9 +349,47 @@ __global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a) {
     }
 }
 
-// Harmonic bond forces at the current positions (minimum image), summed per
-// particle over its partners in a fixed order; with KICK, also the second
-// velocity-Verlet half-kick with the stored coupling force.
+template <typename T>
+__device__ __forceinline__ T quiet_nan();
+template <>
+__device__ __forceinline__ float quiet_nan<float>() { return __int_as_float(0x7fc00000); }
+template <>
+__device__ __forceinline__ double quiet_nan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// Bond force on a particle from a partner at minimum-image separation d
+// (partner minus particle), |d|^2 = r2: g d with
+//   harmonic U = (k/2)(r - r0)^2               g = k (r - r0) / r   (0 at r = 0)
+//   FENE     U = -(k/2) R0^2 ln(1 - (r/R0)^2)  g = k / (1 - (r/R0)^2), R0 = r0
+// (Kremer-Grest springs, Sec. 4); a FENE bond at r >= R0 gives NaN.
+template <typename T>
+__device__ __forceinline__ T bond_gain(uint8_t kind, T k, T r0, T r2) {
+    if (kind == LBMD_BOND_FENE) {
+        const T x = r2 / (r0 * r0);
+        return x < T(1) ? k / (T(1) - x) : quiet_nan<T>();
+    }
+    const T r = sqrt(r2);
+    return r > T(0) ? k * (r - r0) / r : T(0);
+}
+
+// Minimum-image separation of the partner in slot q from a particle at
+// (R, c), through the stored cell indices and offsets.
+template <typename T>
+__device__ __forceinline__ void bond_separation(const PArgs<T> &a, const typename Prec<T>::real4 &R, const CellXYZ &c,
+                                                int64_t q, T &dx, T &dy, T &dz) {
+    using P = Prec<T>;
+    const typename P::real4 S = a.pos4[q];
+    const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
+    dx = T(d.x - c.x) + (S.x - R.x);
+    dy = T(d.y - c.y) + (S.y - R.y);
+    dz = T(d.z - c.z) + (S.z - R.z);
+    dx -= T(a.nx) * rint(dx / T(a.nx));
+    dy -= T(a.ny) * rint(dy / T(a.ny));
+    dz -= T(a.nz) * rint(dz / T(a.nz));
+}
+
+// Bond forces (harmonic or FENE) at the current positions (minimum image),
+// summed per particle over its partners in a fixed order; with KICK, also
+// the second velocity-Verlet half-kick with the stored coupling force.
 template <typename T, bool KICK>
 __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
     using P = Prec<T>;
@@ -361,25 +401,86 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
     T Fx = T(0), Fy = T(0), Fz = T(0);
     const int nbond = a.bond_count[id];
     for (int b = 0; b < nbond; ++b) {
-        const int64_t q = a.slot_of[a.bond_partner[id * LBMD_MAX_BONDS_PER_PARTICLE + b]];
-        const typename P::real4 S = a.pos4[q];
+        const int64_t e = id * LBMD_MAX_BONDS_PER_PARTICLE + b;
+        T dx, dy, dz;
+        bond_separation(a, R, c, a.slot_of[a.bond_partner[e]], dx, dy, dz);
+        const T g = bond_gain(a.bond_kind[e], (T)a.bond_k[e], (T)a.bond_r0[e], dx * dx + dy * dy + dz * dz);
+        Fx += g * dx;
+        Fy += g * dy;
+        Fz += g * dz;
+    }
+    a.fcons4[p] = P::make4(Fx, Fy, Fz, T(0));
+    if (KICK) {
+        typename P::real4 V = a.vel4[p];
+        const typename P::real4 Fc = a.fc4[p];
+        const T hm = a.half_dt * V.w;
+        V.x += hm * (Fx + Fc.x);
+        V.y += hm * (Fy + Fc.y);
+        V.z += hm * (Fz + Fc.z);
+        a.vel4[p] = V;
+    }
+}
+
+// Cell offset d (partner minus particle, |d| < n) to its periodic image
+// nearest to zero, in [-n/2, n/2].
+__device__ __forceinline__ int nearest_image(int d, int n) {
+    const int h = n >> 1;
+    return d > h ? d - n : (d < -h ? d + n : d);
+}
+
+// Conservative forces with Lennard-Jones (Kremer-Grest monomers, Sec. 4):
+// one warp per particle id i.  The lanes run over all other ids j (lane l
+// takes j = l, l + 32, ...), add the LJ force of every j within the cut-off,
+//   F_i += g d,  g = -24 eps (2 t^2 - t) / r^2,  t = (sigma^2 / r^2)^3,
+// d = R_j - R_i at the nearest image (cell offsets wrapped as integers, then
+// the fractional offsets added: exact to the last bit of the offsets; every
+// box edge is at least 2 r_cut + 2, so the nearest image is unique within
+// the cut-off); lane b < n_bonds(i) adds bond b.  The lane sums are combined
+// by a fixed butterfly, so the result does not depend on the slot order.
+// With KICK, lane 0 also makes the second velocity-Verlet half-kick.
+template <typename T, bool KICK>
+__global__ void __launch_bounds__(256) pair_kick_kernel(PArgs<T> a) {
+    using P = Prec<T>;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= a.np) return;  // whole warps
+    const int64_t p = a.slot_of[i];
+    const typename P::real4 R = a.pos4[p];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
+    T Fx = T(0), Fy = T(0), Fz = T(0);
+#pragma unroll 4
+    for (int64_t j = lane; j < a.np; j += 32) {
+        const typename P::real4 S = a.pos4[a.slot_of[j]];
         const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
-        T dx = T(d.x - c.x) + (S.x - R.x);
-        T dy = T(d.y - c.y) + (S.y - R.y);
-        T dz = T(d.z - c.z) + (S.z - R.z);
-        dx -= T(a.nx) * rint(dx / T(a.nx));
-        dy -= T(a.ny) * rint(dy / T(a.ny));
-        dz -= T(a.nz) * rint(dz / T(a.nz));
-        const T r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (r > T(0)) {
-            const T k = (T)a.bond_k[id * LBMD_MAX_BONDS_PER_PARTICLE + b];
-            const T r0 = (T)a.bond_r0[id * LBMD_MAX_BONDS_PER_PARTICLE + b];
-            const T mag = k * (r - r0) / r;
-            Fx += mag * dx;
-            Fy += mag * dy;
-            Fz += mag * dz;
+        const T dx = T(nearest_image(d.x - c.x, a.nx)) + (S.x - R.x);
+        const T dy = T(nearest_image(d.y - c.y, a.ny)) + (S.y - R.y);
+        const T dz = T(nearest_image(d.z - c.z, a.nz)) + (S.z - R.z);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        if (j != i && r2 < a.lj_rc2) {
+            const T s = a.lj_sig2 / r2;
+            const T t = s * s * s;
+            const T g = -a.lj_eps24 * (T(2) * t * t - t) / r2;
+            Fx += g * dx;
+            Fy += g * dy;
+            Fz += g * dz;
         }
     }
+    if (lane < a.bond_count[i]) {
+        const int64_t e = i * LBMD_MAX_BONDS_PER_PARTICLE + lane;
+        T dx, dy, dz;
+        bond_separation(a, R, c, a.slot_of[a.bond_partner[e]], dx, dy, dz);
+        const T g = bond_gain(a.bond_kind[e], (T)a.bond_k[e], (T)a.bond_r0[e], dx * dx + dy * dy + dz * dz);
+        Fx += g * dx;
+        Fy += g * dy;
+        Fz += g * dz;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        Fx += __shfl_xor_sync(0xffffffffu, Fx, off);
+        Fy += __shfl_xor_sync(0xffffffffu, Fy, off);
+        Fz += __shfl_xor_sync(0xffffffffu, Fz, off);
+    }
+    if (lane != 0) return;
     a.fcons4[p] = P::make4(Fx, Fy, Fz, T(0));
     if (KICK) {
         typename P::real4 V = a.vel4[p];
@@ -601,6 +702,10 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.bond_partner = ctx->bond_partner;
     a.bond_k = ctx->bond_k;
     a.bond_r0 = ctx->bond_r0;
+    a.bond_kind = ctx->bond_kind;
+    a.lj_eps24 = (T)(24.0 * ctx->lj_eps);
+    a.lj_sig2 = (T)(ctx->lj_sigma * ctx->lj_sigma);
+    a.lj_rc2 = (T)(ctx->lj_rc * ctx->lj_rc);
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
@@ -636,17 +741,20 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     if (ctx->np == 0) return cudaSuccess;
     PArgs<T> a = make_pargs<T>(ctx, substep);
     const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
-    const bool bonds = ctx->nb > 0;
+    const bool cons = has_cons(ctx);
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
     cudaError_t e;
-    if (bonds)
+    if (cons)
         couple_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
     else
         couple_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (bonds) {
-        bond_kick_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
+    if (cons) {
+        if (ctx->lj_rc > 0.0)
+            pair_kick_kernel<T, true><<<(unsigned)((32 * ctx->np + 255) / 256), 256, 0, ctx->stream>>>(a);
+        else
+            bond_kick_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -668,7 +776,10 @@ static cudaError_t bond_forces_t(lbmd_ctx *ctx) {
     if (ctx->np == 0) return cudaSuccess;
     PArgs<T> a = make_pargs<T>(ctx, 0);
     const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
-    bond_kick_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
+    if (ctx->lj_rc > 0.0)
+        pair_kick_kernel<T, false><<<(unsigned)((32 * ctx->np + 255) / 256), 256, 0, ctx->stream>>>(a);
+    else
+        bond_kick_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -696,7 +807,7 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
             static_cast<const R4 *>(ctx->fcons4[b]), ctx->pid[b], static_cast<R4 *>(ctx->pos4[o]),
             static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]), ctx->pid[o], ctx->slot_of,
             ctx->slot_row, ctx->row_start, ctx->sort_rank, ctx->np, make_fastdiv((uint32_t)ctx->p.nx),
-            ctx->nb > 0 ? 1 : 0);
+            has_cons(ctx) ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ctx->pcur = o;

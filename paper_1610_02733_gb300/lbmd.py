@@ -29,7 +29,8 @@ PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_D
 
 # every symbol include/lbmd.h declares
 EXPORTS = (
-    "lbmd_create", "lbmd_destroy", "lbmd_add_particles", "lbmd_add_bonds", "lbmd_set_particles",
+    "lbmd_create", "lbmd_destroy", "lbmd_add_particles", "lbmd_add_bonds", "lbmd_add_fene_bonds", "lbmd_set_lj",
+    "lbmd_set_particles",
     "lbmd_md_substep", "lbmd_lb_step", "lbmd_run_cycles", "lbmd_observables", "lbmd_get_populations",
     "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
@@ -105,6 +106,8 @@ def load():
     L.lbmd_destroy.argtypes = [P]
     L.lbmd_add_particles.argtypes = [P, ct.c_int64, dp, dp, dp, i64p]
     L.lbmd_add_bonds.argtypes = [P, ct.c_int64, i64p, ct.c_double, ct.c_double]
+    L.lbmd_add_fene_bonds.argtypes = [P, ct.c_int64, i64p, ct.c_double, ct.c_double]
+    L.lbmd_set_lj.argtypes = [P, ct.c_double, ct.c_double, ct.c_double]
     L.lbmd_set_particles.argtypes = [P, ct.c_void_p, ct.c_void_p]
     L.lbmd_md_substep.argtypes = [P]
     L.lbmd_lb_step.argtypes = [P]
@@ -288,6 +291,17 @@ class LBMD:
         pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
         _check(self._h, load().lbmd_add_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
                                               float(k), float(r0)), "lbmd_add_bonds")
+
+    def add_fene_bonds(self, pairs, k, R0):
+        """FENE springs U = -(k/2) R0^2 ln(1 - (r/R0)^2) (Kremer-Grest chains, Sec. 4)."""
+        pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+        _check(self._h, load().lbmd_add_fene_bonds(self._h, pairs.shape[0],
+                                                   pairs.ctypes.data_as(ct.POINTER(ct.c_int64)), float(k), float(R0)),
+               "lbmd_add_fene_bonds")
+
+    def set_lj(self, eps, sigma, r_cut):
+        """Lennard-Jones between all particles, cut off (and shifted) at r_cut; r_cut = 0: off (Sec. 4)."""
+        _check(self._h, load().lbmd_set_lj(self._h, float(eps), float(sigma), float(r_cut)), "lbmd_set_lj")
 
     def set_particles(self, pos=None, vel=None):
         """Host arrays (numpy or pinned torch tensors, float64, 3 N each)."""
