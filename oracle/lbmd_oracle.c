@@ -203,6 +203,7 @@ static void compute_moments(orc_state *s) {
 orc_state *orc_create(const orc_params *p) {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->n_sub < 1) return NULL;
     if (p->variant < 0 || p->variant > 2) return NULL;
+    if (p->integrator != 0 && p->integrator != 1) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     if (!s) return NULL;
     s->p = *p;
@@ -531,14 +532,54 @@ static void orc_forcing_update(orc_state *s) {
     memset(s->jacc, 0, sizeof(double) * 3 * n);
 }
 
+/* Coupling force of Eq. (4) on every particle at its current position and
+ * velocity: the node velocities as they stand (Eq. (5)), the random force of
+ * MD step md_step; fills s->fc and the interpolation corners and weights.
+ * Every particle reads the nodes before any transfer of the step is made. */
+static void coupling_forces(orc_state *s, double dt, int64_t *corner, double *delta) {
+    uint32_t key[2];
+    key_of(s, key);
+    double amp = sqrt(2.0 * s->p.zeta * s->p.kT / dt);
+    for (int64_t p = 0; p < s->np; ++p) {
+        int64_t *ck = corner + 8 * p;
+        double *dk = delta + 8 * p;
+        orc_trilinear(s, s->pos + 3 * p, ck, dk);
+        double uR[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 8; ++k) {
+            double jn[3];
+            node_momentum_seen(s, ck[k], jn);
+            for (int a = 0; a < 3; ++a) uR[a] += dk[k] * jn[a] / s->rho[ck[k]];
+        }
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)s->md_step, 1u, 0u}, out[4];
+        orc_philox4x32_10(ctr, key, out);
+        for (int a = 0; a < 3; ++a) {
+            double frand = s->p.kT > 0.0 ? amp * orc_uniform_unit(out[a]) : 0.0;
+            s->fc[3 * p + a] = -s->p.zeta * (s->vel[3 * p + a] - uR[a]) + frand;
+        }
+    }
+}
+
 /* One MD step of length dt = tau_LB / m for every particle (Sec. 3).
- * 1. Noise, then friction with the node velocities as they stand
- *    (Eqs. (4) and (5)); position and velocity are those at the beginning of
- *    the step, so Delta P = dt F_c (Eq. (6)).
- * 2. Velocity Verlet with F_c held fixed over the step.
- * 3. Newton's third law: node r_k receives Delta j_k = -delta_k Delta P / a^3
- *    (Eqs. (7) and (8)), with the same weights as the interpolation.  Every
- *    particle reads the nodes before any transfer of this step is added. */
+ * integrator 0 (the reading of Eq. (6): R, v and F_rand of the beginning of
+ * the step):
+ *   1. noise, then friction with the node velocities as they stand
+ *      (Eqs. (4), (5)) at R, v of the start of the step: F_c, and
+ *      Delta P = dt F_c (Eq. (6));
+ *   2. velocity Verlet with F_c held fixed over the step (half kick, drift,
+ *      conservative forces at the new positions, half kick);
+ *   3. Newton's third law: node r_k around the start position receives
+ *      Delta j_k = -delta_k Delta P / a^3 (Eqs. (7), (8)).
+ * integrator 1 (velocity Verlet with the forces evaluated where an MD code
+ * evaluates them, after the drift):
+ *   1. half kick with the previous step's F_c and F_cons, drift;
+ *   2. F_cons at the new positions; F_c from the half-step velocity and the
+ *      node velocities interpolated at the new position;
+ *   3. half kick with F_c + F_cons;
+ *   4. transfer -delta_k dt F_c around the new position.
+ *   The particle takes dt F_c in two halves (this step and the next), the
+ *   fluid in full now: fluid + particle momentum + dt/2 sum F_c is conserved.
+ * In both, every particle reads the nodes before any transfer of this step
+ * is added. */
 int orc_md_substep(orc_state *s) {
     if (s->sub_done >= s->p.n_sub) return ORC_ERR_SEQUENCE;
     int64_t np = s->np;
@@ -547,44 +588,32 @@ int orc_md_substep(orc_state *s) {
         if (!s->fcons_valid) compute_conservative_forces(s, NULL);
         int64_t *corner = (int64_t *)malloc(sizeof(int64_t) * 8 * np);
         double *delta = (double *)malloc(sizeof(double) * 8 * np);
-        double *dP = (double *)malloc(sizeof(double) * 3 * np);
-        if (!corner || !delta || !dP) {
-            free(corner); free(delta); free(dP);
+        if (!corner || !delta) {
+            free(corner); free(delta);
             return ORC_ERR_OOM;
         }
-        uint32_t key[2];
-        key_of(s, key);
-        double amp = sqrt(2.0 * s->p.zeta * s->p.kT / dt);
-        for (int64_t p = 0; p < np; ++p) {
-            int64_t *ck = corner + 8 * p;
-            double *dk = delta + 8 * p;
-            orc_trilinear(s, s->pos + 3 * p, ck, dk);
-            double uR[3] = {0.0, 0.0, 0.0};
-            for (int k = 0; k < 8; ++k) {
-                double jn[3];
-                node_momentum_seen(s, ck[k], jn);
-                for (int a = 0; a < 3; ++a) uR[a] += dk[k] * jn[a] / s->rho[ck[k]];
-            }
-            uint32_t ctr[4] = {(uint32_t)p, (uint32_t)s->md_step, 1u, 0u}, out[4];
-            orc_philox4x32_10(ctr, key, out);
-            for (int a = 0; a < 3; ++a) {
-                double frand = s->p.kT > 0.0 ? amp * orc_uniform_unit(out[a]) : 0.0;
-                double fc = -s->p.zeta * (s->vel[3 * p + a] - uR[a]) + frand;
-                s->fc[3 * p + a] = fc;
-                dP[3 * p + a] = dt * fc;
-            }
-        }
-        /* Velocity Verlet: half kick, drift, forces at the new positions,
-         * half kick. */
         double L[3] = {s->p.nx, s->p.ny, s->p.nz};
-        for (int64_t p = 0; p < np; ++p) {
-            double hm = 0.5 * dt / s->mass[p];
-            for (int a = 0; a < 3; ++a) {
-                s->vel[3 * p + a] += hm * (s->fcons[3 * p + a] + s->fc[3 * p + a]);
-                s->pos[3 * p + a] = wrap_pos(s->pos[3 * p + a] + dt * s->vel[3 * p + a], L[a]);
+        if (s->p.integrator == 0) {
+            coupling_forces(s, dt, corner, delta);
+            for (int64_t p = 0; p < np; ++p) {
+                double hm = 0.5 * dt / s->mass[p];
+                for (int a = 0; a < 3; ++a) {
+                    s->vel[3 * p + a] += hm * (s->fcons[3 * p + a] + s->fc[3 * p + a]);
+                    s->pos[3 * p + a] = wrap_pos(s->pos[3 * p + a] + dt * s->vel[3 * p + a], L[a]);
+                }
             }
+            compute_conservative_forces(s, NULL);
+        } else {
+            for (int64_t p = 0; p < np; ++p) {
+                double hm = 0.5 * dt / s->mass[p];
+                for (int a = 0; a < 3; ++a) {
+                    s->vel[3 * p + a] += hm * (s->fcons[3 * p + a] + s->fc[3 * p + a]);
+                    s->pos[3 * p + a] = wrap_pos(s->pos[3 * p + a] + dt * s->vel[3 * p + a], L[a]);
+                }
+            }
+            compute_conservative_forces(s, NULL);
+            coupling_forces(s, dt, corner, delta);
         }
-        compute_conservative_forces(s, NULL);
         for (int64_t p = 0; p < np; ++p) {
             double hm = 0.5 * dt / s->mass[p];
             for (int a = 0; a < 3; ++a) s->vel[3 * p + a] += hm * (s->fcons[3 * p + a] + s->fc[3 * p + a]);
@@ -593,8 +622,8 @@ int orc_md_substep(orc_state *s) {
         for (int64_t p = 0; p < np; ++p)
             for (int k = 0; k < 8; ++k)
                 for (int a = 0; a < 3; ++a)
-                    s->jacc[3 * corner[8 * p + k] + a] -= delta[8 * p + k] * dP[3 * p + a];
-        free(corner); free(delta); free(dP);
+                    s->jacc[3 * corner[8 * p + k] + a] -= delta[8 * p + k] * (dt * s->fc[3 * p + a]);
+        free(corner); free(delta);
     }
     if (s->p.variant == 2) orc_forcing_update(s);
     s->md_step += 1;

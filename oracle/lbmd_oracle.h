@@ -21,7 +21,9 @@ typedef struct orc_params {
     int32_t nx, ny, nz;   /* periodic lattice, nodes per axis, a = 1 */
     int32_t n_sub;        /* m = tau_LB / dt, MD steps per LB step */
     int32_t variant;      /* 0 = variant A, 1 = variant B (Sec. 3), 2 = variant C (Sec. 4) */
-    int32_t pad_;
+    int32_t integrator;   /* 0: coupling force from R, v at the start of the MD step (Eq. (6)),
+                             held over both half-kicks; 1: from the half-step velocity after the
+                             drift, at the new position (see orc_md_substep) */
     double rho0;          /* initial fluid density */
     double nu;            /* kinematic shear viscosity */
     double nu_bulk;       /* bulk viscosity; < 0 selects gamma_bulk = 0 */

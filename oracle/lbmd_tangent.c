@@ -103,7 +103,10 @@ static void moments(tan_state *t) {
 }
 
 tan_state *tan_create(const orc_params *p) {
-    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->n_sub < 1 || (p->variant != 0 && p->variant != 1)) return NULL;
+    /* the tangent follows integrator 0 only */
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->n_sub < 1 || (p->variant != 0 && p->variant != 1) ||
+        p->integrator != 0)
+        return NULL;
     tan_state *t = (tan_state *)calloc(1, sizeof(tan_state));
     if (!t) return NULL;
     t->p = *p;

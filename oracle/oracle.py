@@ -44,7 +44,7 @@ def build(force: bool = False) -> str:
 class OrcParams(ct.Structure):
     _fields_ = [
         ("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32),
-        ("n_sub", ct.c_int32), ("variant", ct.c_int32), ("pad_", ct.c_int32),
+        ("n_sub", ct.c_int32), ("variant", ct.c_int32), ("integrator", ct.c_int32),
         ("rho0", ct.c_double), ("nu", ct.c_double), ("nu_bulk", ct.c_double),
         ("gamma_ghost", ct.c_double), ("kT", ct.c_double), ("zeta", ct.c_double),
         ("body_force", ct.c_double * 3), ("seed", ct.c_uint64),
@@ -145,14 +145,16 @@ class Oracle:
     """The oracle's state: populations, pending momentum transfer, particles.
 
     Parameters follow the C-ABI of the GPU library: lattice units (a = 1,
-    tau_LB = 1), ``n_sub`` = m MD steps per LB step, ``variant`` 0 = A, 1 = B, 2 = C.
+    tau_LB = 1), ``n_sub`` = m MD steps per LB step, ``variant`` 0 = A, 1 = B, 2 = C,
+    ``integrator`` 0 = coupling force from the start of the MD step (Eq. (6)),
+    1 = from the half-step velocity after the drift (see orc_md_substep).
     """
 
     def __init__(self, nx, ny, nz, *, n_sub=1, variant=1, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
-                 gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1):
+                 gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1, integrator=0):
         p = OrcParams()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
-        p.n_sub, p.variant = int(n_sub), int(variant)
+        p.n_sub, p.variant, p.integrator = int(n_sub), int(variant), int(integrator)
         p.rho0, p.nu, p.nu_bulk, p.gamma_ghost = float(rho0), float(nu), float(nu_bulk), float(gamma_ghost)
         p.kT, p.zeta = float(kT), float(zeta)
         for a in range(3):
