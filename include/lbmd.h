@@ -70,6 +70,18 @@ enum { LBMD_VARIANT_A = 0, LBMD_VARIANT_B = 1, LBMD_VARIANT_C = 2 };
  * arithmetic as in FP32; the rounding of the stored deviations breaks exact
  * mass conservation at the level of their last bit. */
 enum { LBMD_FP32 = 0, LBMD_FP64 = 1, LBMD_FP16_DEV = 2, LBMD_BF16_DEV = 3 };
+/* Where velocity Verlet evaluates the coupling force of Eq. (4).
+ * START (default, the reading of Eq. (6): R, v and F_rand of the beginning of
+ *   the MD step): F_c from R, v at the start of the step, used in both
+ *   half-kicks; the transfer goes to the nodes around the start position.
+ * HALF_STEP: after the first half-kick (with the previous step's F_c) and the
+ *   drift, F_c from the half-step velocity and the node velocities at the new
+ *   position, then the second half-kick; the transfer goes to the nodes around
+ *   the new position.  The particle takes dt F_c in two halves (this step and
+ *   the next), so fluid + particle momentum + dt/2 sum F_c is conserved.  In
+ *   a bath at rest the full-step velocity then has exactly the temperature
+ *   kT, where START gives kT / (1 - zeta dt / 2m). */
+enum { LBMD_INTEGRATOR_START = 0, LBMD_INTEGRATOR_HALF_STEP = 1 };
 
 typedef struct lbmd_params {
     int32_t nx, ny, nz;    /* lattice nodes per axis (periodic), each >= 2 */
@@ -88,6 +100,8 @@ typedef struct lbmd_params {
     int64_t max_bonds;     /* capacity reserved at creation */
     void *stream;          /* cudaStream_t to enqueue on (borrowed); NULL: the
                               context creates and owns a stream of its own */
+    int32_t integrator;    /* LBMD_INTEGRATOR_START or LBMD_INTEGRATOR_HALF_STEP */
+    int32_t reserved_;     /* 0 */
 } lbmd_params;
 
 typedef struct lbmd_ctx lbmd_ctx;

@@ -43,14 +43,16 @@ size_t pop_size(const lbmd_ctx *ctx) {
 }
 
 void free_all(lbmd_ctx *ctx) {
-    void *bufs[] = {ctx->f[0],      ctx->f[1],       ctx->node,        ctx->jacc,      ctx->pos4[0],
-                    ctx->pos4[1],   ctx->vel4[0],    ctx->vel4[1],     ctx->fcons4[0], ctx->fcons4[1],
-                    ctx->pid[0],    ctx->pid[1],     ctx->slot_of,     ctx->row_count, ctx->sort_rank, ctx->chunk_total,
-                    ctx->row_start, ctx->slot_row, ctx->migrant_slot, ctx->migrant_count,
-                    ctx->fc4,       ctx->old4,       ctx->bond_count,  ctx->bond_partner, ctx->bond_k,
-                    ctx->bond_r0,   ctx->bond_kind, ctx->staging,    ctx->red_partial, ctx->red_out,   ctx->d_lb_step,
-                    ctx->occw[0],   ctx->occw[1],    ctx->cact[0],     ctx->cact[1],   ctx->blk_done,
-                    ctx->lb_missed, ctx->missed_list};
+    void *bufs[] = {ctx->f[0],         ctx->f[1],          ctx->node,          ctx->jacc,
+                    ctx->pos4[0],      ctx->pos4[1],       ctx->vel4[0],       ctx->vel4[1],
+                    ctx->fcons4[0],    ctx->fcons4[1],     ctx->pid[0],        ctx->pid[1],
+                    ctx->slot_of,      ctx->row_count,     ctx->sort_rank,     ctx->chunk_total,
+                    ctx->row_start,    ctx->slot_row,      ctx->migrant_slot,  ctx->migrant_count,
+                    ctx->fc4[0],       ctx->fc4[1],        ctx->old4,          ctx->bond_count,
+                    ctx->bond_partner, ctx->bond_k,        ctx->bond_r0,       ctx->bond_kind,
+                    ctx->staging,      ctx->red_partial,   ctx->red_out,       ctx->d_lb_step,
+                    ctx->occw[0],      ctx->occw[1],       ctx->cact[0],       ctx->cact[1],
+                    ctx->blk_done,     ctx->lb_missed,     ctx->missed_list};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 4; ++i)
@@ -107,6 +109,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         return fail(nullptr, LBMD_ERR_ARG, "nx must not exceed 4096 (FP32) / 2048 (FP64): row gather shared memory");
     for (int d = 0; d < 3; ++d)
         if (!is_finite_d(p->body_force[d])) return fail(nullptr, LBMD_ERR_ARG, "non-finite body force");
+    if (p->integrator != LBMD_INTEGRATOR_START && p->integrator != LBMD_INTEGRATOR_HALF_STEP)
+        return fail(nullptr, LBMD_ERR_ARG, "integrator must be START or HALF_STEP");
 
     lbmd_ctx *ctx = new (std::nothrow) lbmd_ctx();
     if (!ctx) return fail(nullptr, LBMD_ERR_OOM, "host allocation");
@@ -185,7 +189,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->slot_row, (size_t)maxp * sizeof(int32_t)},
         {(void **)&ctx->migrant_slot, (size_t)2 * maxp * sizeof(int32_t)},
         {(void **)&ctx->migrant_count, 2 * sizeof(int32_t)},
-        {&ctx->fc4, (size_t)maxp * 4 * rs},
+        {&ctx->fc4[0], (size_t)maxp * 4 * rs},
+        {&ctx->fc4[1], (size_t)maxp * 4 * rs},
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
         {(void **)&ctx->occw[0], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
         {(void **)&ctx->occw[1], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
@@ -230,7 +235,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->blk_done, 0, (size_t)n_lb_blocks * sizeof(uint32_t), ctx->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(ctx->fcons4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fc4, 0, (size_t)maxp * 4 * rs, ctx->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        e = cudaMemsetAsync(ctx->fc4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
     if (e == cudaSuccess && ctx->jacc) e = cudaMemsetAsync(ctx->jacc, 0, (size_t)N * node_bytes, ctx->stream);
     if (e == cudaSuccess) e = setup_particle_kernels(ctx);
     if (e == cudaSuccess) e = launch_init_equilibrium(ctx);
@@ -281,7 +287,7 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     CK(ctx, cudaMemsetAsync((char *)ctx->fcons4[ctx->pcur] + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     // new slots are in no row bucket until the next re-ordering
     CK(ctx, cudaMemsetAsync(ctx->slot_row + ctx->np, 0xff, n * sizeof(int32_t), ctx->stream));
-    CK(ctx, cudaMemsetAsync((char *)ctx->fc4 + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
+    CK(ctx, cudaMemsetAsync((char *)ctx->fc4[ctx->pcur] + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     ctx->np += n;
     if (has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));

@@ -62,7 +62,7 @@ struct lbmd_ctx {
     void *pos4[2], *vel4[2], *fcons4[2];
     int32_t *pid[2];
     int32_t *slot_of;
-    void *fc4, *old4;
+    void *fc4[2], *old4;  // fc4 indexed by pcur: it carries the last F_c over steps (HALF_STEP)
     int32_t *row_count, *sort_rank, *chunk_total;
     int32_t *row_start;     // first slot of every cell row (ny*nz + 1 entries)
     int32_t *slot_row;      // per slot: the row bucket it belongs to, -1 if none

@@ -79,6 +79,87 @@ __device__ __forceinline__ void corner_pair(const PArgs<T> &a, uint32_t row, int
     n1 = s1 >= 0 ? a.cact[s1] : a.node[r0 + x1];
 }
 
+// Fluid velocity at a particle in cell c with fractional offsets (fx, fy, fz),
+// Eq. (5): corners k = ox + 2 oy + 4 oz = 0..7 with weights delta_k = wx wy wz;
+// variant B reads an active corner's compact record.
+template <typename T>
+__device__ __forceinline__ void interp_u(const PArgs<T> &a, const CellXYZ &c, T fx, T fy, T fz, T &ux, T &uy,
+                                         T &uz) {
+    using P = Prec<T>;
+    ux = T(0);
+    uy = T(0);
+    uz = T(0);
+    uint32_t rows[4];
+    corner_rows(c, a.ny, a.nz, rows);
+    const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
+    const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        typename P::node4 n[2];
+        if (a.variant == LBMD_VARIANT_B) {
+            corner_pair(a, rows[q], c.x, x1, n[0], n[1]);
+        } else {
+            const size_t r0 = (size_t)rows[q] * (uint32_t)a.nx;
+            n[0] = a.node[r0 + c.x];
+            n[1] = a.node[r0 + x1];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const T w = (wx[h] * wy[q & 1] * wz[q >> 1]) / P::rho_of(n[h]);
+            ux += w * P::from_fix(P::jx_of(n[h]));
+            uy += w * P::from_fix(P::jy_of(n[h]));
+            uz += w * P::from_fix(P::jz_of(n[h]));
+        }
+    }
+}
+
+// Coupling force of Eq. (4) without the conservative part: friction against
+// the interpolated fluid velocity plus the random force of Philox(id, s, 1, 0).
+template <typename T>
+__device__ __forceinline__ void coupling_force(const PArgs<T> &a, int64_t p, const typename Prec<T>::real4 &V, T ux,
+                                               T uy, T uz, T &Fx, T &Fy, T &Fz) {
+    Fx = -a.zeta * (V.x - ux);
+    Fy = -a.zeta * (V.y - uy);
+    Fz = -a.zeta * (V.z - uz);
+    if (a.noisy) {
+        const uint32_t md_step = (uint32_t)((*a.lb_step) * (unsigned long long)a.n_sub + (unsigned)a.substep);
+        const U4 r = philox4x32_10(U4{(uint32_t)a.pid[p], md_step, 1u, 0u}, a.key0, a.key1);
+        Fx += a.amp * unit_uniform<T>(r.x);
+        Fy += a.amp * unit_uniform<T>(r.y);
+        Fz += a.amp * unit_uniform<T>(r.z);
+    }
+}
+
+// Newton's third law for the particle in slot p whose transfer -delta_k dt F
+// belongs to the nodes around position R (cell c): variants A and C add it to
+// J_acc at once (nothing reads J_acc during the MD step; C then moves it into
+// the populations, forcing_update_kernel); variant B keeps R for the row
+// gather, and a particle whose cell row is no longer the row bucket it was
+// sorted into is listed as a migrant (two lists alternating with the parity
+// of the MD step).
+template <typename T>
+__device__ __forceinline__ void hand_over(const PArgs<T> &a, int64_t p, const typename Prec<T>::real4 &R,
+                                          const CellXYZ &c, T Fx, T Fy, T Fz) {
+    using P = Prec<T>;
+    if (a.variant != LBMD_VARIANT_B) {
+        uint32_t idx[8];
+        T delta[8];
+        corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
+        spread_to<T>(a.jacc, idx, delta, Fx * a.neg_scale_dt, Fy * a.neg_scale_dt, Fz * a.neg_scale_dt);
+    } else {
+        a.old4[p] = R;
+        const int32_t srow = a.slot_row[p];
+        if (srow < 0 || (uint32_t)P::cell_of(R) - (uint32_t)srow * (uint32_t)a.nx >= (uint32_t)a.nx) {
+            a.migrant_slot[(int64_t)a.mig_par * a.np_cap + atomicAdd(a.migrant_count + a.mig_par, 1)] = (int32_t)p;
+        }
+    }
+}
+
+// One MD step, coupling force from the start of the step (integrator START):
+// F = -zeta (v - u(R)) + F_rand with R, v of the beginning of the step
+// (Eqs. (4)-(6)), velocity Verlet with F held over both half-kicks (the
+// second one here for particles without conservative forces, in the bond /
+// pair kernel otherwise), transfer around the start position.
 // The variant is a run-time flag (one instruction sequence for both
 // variants, as in the LB kernel).  At least 5 blocks of 256 threads per SM
 // (3 in FP64): the corner loads are scattered, so latency hiding needs many
@@ -91,43 +172,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PAr
     const typename P::real4 R = a.pos4[p];
     typename P::real4 V = a.vel4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
-
-    // fluid velocity at the particle, Eq. (5), corners in the order
-    // k = ox + 2 oy + 4 oz = 0..7 with weights delta_k = wx wy wz
-    T ux = T(0), uy = T(0), uz = T(0);
-    {
-        uint32_t rows[4];
-        corner_rows(c, a.ny, a.nz, rows);
-        const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
-        const T wx[2] = {T(1) - R.x, R.x}, wy[2] = {T(1) - R.y, R.y}, wz[2] = {T(1) - R.z, R.z};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            typename P::node4 n[2];
-            if (a.variant == LBMD_VARIANT_B) {
-                corner_pair(a, rows[q], c.x, x1, n[0], n[1]);
-            } else {
-                const size_t r0 = (size_t)rows[q] * (uint32_t)a.nx;
-                n[0] = a.node[r0 + c.x];
-                n[1] = a.node[r0 + x1];
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const T w = (wx[h] * wy[q & 1] * wz[q >> 1]) / P::rho_of(n[h]);
-                ux += w * P::from_fix(P::jx_of(n[h]));
-                uy += w * P::from_fix(P::jy_of(n[h]));
-                uz += w * P::from_fix(P::jz_of(n[h]));
-            }
-        }
-    }
-    // coupling force, Eq. (4) without the conservative part
-    T Fx = -a.zeta * (V.x - ux), Fy = -a.zeta * (V.y - uy), Fz = -a.zeta * (V.z - uz);
-    if (a.noisy) {
-        const uint32_t md_step = (uint32_t)((*a.lb_step) * (unsigned long long)a.n_sub + (unsigned)a.substep);
-        const U4 r = philox4x32_10(U4{(uint32_t)a.pid[p], md_step, 1u, 0u}, a.key0, a.key1);
-        Fx += a.amp * unit_uniform<T>(r.x);
-        Fy += a.amp * unit_uniform<T>(r.y);
-        Fz += a.amp * unit_uniform<T>(r.z);
-    }
+    T ux, uy, uz, Fx, Fy, Fz;
+    interp_u(a, c, R.x, R.y, R.z, ux, uy, uz);
+    coupling_force(a, p, V, ux, uy, uz, Fx, Fy, Fz);
     // velocity Verlet with F held fixed over the step
     const T hm = a.half_dt * V.w;  // V.w = 1 / mass
     T Gx = Fx, Gy = Fy, Gz = Fz;
@@ -153,24 +200,51 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PAr
     a.pos4[p] = P::make_pos(fx, fy, fz, cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz));
     a.vel4[p] = V;
     if (BONDS || a.variant == LBMD_VARIANT_B) a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
+    hand_over(a, p, R, c, Fx, Fy, Fz);
+}
 
-    if (a.variant != LBMD_VARIANT_B) {
-        // Newton's third law, Eqs. (7), (8): straight into J_acc (variant C
-        // then moves it into the populations, forcing_update_kernel)
-        uint32_t idx[8];
-        T delta[8];
-        corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
-        spread_to<T>(a.jacc, idx, delta, Fx * a.neg_scale_dt, Fy * a.neg_scale_dt, Fz * a.neg_scale_dt);
-    } else {
-        a.old4[p] = R;
-        // a particle whose cell row is no longer the row bucket it was sorted
-        // into is spread separately, after the row gather; the two lists
-        // alternate with the parity of the MD step
-        const int32_t srow = a.slot_row[p];
-        if (srow < 0 || (uint32_t)P::cell_of(R) - (uint32_t)srow * (uint32_t)a.nx >= (uint32_t)a.nx) {
-            a.migrant_slot[(int64_t)a.mig_par * a.np_cap + atomicAdd(a.migrant_count + a.mig_par, 1)] = (int32_t)p;
-        }
+// One MD step, coupling force from the half-step velocity (integrator
+// HALF_STEP): first half-kick with the previous step's F (kept in fc4) and
+// the conservative force, drift, then F = -zeta (v_half - u(R')) + F_rand at
+// the new position R', second half-kick (here without conservative forces,
+// in the bond / pair kernel otherwise), transfer around R'.
+template <typename T, bool BONDS>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_half_kernel(PArgs<T> a) {
+    using P = Prec<T>;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const typename P::real4 R = a.pos4[p];
+    typename P::real4 V = a.vel4[p];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
+    const T hm = a.half_dt * V.w;  // V.w = 1 / mass
+    typename P::real4 G = a.fc4[p];
+    if (BONDS) {
+        const typename P::real4 Fc = a.fcons4[p];
+        G.x += Fc.x;
+        G.y += Fc.y;
+        G.z += Fc.z;
     }
+    V.x += hm * G.x;
+    V.y += hm * G.y;
+    V.z += hm * G.z;
+    T fx = R.x, fy = R.y, fz = R.z;
+    CellXYZ cn = c;
+    advance(fx, cn.x, a.dt * V.x, a.nx);
+    advance(fy, cn.y, a.dt * V.y, a.ny);
+    advance(fz, cn.z, a.dt * V.z, a.nz);
+    const typename P::real4 Rn = P::make_pos(fx, fy, fz, cn.x + (int64_t)a.nx * (cn.y + (int64_t)a.ny * cn.z));
+    T ux, uy, uz, Fx, Fy, Fz;
+    interp_u(a, cn, fx, fy, fz, ux, uy, uz);
+    coupling_force(a, p, V, ux, uy, uz, Fx, Fy, Fz);
+    if (!BONDS) {
+        V.x += hm * Fx;
+        V.y += hm * Fy;
+        V.z += hm * Fz;
+    }
+    a.pos4[p] = Rn;
+    a.vel4[p] = V;
+    a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
+    hand_over(a, p, Rn, cn, Fx, Fy, Fz);
 }
 
 
@@ -556,15 +630,17 @@ __global__ void __launch_bounds__(1024) sort_finalize_kernel(const int32_t *row_
     if (i == n - 1) row_start[n] = np;
 }
 
-// Move every particle to row_start[row] + rank within the row.
+// Move every particle to row_start[row] + rank within the row, with its
+// conservative force (if any) and its last coupling force (integrator
+// HALF_STEP, where it carries over to the next MD step).
 template <typename T>
 __global__ void __launch_bounds__(256)
     sort_scatter_kernel(const typename Prec<T>::real4 *pos_in, const typename Prec<T>::real4 *vel_in,
-                        const typename Prec<T>::real4 *fcons_in, const int32_t *pid_in,
-                        typename Prec<T>::real4 *pos_out,
-                        typename Prec<T>::real4 *vel_out, typename Prec<T>::real4 *fcons_out, int32_t *pid_out,
+                        const typename Prec<T>::real4 *fcons_in, const typename Prec<T>::real4 *fc_in,
+                        const int32_t *pid_in, typename Prec<T>::real4 *pos_out, typename Prec<T>::real4 *vel_out,
+                        typename Prec<T>::real4 *fcons_out, typename Prec<T>::real4 *fc_out, int32_t *pid_out,
                         int32_t *slot_of, int32_t *slot_row, const int32_t *row_start, const int32_t *rank, int64_t np,
-                        FastDiv fnx, int bonds) {
+                        FastDiv fnx, int bonds, int carry_fc) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const typename Prec<T>::real4 R = pos_in[p];
@@ -574,6 +650,7 @@ __global__ void __launch_bounds__(256)
     pos_out[dst] = R;
     vel_out[dst] = vel_in[p];
     if (bonds) fcons_out[dst] = fcons_in[p];
+    if (carry_fc) fc_out[dst] = fc_in[p];
     const int32_t id = pid_in[p];
     pid_out[dst] = id;
     slot_of[id] = dst;
@@ -694,7 +771,7 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.fcons4 = static_cast<typename P::real4 *>(ctx->fcons4[b]);
     a.pid = ctx->pid[b];
     a.slot_of = ctx->slot_of;
-    a.fc4 = static_cast<typename P::real4 *>(ctx->fc4);
+    a.fc4 = static_cast<typename P::real4 *>(ctx->fc4[b]);
     a.old4 = static_cast<typename P::real4 *>(ctx->old4);
     a.node = static_cast<typename P::node4 *>(ctx->node);
     a.jacc = static_cast<typename P::node4 *>(ctx->jacc);
@@ -744,10 +821,16 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     const bool cons = has_cons(ctx);
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
     cudaError_t e;
-    if (cons)
+    if (ctx->p.integrator == LBMD_INTEGRATOR_HALF_STEP) {
+        if (cons)
+            couple_half_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
+        else
+            couple_half_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
+    } else if (cons) {
         couple_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
-    else
+    } else {
         couple_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (cons) {
@@ -804,10 +887,11 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sort_scatter_kernel<T><<<blocks, 256, 0, ctx->stream>>>(
             static_cast<const R4 *>(ctx->pos4[b]), static_cast<const R4 *>(ctx->vel4[b]),
-            static_cast<const R4 *>(ctx->fcons4[b]), ctx->pid[b], static_cast<R4 *>(ctx->pos4[o]),
-            static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]), ctx->pid[o], ctx->slot_of,
-            ctx->slot_row, ctx->row_start, ctx->sort_rank, ctx->np, make_fastdiv((uint32_t)ctx->p.nx),
-            has_cons(ctx) ? 1 : 0);
+            static_cast<const R4 *>(ctx->fcons4[b]), static_cast<const R4 *>(ctx->fc4[b]), ctx->pid[b],
+            static_cast<R4 *>(ctx->pos4[o]), static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]),
+            static_cast<R4 *>(ctx->fc4[o]), ctx->pid[o], ctx->slot_of, ctx->slot_row, ctx->row_start,
+            ctx->sort_rank, ctx->np, make_fastdiv((uint32_t)ctx->p.nx), has_cons(ctx) ? 1 : 0,
+            ctx->p.integrator == LBMD_INTEGRATOR_HALF_STEP ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ctx->pcur = o;

@@ -36,13 +36,14 @@ def _chains(n_chains, n_beads, box, seed):
 
 
 def build_system(variant: str, m: int, dt: float, zeta: float, *, n_chains=10, n_beads=256, box=20, seed=1,
-                 precision="fp32"):
+                 precision="fp32", integrator="start"):
     """One context holding the Kremer-Grest system at one grid point."""
     lp = lj_units.lattice_params(m, dt, zeta)
     pos, bonds = _chains(n_chains, n_beads, box, seed)
     n = pos.shape[0]
     sim = lbmd.LBMD(box, box, box, variant=variant, precision=precision, n_sub=m, kT=lp["kT"], zeta=lp["zeta"],
-                    nu=lp["nu"], rho0=lp["rho0"], seed=seed, max_particles=n, max_bonds=bonds.shape[0])
+                    nu=lp["nu"], rho0=lp["rho0"], seed=seed, max_particles=n, max_bonds=bonds.shape[0],
+                    integrator=integrator)
     sim.add_particles(pos, inputs.maxwell_velocities(n, lp["kT"], seed))
     sim.set_lj(lp["lj_eps"], lp["lj_sigma"], lp["lj_rc"])
     sim.add_fene_bonds(bonds, lp["fene_k"], lp["fene_R0"])
@@ -68,7 +69,8 @@ def measure_temperature(variant: str, m: int, dt: float, zeta: float, *, equil_t
     wall = time.perf_counter() - t0
     sim.close()
     blocks = temps.reshape(n_blocks, -1).mean(axis=1)
-    return {"variant": variant, "m": m, "dt": dt, "zeta": zeta, "T": float(temps.mean()),
+    return {"variant": variant, "m": m, "dt": dt, "zeta": zeta, "integrator": kw.get("integrator", "start"),
+            "T": float(temps.mean()),
             "stderr": float(blocks.std(ddof=1) / np.sqrt(n_blocks)), "samples": int(n_samples),
             "measure_tau": n_samples * every * tau_lb,
             "ms_per_md_step": 1e3 * wall / (n_samples * every * m)}
@@ -98,6 +100,9 @@ def main(argv=None):
     ap.add_argument("--variants", default="A,B,C")
     ap.add_argument("--quick", action="store_true", help="shorter windows (equilibrate 10 tau, measure 30 tau)")
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--integrator", default="start", choices=["start", "half_step"],
+                    help="where velocity Verlet evaluates the coupling force (lbmd_params.integrator)")
+    ap.add_argument("--no-costs", action="store_true")
     args = ap.parse_args(argv)
     eq, ms = (10.0, 30.0) if args.quick else (20.0, 100.0)
     rows = []
@@ -106,10 +111,11 @@ def main(argv=None):
         for m in PAPER_MS:
             for dt in dts:
                 for z in ZETAS:
-                    r = measure_temperature(v, m, dt, z, equil_tau=eq, measure_tau=ms, precision=args.precision)
+                    r = measure_temperature(v, m, dt, z, equil_tau=eq, measure_tau=ms, precision=args.precision,
+                                            integrator=args.integrator)
                     rows.append(r)
                     print(json.dumps(r), flush=True)
-    costs = [variant_costs(m) for m in PAPER_MS]
+    costs = [] if args.no_costs else [variant_costs(m, integrator=args.integrator) for m in PAPER_MS]
     for c in costs:
         print(json.dumps(c), flush=True)
     if args.out:
