@@ -40,7 +40,8 @@ def test_params_struct_layout():
     assert P.body_force.offset == 24 + 6 * 8
     assert P.seed.offset == 24 + 9 * 8
     assert P.stream.offset == 24 + 12 * 8
-    assert ct.sizeof(P) == 24 + 13 * 8
+    assert P.integrator.offset == 24 + 13 * 8
+    assert ct.sizeof(P) == 24 + 14 * 8
     O = lbmd.LbmdObservables
     assert O.lb_step.offset == 9 * 8 and ct.sizeof(O) == 11 * 8
 
@@ -58,3 +59,22 @@ def test_product_package_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 for bad in ("import oracle", "from oracle", "lbmd_oracle", "orc_"):
                     assert bad not in text, (f, bad)
+
+
+def test_params_layout_matches_the_c_compiler(tmp_path):
+    # every field offset of the ctypes mirror equals the C compiler's offsetof
+    import os
+    import subprocess
+    from paper_1610_02733_gb300 import lbmd
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    names = [f[0] for f in lbmd.LbmdParams._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbmd.h"\nint main(void) {\n' +
+                   "".join('printf("%%zu\\n", offsetof(lbmd_params, %s));\n' % n for n in names) +
+                   'printf("%zu\\n", sizeof(lbmd_params));\nreturn 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [getattr(lbmd.LbmdParams, n).offset for n in names] + [ct.sizeof(lbmd.LbmdParams)]
+    assert got == want
+
