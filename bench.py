@@ -280,6 +280,42 @@ def _variant_costs(torch, lbmd, inputs, stream, pos, vel, steps, ms_b):
     return out
 
 
+def _kremer_grest_form(torch, stream):
+    """The paper's test system (Sec. 4): 10 Kremer-Grest chains of 256 beads in
+    (20 sigma)^3, LJ units converted to lattice units, HALF_STEP integrator.
+    GPU time per MD step (graph-replayed cycles, CUDA events) of variants A,
+    B and C at m = 10, dt = 0.005 tau, zeta = 20 mu/tau (the paper's cost
+    comparison), and the share of the all-pairs Lennard-Jones forces (B with
+    the LJ forces switched off, FENE springs kept)."""
+    from paper_1610_02733_gb300 import sweep
+
+    def per_md_step(variant, lj=True, cycles=300):
+        sim, lp = sweep.build_system(variant, 10, 0.005, 20.0, integrator="half_step", stream=stream.cuda_stream)
+        if not lj:
+            sim.set_lj(0.0, 1.0, 0.0)
+        sim.run_cycles(20)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        sim.run_cycles(cycles)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / (cycles * 10)
+        sim.close()
+        return ms
+
+    ms = {v: per_md_step(v) for v in ("A", "B", "C")}
+    no_lj = per_md_step("B", lj=False)
+    n = 2560
+    return {"workload": "10 x 256-bead Kremer-Grest chains in (20 sigma)^3 (2560 beads, 20^3 lattice), m=10, "
+                        "dt=0.005 tau, zeta=20 mu/tau, kT=epsilon, HALF_STEP integrator, FP32",
+            "ms_per_md_step": {v: round(x, 5) for v, x in ms.items()},
+            "particle_substeps_per_s": {v: float("%.4g" % (n / (x * 1e-3))) for v, x in ms.items()},
+            "extra_vs_A": {v: round(ms[v] / ms["A"] - 1.0, 4) for v in ("B", "C")},
+            "lj_ms_per_md_step": round(ms["B"] - no_lj, 5),
+            "lj_pairs_per_s": float("%.4g" % (n * (n - 1) / ((ms["B"] - no_lj) * 1e-3))) if ms["B"] > no_lj else None}
+
+
 def _adjoint_form(torch, lbmd, inputs):
     """The adjoint form: L = mean particle drag along x over 200 MD steps
     (32^3, 64 ideal particles, zeta = 1.5, m = 10, body force 1e-5 along x,
@@ -479,6 +515,7 @@ def run_gpu(args):
         line["variants"] = _variant_costs(torch, lbmd, inputs, stream, pos0, vel0, min(args.steps, 30), ms_per_step)
         line["batched_replicas"] = _batched_replicas(torch, lbmd, inputs, stream, peak)
         line["adjoint"] = _adjoint_form(torch, lbmd, inputs)
+        line["kremer_grest"] = _kremer_grest_form(torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -569,7 +606,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the reduced-precision, variant A/C, batched and adjoint forms")
+                    help="skip the reduced-precision, variant A/C, batched, adjoint and Kremer-Grest forms")
     ap.add_argument("--edge", type=int, default=256, help="lattice edge (profiling of smaller cases)")
     ap.add_argument("--lattice", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="non-cubic lattice (profiling of smaller cases with 256-node rows)")

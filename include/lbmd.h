@@ -82,6 +82,15 @@ enum { LBMD_FP32 = 0, LBMD_FP64 = 1, LBMD_FP16_DEV = 2, LBMD_BF16_DEV = 3 };
  *   a bath at rest the full-step velocity then has exactly the temperature
  *   kT, where START gives kT / (1 - zeta dt / 2m). */
 enum { LBMD_INTEGRATOR_START = 0, LBMD_INTEGRATOR_HALF_STEP = 1 };
+/* How variant B hands each MD step's transfers to the nodes (Eqs. (7), (8)).
+ * ROWS: a gather per lattice row over the particles re-ordered by row, plus
+ * atomics for the particles that left their row (few atomics; pays off for
+ * many particles).  ATOMIC: every particle adds its 8 corner transfers with
+ * integer atomics (one launch; pays off for few particles).  AUTO: ATOMIC
+ * below LBMD_SPREAD_ATOMIC_MAX particles, ROWS above.  The transfers are
+ * fixed-point integers, so all three give bitwise the same results. */
+enum { LBMD_SPREAD_AUTO = 0, LBMD_SPREAD_ROWS = 1, LBMD_SPREAD_ATOMIC = 2 };
+#define LBMD_SPREAD_ATOMIC_MAX 32768
 
 typedef struct lbmd_params {
     int32_t nx, ny, nz;    /* lattice nodes per axis (periodic), each >= 2 */
@@ -101,7 +110,7 @@ typedef struct lbmd_params {
     void *stream;          /* cudaStream_t to enqueue on (borrowed); NULL: the
                               context creates and owns a stream of its own */
     int32_t integrator;    /* LBMD_INTEGRATOR_START or LBMD_INTEGRATOR_HALF_STEP */
-    int32_t reserved_;     /* 0 */
+    int32_t spread;        /* variant B: LBMD_SPREAD_AUTO, _ROWS or _ATOMIC */
 } lbmd_params;
 
 typedef struct lbmd_ctx lbmd_ctx;

@@ -111,6 +111,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         if (!is_finite_d(p->body_force[d])) return fail(nullptr, LBMD_ERR_ARG, "non-finite body force");
     if (p->integrator != LBMD_INTEGRATOR_START && p->integrator != LBMD_INTEGRATOR_HALF_STEP)
         return fail(nullptr, LBMD_ERR_ARG, "integrator must be START or HALF_STEP");
+    if (p->spread < LBMD_SPREAD_AUTO || p->spread > LBMD_SPREAD_ATOMIC)
+        return fail(nullptr, LBMD_ERR_ARG, "spread must be AUTO, ROWS or ATOMIC");
 
     lbmd_ctx *ctx = new (std::nothrow) lbmd_ctx();
     if (!ctx) return fail(nullptr, LBMD_ERR_OOM, "host allocation");

@@ -30,6 +30,9 @@
 // is about as large as the touched part of the lattice rather than the whole
 // node field, and a node that is not active (one a particle reaches only
 // after moving to another cell) through the node field, as before.
+#include <algorithm>
+#include <cmath>
+
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
 #include "particle_core.cuh"
@@ -46,6 +49,7 @@ struct PArgs {
     const double *bond_k, *bond_r0;
     const uint8_t *bond_kind;
     T lj_eps24, lj_sig2, lj_rc2;  // Lennard-Jones: 24 eps, sigma^2, r_cut^2
+    int lj_cells;                 // ceil(r_cut): larger cell offsets are beyond the cut-off
     int nx, ny, nz;
     FastDiv fd_nx, fd_ny;  // division by nx and ny
     int64_t np;
@@ -62,6 +66,8 @@ struct PArgs {
     typename P::node4 *cact;
     int occ_words;
     int32_t *migrant_slot, *migrant_count;  // two lists of np_cap slots, two counters
+    int b_atomic;      // variant B spreads every particle with atomics (no row gather, no migrant lists)
+    int kick_spreads;  // ... and the bond / pair kernel does it, after every particle has read the nodes
     int64_t np_cap;
 };
 
@@ -148,6 +154,7 @@ __device__ __forceinline__ void hand_over(const PArgs<T> &a, int64_t p, const ty
         spread_to<T>(a.jacc, idx, delta, Fx * a.neg_scale_dt, Fy * a.neg_scale_dt, Fz * a.neg_scale_dt);
     } else {
         a.old4[p] = R;
+        if (a.b_atomic) return;
         const int32_t srow = a.slot_row[p];
         if (srow < 0 || (uint32_t)P::cell_of(R) - (uint32_t)srow * (uint32_t)a.nx >= (uint32_t)a.nx) {
             a.migrant_slot[(int64_t)a.mig_par * a.np_cap + atomicAdd(a.migrant_count + a.mig_par, 1)] = (int32_t)p;
@@ -392,34 +399,39 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) spread_rows_kernel(PArgs<T>
 
 // Variant B: the migrants of this MD step, spread with atomics once the row
 // gather is done (into the compact record of an active corner, the node
-// field entry of an inactive one).
+// field entry of an inactive one).  With `all`, every particle is spread this
+// way and the row gather does not run (LBMD_SPREAD_ATOMIC).
 template <typename T>
-__global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a) {
+__device__ __forceinline__ void spread_corner_atomic(const PArgs<T> &a, int64_t p, int k) {
+    using P = Prec<T>;
+    const typename P::real4 R = a.old4[p];
+    const typename P::real4 F = a.fc4[p];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
+    const int ox = k & 1, oy = (k >> 1) & 1, oz = k >> 2;
+    const int xn = ox ? (c.x + 1 == a.nx ? 0 : c.x + 1) : c.x;
+    const int yn = oy ? (c.y + 1 == a.ny ? 0 : c.y + 1) : c.y;
+    const int zn = oz ? (c.z + 1 == a.nz ? 0 : c.z + 1) : c.z;
+    const T delta = (ox ? R.x : T(1) - R.x) * (oy ? R.y : T(1) - R.y) * (oz ? R.z : T(1) - R.z);
+    const uint32_t row = (uint32_t)yn + (uint32_t)a.ny * (uint32_t)zn;
+    const int sl = active_slot(a.occw[(size_t)row * (uint32_t)a.occ_words + (xn >> 5)], xn);
+    typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[(size_t)row * (uint32_t)a.nx + xn];
+    const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
+    P::add_transfer(rec, P::to_fix_neg(delta, sx), P::to_fix_neg(delta, sy), P::to_fix_neg(delta, sz));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a, int all) {
     using P = Prec<T>;
     const int par = a.mig_par;
-    const int n = a.migrant_count[par];
+    const int n = all ? (int)a.np : a.migrant_count[par];
     // the other list serves the next MD step: empty it now (nobody uses it
     // during this one)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.migrant_count[par ^ 1] = 0;
     const int32_t *list = a.migrant_slot + (int64_t)par * a.np_cap;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int64_t p = list[t];
-        const typename P::real4 R = a.old4[p];
-        const typename P::real4 F = a.fc4[p];
-        const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
-        uint32_t idx[8], rows[4];
-        T delta[8];
-        corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
-        corner_rows(c, a.ny, a.nz, rows);
-        const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
-        const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
+        const int64_t p = all ? (int64_t)t : (int64_t)list[t];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int xn = (k & 1) ? x1 : c.x;
-            const int sl = active_slot(a.occw[(size_t)rows[k >> 1] * (uint32_t)a.occ_words + (xn >> 5)], xn);
-            typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[idx[k]];
-            P::add_transfer(rec, P::to_fix_neg(delta[k], sx), P::to_fix_neg(delta[k], sy), P::to_fix_neg(delta[k], sz));
-        }
+        for (int k = 0; k < 8; ++k) spread_corner_atomic(a, p, k);
     }
 }
 
@@ -492,6 +504,12 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
         V.y += hm * (Fy + Fc.y);
         V.z += hm * (Fz + Fc.z);
         a.vel4[p] = V;
+        // variant B, all atomics: every particle has read the nodes (couple
+        // kernel), so the transfers can go in now
+        if (a.kick_spreads) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) spread_corner_atomic(a, p, k);
+        }
     }
 }
 
@@ -503,8 +521,11 @@ __device__ __forceinline__ int nearest_image(int d, int n) {
 }
 
 // Conservative forces with Lennard-Jones (Kremer-Grest monomers, Sec. 4):
-// one warp per particle id i.  The lanes run over all other ids j (lane l
-// takes j = l, l + 32, ...), add the LJ force of every j within the cut-off,
+// one warp per particle id i, eight per block.  The block stages the other
+// particles in tiles of PairTile ids in shared memory (cell coordinates and
+// offsets, decoded once per block instead of once per pair); the lanes then
+// run over the tile (lane l takes ids l, l + 32, ...) and add the LJ force of
+// every j within the cut-off,
 //   F_i += g d,  g = -24 eps (2 t^2 - t) / r^2,  t = (sigma^2 / r^2)^3,
 // d = R_j - R_i at the nearest image (cell offsets wrapped as integers, then
 // the fractional offsets added: exact to the last bit of the offsets; every
@@ -512,33 +533,64 @@ __device__ __forceinline__ int nearest_image(int d, int n) {
 // the cut-off); lane b < n_bonds(i) adds bond b.  The lane sums are combined
 // by a fixed butterfly, so the result does not depend on the slot order.
 // With KICK, lane 0 also makes the second velocity-Verlet half-kick.
+template <typename T>
+struct PairTile {
+    static constexpr int N = sizeof(T) == 4 ? 2048 : 1024;  // 48 / 36 KB of shared memory
+};
+
+constexpr int PAIR_THREADS = 256;  // eight particles per block
+
 template <typename T, bool KICK>
-__global__ void __launch_bounds__(256) pair_kick_kernel(PArgs<T> a) {
+__global__ void __launch_bounds__(PAIR_THREADS) pair_kick_kernel(PArgs<T> a) {
     using P = Prec<T>;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    constexpr int TILE = PairTile<T>::N;
+    __shared__ T s_f[3][TILE];
+    __shared__ int s_c[3][TILE];
     const int lane = threadIdx.x & 31;
-    if (i >= a.np) return;  // whole warps
-    const int64_t p = a.slot_of[i];
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const bool live = i < a.np;
+    const int64_t p = live ? a.slot_of[i] : 0;
     const typename P::real4 R = a.pos4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
     T Fx = T(0), Fy = T(0), Fz = T(0);
-#pragma unroll 4
-    for (int64_t j = lane; j < a.np; j += 32) {
-        const typename P::real4 S = a.pos4[a.slot_of[j]];
-        const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
-        const T dx = T(nearest_image(d.x - c.x, a.nx)) + (S.x - R.x);
-        const T dy = T(nearest_image(d.y - c.y, a.ny)) + (S.y - R.y);
-        const T dz = T(nearest_image(d.z - c.z, a.nz)) + (S.z - R.z);
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        if (j != i && r2 < a.lj_rc2) {
-            const T s = a.lj_sig2 / r2;
-            const T t = s * s * s;
-            const T g = -a.lj_eps24 * (T(2) * t * t - t) / r2;
-            Fx += g * dx;
-            Fy += g * dy;
-            Fz += g * dz;
+    for (int64_t j0 = 0; j0 < a.np; j0 += TILE) {
+        const int cnt = a.np - j0 < TILE ? (int)(a.np - j0) : TILE;
+        __syncthreads();  // the previous tile is consumed
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const typename P::real4 S = a.pos4[a.slot_of[j0 + k]];
+            const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
+            s_f[0][k] = S.x;
+            s_f[1][k] = S.y;
+            s_f[2][k] = S.z;
+            s_c[0][k] = d.x;
+            s_c[1][k] = d.y;
+            s_c[2][k] = d.z;
+        }
+        __syncthreads();
+        if (!live) continue;
+        for (int k = lane; k < cnt; k += 32) {
+            // cell offsets first: |d| > |cell offset| - 1, so a pair more than
+            // lj_cells cells apart along an axis is beyond the cut-off (the
+            // exact test below would reject it too)
+            const int ix = nearest_image(s_c[0][k] - c.x, a.nx);
+            const int iy = nearest_image(s_c[1][k] - c.y, a.ny);
+            const int iz = nearest_image(s_c[2][k] - c.z, a.nz);
+            if (abs(ix) > a.lj_cells || abs(iy) > a.lj_cells || abs(iz) > a.lj_cells) continue;
+            const T dx = T(ix) + (s_f[0][k] - R.x);
+            const T dy = T(iy) + (s_f[1][k] - R.y);
+            const T dz = T(iz) + (s_f[2][k] - R.z);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (j0 + k != i && r2 < a.lj_rc2) {
+                const T s = a.lj_sig2 / r2;
+                const T t = s * s * s;
+                const T g = -a.lj_eps24 * (T(2) * t * t - t) / r2;
+                Fx += g * dx;
+                Fy += g * dy;
+                Fz += g * dz;
+            }
         }
     }
+    if (!live) return;  // whole warps, after the block's last barrier
     if (lane < a.bond_count[i]) {
         const int64_t e = i * LBMD_MAX_BONDS_PER_PARTICLE + lane;
         T dx, dy, dz;
@@ -554,6 +606,9 @@ __global__ void __launch_bounds__(256) pair_kick_kernel(PArgs<T> a) {
         Fy += __shfl_xor_sync(0xffffffffu, Fy, off);
         Fz += __shfl_xor_sync(0xffffffffu, Fz, off);
     }
+    // variant B, all atomics: the couple kernel is done, so every particle
+    // has read the nodes; lanes 0..7 hand over the 8 corner transfers
+    if (KICK && a.kick_spreads && lane < 8) spread_corner_atomic(a, p, lane);
     if (lane != 0) return;
     a.fcons4[p] = P::make4(Fx, Fy, Fz, T(0));
     if (KICK) {
@@ -783,6 +838,7 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.lj_eps24 = (T)(24.0 * ctx->lj_eps);
     a.lj_sig2 = (T)(ctx->lj_sigma * ctx->lj_sigma);
     a.lj_rc2 = (T)(ctx->lj_rc * ctx->lj_rc);
+    a.lj_cells = (int)std::ceil(ctx->lj_rc);
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
@@ -807,6 +863,8 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.migrant_slot = ctx->migrant_slot;
     a.migrant_count = ctx->migrant_count;
     a.np_cap = ctx->p.max_particles > 0 ? ctx->p.max_particles : 1;
+    a.b_atomic = 0;
+    a.kick_spreads = 0;
     a.occw = active_words_now(ctx);
     a.cact = static_cast<typename P::node4 *>(active_records_now(ctx));
     a.occ_words = active_words(ctx->p.nx);
@@ -820,6 +878,10 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
     const bool cons = has_cons(ctx);
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
+    const bool atomic = B && (ctx->p.spread == LBMD_SPREAD_ATOMIC ||
+                              (ctx->p.spread == LBMD_SPREAD_AUTO && ctx->np < LBMD_SPREAD_ATOMIC_MAX));
+    a.b_atomic = atomic ? 1 : 0;
+    a.kick_spreads = atomic && cons ? 1 : 0;
     cudaError_t e;
     if (ctx->p.integrator == LBMD_INTEGRATOR_HALF_STEP) {
         if (cons)
@@ -835,7 +897,7 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     if (e != cudaSuccess) return e;
     if (cons) {
         if (ctx->lj_rc > 0.0)
-            pair_kick_kernel<T, true><<<(unsigned)((32 * ctx->np + 255) / 256), 256, 0, ctx->stream>>>(a);
+            pair_kick_kernel<T, true><<<(unsigned)((ctx->np + 7) / 8), PAIR_THREADS, 0, ctx->stream>>>(a);
         else
             bond_kick_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
         e = cudaGetLastError();
@@ -843,12 +905,19 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     }
     if (ctx->p.variant == LBMD_VARIANT_C) return launch_forcing_update(ctx);
     if (B) {
-        const int rows = (int)((int64_t)ctx->p.ny * ctx->p.nz);
-        const int gw = ctx->gather_warps;
-        const unsigned gblocks = (unsigned)((rows + gw - 1) / gw);
-        spread_rows_kernel<T><<<gblocks, 32 * gw, gather_smem_bytes<T>(ctx, gw), ctx->stream>>>(a, rows);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        migrant_spread_kernel<T><<<ctx->sm_count, 256, 0, ctx->stream>>>(a);
+        if (atomic && cons) {
+            // spread by the bond / pair kernel above
+        } else if (atomic) {
+            const unsigned sb = (unsigned)std::min<int64_t>(ctx->sm_count, (ctx->np + 255) / 256);
+            migrant_spread_kernel<T><<<sb, 256, 0, ctx->stream>>>(a, 1);
+        } else {
+            const int rows = (int)((int64_t)ctx->p.ny * ctx->p.nz);
+            const int gw = ctx->gather_warps;
+            const unsigned gblocks = (unsigned)((rows + gw - 1) / gw);
+            spread_rows_kernel<T><<<gblocks, 32 * gw, gather_smem_bytes<T>(ctx, gw), ctx->stream>>>(a, rows);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            migrant_spread_kernel<T><<<ctx->sm_count, 256, 0, ctx->stream>>>(a, 0);
+        }
         e = cudaGetLastError();
     }
     return e;
@@ -860,7 +929,7 @@ static cudaError_t bond_forces_t(lbmd_ctx *ctx) {
     PArgs<T> a = make_pargs<T>(ctx, 0);
     const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
     if (ctx->lj_rc > 0.0)
-        pair_kick_kernel<T, false><<<(unsigned)((32 * ctx->np + 255) / 256), 256, 0, ctx->stream>>>(a);
+        pair_kick_kernel<T, false><<<(unsigned)((ctx->np + 7) / 8), PAIR_THREADS, 0, ctx->stream>>>(a);
     else
         bond_kick_kernel<T, false><<<blocks, 256, 0, ctx->stream>>>(a);
     return cudaGetLastError();

@@ -36,14 +36,14 @@ def _chains(n_chains, n_beads, box, seed):
 
 
 def build_system(variant: str, m: int, dt: float, zeta: float, *, n_chains=10, n_beads=256, box=20, seed=1,
-                 precision="fp32", integrator="start"):
+                 precision="fp32", integrator="start", stream=None):
     """One context holding the Kremer-Grest system at one grid point."""
     lp = lj_units.lattice_params(m, dt, zeta)
     pos, bonds = _chains(n_chains, n_beads, box, seed)
     n = pos.shape[0]
     sim = lbmd.LBMD(box, box, box, variant=variant, precision=precision, n_sub=m, kT=lp["kT"], zeta=lp["zeta"],
                     nu=lp["nu"], rho0=lp["rho0"], seed=seed, max_particles=n, max_bonds=bonds.shape[0],
-                    integrator=integrator)
+                    integrator=integrator, stream=stream)
     sim.add_particles(pos, inputs.maxwell_velocities(n, lp["kT"], seed))
     sim.set_lj(lp["lj_eps"], lp["lj_sigma"], lp["lj_rc"])
     sim.add_fene_bonds(bonds, lp["fene_k"], lp["fene_R0"])
@@ -103,7 +103,24 @@ def main(argv=None):
     ap.add_argument("--integrator", default="start", choices=["start", "half_step"],
                     help="where velocity Verlet evaluates the coupling force (lbmd_params.integrator)")
     ap.add_argument("--no-costs", action="store_true")
+    ap.add_argument("--point", nargs=4, metavar=("VARIANT", "M", "DT", "ZETA"), default=None,
+                    help="only run one grid point for --cycles LB cycles (e.g. under a profiler)")
+    ap.add_argument("--cycles", type=int, default=100)
     args = ap.parse_args(argv)
+    if args.point:
+        v, m, dt, z = args.point[0], int(args.point[1]), float(args.point[2]), float(args.point[3])
+        sim, lp = build_system(v, m, dt, z, precision=args.precision, integrator=args.integrator)
+        sim.run_cycles(3)
+        sim.observables()
+        t0 = time.perf_counter()
+        sim.run_cycles(args.cycles)
+        ob = sim.observables()
+        wall = time.perf_counter() - t0
+        print(json.dumps({"variant": v, "m": m, "dt": dt, "zeta": z, "cycles": args.cycles,
+                          "ms_per_md_step": 1e3 * wall / (args.cycles * m),
+                          "T": lj_units.temperature_in_lj(ob["kT_particles"], lp)}))
+        sim.close()
+        return
     eq, ms = (10.0, 30.0) if args.quick else (20.0, 100.0)
     rows = []
     for v in args.variants.split(","):

@@ -54,6 +54,34 @@ def test_one_md_step_with_lj_and_fene(precision, variant):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_lj_unordered_particles(precision):
+    # LJ between particles in no spatial order by id (every chunk of 32 ids
+    # spans the box), more than one tile of ids: the pair kernel cannot skip
+    # chunks and runs over several tiles
+    shape, n = (14, 12, 11), 1400
+    lp = lj_units.lattice_params(5, 0.005, 5.0)
+    o, g = pair(shape, precision=precision, variant="B", n_sub=5, kT=lp["kT"], zeta=lp["zeta"], nu=lp["nu"],
+                seed=25, max_particles=n)
+    # well separated start (> 1.07 apart, across the periodic faces too): a
+    # jittered lattice whose spacing divides the box, shuffled ids
+    axes = [np.arange(L // 1.05) * (L / (L // 1.05)) for L in shape]
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(25)
+    pos = grid[rng.permutation(grid.shape[0])[:n]] + 0.02 * rng.random((n, 3))
+    vel = inputs.maxwell_velocities(n, lp["kT"], 25)
+    for obj in (o, g):
+        obj.add_particles(pos, vel)
+        obj.set_lj(lp["lj_eps"], lp["lj_sigma"], lp["lj_rc"])
+    for _ in range(2):
+        o.md_substep()
+        g.md_substep()
+    po, vo = o.particles()
+    pg, vg = g.particles()
+    assert_vec_close(vg, vo, precision, "velocities")
+    assert np.abs(_periodic_diff(pg, po, shape)).max() <= {"fp32": 1e-5, "fp64": 1e-12}[precision] * max(shape)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("variant", ["A", "B", "C"])
 def test_chains_several_cycles(precision, variant):
     shape = (16, 12, 10)
@@ -120,3 +148,28 @@ def test_lj_argument_checks():
     g.add_particles(np.array([[1.0, 1, 1], [2.0, 1, 1]]), np.zeros((2, 3)))
     with pytest.raises(lbmd.LbmdError):
         g.add_fene_bonds(np.array([[0, 1]]), 30.0, 0.0)
+
+
+@pytest.mark.parametrize("integrator", ["start", "half_step"])
+def test_variant_b_spread_paths_agree_bitwise(integrator):
+    # variant B with conservative forces: the row gather, and the transfers
+    # handed over inside the LJ / bond kernel, give the same fixed-point sums
+    shape, m = (16, 12, 10), 5
+    lp = lj_units.lattice_params(m, 0.005, 5.0)
+    pos, bonds = inputs.self_avoiding_chains(4, 32, shape, 26)
+    n = pos.shape[0]
+    vel = inputs.maxwell_velocities(n, lp["kT"], 26)
+    runs = {}
+    for lj in (True, False):
+        for spread in ("rows", "atomic"):
+            g = lbmd.LBMD(*shape, variant="B", precision="fp32", n_sub=m, kT=lp["kT"], zeta=lp["zeta"], nu=lp["nu"],
+                          seed=26, max_particles=n, max_bonds=bonds.shape[0], integrator=integrator, spread=spread)
+            g.add_particles(pos, vel)
+            if lj:
+                g.set_lj(lp["lj_eps"], lp["lj_sigma"], lp["lj_rc"])
+            g.add_fene_bonds(bonds, lp["fene_k"], lp["fene_R0"])
+            g.run_cycles(3)
+            runs[(lj, spread)] = (g.populations(), *g.particles())
+        for a, b in zip(runs[(lj, "rows")], runs[(lj, "atomic")]):
+            np.testing.assert_array_equal(a, b)
+

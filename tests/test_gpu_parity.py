@@ -9,7 +9,7 @@ m = 1, repeated runs, graph replay) must match bit for bit.
 import numpy as np
 import pytest
 
-from gpu_common import W, assert_pops_close, assert_vec_close, pair, random_state
+from gpu_common import TOL, W, assert_pops_close, assert_vec_close, pair, random_state
 from paper_1610_02733_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -224,3 +224,28 @@ def test_variant_c_several_cycles(precision):
         _, vg = g.particles()
         _, vo = o.particles()
         assert_vec_close(vg, vo, "fp32", "velocities")
+
+
+@pytest.mark.parametrize("integrator", ["start", "half_step"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_variant_b_spread_paths_agree_bitwise(precision, integrator):
+    # the row gather (+ migrant atomics) and the all-atomic path hand over the
+    # same fixed-point transfers: bitwise equal, and equal to the oracle
+    shape, n = (24, 20, 18), 3000
+    runs = {}
+    for spread in ("rows", "atomic"):
+        o, g = pair(shape, precision=precision, variant="B", n_sub=5, kT=1e-4, zeta=1.5, seed=41, max_particles=n,
+                    integrator=integrator, spread=spread)
+        pos, vel = inputs.uniform_positions(n, shape, 41), inputs.maxwell_velocities(n, 1e-4, 41)
+        g.add_particles(pos, vel)
+        g.cycle(2)
+        runs[spread] = (g.populations(), *g.particles())
+    for a, b in zip(runs["rows"], runs["atomic"]):
+        np.testing.assert_array_equal(a, b)
+    o.add_particles(pos, vel)
+    o.cycle(2)
+    assert_pops_close(runs["rows"][0], o.populations(), precision)
+    po, vo = o.particles()
+    assert np.abs(_periodic_diff(runs["rows"][1], po, shape)).max() <= TOL[precision] * max(shape)
+    assert_vec_close(runs["rows"][2], vo, precision, "velocities")
+
