@@ -49,7 +49,7 @@ struct PArgs {
     const double *bond_k, *bond_r0;
     const uint8_t *bond_kind;
     T lj_eps24, lj_sig2, lj_rc2;  // Lennard-Jones: 24 eps, sigma^2, r_cut^2
-    int lj_cells;                 // ceil(r_cut): larger cell offsets are beyond the cut-off
+    float lj_filter2;             // (r_cut + rounding margin of FP32 absolute positions)^2
     int nx, ny, nz;
     FastDiv fd_nx, fd_ny;  // division by nx and ny
     int64_t np;
@@ -535,7 +535,7 @@ __device__ __forceinline__ int nearest_image(int d, int n) {
 // With KICK, lane 0 also makes the second velocity-Verlet half-kick.
 template <typename T>
 struct PairTile {
-    static constexpr int N = sizeof(T) == 4 ? 2048 : 1024;  // 48 / 36 KB of shared memory
+    static constexpr int N = sizeof(T) == 4 ? 1024 : 512;  // 40 / 26 KB of shared memory
 };
 
 constexpr int PAIR_THREADS = 256;  // eight particles per block
@@ -546,12 +546,16 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_kick_kernel(PArgs<T> a) {
     constexpr int TILE = PairTile<T>::N;
     __shared__ T s_f[3][TILE];
     __shared__ int s_c[3][TILE];
+    __shared__ float4 s_abs[TILE];  // FP32 absolute positions, for the filter
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const bool live = i < a.np;
     const int64_t p = live ? a.slot_of[i] : 0;
     const typename P::real4 R = a.pos4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
+    const float xi = (float)(T(c.x) + R.x), yi = (float)(T(c.y) + R.y), zi = (float)(T(c.z) + R.z);
+    const float fnx = (float)a.nx, fny = (float)a.ny, fnz = (float)a.nz;
+    const float inx = 1.0f / fnx, iny = 1.0f / fny, inz = 1.0f / fnz;
     T Fx = T(0), Fy = T(0), Fz = T(0);
     for (int64_t j0 = 0; j0 < a.np; j0 += TILE) {
         const int cnt = a.np - j0 < TILE ? (int)(a.np - j0) : TILE;
@@ -565,17 +569,23 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_kick_kernel(PArgs<T> a) {
             s_c[0][k] = d.x;
             s_c[1][k] = d.y;
             s_c[2][k] = d.z;
+            s_abs[k] = make_float4((float)(T(d.x) + S.x), (float)(T(d.y) + S.y), (float)(T(d.z) + S.z), 0.0f);
         }
         __syncthreads();
         if (!live) continue;
         for (int k = lane; k < cnt; k += 32) {
-            // cell offsets first: |d| > |cell offset| - 1, so a pair more than
-            // lj_cells cells apart along an axis is beyond the cut-off (the
-            // exact test below would reject it too)
+            // filter on FP32 absolute positions: a pair whose approximate
+            // distance is beyond the cut-off plus the rounding margin is
+            // beyond the cut-off (the exact test below would reject it too)
+            const float4 A = s_abs[k];
+            float ex = A.x - xi, ey = A.y - yi, ez = A.z - zi;
+            ex -= fnx * rintf(ex * inx);
+            ey -= fny * rintf(ey * iny);
+            ez -= fnz * rintf(ez * inz);
+            if (ex * ex + ey * ey + ez * ez >= a.lj_filter2) continue;
             const int ix = nearest_image(s_c[0][k] - c.x, a.nx);
             const int iy = nearest_image(s_c[1][k] - c.y, a.ny);
             const int iz = nearest_image(s_c[2][k] - c.z, a.nz);
-            if (abs(ix) > a.lj_cells || abs(iy) > a.lj_cells || abs(iz) > a.lj_cells) continue;
             const T dx = T(ix) + (s_f[0][k] - R.x);
             const T dy = T(iy) + (s_f[1][k] - R.y);
             const T dz = T(iz) + (s_f[2][k] - R.z);
@@ -838,7 +848,14 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.lj_eps24 = (T)(24.0 * ctx->lj_eps);
     a.lj_sig2 = (T)(ctx->lj_sigma * ctx->lj_sigma);
     a.lj_rc2 = (T)(ctx->lj_rc * ctx->lj_rc);
-    a.lj_cells = (int)std::ceil(ctx->lj_rc);
+    {
+        // |error| of an FP32 absolute coordinate <= max edge * 2^-24, of a
+        // distance <= sqrt(3) * 2 of that (plus the float arithmetic); the
+        // margin is a generous multiple of it
+        const double edge = std::max(ctx->p.nx, std::max(ctx->p.ny, ctx->p.nz));
+        const double margin = edge * std::ldexp(1.0, -18) + 1e-6;
+        a.lj_filter2 = (float)((ctx->lj_rc + margin) * (ctx->lj_rc + margin));
+    }
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
