@@ -419,6 +419,29 @@ __device__ __forceinline__ void spread_corner_atomic(const PArgs<T> &a, int64_t 
     P::add_transfer(rec, P::to_fix_neg(delta, sx), P::to_fix_neg(delta, sy), P::to_fix_neg(delta, sz));
 }
 
+// All 8 corner transfers of the particle in slot p (position and force read
+// and the cell decoded once).
+template <typename T>
+__device__ __forceinline__ void spread_particle_atomic(const PArgs<T> &a, int64_t p) {
+    using P = Prec<T>;
+    const typename P::real4 R = a.old4[p];
+    const typename P::real4 F = a.fc4[p];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
+    uint32_t idx[8], rows[4];
+    T delta[8];
+    corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
+    corner_rows(c, a.ny, a.nz, rows);
+    const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
+    const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int xn = (k & 1) ? x1 : c.x;
+        const int sl = active_slot(a.occw[(size_t)rows[k >> 1] * (uint32_t)a.occ_words + (xn >> 5)], xn);
+        typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[idx[k]];
+        P::add_transfer(rec, P::to_fix_neg(delta[k], sx), P::to_fix_neg(delta[k], sy), P::to_fix_neg(delta[k], sz));
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a, int all) {
     using P = Prec<T>;
@@ -429,9 +452,7 @@ __global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a, int all
     if (blockIdx.x == 0 && threadIdx.x == 0) a.migrant_count[par ^ 1] = 0;
     const int32_t *list = a.migrant_slot + (int64_t)par * a.np_cap;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int64_t p = all ? (int64_t)t : (int64_t)list[t];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) spread_corner_atomic(a, p, k);
+        spread_particle_atomic(a, all ? (int64_t)t : (int64_t)list[t]);
     }
 }
 
@@ -506,10 +527,7 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
         a.vel4[p] = V;
         // variant B, all atomics: every particle has read the nodes (couple
         // kernel), so the transfers can go in now
-        if (a.kick_spreads) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) spread_corner_atomic(a, p, k);
-        }
+        if (a.kick_spreads) spread_particle_atomic(a, p);
     }
 }
 
