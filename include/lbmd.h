@@ -248,6 +248,24 @@ lbmd_status lbmd_get_particles_device(lbmd_ctx *ctx, double *pos, double *vel);
 lbmd_status lbmd_get_counts(lbmd_ctx *ctx, int64_t *n_particles, int64_t *n_bonds, int64_t *lb_step,
                             int64_t *md_step, int32_t *substeps_done);
 
+/* Saved state (checkpoint / resume; the paper has no counterpart).  At a
+ * cycle boundary, the state of a context is its populations, its particles
+ * (positions, velocities, the last coupling force, ids, masses), its bonds,
+ * its Lennard-Jones parameters and the LB / MD step counters, which key the
+ * Philox noise.  Saved in the device representation, so a context restored
+ * from it continues bit for bit as the saved one would have.
+ *   lbmd_state_size: bytes the state of this context takes now.
+ *   lbmd_save_state: writes it to a host buffer of at least that many bytes;
+ *     synchronising; LBMD_ERR_SEQUENCE unless at a cycle boundary,
+ *     LBMD_ERR_CAPACITY if the buffer is too small.
+ *   lbmd_load_state: restores it into a context created with the same
+ *     parameters (capacities may differ) that has no particles yet;
+ *     synchronising; LBMD_ERR_ARG for another context's parameters or a
+ *     damaged buffer, LBMD_ERR_CAPACITY if the capacities are too small. */
+lbmd_status lbmd_state_size(lbmd_ctx *ctx, int64_t *bytes);
+lbmd_status lbmd_save_state(lbmd_ctx *ctx, void *buf, int64_t bytes);
+lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Particle momentum and kinetic energy of caller-owned device arrays, like the
  * p_particles / e_kin part of lbmd_observables, but without allocating any
  * device memory.  The paper has no counterpart: this is a service for callers

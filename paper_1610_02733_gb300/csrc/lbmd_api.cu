@@ -559,4 +559,185 @@ lbmd_status lbmd_get_counts(lbmd_ctx *ctx, int64_t *n_particles, int64_t *n_bond
     return LBMD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Saved state: header, populations as stored, particle records as stored
+// (slot order, with their ids), the bonds per particle id.  Everything is
+// copied in the device representation, so a restored run continues bit for
+// bit.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct StateHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, n_sub, variant, precision, integrator;
+    double rho0, nu, nu_bulk, gamma_ghost, kT, zeta, body_force[3];
+    uint64_t seed;
+    int64_t np, nb, lb_step, md_step;
+    double lj_eps, lj_sigma, lj_rc;
+};
+constexpr char STATE_MAGIC[8] = {'L', 'B', 'M', 'D', 'S', 'T', 'A', 'T'};
+
+size_t align8(size_t b) { return (b + 7) & ~(size_t)7; }
+
+// byte sizes of the sections for np particles
+struct StateLayout {
+    size_t pops, recs, pid, bonds, total;
+};
+StateLayout state_layout(const lbmd_ctx *ctx, int64_t np) {
+    const int M = LBMD_MAX_BONDS_PER_PARTICLE;
+    StateLayout L;
+    L.pops = align8((size_t)19 * ctx->N * pop_size(ctx));
+    L.recs = (size_t)3 * np * 4 * real_size(ctx);  // pos4, vel4, fc4
+    L.pid = align8((size_t)np * sizeof(int32_t));
+    L.bonds = align8((size_t)np * sizeof(int32_t)) + align8((size_t)np * M * sizeof(int32_t)) +
+              (size_t)2 * np * M * sizeof(double) + align8((size_t)np * M);
+    L.total = sizeof(StateHeader) + L.pops + L.recs + L.pid + L.bonds;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbmd_status lbmd_state_size(lbmd_ctx *ctx, int64_t *bytes) {
+    if (!ctx || !bytes) return LBMD_ERR_ARG;
+    *bytes = (int64_t)state_layout(ctx, ctx->np).total;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_save_state(lbmd_ctx *ctx, void *buf, int64_t bytes) {
+    if (!ctx || !buf) return LBMD_ERR_ARG;
+    if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "save_state only at a cycle boundary");
+    const StateLayout L = state_layout(ctx, ctx->np);
+    if (bytes < (int64_t)L.total) return fail(ctx, LBMD_ERR_CAPACITY, "state buffer smaller than lbmd_state_size");
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, STATE_MAGIC, 8);
+    h.version = 1;
+    h.nx = ctx->p.nx;
+    h.ny = ctx->p.ny;
+    h.nz = ctx->p.nz;
+    h.n_sub = ctx->p.n_sub;
+    h.variant = ctx->p.variant;
+    h.precision = ctx->p.precision;
+    h.integrator = ctx->p.integrator;
+    h.rho0 = ctx->p.rho0;
+    h.nu = ctx->p.nu;
+    h.nu_bulk = ctx->p.nu_bulk;
+    h.gamma_ghost = ctx->p.gamma_ghost;
+    h.kT = ctx->p.kT;
+    h.zeta = ctx->p.zeta;
+    for (int d = 0; d < 3; ++d) h.body_force[d] = ctx->p.body_force[d];
+    h.seed = ctx->p.seed;
+    h.np = ctx->np;
+    h.nb = ctx->nb;
+    h.lb_step = ctx->lb_step;
+    h.md_step = ctx->md_step;
+    h.lj_eps = ctx->lj_eps;
+    h.lj_sigma = ctx->lj_sigma;
+    h.lj_rc = ctx->lj_rc;
+    char *o = static_cast<char *>(buf);
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    const int b = ctx->pcur, M = LBMD_MAX_BONDS_PER_PARTICLE;
+    const size_t rb = (size_t)ctx->np * 4 * real_size(ctx), np = (size_t)ctx->np;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    CK(ctx, cudaMemcpy(o, ctx->f[ctx->cur], (size_t)19 * ctx->N * pop_size(ctx), cudaMemcpyDeviceToHost));
+    o += L.pops;
+    if (np) {
+        CK(ctx, cudaMemcpy(o, ctx->pos4[b], rb, cudaMemcpyDeviceToHost));
+        CK(ctx, cudaMemcpy(o + rb, ctx->vel4[b], rb, cudaMemcpyDeviceToHost));
+        CK(ctx, cudaMemcpy(o + 2 * rb, ctx->fc4[b], rb, cudaMemcpyDeviceToHost));
+        o += L.recs;
+        CK(ctx, cudaMemcpy(o, ctx->pid[b], np * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        o += L.pid;
+        CK(ctx, cudaMemcpy(o, ctx->bond_count, np * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        o += align8(np * sizeof(int32_t));
+        CK(ctx, cudaMemcpy(o, ctx->bond_partner, np * M * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        o += align8(np * M * sizeof(int32_t));
+        CK(ctx, cudaMemcpy(o, ctx->bond_k, np * M * sizeof(double), cudaMemcpyDeviceToHost));
+        o += np * M * sizeof(double);
+        CK(ctx, cudaMemcpy(o, ctx->bond_r0, np * M * sizeof(double), cudaMemcpyDeviceToHost));
+        o += np * M * sizeof(double);
+        CK(ctx, cudaMemcpy(o, ctx->bond_kind, np * M, cudaMemcpyDeviceToHost));
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes) {
+    if (!ctx || !buf) return LBMD_ERR_ARG;
+    if (bytes < (int64_t)sizeof(StateHeader)) return fail(ctx, LBMD_ERR_ARG, "state buffer too small");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, STATE_MAGIC, 8) != 0 || h.version != 1)
+        return fail(ctx, LBMD_ERR_ARG, "not a saved lbmd state");
+    const lbmd_params &p = ctx->p;
+    bool same = h.nx == p.nx && h.ny == p.ny && h.nz == p.nz && h.n_sub == p.n_sub && h.variant == p.variant &&
+                h.precision == p.precision && h.integrator == p.integrator && h.rho0 == p.rho0 && h.nu == p.nu &&
+                h.nu_bulk == p.nu_bulk && h.gamma_ghost == p.gamma_ghost && h.kT == p.kT && h.zeta == p.zeta &&
+                h.seed == p.seed;
+    for (int d = 0; d < 3; ++d) same = same && h.body_force[d] == p.body_force[d];
+    if (!same) return fail(ctx, LBMD_ERR_ARG, "saved state comes from other parameters");
+    if (ctx->np != 0 || ctx->sub_done != 0)
+        return fail(ctx, LBMD_ERR_SEQUENCE, "load_state needs a context without particles, at a cycle boundary");
+    if (h.np < 0 || h.np > p.max_particles || h.nb < 0 || h.nb > p.max_bonds)
+        return fail(ctx, LBMD_ERR_CAPACITY, "saved state needs more particles or bonds than reserved");
+    const StateLayout L = state_layout(ctx, h.np);
+    if (bytes < (int64_t)L.total) return fail(ctx, LBMD_ERR_ARG, "state buffer shorter than its header says");
+    const int b = ctx->pcur, M = LBMD_MAX_BONDS_PER_PARTICLE;
+    const size_t np = (size_t)h.np, rb = np * 4 * real_size(ctx);
+    const char *in = static_cast<const char *>(buf) + sizeof(h);
+    // the ids: a permutation of 0..np-1
+    std::vector<int32_t> pid(np), slot_of(np, -1);
+    std::memcpy(pid.data(), in + L.pops + L.recs, np * sizeof(int32_t));
+    for (size_t s = 0; s < np; ++s) {
+        if (pid[s] < 0 || (size_t)pid[s] >= np || slot_of[pid[s]] >= 0)
+            return fail(ctx, LBMD_ERR_ARG, "saved state: particle ids are not a permutation");
+        slot_of[pid[s]] = (int32_t)s;
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    CK(ctx, cudaMemcpy(ctx->f[ctx->cur], in, (size_t)19 * ctx->N * pop_size(ctx), cudaMemcpyHostToDevice));
+    in += L.pops;
+    if (np) {
+        CK(ctx, cudaMemcpy(ctx->pos4[b], in, rb, cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(ctx->vel4[b], in + rb, rb, cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(ctx->fc4[b], in + 2 * rb, rb, cudaMemcpyHostToDevice));
+        in += L.recs;
+        CK(ctx, cudaMemcpy(ctx->pid[b], pid.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(ctx->slot_of, slot_of.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+        in += L.pid;
+        CK(ctx, cudaMemcpy(ctx->bond_count, in, np * sizeof(int32_t), cudaMemcpyHostToDevice));
+        in += align8(np * sizeof(int32_t));
+        CK(ctx, cudaMemcpy(ctx->bond_partner, in, np * M * sizeof(int32_t), cudaMemcpyHostToDevice));
+        in += align8(np * M * sizeof(int32_t));
+        CK(ctx, cudaMemcpy(ctx->bond_k, in, np * M * sizeof(double), cudaMemcpyHostToDevice));
+        in += np * M * sizeof(double);
+        CK(ctx, cudaMemcpy(ctx->bond_r0, in, np * M * sizeof(double), cudaMemcpyHostToDevice));
+        in += np * M * sizeof(double);
+        CK(ctx, cudaMemcpy(ctx->bond_kind, in, np * M, cudaMemcpyHostToDevice));
+        // no row buckets until the next re-ordering; no migrants listed
+        CK(ctx, cudaMemset(ctx->slot_row, 0xff, np * sizeof(int32_t)));
+        CK(ctx, cudaMemset(ctx->migrant_count, 0, 2 * sizeof(int32_t)));
+    }
+    ctx->np = h.np;
+    ctx->nb = h.nb;
+    ctx->lb_step = h.lb_step;
+    ctx->md_step = h.md_step;
+    ctx->lj_eps = h.lj_eps;
+    ctx->lj_sigma = h.lj_sigma;
+    ctx->lj_rc = h.lj_rc;
+    const unsigned long long step = (unsigned long long)h.lb_step;
+    CK(ctx, cudaMemcpy(ctx->d_lb_step, &step, sizeof(step), cudaMemcpyHostToDevice));
+    // node field of the restored populations (no pending transfer at a cycle
+    // boundary) and the conservative forces at the restored positions
+    CK(ctx, launch_node_moments(ctx, false));
+    CK(ctx, launch_clear_transfer(ctx));
+    if (ctx->np > 0 && has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    drop_cycle_graphs(ctx);
+    return LBMD_OK;
+}
+
 }  // extern "C"

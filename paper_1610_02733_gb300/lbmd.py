@@ -34,7 +34,7 @@ SPREADS = {"auto": SPREAD_AUTO, "rows": SPREAD_ROWS, "atomic": SPREAD_ATOMIC}
 # every symbol include/lbmd.h declares
 EXPORTS = (
     "lbmd_create", "lbmd_destroy", "lbmd_add_particles", "lbmd_add_bonds", "lbmd_add_fene_bonds", "lbmd_set_lj",
-    "lbmd_set_particles",
+    "lbmd_set_particles", "lbmd_state_size", "lbmd_save_state", "lbmd_load_state",
     "lbmd_md_substep", "lbmd_lb_step", "lbmd_run_cycles", "lbmd_observables", "lbmd_get_populations",
     "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
@@ -113,6 +113,9 @@ def load():
     L.lbmd_add_bonds.argtypes = [P, ct.c_int64, i64p, ct.c_double, ct.c_double]
     L.lbmd_add_fene_bonds.argtypes = [P, ct.c_int64, i64p, ct.c_double, ct.c_double]
     L.lbmd_set_lj.argtypes = [P, ct.c_double, ct.c_double, ct.c_double]
+    L.lbmd_state_size.argtypes = [P, i64p]
+    L.lbmd_save_state.argtypes = [P, ct.c_void_p, ct.c_int64]
+    L.lbmd_load_state.argtypes = [P, ct.c_void_p, ct.c_int64]
     L.lbmd_set_particles.argtypes = [P, ct.c_void_p, ct.c_void_p]
     L.lbmd_md_substep.argtypes = [P]
     L.lbmd_lb_step.argtypes = [P]
@@ -310,6 +313,20 @@ class LBMD:
         _check(self._h, load().lbmd_add_fene_bonds(self._h, pairs.shape[0],
                                                    pairs.ctypes.data_as(ct.POINTER(ct.c_int64)), float(k), float(R0)),
                "lbmd_add_fene_bonds")
+
+    def save_state(self) -> bytes:
+        """The context's state at a cycle boundary (populations, particles,
+        bonds, LJ parameters, step counters) as bytes; load_state restores it."""
+        size = ct.c_int64(0)
+        _check(self._h, load().lbmd_state_size(self._h, ct.byref(size)), "lbmd_state_size")
+        buf = ct.create_string_buffer(size.value)
+        _check(self._h, load().lbmd_save_state(self._h, buf, size.value), "lbmd_save_state")
+        return buf.raw
+
+    def load_state(self, state: bytes):
+        """Restore a saved state into this context (same parameters, no particles yet)."""
+        buf = ct.create_string_buffer(bytes(state), len(state))
+        _check(self._h, load().lbmd_load_state(self._h, buf, len(state)), "lbmd_load_state")
 
     def set_lj(self, eps, sigma, r_cut):
         """Lennard-Jones between all particles, cut off (and shifted) at r_cut; r_cut = 0: off (Sec. 4)."""
