@@ -197,9 +197,13 @@ lbmd_status lbmd_set_particles(lbmd_ctx *ctx, const double *pos, const double *v
  *   F_rand with variance 2 zeta kT / dt per component; Delta P = dt F with
  *   R, v, F_rand of the start of the step (Eq. (6)); velocity Verlet with
  *   that F held fixed; Delta j_k = -delta_k Delta P / a^3 to the 8 nodes
- *   (Eqs. (7), (8)).
+ *   (Eqs. (7), (8)).  With LBMD_INTEGRATOR_HALF_STEP, F is instead taken
+ *   after the drift from the half-step velocity at the new position (see the
+ *   integrator enum).  Conservative forces (bonds, Lennard-Jones) enter both
+ *   half-kicks at the positions of the kick.
  * Variant A reads the node velocities of the last LB update; variant B reads
- * them updated by every earlier MD step since (Sec. 3).  All particles read
+ * them updated by every earlier MD step since (Sec. 3); variant C moves each
+ * MD step's transfers into the populations (Sec. 4).  All particles read
  * the nodes before any transfer of the same step is applied.
  * Enqueue only.  LBMD_ERR_SEQUENCE if m MD steps were already done since the
  * last LB step. */
