@@ -141,7 +141,9 @@ lbmd_status lbmd_destroy(lbmd_ctx *ctx);
  * or NULL for mass 1.  Particle ids are assigned consecutively; the first is
  * written to *first_id_out if it is not NULL.
  * Errors: LBMD_ERR_CAPACITY beyond max_particles, LBMD_ERR_ARG for
- * non-finite input or mass <= 0. */
+ * non-finite input, mass <= 0, or zeta dt / mass >= 2 (where the explicit
+ * friction step of a particle alone already diverges; the coupled system
+ * can become unstable below that, see lbmd_observables' non-finite check). */
 lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, const double *vel, const double *mass,
                                int64_t *first_id_out);
 

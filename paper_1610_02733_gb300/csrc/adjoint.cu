@@ -797,6 +797,7 @@ lbmd_status lbmd_adjoint_destroy(lbmd_adjoint *a) {
 
 lbmd_status lbmd_adjoint_forward(lbmd_adjoint *a, double zeta, const double *pos0, const double *vel0,
                                  double *loss) {
+    LBMD_TRACE("lbmd_adjoint_forward");
     if (!a || !loss || !(zeta >= 0) || !ad_finite(zeta) || (a->p.n_particles > 0 && (!pos0 || !vel0)))
         return afail(a, LBMD_ERR_ARG, "bad arguments");
     for (int64_t q = 0; q < 3 * (int64_t)a->p.n_particles; ++q)
@@ -810,6 +811,7 @@ lbmd_status lbmd_adjoint_forward(lbmd_adjoint *a, double zeta, const double *pos
 }
 
 lbmd_status lbmd_adjoint_backward(lbmd_adjoint *a, double *dloss_dzeta, double *dloss_dpos0) {
+    LBMD_TRACE("lbmd_adjoint_backward");
     if (!a || !dloss_dzeta || (a->p.n_particles > 0 && !dloss_dpos0)) return afail(a, LBMD_ERR_ARG, "bad arguments");
     if (!a->have_forward) return afail(a, LBMD_ERR_SEQUENCE, "backward before forward");
     cudaError_t e = a->p.precision == LBMD_FP64 ? backward_t<double>(a, dloss_dzeta, dloss_dpos0)

@@ -898,6 +898,7 @@ lbmd_status lbmd_batch_add_particles(lbmd_batch *b, int32_t r, int64_t n, const 
 }
 
 lbmd_status lbmd_batch_run(lbmd_batch *b, int64_t md_steps) {
+    LBMD_TRACE("lbmd_batch_run");
     if (!b || md_steps < 0) return LBMD_ERR_ARG;
     if (!b->particles_tuned && b->n_slots > 0) BCK(b, LBMD_BATCH_DISPATCH(b, tune_particles, b));
     int64_t left = md_steps;

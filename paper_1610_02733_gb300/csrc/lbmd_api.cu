@@ -86,6 +86,7 @@ const char *lbmd_last_error(lbmd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_c
 void *lbmd_stream(lbmd_ctx *ctx) { return ctx ? (void *)ctx->stream : nullptr; }
 
 lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
+    LBMD_TRACE("lbmd_create");
     if (!p || !out) return fail(nullptr, LBMD_ERR_ARG, "null argument");
     *out = nullptr;
     if (p->nx < 2 || p->ny < 2 || p->nz < 2) return fail(nullptr, LBMD_ERR_ARG, "lattice sides must be >= 2");
@@ -255,6 +256,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
 }
 
 lbmd_status lbmd_destroy(lbmd_ctx *ctx) {
+    LBMD_TRACE("lbmd_destroy");
     if (!ctx) return LBMD_OK;
     cudaStreamSynchronize(ctx->stream);
     free_all(ctx);
@@ -264,6 +266,7 @@ lbmd_status lbmd_destroy(lbmd_ctx *ctx) {
 
 lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, const double *vel, const double *mass,
                                int64_t *first_id_out) {
+    LBMD_TRACE("lbmd_add_particles");
     if (!ctx) return LBMD_ERR_ARG;
     if (n < 0 || (n > 0 && (!pos || !vel))) return fail(ctx, LBMD_ERR_ARG, "bad particle arrays");
     if (ctx->np + n > ctx->p.max_particles) return fail(ctx, LBMD_ERR_CAPACITY, "max_particles exceeded");
@@ -272,6 +275,11 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     if (mass)
         for (int64_t q = 0; q < n; ++q)
             if (!(mass[q] > 0) || !is_finite_d(mass[q])) return fail(ctx, LBMD_ERR_ARG, "mass must be positive");
+    // the explicit friction step multiplies the relative velocity by
+    // 1 - zeta dt / m per MD step: at zeta dt / m >= 2 it grows without bound
+    for (int64_t q = 0; q < (mass ? n : (n > 0 ? 1 : 0)); ++q)
+        if (ctx->p.zeta * ctx->dt / (mass ? mass[q] : 1.0) >= 2.0)
+            return fail(ctx, LBMD_ERR_ARG, "zeta dt / mass >= 2: the explicit friction step is unstable");
     if (first_id_out) *first_id_out = ctx->np;
     if (n == 0) return LBMD_OK;
     // stage in chunks through the device staging buffer (3 + 3 + 1 doubles each)
@@ -349,6 +357,7 @@ static lbmd_status add_bonds_of_kind(lbmd_ctx *ctx, int64_t nb, const int64_t *p
 }
 
 lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0) {
+    LBMD_TRACE("lbmd_add_bonds");
     if (!ctx) return LBMD_ERR_ARG;
     if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !is_finite_d(r0))
         return fail(ctx, LBMD_ERR_ARG, "bad bonds");
@@ -356,6 +365,7 @@ lbmd_status lbmd_add_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, doub
 }
 
 lbmd_status lbmd_add_fene_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double R0) {
+    LBMD_TRACE("lbmd_add_fene_bonds");
     if (!ctx) return LBMD_ERR_ARG;
     if (nb < 0 || (nb > 0 && !pairs) || !is_finite_d(k) || !(k >= 0) || !is_finite_d(R0) || !(R0 > 0))
         return fail(ctx, LBMD_ERR_ARG, "bad FENE bonds");
@@ -363,6 +373,7 @@ lbmd_status lbmd_add_fene_bonds(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs,
 }
 
 lbmd_status lbmd_set_lj(lbmd_ctx *ctx, double eps, double sigma, double r_cut) {
+    LBMD_TRACE("lbmd_set_lj");
     if (!ctx) return LBMD_ERR_ARG;
     if (!is_finite_d(eps) || !(eps >= 0) || !is_finite_d(sigma) || !(sigma > 0) || !is_finite_d(r_cut) ||
         !(r_cut >= 0))
@@ -389,6 +400,7 @@ lbmd_status lbmd_set_lj(lbmd_ctx *ctx, double eps, double sigma, double r_cut) {
 }
 
 lbmd_status lbmd_set_particles(lbmd_ctx *ctx, const double *pos, const double *vel) {
+    LBMD_TRACE("lbmd_set_particles");
     if (!ctx) return LBMD_ERR_ARG;
     const int64_t n = ctx->np;
     if (n == 0 || (!pos && !vel)) return LBMD_OK;
@@ -402,6 +414,7 @@ lbmd_status lbmd_set_particles(lbmd_ctx *ctx, const double *pos, const double *v
 }
 
 lbmd_status lbmd_md_substep(lbmd_ctx *ctx) {
+    LBMD_TRACE("lbmd_md_substep");
     if (!ctx) return LBMD_ERR_ARG;
     if (ctx->sub_done >= ctx->p.n_sub) return fail(ctx, LBMD_ERR_SEQUENCE, "n_sub MD steps already done");
     CK(ctx, launch_md_substep(ctx, ctx->sub_done));
@@ -411,6 +424,7 @@ lbmd_status lbmd_md_substep(lbmd_ctx *ctx) {
 }
 
 lbmd_status lbmd_lb_step(lbmd_ctx *ctx) {
+    LBMD_TRACE("lbmd_lb_step");
     if (!ctx) return LBMD_ERR_ARG;
     if (ctx->sub_done != ctx->p.n_sub) return fail(ctx, LBMD_ERR_SEQUENCE, "LB step before n_sub MD steps");
     CK(ctx, launch_lb_step(ctx));
@@ -420,6 +434,7 @@ lbmd_status lbmd_lb_step(lbmd_ctx *ctx) {
 }
 
 lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
+    LBMD_TRACE("lbmd_run_cycles");
     if (!ctx || n < 0) return LBMD_ERR_ARG;
     if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "run_cycles must start at a cycle boundary");
     for (int64_t c = 0; c < n; ++c) {
@@ -457,6 +472,7 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
 }
 
 lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
+    LBMD_TRACE("lbmd_observables");
     if (!ctx || !out) return LBMD_ERR_ARG;
     double h[8];
     CK(ctx, launch_active_sync(ctx));
@@ -478,6 +494,7 @@ lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
 }
 
 lbmd_status lbmd_get_populations(lbmd_ctx *ctx, double *out) {
+    LBMD_TRACE("lbmd_get_populations");
     if (!ctx || !out) return LBMD_ERR_ARG;
     const int64_t total = 19 * ctx->N;
     for (int64_t s = 0; s < total; s += ctx->staging_len) {
@@ -490,6 +507,7 @@ lbmd_status lbmd_get_populations(lbmd_ctx *ctx, double *out) {
 }
 
 lbmd_status lbmd_set_populations(lbmd_ctx *ctx, const double *in) {
+    LBMD_TRACE("lbmd_set_populations");
     if (!ctx || !in) return LBMD_ERR_ARG;
     if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "set_populations only at a cycle boundary");
     const int64_t total = 19 * ctx->N;
@@ -520,16 +538,19 @@ static lbmd_status node_out(lbmd_ctx *ctx, double *out, bool transfer) {
 }
 
 lbmd_status lbmd_get_node_field(lbmd_ctx *ctx, double *out) {
+    LBMD_TRACE("lbmd_get_node_field");
     if (!ctx || !out) return LBMD_ERR_ARG;
     return node_out(ctx, out, false);
 }
 
 lbmd_status lbmd_get_transfer(lbmd_ctx *ctx, double *out) {
+    LBMD_TRACE("lbmd_get_transfer");
     if (!ctx || !out) return LBMD_ERR_ARG;
     return node_out(ctx, out, true);
 }
 
 lbmd_status lbmd_get_particles(lbmd_ctx *ctx, double *pos, double *vel) {
+    LBMD_TRACE("lbmd_get_particles");
     if (!ctx) return LBMD_ERR_ARG;
     const int64_t n = ctx->np;
     if (n == 0 || (!pos && !vel)) return LBMD_OK;
@@ -608,6 +629,7 @@ lbmd_status lbmd_state_size(lbmd_ctx *ctx, int64_t *bytes) {
 }
 
 lbmd_status lbmd_save_state(lbmd_ctx *ctx, void *buf, int64_t bytes) {
+    LBMD_TRACE("lbmd_save_state");
     if (!ctx || !buf) return LBMD_ERR_ARG;
     if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "save_state only at a cycle boundary");
     const StateLayout L = state_layout(ctx, ctx->np);
@@ -667,6 +689,7 @@ lbmd_status lbmd_save_state(lbmd_ctx *ctx, void *buf, int64_t bytes) {
 }
 
 lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes) {
+    LBMD_TRACE("lbmd_load_state");
     if (!ctx || !buf) return LBMD_ERR_ARG;
     if (bytes < (int64_t)sizeof(StateHeader)) return fail(ctx, LBMD_ERR_ARG, "state buffer too small");
     StateHeader h;

@@ -40,6 +40,18 @@
 
 #include "../../include/lbmd.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+// A named NVTX range around a C-ABI call (visible in Nsight tools, free
+// otherwise): LBMD_TRACE("lbmd_md_substep");
+struct LbmdTraceRange {
+    explicit LbmdTraceRange(const char *name) { nvtxRangePushA(name); }
+    ~LbmdTraceRange() { nvtxRangePop(); }
+    LbmdTraceRange(const LbmdTraceRange &) = delete;
+    LbmdTraceRange &operator=(const LbmdTraceRange &) = delete;
+};
+#define LBMD_TRACE(name) LbmdTraceRange lbmd_trace_range_(name)
+
 #define LBMD_MAX_BONDS_PER_PARTICLE 8
 
 struct LbCoeffs {

@@ -67,7 +67,7 @@ def test_variants_a_and_b_coincide_bitwise_at_m_equal_one(precision):
     shape, n = (12, 10, 8), 50
     runs = {}
     for variant in ("A", "B"):
-        _, g = pair(shape, precision=precision, variant=variant, n_sub=1, kT=1e-3, zeta=3.0, seed=9,
+        _, g = pair(shape, precision=precision, variant=variant, n_sub=1, kT=1e-3, zeta=1.5, seed=9,
                     max_particles=n, integrator="half_step")
         g.add_particles(inputs.uniform_positions(n, shape, 2), inputs.maxwell_velocities(n, 1e-3, 2))
         g.cycle(5)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from gpu_common import TOL, W, assert_pops_close, assert_vec_close, pair, random_state
-from paper_1610_02733_gb300 import inputs
+from paper_1610_02733_gb300 import inputs, lbmd
 
 pytestmark = pytest.mark.gpu
 
@@ -117,7 +117,7 @@ def test_variants_a_and_b_coincide_bitwise_at_m_equal_one(precision):
     shape, n = (12, 10, 8), 50
     runs = {}
     for variant in ("A", "B"):
-        o, g = pair(shape, precision=precision, variant=variant, n_sub=1, kT=1e-3, zeta=3.0, seed=9,
+        o, g = pair(shape, precision=precision, variant=variant, n_sub=1, kT=1e-3, zeta=1.5, seed=9,
                     max_particles=n)
         g.add_particles(inputs.uniform_positions(n, shape, 2), inputs.maxwell_velocities(n, 1e-3, 2))
         g.cycle(5)
@@ -248,4 +248,13 @@ def test_variant_b_spread_paths_agree_bitwise(precision, integrator):
     po, vo = o.particles()
     assert np.abs(_periodic_diff(runs["rows"][1], po, shape)).max() <= TOL[precision] * max(shape)
     assert_vec_close(runs["rows"][2], vo, precision, "velocities")
+
+
+def test_unstable_friction_step_rejected():
+    # zeta dt / m = 2.5 (zeta = 5, m = 2 MD steps per LB step, unit mass)
+    g = lbmd.LBMD(8, 8, 8, n_sub=2, zeta=5.0, max_particles=4)
+    with pytest.raises(lbmd.LbmdError) as ei:
+        g.add_particles(np.ones((1, 3)), np.zeros((1, 3)))
+    assert ei.value.status == lbmd.LBMD_ERR_ARG
+    g.add_particles(np.ones((1, 3)), np.zeros((1, 3)), np.array([3.0]))  # heavier: 5 / 2 / 3 < 2
 
