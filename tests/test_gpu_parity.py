@@ -258,3 +258,23 @@ def test_unstable_friction_step_rejected():
     assert ei.value.status == lbmd.LBMD_ERR_ARG
     g.add_particles(np.ones((1, 3)), np.zeros((1, 3)), np.array([3.0]))  # heavier: 5 / 2 / 3 < 2
 
+
+@pytest.mark.parametrize("precision,nx", [("fp32", 4096), ("fp64", 2048)])
+def test_longest_rows(precision, nx):
+    # the longest node rows the row gather accepts (its shared memory per
+    # warp grows with nx; fewer warps per block then), ragged ny, nz
+    shape, n = (nx, 3, 4), 3000
+    o, g = pair(shape, precision=precision, variant="B", n_sub=3, kT=1e-4, zeta=1.5, seed=61, max_particles=n,
+                spread="rows")
+    pos, vel = inputs.uniform_positions(n, shape, 61), inputs.maxwell_velocities(n, 1e-4, 61)
+    for obj in (o, g):
+        obj.add_particles(pos, vel)
+        obj.cycle(2)
+    assert_pops_close(g.populations(), o.populations(), precision)
+    po, vo = o.particles()
+    pg, vg = g.particles()
+    assert np.abs(_periodic_diff(pg, po, shape)).max() <= TOL[precision] * nx
+    assert_vec_close(vg, vo, precision, "velocities")
+    with pytest.raises(lbmd.LbmdError):
+        lbmd.LBMD(nx + 1 if precision == "fp32" else nx * 2 + 1, 2, 2, precision=precision)
+
