@@ -395,6 +395,7 @@ static cudaError_t init_equilibrium_t(lbmd_ctx *ctx) {
 cudaError_t launch_lb_step(lbmd_ctx *ctx) {
     cudaError_t e = launch_sort_particles(ctx);
     if (e != cudaSuccess) return e;
+    if ((e = launch_nb_build(ctx)) != cudaSuccess) return e;
     if ((e = launch_active_set(ctx)) != cudaSuccess) return e;
     if ((e = LBMD_DISPATCH_POPS(ctx, lbmd::lb_step_t, ctx)) != cudaSuccess) return e;
     ctx->cur ^= 1;

@@ -52,7 +52,8 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->bond_partner, ctx->bond_k,        ctx->bond_r0,       ctx->bond_kind,
                     ctx->staging,      ctx->red_partial,   ctx->red_out,       ctx->d_lb_step,
                     ctx->occw[0],      ctx->occw[1],       ctx->cact[0],       ctx->cact[1],
-                    ctx->blk_done,     ctx->lb_missed,     ctx->missed_list};
+                    ctx->blk_done,     ctx->lb_missed,     ctx->missed_list,   ctx->nb_list,
+                    ctx->nb_count,     ctx->nb_invalid,    ctx->nb_ref4};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 4; ++i)
@@ -264,6 +265,35 @@ lbmd_status lbmd_destroy(lbmd_ctx *ctx) {
     return LBMD_OK;
 }
 
+// The LJ neighbour lists, allocated when LJ forces are first switched on.
+static lbmd_status ensure_nb_lists(lbmd_ctx *ctx) {
+    if (ctx->nb_list) return LBMD_OK;
+    const size_t maxp = (size_t)std::max<int64_t>(ctx->p.max_particles, 1);
+    void *bufs[4] = {nullptr, nullptr, nullptr, nullptr};
+    const size_t bytes[4] = {maxp * LBMD_NB_MAX * sizeof(int32_t), maxp * sizeof(int32_t), sizeof(int32_t),
+                             maxp * 4 * real_size(ctx)};
+    for (int k = 0; k < 4; ++k)
+        if (cudaMalloc(&bufs[k], bytes[k]) != cudaSuccess) {
+            for (int q = 0; q < 4; ++q)
+                if (bufs[q]) cudaFree(bufs[q]);
+            cudaGetLastError();
+            return fail(ctx, LBMD_ERR_OOM, "Lennard-Jones neighbour lists");
+        }
+    ctx->nb_list = static_cast<int32_t *>(bufs[0]);
+    ctx->nb_count = static_cast<int32_t *>(bufs[1]);
+    ctx->nb_invalid = static_cast<int32_t *>(bufs[2]);
+    ctx->nb_ref4 = bufs[3];
+    return LBMD_OK;
+}
+
+// Positions changed outside the MD steps (or the lists were never built):
+// the pair kernel uses all pairs until the next re-ordering rebuilds them.
+static cudaError_t invalidate_nb_lists(lbmd_ctx *ctx) {
+    if (!ctx->nb_invalid) return cudaSuccess;
+    const int32_t one = 1;
+    return cudaMemcpyAsync(ctx->nb_invalid, &one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream);
+}
+
 lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, const double *vel, const double *mass,
                                int64_t *first_id_out) {
     LBMD_TRACE("lbmd_add_particles");
@@ -299,6 +329,7 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     CK(ctx, cudaMemsetAsync(ctx->slot_row + ctx->np, 0xff, n * sizeof(int32_t), ctx->stream));
     CK(ctx, cudaMemsetAsync((char *)ctx->fc4[ctx->pcur] + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     ctx->np += n;
+    CK(ctx, invalidate_nb_lists(ctx));
     if (has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     for (int i = 0; i < 4; ++i)
@@ -386,6 +417,11 @@ lbmd_status lbmd_set_lj(lbmd_ctx *ctx, double eps, double sigma, double r_cut) {
             if ((double)d < 2.0 * r_cut + 2.0)
                 return fail(ctx, LBMD_ERR_ARG, "Lennard-Jones: every box edge must be at least 2 r_cut + 2");
     }
+    if (r_cut > 0) {
+        const lbmd_status st = ensure_nb_lists(ctx);
+        if (st != LBMD_OK) return st;
+    }
+    CK(ctx, invalidate_nb_lists(ctx));  // lists of the old parameters are void until the next build
     ctx->lj_eps = eps;
     ctx->lj_sigma = sigma;
     ctx->lj_rc = r_cut;
@@ -409,6 +445,7 @@ lbmd_status lbmd_set_particles(lbmd_ctx *ctx, const double *pos, const double *v
     if (pos) CK(ctx, cudaMemcpyAsync(dpos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     if (vel) CK(ctx, cudaMemcpyAsync(dvel, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, launch_particles_from_double(ctx, 0, n, dpos, dvel, nullptr, pos != nullptr, vel != nullptr, false));
+    if (pos) CK(ctx, invalidate_nb_lists(ctx));
     if (pos && has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
     return LBMD_OK;
 }
@@ -751,6 +788,11 @@ lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes) {
     ctx->lj_eps = h.lj_eps;
     ctx->lj_sigma = h.lj_sigma;
     ctx->lj_rc = h.lj_rc;
+    if (h.lj_rc > 0) {
+        const lbmd_status st = ensure_nb_lists(ctx);
+        if (st != LBMD_OK) return st;
+    }
+    CK(ctx, invalidate_nb_lists(ctx));
     const unsigned long long step = (unsigned long long)h.lb_step;
     CK(ctx, cudaMemcpy(ctx->d_lb_step, &step, sizeof(step), cudaMemcpyHostToDevice));
     // node field of the restored populations (no pending transfer at a cycle

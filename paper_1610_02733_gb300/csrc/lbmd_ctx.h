@@ -99,6 +99,12 @@ struct lbmd_ctx {
     // Lennard-Jones between all particles (Kremer-Grest monomers); off while
     // lj_rc == 0
     double lj_eps, lj_sigma, lj_rc;
+    // Verlet lists of the LJ forces: per id the ids within lj_rc +
+    // LBMD_NB_SKIN, ascending, and the position at the build; a flag set once
+    // any particle moved more than half the skin since (the lists are then not
+    // used until the next re-ordering rebuilds them)
+    int32_t *nb_list, *nb_count, *nb_invalid;
+    void *nb_ref4;
     double *staging;   // device staging buffer for host <-> device conversions
     int64_t staging_len;
     double *red_partial;  // per-block partial sums of the observables
@@ -133,6 +139,9 @@ cudaError_t launch_md_substep(lbmd_ctx *ctx, int substep);
 cudaError_t launch_bond_forces_only(lbmd_ctx *ctx);
 // conservative forces present (bonds or Lennard-Jones)
 inline bool has_cons(const lbmd_ctx *ctx) { return ctx->nb > 0 || ctx->lj_rc > 0.0; }
+constexpr int LBMD_NB_MAX = 128;      // list entries per particle (more: that particle's block uses all pairs)
+constexpr double LBMD_NB_SKIN = 0.5;  // lattice spacings beyond the cut-off
+cudaError_t launch_nb_build(lbmd_ctx *ctx);
 cudaError_t launch_observables(lbmd_ctx *ctx);
 cudaError_t launch_populations_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst);
 cudaError_t launch_populations_from_double(lbmd_ctx *ctx, int64_t first, int64_t count, const double *src);

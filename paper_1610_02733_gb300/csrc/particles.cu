@@ -50,6 +50,11 @@ struct PArgs {
     const uint8_t *bond_kind;
     T lj_eps24, lj_sig2, lj_rc2;  // Lennard-Jones: 24 eps, sigma^2, r_cut^2
     float lj_filter2;             // (r_cut + rounding margin of FP32 absolute positions)^2
+    // LJ Verlet lists (null when LJ is off)
+    const int32_t *nb_list, *nb_count;
+    int32_t *nb_invalid;
+    const typename P::real4 *nb_ref4;  // positions at the list build, per id
+    T nb_half_skin2;                   // (skin / 2)^2: a larger move since the build voids the lists
     int nx, ny, nz;
     FastDiv fd_nx, fd_ny;  // division by nx and ny
     int64_t np;
@@ -162,6 +167,27 @@ __device__ __forceinline__ void hand_over(const PArgs<T> &a, int64_t p, const ty
     }
 }
 
+// Cell offset d (partner minus particle, |d| < n) to its periodic image
+// nearest to zero, in [-n/2, n/2].
+__device__ __forceinline__ int nearest_image(int d, int n) {
+    const int h = n >> 1;
+    return d > h ? d - n : (d < -h ? d + n : d);
+}
+
+// LJ Verlet lists: a particle that moved more than half the skin since the
+// lists were built voids them (flag read by the pair kernel of this step).
+template <typename T>
+__device__ __forceinline__ void check_list_skin(const PArgs<T> &a, int64_t p, const CellXYZ &cn, T fx, T fy, T fz) {
+    using P = Prec<T>;
+    if (!a.nb_ref4 || *a.nb_invalid) return;
+    const typename P::real4 S = a.nb_ref4[a.pid[p]];
+    const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
+    const T dx = T(nearest_image(cn.x - d.x, a.nx)) + (fx - S.x);
+    const T dy = T(nearest_image(cn.y - d.y, a.ny)) + (fy - S.y);
+    const T dz = T(nearest_image(cn.z - d.z, a.nz)) + (fz - S.z);
+    if (dx * dx + dy * dy + dz * dz > a.nb_half_skin2) atomicOr(a.nb_invalid, 1);
+}
+
 // One MD step, coupling force from the start of the step (integrator START):
 // F = -zeta (v - u(R)) + F_rand with R, v of the beginning of the step
 // (Eqs. (4)-(6)), velocity Verlet with F held over both half-kicks (the
@@ -204,6 +230,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PAr
         V.y += hm * Fy;
         V.z += hm * Fz;
     }
+    if (BONDS) check_list_skin(a, p, CellXYZ{cx, cy, cz}, fx, fy, fz);
     a.pos4[p] = P::make_pos(fx, fy, fz, cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz));
     a.vel4[p] = V;
     if (BONDS || a.variant == LBMD_VARIANT_B) a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
@@ -240,6 +267,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_half_kerne
     advance(fy, cn.y, a.dt * V.y, a.ny);
     advance(fz, cn.z, a.dt * V.z, a.nz);
     const typename P::real4 Rn = P::make_pos(fx, fy, fz, cn.x + (int64_t)a.nx * (cn.y + (int64_t)a.ny * cn.z));
+    if (BONDS) check_list_skin(a, p, cn, fx, fy, fz);
     T ux, uy, uz, Fx, Fy, Fz;
     interp_u(a, cn, fx, fy, fz, ux, uy, uz);
     coupling_force(a, p, V, ux, uy, uz, Fx, Fy, Fz);
@@ -531,12 +559,6 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
     }
 }
 
-// Cell offset d (partner minus particle, |d| < n) to its periodic image
-// nearest to zero, in [-n/2, n/2].
-__device__ __forceinline__ int nearest_image(int d, int n) {
-    const int h = n >> 1;
-    return d > h ? d - n : (d < -h ? d + n : d);
-}
 
 // Conservative forces with Lennard-Jones (Kremer-Grest monomers, Sec. 4):
 // one warp per particle id i, eight per block.  The block stages the other
@@ -575,7 +597,52 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_kick_kernel(PArgs<T> a) {
     const float fnx = (float)a.nx, fny = (float)a.ny, fnz = (float)a.nz;
     const float inx = 1.0f / fnx, iny = 1.0f / fny, inz = 1.0f / fnz;
     T Fx = T(0), Fy = T(0), Fz = T(0);
-    for (int64_t j0 = 0; j0 < a.np; j0 += TILE) {
+    // Verlet lists when they hold every pair within the cut-off (no particle
+    // moved more than half the skin since the build, no list overflowed in
+    // this block).  Lane l takes the listed ids j = l (mod 32) in ascending
+    // order: the same terms in the same order as the all-pairs loop below,
+    // so both give the same bits.
+    int use_all = a.nb_list == nullptr || *a.nb_invalid != 0;
+    if (!use_all && live && a.nb_count[i] < 0) use_all = 1;
+    use_all = __syncthreads_or(use_all);
+    if (!use_all && live) {
+        // the lanes evaluate 32 listed pairs at a time; each term then goes,
+        // in list (= id) order, to the lane that owns its id (j mod 32)
+        const int cnt = a.nb_count[i];
+        const int32_t *L = a.nb_list + i * LBMD_NB_MAX;
+        for (int e0 = 0; e0 < cnt; e0 += 32) {
+            int32_t j = -1;
+            T g = T(0), dx = T(0), dy = T(0), dz = T(0);
+            if (e0 + lane < cnt) {
+                j = L[e0 + lane];
+                const typename P::real4 S = a.pos4[a.slot_of[j]];
+                const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
+                dx = T(nearest_image(d.x - c.x, a.nx)) + (S.x - R.x);
+                dy = T(nearest_image(d.y - c.y, a.ny)) + (S.y - R.y);
+                dz = T(nearest_image(d.z - c.z, a.nz)) + (S.z - R.z);
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < a.lj_rc2) {  // beyond the cut-off: g = 0 adds nothing
+                    const T s = a.lj_sig2 / r2;
+                    const T t = s * s * s;
+                    g = -a.lj_eps24 * (T(2) * t * t - t) / r2;
+                }
+            }
+            const int m = cnt - e0 < 32 ? cnt - e0 : 32;
+            for (int k = 0; k < m; ++k) {
+                const int32_t jk = __shfl_sync(0xffffffffu, j, k);
+                const T gk = __shfl_sync(0xffffffffu, g, k);
+                const T xk = __shfl_sync(0xffffffffu, dx, k);
+                const T yk = __shfl_sync(0xffffffffu, dy, k);
+                const T zk = __shfl_sync(0xffffffffu, dz, k);
+                if ((jk & 31) == lane) {
+                    Fx += gk * xk;
+                    Fy += gk * yk;
+                    Fz += gk * zk;
+                }
+            }
+        }
+    }
+    for (int64_t j0 = 0; use_all && j0 < a.np; j0 += TILE) {
         const int cnt = a.np - j0 < TILE ? (int)(a.np - j0) : TILE;
         __syncthreads();  // the previous tile is consumed
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
@@ -649,6 +716,101 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_kick_kernel(PArgs<T> a) {
         a.vel4[p] = V;
     }
 }
+
+// LJ Verlet lists, rebuilt after each re-ordering (rebuilding only voided
+// lists made the all-pairs fallback frequent: the skin is then spent over
+// several LB steps): one warp per slot q (particle i = pid[q]) builds i's
+// list: the lanes run over the particles of the row buckets
+// within ceil(r_list) rows in y and z (each distinct row once; the buckets'
+// slot ranges are concatenated and shared out 32 at a time), keep the ids
+// j != i closer than r_list = r_cut + skin, and write them in ascending order
+// (each lane ranks its entries by counting the smaller ids).  A particle with
+// more than LBMD_NB_MAX candidates gets count -1 (its block then uses all
+// pairs).  The positions at the build are kept per id.
+constexpr int NB_WARPS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * NB_WARPS) nb_build_kernel(PArgs<T> a, T rlist2, int reach) {
+    using P = Prec<T>;
+    __shared__ int32_t s_ids[NB_WARPS][LBMD_NB_MAX];
+    __shared__ int s_cnt[NB_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * NB_WARPS + warp;
+    if (q >= a.np) return;  // whole warps; no block barrier below
+    const int32_t i = a.pid[q];
+    const typename P::real4 R = a.pos4[q];
+    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
+    if (lane == 0) {
+        s_cnt[warp] = 0;
+        const_cast<typename P::real4 *>(a.nb_ref4)[i] = R;
+    }
+    __syncwarp();
+    const int ny_rows = 2 * reach + 1 < a.ny ? 2 * reach + 1 : a.ny;
+    const int nz_rows = 2 * reach + 1 < a.nz ? 2 * reach + 1 : a.nz;
+    const int y0 = 2 * reach + 1 < a.ny ? c.y - reach + a.ny : 0;
+    const int z0 = 2 * reach + 1 < a.nz ? c.z - reach + a.nz : 0;
+    const int nrows = ny_rows * nz_rows;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+        // lane r: the slot range of candidate row r0 + r, and its offset in
+        // the concatenation of the ranges
+        int lo = 0, cnt = 0;
+        if (r0 + lane < nrows) {
+            const int ky = (r0 + lane) % ny_rows, kz = (r0 + lane) / ny_rows;
+            const int row = (y0 + ky) % a.ny + a.ny * ((z0 + kz) % a.nz);
+            lo = a.row_start[row];
+            cnt = a.row_start[row + 1] - lo;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            // the last row whose range starts at or before t
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, excl, r + step);
+                if (v <= t) r += step;
+            }
+            const int lo_r = __shfl_sync(0xffffffffu, lo, r), ex_r = __shfl_sync(0xffffffffu, excl, r);
+            if (t >= total) continue;
+            const int sl = lo_r + (t - ex_r);
+            const int32_t j = a.pid[sl];
+            if (j == i) continue;
+            const typename P::real4 S = a.pos4[sl];
+            const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
+            const T dx = T(nearest_image(d.x - c.x, a.nx)) + (S.x - R.x);
+            const T dy = T(nearest_image(d.y - c.y, a.ny)) + (S.y - R.y);
+            const T dz = T(nearest_image(d.z - c.z, a.nz)) + (S.z - R.z);
+            if (dx * dx + dy * dy + dz * dz < rlist2) {
+                const int k = atomicAdd(&s_cnt[warp], 1);
+                if (k < LBMD_NB_MAX) s_ids[warp][k] = j;
+            }
+        }
+    }
+    __syncwarp();
+    const int cnt = s_cnt[warp];
+    if (cnt > LBMD_NB_MAX) {
+        if (lane == 0) const_cast<int32_t *>(a.nb_count)[i] = -1;
+        return;
+    }
+    int32_t *L = const_cast<int32_t *>(a.nb_list) + (int64_t)i * LBMD_NB_MAX;
+    for (int k = lane; k < cnt; k += 32) {
+        const int32_t j = s_ids[warp][k];
+        int rank = 0;
+        for (int m = 0; m < cnt; ++m) rank += s_ids[warp][m] < j ? 1 : 0;
+        L[rank] = j;
+    }
+    if (lane == 0) const_cast<int32_t *>(a.nb_count)[i] = cnt;
+}
+
+// after a build (or none): the lists hold every pair within the cut-off
+__global__ void nb_validate_kernel(int32_t *invalid) { *invalid = 0; }
 
 // ---------------------------------------------------------------------------
 // Re-ordering by lattice row.
@@ -874,6 +1036,12 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
         const double margin = edge * std::ldexp(1.0, -18) + 1e-6;
         a.lj_filter2 = (float)((ctx->lj_rc + margin) * (ctx->lj_rc + margin));
     }
+    const bool lists = ctx->lj_rc > 0.0 && ctx->nb_list;
+    a.nb_list = lists ? ctx->nb_list : nullptr;
+    a.nb_count = lists ? ctx->nb_count : nullptr;
+    a.nb_invalid = lists ? ctx->nb_invalid : nullptr;
+    a.nb_ref4 = lists ? static_cast<const typename P::real4 *>(ctx->nb_ref4) : nullptr;
+    a.nb_half_skin2 = (T)(0.25 * LBMD_NB_SKIN * LBMD_NB_SKIN);
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
@@ -1032,6 +1200,19 @@ static cudaError_t active_sync_t(lbmd_ctx *ctx) {
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t nb_build_t(lbmd_ctx *ctx) {
+    if (ctx->np == 0 || !(ctx->lj_rc > 0.0) || !ctx->nb_list) return cudaSuccess;
+    PArgs<T> a = make_pargs<T>(ctx, 0);
+    const double rl = ctx->lj_rc + LBMD_NB_SKIN;
+    nb_build_kernel<T><<<(unsigned)((ctx->np + NB_WARPS - 1) / NB_WARPS), 32 * NB_WARPS, 0, ctx->stream>>>(
+        a, (T)(rl * rl), (int)std::ceil(rl));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    nb_validate_kernel<<<1, 1, 0, ctx->stream>>>(ctx->nb_invalid);
+    return cudaGetLastError();
+}
+
 }  // namespace lbmd
 
 cudaError_t launch_active_set(lbmd_ctx *ctx) {
@@ -1055,6 +1236,10 @@ cudaError_t launch_bond_forces_only(lbmd_ctx *ctx) {
 
 cudaError_t setup_particle_kernels(lbmd_ctx *ctx) {
     return ctx->p.precision == LBMD_FP64 ? lbmd::setup_t<double>(ctx) : lbmd::setup_t<float>(ctx);
+}
+
+cudaError_t launch_nb_build(lbmd_ctx *ctx) {
+    return ctx->p.precision == LBMD_FP64 ? lbmd::nb_build_t<double>(ctx) : lbmd::nb_build_t<float>(ctx);
 }
 
 cudaError_t launch_sort_particles(lbmd_ctx *ctx) {

@@ -173,3 +173,29 @@ def test_variant_b_spread_paths_agree_bitwise(integrator):
         for a, b in zip(runs[(lj, "rows")], runs[(lj, "atomic")]):
             np.testing.assert_array_equal(a, b)
 
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_verlet_lists_give_the_all_pairs_bits(precision):
+    # the LJ forces from the Verlet lists (built at every re-ordering) equal
+    # the all-pairs loop bit for bit: the same run with the lists voided every
+    # cycle (re-setting the same LJ parameters voids them until the next
+    # re-ordering) must not differ
+    shape, m = (20, 20, 20), 10
+    lp = lj_units.lattice_params(m, 0.01, 20.0)
+    pos, bonds = inputs.self_avoiding_chains(10, 256, shape, 27)
+    n = pos.shape[0]
+    runs = []
+    for void in (False, True):
+        g = lbmd.LBMD(*shape, variant="B", precision=precision, n_sub=m, kT=lp["kT"], zeta=lp["zeta"], nu=lp["nu"],
+                      seed=27, max_particles=n, max_bonds=bonds.shape[0], integrator="half_step")
+        g.add_particles(pos, inputs.maxwell_velocities(n, lp["kT"], 27))
+        g.set_lj(lp["lj_eps"], lp["lj_sigma"], lp["lj_rc"])
+        g.add_fene_bonds(bonds, lp["fene_k"], lp["fene_R0"])
+        for _ in range(6):
+            if void:
+                g.set_lj(lp["lj_eps"], lp["lj_sigma"], lp["lj_rc"])
+            g.cycle(1)
+        runs.append((g.populations(), *g.particles()))
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
+
