@@ -87,10 +87,11 @@ enum { LBMD_INTEGRATOR_START = 0, LBMD_INTEGRATOR_HALF_STEP = 1 };
  * atomics for the particles that left their row (few atomics; pays off for
  * many particles).  ATOMIC: every particle adds its 8 corner transfers with
  * integer atomics (one launch; pays off for few particles).  AUTO: ATOMIC
- * below LBMD_SPREAD_ATOMIC_MAX particles, ROWS above.  The transfers are
+ * while there are fewer than LBMD_SPREAD_ATOMIC_PER_ROW particles per lattice
+ * row (y, z) on average, ROWS above (measured crossover).  The transfers are
  * fixed-point integers, so all three give bitwise the same results. */
 enum { LBMD_SPREAD_AUTO = 0, LBMD_SPREAD_ROWS = 1, LBMD_SPREAD_ATOMIC = 2 };
-#define LBMD_SPREAD_ATOMIC_MAX 32768
+#define LBMD_SPREAD_ATOMIC_PER_ROW 10
 
 typedef struct lbmd_params {
     int32_t nx, ny, nz;    /* lattice nodes per axis (periodic), each >= 2 */

@@ -1082,7 +1082,8 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     const bool cons = has_cons(ctx);
     const bool B = ctx->p.variant == LBMD_VARIANT_B;
     const bool atomic = B && (ctx->p.spread == LBMD_SPREAD_ATOMIC ||
-                              (ctx->p.spread == LBMD_SPREAD_AUTO && ctx->np < LBMD_SPREAD_ATOMIC_MAX));
+                              (ctx->p.spread == LBMD_SPREAD_AUTO &&
+                               ctx->np < (int64_t)LBMD_SPREAD_ATOMIC_PER_ROW * ctx->p.ny * ctx->p.nz));
     a.b_atomic = atomic ? 1 : 0;
     a.kick_spreads = atomic && cons ? 1 : 0;
     cudaError_t e;
