@@ -159,7 +159,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    ctx->red_blocks = 2 * sms;
+    ctx->red_blocks = 4 * sms;
     ctx->sm_count = sms;
     // active nodes: every particle makes at most the 8 corners of its cell
     // active
@@ -512,7 +512,6 @@ lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
     LBMD_TRACE("lbmd_observables");
     if (!ctx || !out) return LBMD_ERR_ARG;
     double h[8];
-    CK(ctx, launch_active_sync(ctx));
     CK(ctx, launch_observables(ctx));
     CK(ctx, cudaMemcpyAsync(h, ctx->red_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));

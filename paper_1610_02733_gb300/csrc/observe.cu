@@ -34,27 +34,65 @@ __device__ __forceinline__ void block_reduce_store(double v[NV], double *row) {
     }
 }
 
+// Momentum sums in fixed-point units: FP32 records hold 32-bit integers,
+// whose per-thread sums are exact in 64-bit integers (and exact again as
+// doubles, being far below 2^53); FP64 records (56 fraction bits) are summed
+// in doubles.
+template <typename T>
+struct MomentumSum {
+    using type = double;
+};
+template <>
+struct MomentumSum<float> {
+    using type = long long;
+};
+
+// Variant B keeps the records of the active nodes in their compact array
+// during a cycle: a node's current record is found through the active words
+// (occw non-null), so no copy back is needed first.
 template <typename T, int VARIANT>
 __global__ void __launch_bounds__(RED_THREADS)
-    observe_nodes_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc, int64_t N,
+    observe_nodes_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc,
+                         const uint2 *occw, const typename Prec<T>::node4 *cact, int W, FastDiv fnx, int64_t N,
                          double *partial) {
     using P = Prec<T>;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    using M = typename MomentumSum<T>::type;
+    double rho = 0.0;
+    M jx = 0, jy = 0, jz = 0;
     const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-    for (int64_t r = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; r < N; r += stride) {
-        const typename P::node4 n = node[r];
-        v[0] += (double)P::rho_of(n);
-        v[1] += (double)P::jx_of(n);
-        v[2] += (double)P::jy_of(n);
-        v[3] += (double)P::jz_of(n);
-        if (VARIANT == LBMD_VARIANT_A) {
-            const typename P::node4 J = jacc[r];
-            v[1] += (double)P::jx_of(J);
-            v[2] += (double)P::jy_of(J);
-            v[3] += (double)P::jz_of(J);
+    // four nodes per pass, all loaded before use (memory-level parallelism)
+    for (int64_t r0 = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; r0 < N; r0 += 4 * stride) {
+        typename P::node4 n[4], J[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t r = r0 + u * stride;
+            if (r >= N) continue;
+            if (occw) {
+                const uint32_t row = fdiv((uint32_t)r, fnx);
+                const int x = (int)((uint32_t)r - row * fnx.d);
+                const int sl = active_slot(occw[(size_t)row * W + (x >> 5)], x);
+                n[u] = sl >= 0 ? cact[sl] : node[r];
+            } else {
+                n[u] = node[r];
+            }
+            if (VARIANT == LBMD_VARIANT_A) J[u] = jacc[r];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (r0 + u * stride >= N) continue;
+            rho += (double)P::rho_of(n[u]);
+            jx += (M)P::jx_of(n[u]);
+            jy += (M)P::jy_of(n[u]);
+            jz += (M)P::jz_of(n[u]);
+            if (VARIANT == LBMD_VARIANT_A) {
+                jx += (M)P::jx_of(J[u]);
+                jy += (M)P::jy_of(J[u]);
+                jz += (M)P::jz_of(J[u]);
+            }
         }
     }
     // momenta stay in fixed-point units until the final scaling
+    double v[4] = {rho, (double)jx, (double)jy, (double)jz};
     block_reduce_store<4>(v, partial + (int64_t)blockIdx.x * RED_COLS);
 }
 
@@ -66,25 +104,38 @@ __global__ void __launch_bounds__(RED_THREADS)
                              double *partial) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-    for (int64_t id = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; id < np; id += stride) {
-        const typename Prec<T>::real4 V = vel4[slot_of[id]];
-        const double m = 1.0 / (double)V.w;
-        const double vx = V.x, vy = V.y, vz = V.z;
-        v[0] += m * vx;
-        v[1] += m * vy;
-        v[2] += m * vz;
-        v[3] += m * (vx * vx + vy * vy + vz * vz);
+    for (int64_t id0 = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; id0 < np; id0 += 4 * stride) {
+        typename Prec<T>::real4 Vs[4];
+        int32_t sl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sl[u] = id0 + u * stride < np ? slot_of[id0 + u * stride] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (sl[u] >= 0) Vs[u] = vel4[sl[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (sl[u] < 0) continue;
+            const double m = 1.0 / (double)Vs[u].w;
+            const double vx = Vs[u].x, vy = Vs[u].y, vz = Vs[u].z;
+            v[0] += m * vx;
+            v[1] += m * vy;
+            v[2] += m * vz;
+            v[3] += m * (vx * vx + vy * vy + vz * vz);
+        }
     }
     block_reduce_store<4>(v, partial + (int64_t)blockIdx.x * RED_COLS + 4);
 }
 
+// one warp per column: lane l adds rows l, l + 32, ... in order, then a fixed
+// butterfly combines the lanes
 template <typename T>
-__global__ void observe_final_kernel(const double *partial, int rows, double *out) {
-    // one thread per column, rows added in order
-    const int c = threadIdx.x;
-    if (c >= RED_COLS) return;
+__global__ void __launch_bounds__(32 * RED_COLS) observe_final_kernel(const double *partial, int rows, double *out) {
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int r = 0; r < rows; ++r) s += partial[(int64_t)r * RED_COLS + c];
+    for (int r = lane; r < rows; r += 32) s += partial[(int64_t)r * RED_COLS + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane != 0) return;
     if (c >= 1 && c <= 3) s *= (double)Prec<T>::INV_SCALE;
     out[c] = s;
 }
@@ -93,20 +144,23 @@ template <typename T>
 static cudaError_t observables_t(lbmd_ctx *ctx) {
     using P = Prec<T>;
     const int B = ctx->red_blocks;
+    const FastDiv fnx = make_fastdiv((uint32_t)ctx->p.nx);
     if (ctx->p.variant == LBMD_VARIANT_B)
         observe_nodes_kernel<T, LBMD_VARIANT_B><<<B, RED_THREADS, 0, ctx->stream>>>(
-            static_cast<const typename P::node4 *>(ctx->node), nullptr, ctx->N, ctx->red_partial);
+            static_cast<const typename P::node4 *>(ctx->node), nullptr, active_words_now(ctx),
+            static_cast<const typename P::node4 *>(active_records_now(ctx)), active_words(ctx->p.nx), fnx, ctx->N,
+            ctx->red_partial);
     else
         observe_nodes_kernel<T, LBMD_VARIANT_A><<<B, RED_THREADS, 0, ctx->stream>>>(
             static_cast<const typename P::node4 *>(ctx->node), static_cast<const typename P::node4 *>(ctx->jacc),
-            ctx->N, ctx->red_partial);
+            nullptr, nullptr, 0, fnx, ctx->N, ctx->red_partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     observe_particles_kernel<T><<<B, RED_THREADS, 0, ctx->stream>>>(
         static_cast<const typename P::real4 *>(ctx->vel4[ctx->pcur]), ctx->slot_of, ctx->np, ctx->red_partial);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    observe_final_kernel<T><<<1, 32, 0, ctx->stream>>>(ctx->red_partial, B, ctx->red_out);
+    observe_final_kernel<T><<<1, 32 * RED_COLS, 0, ctx->stream>>>(ctx->red_partial, B, ctx->red_out);
     return cudaGetLastError();
 }
 
