@@ -247,15 +247,17 @@ __global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, type
                                              const double *pos, const double *vel, const double *mass, int set_pos,
                                              int set_vel, int set_mass, int assign_ids, int nx, int ny, int nz) {
     using P = Prec<T>;
+    // one thread per id: the FP64 host arrays are read in order (coalesced),
+    // the device records written to their slots
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
-    const int64_t p = first + t;
-    int64_t src = t;
-    if (assign_ids) {
+    int64_t src = t, p = first + t;
+    if (assign_ids) {  // new particles: slot = id, the arrays hold the new ones only
         pid[p] = (int32_t)p;
         slot_of[p] = (int32_t)p;
-    } else {
-        src = pid[p];
+    } else {  // existing particles: the arrays are indexed by id
+        src = first + t;
+        p = slot_of[src];
     }
     if (set_pos) pos4[p] = pos_from_double<T>(pos + 3 * src, nx, ny, nz);
     typename P::real4 V = vel4[p];
@@ -271,16 +273,19 @@ __global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, type
 // device state -> FP64 arrays in id order
 template <typename T>
 __global__ void particles_to_double_kernel(const typename Prec<T>::real4 *pos4, const typename Prec<T>::real4 *vel4,
-                                           const int32_t *pid, int64_t np, double *pos, double *vel, int nx, int ny) {
+                                           const int32_t *slot_of, int64_t np, double *pos, double *vel, int nx,
+                                           int ny) {
     using P = Prec<T>;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    const int64_t id = pid[p];
+    // one thread per id: the FP64 host arrays are written in order
+    // (coalesced), the device records read from their slots
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= np) return;
+    const int64_t p = slot_of[id];
     if (pos) {
         const typename P::real4 R = pos4[p];
-        const int64_t cell = P::cell_of(R);
-        const int64_t nxy = (int64_t)nx * ny;
-        const int64_t z = cell / nxy, rem = cell - z * nxy, y = rem / nx, x = rem - y * nx;
+        const uint32_t cell = (uint32_t)P::cell_of(R);  // < nx ny nz <= 2^32
+        const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+        const uint32_t z = cell / nxy, rem = cell - z * nxy, y = rem / (uint32_t)nx, x = rem - y * (uint32_t)nx;
         pos[3 * id + 0] = (double)x + (double)R.x;
         pos[3 * id + 1] = (double)y + (double)R.y;
         pos[3 * id + 2] = (double)z + (double)R.z;
@@ -385,12 +390,12 @@ cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel) 
     if (ctx->p.precision == LBMD_FP64)
         particles_to_double_kernel<double><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
             static_cast<const Prec<double>::real4 *>(ctx->pos4[b]),
-            static_cast<const Prec<double>::real4 *>(ctx->vel4[b]), ctx->pid[b], ctx->np, pos, vel, ctx->p.nx,
+            static_cast<const Prec<double>::real4 *>(ctx->vel4[b]), ctx->slot_of, ctx->np, pos, vel, ctx->p.nx,
             ctx->p.ny);
     else
         particles_to_double_kernel<float><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
             static_cast<const Prec<float>::real4 *>(ctx->pos4[b]),
             static_cast<const Prec<float>::real4 *>(ctx->vel4[b]),
-            ctx->pid[b], ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
+            ctx->slot_of, ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
     return cudaGetLastError();
 }

@@ -92,8 +92,10 @@ __device__ __forceinline__ typename Prec<T>::real4 pos_from_double(const double 
     int64_t cl[3];
     for (int d = 0; d < 3; ++d) {
         double x = x3[d];
-        x -= L[d] * floor(x / L[d]);
-        if (x >= L[d]) x -= L[d];
+        if (!(x >= 0.0 && x < L[d])) {  // outside the box: wrap (inside, this changes nothing)
+            x -= L[d] * floor(x / L[d]);
+            if (x >= L[d]) x -= L[d];
+        }
         double b = floor(x);
         T f = (T)(x - b);
         if (f >= T(1)) {  // rounding to the storage precision reached the next node
