@@ -25,11 +25,12 @@
 //
 // active_*: variant B, after each re-ordering: the corners of the particles'
 // cells become the active nodes, numbered row by row into a compact array of
-// node records (filled by the LB moments kernel).  Between LB updates the MD
-// kernels read and update an active node through its compact record, which
-// is about as large as the touched part of the lattice rather than the whole
-// node field, and a node that is not active (one a particle reaches only
-// after moving to another cell) through the node field, as before.
+// node records (filled by the post-stream moments of the LB step).  Between
+// LB updates the MD kernels read and update an active node through its
+// compact record, which is about as large as the touched part of the lattice
+// rather than the whole node field, and a node that is not active (one a
+// particle reaches only after moving to another cell) through the node
+// field, as before.
 #include <algorithm>
 #include <cmath>
 
