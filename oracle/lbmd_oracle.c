@@ -18,7 +18,9 @@
  * Where the paper defers to its references (the MRT collision operator, the
  * stochastic collision operator and the forcing term Delta'_i), the standard
  * moment-space formulation of the fluctuating lattice Boltzmann method is
- * used.  Every such reading is listed in DESIGN.md under "Readings".
+ * used: orthogonal 19-mode basis, relaxation factors per mode group, noise of
+ * variance mu rho b_k (1 - gamma_k^2) on the non-conserved modes, and Guo's
+ * forcing in moment space (the functions below say which at each place).
  *
  * Parity pins (tests/test_oracle_*.py) tie each function below to something
  * other than itself; none of them is "parity unpinned".

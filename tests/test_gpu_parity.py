@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle, on
 the same seeded inputs, element by element.
 
-Tolerances (see DESIGN.md): populations 1e-5 in FP32 and 1e-12 in FP64 after
+Tolerances: populations 1e-5 in FP32 and 1e-12 in FP64 after
 one LB step, relative to each population's scale w_i rho0; particle and node vectors 1e-5 / 1e-12
 relative to their largest magnitude.  Integer-valued results (A and B at
 m = 1, repeated runs, graph replay) must match bit for bit.
