@@ -614,6 +614,8 @@ def main():
     ap.add_argument("--kT", type=float, default=1e-4, help="temperature (profiling: 0 switches the noise off)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev"],
                     help="population storage of the timed workload (profiling)")
+    ap.add_argument("--only-form", default=None, choices=["batched_replicas"],
+                    help="run only this form and print its JSON object (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     global SHAPE, N_PARTICLES, WORKLOAD, KT, PRECISION
@@ -630,6 +632,12 @@ def main():
         return
     import __graft_entry__
     __graft_entry__.build()
+    if args.only_form == "batched_replicas":
+        import torch
+        from paper_1610_02733_gb300 import inputs, lbmd
+        out = _batched_replicas(torch, lbmd, inputs, torch.cuda.Stream(), _peaks()[0])
+        print(json.dumps(out))
+        return
     run_gpu(args)
 
 

@@ -12,8 +12,9 @@
 // step after every m_r-th tick.  A period of P = lcm(m_r) ticks repeats, and
 // is captured once into a CUDA graph: per tick the couple kernel (every
 // particle), the transfer kernel (variant-B particles), and, for the replicas
-// whose LB step is due, the collide, moments and step-counter kernels driven
-// by a precomputed table of (replica, first node) per block.
+// whose LB step is due, the collide and moments kernels driven by a
+// precomputed table of work items (replica, first node); the moments kernel
+// also advances the LB step counters.
 //
 // Transfers are integer atomics on the replica's node field (B) or transfer
 // accumulator (A): the boxes are small enough to stay in L2, and integer sums
@@ -25,7 +26,7 @@
 // lattice unit per time unit, or not finite) is flagged unstable and frozen,
 // and reported as such.
 //
-// Autotuner.  The block sizes of the node kernels (nodes per block) and of
+// Autotuner.  The block sizes of the node kernels (nodes per item) and of
 // the particle kernels are chosen by timing each candidate with CUDA events
 // on this batch (node kernels at creation on the rest state, which is then
 // restored; particle kernels at the first run, on copies of the state).
@@ -48,6 +49,8 @@ namespace lbmd {
 constexpr int BATCH_MAX_EDGE = 512;
 constexpr int64_t BATCH_MAX_PERIOD = 256;
 constexpr int BATCH_VMAX2 = 1;  // |v|^2 beyond which a replica counts as unstable
+constexpr int BATCH_LB_MAX_NODES = 256;  // nodes per work item of the LB kernels, at most
+constexpr int BATCH_LB_MAX_THREADS = BATCH_LB_MAX_NODES + 32;
 
 // Per-replica constants, one entry per replica in device memory.
 template <typename T>
@@ -77,11 +80,14 @@ struct BArgs {
 template <typename T>
 struct BLbArgs {
     const BRep<T> *rep;
-    const int2 *work;  // per block: replica, first node
+    const int2 *work;  // per item: replica, first node
+    int64_t n_items;
     T *f0, *f1;        // population buffers: replica r's 19 N_r values at 19 node_off
     typename Prec<T>::node4 *node, *jacc;
-    const unsigned long long *lb_step;
+    unsigned long long *lb_step;
     const int *unstable;
+    unsigned *items_done;  // per replica: items of the moments kernel taken so far
+    int advance;           // the moments kernel advances the LB step counters
     int nodes_per_block;
     // members read by collide()
     T gamma_bulk, gamma_shear, gamma_ghost;
@@ -174,82 +180,253 @@ __global__ void __launch_bounds__(256) batch_transfer_kernel(BArgs<T> a) {
                  F.z * rp.neg_scale_dt);
 }
 
-// LB collide and push of the due replicas (Eq. (3)); block b covers nodes
-// [work[b].y, work[b].y + nodes_per_block) of replica work[b].x.
-template <typename T, bool RELAX_FULL>
-__global__ void __launch_bounds__(256) batch_collide_kernel(BLbArgs<T> a) {
-    using P = Prec<T>;
-    const int2 w = a.work[blockIdx.x];
-    const int r = w.x;
-    const BRep<T> &rp = a.rep[r];
-    const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
-    const int64_t loc = (int64_t)w.y + threadIdx.x;
-    if (threadIdx.x >= (unsigned)a.nodes_per_block || loc >= N || a.unstable[r]) return;
-    const unsigned long long step = a.lb_step[r];
-    const T *fin = ((step & 1ull) ? a.f1 : a.f0) + 19 * rp.node_off;
-    T *fout = ((step & 1ull) ? a.f0 : a.f1) + 19 * rp.node_off;
-    const uint32_t u = (uint32_t)loc;
-    const uint32_t row = fdiv(u, rp.fd_nx);
-    const int x = (int)(u - row * rp.fd_nx.d);
-    const int z = (int)fdiv(row, rp.fd_ny);
-    const int y = (int)(row - (uint32_t)z * rp.fd_ny.d);
-    T f[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = fin[(int64_t)i * N + loc];
-    T rho, jx, jy, jz;
-    node_moments(f, rho, jx, jy, jz);
-    T Fx, Fy, Fz;
-    if (rp.variant == LBMD_VARIANT_B) {
-        const typename P::node4 n = a.node[rp.node_off + loc];
-        Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx));
-        Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy));
-        Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz));
-    } else {
-        typename P::node4 *J = a.jacc + rp.node_off + loc;
-        const typename P::node4 Jv = *J;
-        Fx = P::from_fix(P::jx_of(Jv));
-        Fy = P::from_fix(P::jy_of(Jv));
-        Fz = P::from_fix(P::jz_of(Jv));
-        typename P::node4 zero;
-        zero.x = zero.y = zero.z = zero.w = 0;
-        *J = zero;
-    }
-    collide<T, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, rp.key0, rp.key1, u, (uint32_t)step);
-    const int xm = x == 0 ? rp.nx - 1 : x - 1, xp = x == rp.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? rp.ny - 1 : y - 1, yp = y == rp.ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? rp.nz - 1 : z - 1, zp = z == rp.nz - 1 ? 0 : z + 1;
-    const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int64_t t = (int64_t)X[CX(i) + 1] + (int64_t)rp.nx * (Y[CY(i) + 1] + (int64_t)rp.ny * Z[CZ(i) + 1]);
-        fout[(int64_t)i * N + t] = f[i];
-    }
-}
-
-// Post-stream moments of the due replicas -> node field (their step counter
-// is advanced afterwards by batch_step_kernel, so every block reads the same
-// buffer parity).
+// The LB kernels walk their work table with persistent blocks: block b takes
+// items b, b + G, b + 2G, ... (G = grid size).  Every block has one warp more
+// than it has nodes per item; that warp fetches the headers of the coming
+// items (work entry, the replica's constants and LB step counter) into shared
+// memory while the others process the current item, so no block waits on
+// that chain of dependent loads.  It reads the work entries of 32 of the
+// block's items at a time, with their replicas' frozen flags, and skips the
+// items of frozen replicas.
 template <typename T>
-__global__ void __launch_bounds__(256) batch_moments_kernel(BLbArgs<T> a) {
-    using P = Prec<T>;
-    const int2 w = a.work[blockIdx.x];
-    const int r = w.x;
-    const BRep<T> &rp = a.rep[r];
-    const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
-    const int64_t loc = (int64_t)w.y + threadIdx.x;
-    if (threadIdx.x >= (unsigned)a.nodes_per_block || loc >= N || a.unstable[r]) return;
-    const T *f = (((a.lb_step[r] + 1ull) & 1ull) ? a.f1 : a.f0) + 19 * rp.node_off;
-    T fl[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fl[i] = f[(int64_t)i * N + loc];
-    T rho, jx, jy, jz;
-    node_moments(fl, rho, jx, jy, jz);
-    a.node[rp.node_off + loc] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+struct BItem {
+    BRep<T> rep;
+    unsigned long long step;  // the replica's LB step counter
+    int r, first;             // replica (< 0: the block has no further item), first node
+};
+static_assert(sizeof(BRep<float>) % 4 == 0 && sizeof(BRep<double>) % 4 == 0, "BRep is copied by words");
+
+// State of the prefetch warp: the next window of 32 items, and in the current
+// one each lane's work entry and the mask of the live items not yet taken.
+struct ItemWindow {
+    int64_t next;
+    int2 w;
+    unsigned live;
+};
+
+// The prefetch warp: the next live item of this block into *out (r < 0 once
+// the table is exhausted).
+template <typename T>
+__device__ __forceinline__ void fetch_item(const BLbArgs<T> &a, ItemWindow &win, BItem<T> *out) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t stride = gridDim.x;
+    while (win.live == 0u) {
+        if (win.next >= a.n_items) {
+            if (lane == 0) out->r = -1;
+            return;
+        }
+        const int64_t it = win.next + lane * stride;
+        win.w = make_int2(-1, 0);
+        int live = 0;
+        if (it < a.n_items) {
+            win.w = a.work[it];
+            live = !a.unstable[win.w.x];
+        }
+        win.live = __ballot_sync(0xffffffffu, live);
+        win.next += 32 * stride;
+    }
+    const int src = __ffs(win.live) - 1;
+    win.live &= win.live - 1u;
+    const int r = __shfl_sync(0xffffffffu, win.w.x, src);
+    const int first = __shfl_sync(0xffffffffu, win.w.y, src);
+    const uint32_t *rw = reinterpret_cast<const uint32_t *>(a.rep + r);
+    uint32_t *ow = reinterpret_cast<uint32_t *>(&out->rep);
+    for (int k = lane; k < (int)(sizeof(BRep<T>) / 4); k += 32) ow[k] = rw[k];
+    if (lane == 0) {
+        out->step = a.lb_step[r];
+        out->r = r;
+        out->first = first;
+    }
 }
 
-__global__ void batch_step_kernel(const int32_t *due, int n_due, unsigned long long *lb_step, const int *unstable) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_due && !unstable[due[t]]) lb_step[due[t]] += 1ull;
+// Asynchronous copies global -> shared memory (cp.async): a thread stages the
+// values of its node of the next item while it computes the current one, and
+// waits only for its own copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared memory of an LB block: two buffers of the staged populations of an
+// item (population i of node slot t at [buf][i][t]) and, for the collide, of
+// its node records.
+template <typename T>
+size_t lb_smem_bytes(int nodes_per_block, bool with_node) {
+    return (size_t)2 * nodes_per_block * (Q * sizeof(T) + (with_node ? sizeof(typename Prec<T>::node4) : 0));
+}
+
+// The item loop shared by the LB kernels.  Per item k of this block: the
+// prefetch warp fetches the header of item k + 2; every other thread issues
+// the copies of its node of item k + 1 (issue(item, node, buf)), waits for
+// its copies of item k and runs body(item, node, buf) on them, then thread 0
+// runs once(item).  Three header slots and two staging buffers rotate.
+template <typename T, typename Issue, typename Body, typename Once>
+__device__ __forceinline__ void for_items(const BLbArgs<T> &a, Issue issue, Body body, Once once) {
+    __shared__ BItem<T> s_item[3];
+    const bool pre = threadIdx.x >= (unsigned)a.nodes_per_block;
+    ItemWindow win{(int64_t)blockIdx.x, make_int2(-1, 0), 0u};
+    if (pre) fetch_item(a, win, &s_item[0]);
+    __syncthreads();
+    if (s_item[0].r < 0) return;
+    if (pre) {
+        fetch_item(a, win, &s_item[1]);
+    } else {
+        issue(s_item[0], (int64_t)s_item[0].first + threadIdx.x, 0);
+        cp_async_commit();
+    }
+    __syncthreads();
+    int slot = 0;
+    for (int k = 0;; ++k) {
+        const BItem<T> &cur = s_item[slot];
+        if (cur.r < 0) break;
+        const int s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
+        const BItem<T> &nxt = s_item[s1];
+        if (pre) {
+            fetch_item(a, win, &s_item[s2]);
+        } else {
+            if (nxt.r >= 0) issue(nxt, (int64_t)nxt.first + threadIdx.x, (k + 1) & 1);
+            cp_async_commit();
+            cp_async_wait_prev();
+            body(cur, (int64_t)cur.first + threadIdx.x, k & 1);
+            if (threadIdx.x == 0) once(cur);
+        }
+        __syncthreads();
+        slot = s1;
+    }
+    if (!pre) cp_async_wait_all();
+}
+
+// A staged node record, read from shared memory in 16-byte pieces.
+template <typename T>
+__device__ __forceinline__ typename Prec<T>::node4 staged_node(const unsigned char *p) {
+    typename Prec<T>::node4 n;
+    const int4 *src = reinterpret_cast<const int4 *>(p);
+    int4 *dst = reinterpret_cast<int4 *>(&n);
+#pragma unroll
+    for (int h = 0; h < (int)(sizeof(n) / 16); ++h) dst[h] = src[h];
+    return n;
+}
+
+// LB collide and push of the due replicas (Eq. (3)) on the nodes
+// [first, first + nodes_per_block) of each item.  Staged per node: the 19
+// populations and the node record (variant B) or the transfer accumulator
+// (variant A).
+template <typename T, bool RELAX_FULL>
+__global__ void __launch_bounds__(BATCH_LB_MAX_THREADS, sizeof(T) == 4 ? 4 : 2) batch_collide_kernel(BLbArgs<T> a) {
+    using P = Prec<T>;
+    using N4 = typename P::node4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nb = a.nodes_per_block, t = (int)threadIdx.x;
+    unsigned char *s_node = smem;                                         // [2][nb] records
+    T *s_pop = reinterpret_cast<T *>(smem + (size_t)2 * nb * sizeof(N4));  // [2][Q][nb]
+    auto issue = [&](const BItem<T> &it, int64_t loc, int buf) {
+        const BRep<T> &rp = it.rep;
+        const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
+        if (loc >= N) return;
+        const T *fin = ((it.step & 1ull) ? a.f1 : a.f0) + 19 * rp.node_off + loc;
+        T *dst = s_pop + (size_t)buf * Q * nb + t;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) cp_async<sizeof(T)>(dst + i * nb, fin + i * N);
+        const N4 *rec = (rp.variant == LBMD_VARIANT_B ? a.node : a.jacc) + rp.node_off + loc;
+        unsigned char *dn = s_node + ((size_t)buf * nb + t) * sizeof(N4);
+#pragma unroll
+        for (int h = 0; h < (int)(sizeof(N4) / 16); ++h)
+            cp_async<16>(dn + 16 * h, reinterpret_cast<const unsigned char *>(rec) + 16 * h);
+    };
+    auto body = [&](const BItem<T> &it, int64_t loc, int buf) {
+        const BRep<T> &rp = it.rep;
+        const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
+        if (loc >= N) return;
+        const unsigned long long step = it.step;
+        T *__restrict__ fout = ((step & 1ull) ? a.f0 : a.f1) + 19 * rp.node_off;
+        const uint32_t u = (uint32_t)loc;
+        const uint32_t row = fdiv(u, rp.fd_nx);
+        const int x = (int)(u - row * rp.fd_nx.d);
+        const int z = (int)fdiv(row, rp.fd_ny);
+        const int y = (int)(row - (uint32_t)z * rp.fd_ny.d);
+        const T *src = s_pop + (size_t)buf * Q * nb + t;
+        T f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = src[i * nb];
+        T rho, jx, jy, jz;
+        node_moments(f, rho, jx, jy, jz);
+        const N4 n = staged_node<T>(s_node + ((size_t)buf * nb + t) * sizeof(N4));
+        T Fx, Fy, Fz;
+        if (rp.variant == LBMD_VARIANT_B) {
+            Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx));
+            Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy));
+            Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz));
+        } else {
+            Fx = P::from_fix(P::jx_of(n));
+            Fy = P::from_fix(P::jy_of(n));
+            Fz = P::from_fix(P::jz_of(n));
+            N4 zero;
+            zero.x = zero.y = zero.z = zero.w = 0;
+            a.jacc[rp.node_off + loc] = zero;
+        }
+        collide<T, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, rp.key0, rp.key1, u, (uint32_t)step);
+        const int nx = rp.nx, ny = rp.ny, nz = rp.nz;
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int64_t d = (int64_t)X[CX(i) + 1] + (int64_t)nx * (Y[CY(i) + 1] + (int64_t)ny * Z[CZ(i) + 1]);
+            fout[(int64_t)i * N + d] = f[i];
+        }
+    };
+    for_items(a, issue, body, [](const BItem<T> &) {});
+}
+
+// Post-stream moments of the due replicas -> node field.  With advance set,
+// the block that takes the last item of a replica advances the replica's LB
+// step counter: every item of the replica has been fetched, and so has read
+// the counter, by then.
+template <typename T>
+__global__ void __launch_bounds__(BATCH_LB_MAX_THREADS) batch_moments_kernel(BLbArgs<T> a) {
+    using P = Prec<T>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nb = a.nodes_per_block, t = (int)threadIdx.x;
+    T *s_pop = reinterpret_cast<T *>(smem);  // [2][Q][nb]
+    auto issue = [&](const BItem<T> &it, int64_t loc, int buf) {
+        const BRep<T> &rp = it.rep;
+        const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
+        if (loc >= N) return;
+        const T *f = (((it.step + 1ull) & 1ull) ? a.f1 : a.f0) + 19 * rp.node_off + loc;
+        T *dst = s_pop + (size_t)buf * Q * nb + t;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) cp_async<sizeof(T)>(dst + i * nb, f + i * N);
+    };
+    auto body = [&](const BItem<T> &it, int64_t loc, int buf) {
+        const BRep<T> &rp = it.rep;
+        const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
+        if (loc >= N) return;
+        const T *src = s_pop + (size_t)buf * Q * nb + t;
+        T fl[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fl[i] = src[i * nb];
+        T rho, jx, jy, jz;
+        node_moments(fl, rho, jx, jy, jz);
+        a.node[rp.node_off + loc] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    };
+    auto advance = [&](const BItem<T> &it) {
+        if (!a.advance) return;
+        const int64_t N = (int64_t)it.rep.nx * it.rep.ny * it.rep.nz;
+        const unsigned items = (unsigned)((N + a.nodes_per_block - 1) / a.nodes_per_block);
+        if (atomicAdd(&a.items_done[it.r], 1u) == items - 1u) {
+            a.items_done[it.r] = 0u;
+            a.lb_step[it.r] = it.step + 1ull;
+        }
+    };
+    for_items(a, issue, body, advance);
 }
 
 template <typename T>
@@ -361,16 +538,17 @@ struct lbmd_batch {
     void *rep = nullptr;
     unsigned long long *lb_step = nullptr;
     int *unstable = nullptr;
+    unsigned *items_done = nullptr;
     double *kin = nullptr;
     double *staging = nullptr;
     int64_t staging_len = 0;
     // schedule: per tick of the period, the work table (replica, first node)
-    // of the due replicas and their list
+    // of the due replicas
     int nodes_per_block = 128, particle_block = 256;
+    int sms = 1;
     bool particles_tuned = false;
     int2 *work = nullptr;
-    int32_t *due = nullptr;
-    std::vector<int64_t> work_off, work_len, due_off, due_len;
+    std::vector<int64_t> work_off, work_len;
     int64_t ticks = 0;  // MD steps done by every replica
     cudaGraphExec_t graph = nullptr;
     double tune_ms_lb[3] = {0, 0, 0}, tune_ms_part[3] = {0, 0, 0};
@@ -407,7 +585,7 @@ size_t real_bytes(const lbmd_batch *b) { return b->precision == LBMD_FP64 ? 8 : 
 
 void free_batch(lbmd_batch *b) {
     void *bufs[] = {b->f[0], b->f[1], b->node, b->jacc, b->pos4, b->vel4, b->fc4, b->old4, b->prep, b->rep,
-                    b->lb_step, b->unstable, b->kin, b->staging, b->work, b->due};
+                    b->lb_step, b->unstable, b->items_done, b->kin, b->staging, b->work};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -447,41 +625,29 @@ cudaError_t upload_reps(lbmd_batch *b) {
     return cudaMemcpyAsync(b->rep, h.data(), h.size() * sizeof(BRep<T>), cudaMemcpyHostToDevice, b->stream);
 }
 
-// work tables of every tick of the period for the current nodes_per_block;
+// work tables of every tick of the period for the current nodes per item;
 // tick k: replicas with (k + 1) % m_r == 0.  "all" table (index period) for
 // the initial moments and for tuning.
 cudaError_t build_tables(lbmd_batch *b) {
     std::vector<int2> work;
-    std::vector<int32_t> due;
     b->work_off.assign(b->period + 1, 0);
     b->work_len.assign(b->period + 1, 0);
-    b->due_off.assign(b->period + 1, 0);
-    b->due_len.assign(b->period + 1, 0);
     const int nb = b->nodes_per_block;
     for (int64_t k = 0; k <= b->period; ++k) {
         b->work_off[k] = (int64_t)work.size();
-        b->due_off[k] = (int64_t)due.size();
         for (int r = 0; r < b->R; ++r) {
             const bool is_due = k == b->period || (k + 1) % b->n_sub[r] == 0;
             if (!is_due) continue;
-            due.push_back(r);
             const int64_t N = (int64_t)b->nx[r] * b->ny[r] * b->nz[r];
             for (int64_t s = 0; s < N; s += nb) work.push_back(make_int2(r, (int)s));
         }
         b->work_len[k] = (int64_t)work.size() - b->work_off[k];
-        b->due_len[k] = (int64_t)due.size() - b->due_off[k];
     }
     if (b->work) cudaFree(b->work);
-    if (b->due) cudaFree(b->due);
     b->work = nullptr;
-    b->due = nullptr;
     cudaError_t e = cudaMalloc(&b->work, std::max<size_t>(1, work.size()) * sizeof(int2));
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&b->due, std::max<size_t>(1, due.size()) * sizeof(int32_t));
-    if (e != cudaSuccess) return e;
     if (!work.empty()) e = cudaMemcpy(b->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return e;
-    if (!due.empty()) e = cudaMemcpy(b->due, due.data(), due.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     return e;
 }
 
@@ -509,12 +675,15 @@ BLbArgs<T> make_lbargs(lbmd_batch *b, int64_t table) {
     BLbArgs<T> a;
     a.rep = static_cast<const BRep<T> *>(b->rep);
     a.work = b->work + b->work_off[table];
+    a.n_items = b->work_len[table];
     a.f0 = static_cast<T *>(b->f[0]);
     a.f1 = static_cast<T *>(b->f[1]);
     a.node = static_cast<typename Prec<T>::node4 *>(b->node);
     a.jacc = static_cast<typename Prec<T>::node4 *>(b->jacc);
     a.lb_step = b->lb_step;
     a.unstable = b->unstable;
+    a.items_done = b->items_done;
+    a.advance = 0;
     a.nodes_per_block = b->nodes_per_block;
     a.gamma_bulk = (T)b->co.gamma_bulk;
     a.gamma_shear = (T)b->co.gamma_shear;
@@ -524,29 +693,49 @@ BLbArgs<T> make_lbargs(lbmd_batch *b, int64_t table) {
     return a;
 }
 
-int lb_threads(int nodes_per_block) { return nodes_per_block < 32 ? 32 : nodes_per_block; }
+// threads of an LB block: the nodes of one item plus the prefetch warp
+int lb_threads(int nodes_per_block) { return nodes_per_block + 32; }
+
+// persistent grid: as many blocks as fit on the GPU at once, at most one per
+// item (the kernel's dynamic shared memory allowance is raised to smem first)
+template <typename K>
+unsigned lb_grid(const lbmd_batch *b, K kernel, int64_t n_items, size_t smem) {
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, lb_threads(b->nodes_per_block), smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return (unsigned)std::min<int64_t>(n_items, (int64_t)per_sm * b->sms);
+}
 
 template <typename T>
+cudaError_t launch_moments(lbmd_batch *b, const BLbArgs<T> &a) {
+    if (a.n_items == 0) return cudaSuccess;
+    const size_t smem = lb_smem_bytes<T>(b->nodes_per_block, false);
+    batch_moments_kernel<T><<<lb_grid(b, batch_moments_kernel<T>, a.n_items, smem), lb_threads(b->nodes_per_block),
+                              smem, b->stream>>>(a);
+    return cudaGetLastError();
+}
+
+// collide and moments of the work table; with step, the moments kernel
+// advances the LB step counters of the replicas it covered
+template <typename T>
 cudaError_t launch_lb_tables(lbmd_batch *b, int64_t table, bool step) {
-    const int64_t nblk = b->work_len[table];
-    if (nblk == 0) return cudaSuccess;
     BLbArgs<T> a = make_lbargs<T>(b, table);
+    if (a.n_items == 0) return cudaSuccess;
     const int th = lb_threads(b->nodes_per_block);
+    const size_t smem = lb_smem_bytes<T>(b->nodes_per_block, true);
     if (b->co.gamma_bulk == 0.0 && b->co.gamma_ghost == 0.0)
-        batch_collide_kernel<T, true><<<(unsigned)nblk, th, 0, b->stream>>>(a);
+        batch_collide_kernel<T, true>
+            <<<lb_grid(b, batch_collide_kernel<T, true>, a.n_items, smem), th, smem, b->stream>>>(a);
     else
-        batch_collide_kernel<T, false><<<(unsigned)nblk, th, 0, b->stream>>>(a);
+        batch_collide_kernel<T, false>
+            <<<lb_grid(b, batch_collide_kernel<T, false>, a.n_items, smem), th, smem, b->stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    batch_moments_kernel<T><<<(unsigned)nblk, th, 0, b->stream>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (step && b->due_len[table] > 0) {
-        const int n = (int)b->due_len[table];
-        batch_step_kernel<<<(n + 255) / 256, 256, 0, b->stream>>>(b->due + b->due_off[table], n, b->lb_step,
-                                                                   b->unstable);
-        e = cudaGetLastError();
-    }
-    return e;
+    a.advance = step ? 1 : 0;
+    return launch_moments<T>(b, a);
 }
 
 template <typename T>
@@ -590,13 +779,8 @@ cudaError_t init_state(lbmd_batch *b) {
     if ((e = cudaMemcpyAsync(b->f[1], b->f[0], (size_t)19 * b->n_nodes * real_bytes(b), cudaMemcpyDeviceToDevice,
                              b->stream)) != cudaSuccess)
         return e;
-    const int64_t all = b->period;
-    if (b->work_len[all] > 0) {
-        BLbArgs<T> a = make_lbargs<T>(b, all);
-        batch_moments_kernel<T><<<(unsigned)b->work_len[all], lb_threads(b->nodes_per_block), 0, b->stream>>>(a);
-        e = cudaGetLastError();
-    }
-    return e;
+    if ((e = cudaMemsetAsync(b->items_done, 0, b->R * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
+    return launch_moments<T>(b, make_lbargs<T>(b, b->period));
 }
 
 double time_ms(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
@@ -820,6 +1004,7 @@ lbmd_status lbmd_batch_create(const lbmd_batch_params *p, lbmd_batch **out) {
         {&b->rep, (size_t)R * (b->precision == LBMD_FP64 ? sizeof(BRep<double>) : sizeof(BRep<float>))},
         {(void **)&b->lb_step, (size_t)R * sizeof(unsigned long long)},
         {(void **)&b->unstable, (size_t)R * sizeof(int)},
+        {(void **)&b->items_done, (size_t)R * sizeof(unsigned)},
         {(void **)&b->kin, (size_t)R * 5 * sizeof(double)},
         {(void **)&b->staging, (size_t)b->staging_len * sizeof(double)},
     };
@@ -831,6 +1016,12 @@ lbmd_status lbmd_batch_create(const lbmd_batch_params *p, lbmd_batch **out) {
             delete b;
             return s;
         }
+    }
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (b->sms < 1) b->sms = 1;
     }
     std::vector<int32_t> prep((size_t)sl, 0);
     for (int r = 0; r < R; ++r)
@@ -1034,13 +1225,14 @@ lbmd_status lbmd_batch_set_populations(lbmd_batch *b, int32_t r, const double *i
         if (b->precision == LBMD_FP64) {
             BLbArgs<double> a = make_lbargs<double>(b, 0);
             a.work = dw;
-            batch_moments_kernel<double><<<(unsigned)w.size(), lb_threads(b->nodes_per_block), 0, b->stream>>>(a);
+            a.n_items = (int64_t)w.size();
+            e = launch_moments<double>(b, a);
         } else {
             BLbArgs<float> a = make_lbargs<float>(b, 0);
             a.work = dw;
-            batch_moments_kernel<float><<<(unsigned)w.size(), lb_threads(b->nodes_per_block), 0, b->stream>>>(a);
+            a.n_items = (int64_t)w.size();
+            e = launch_moments<float>(b, a);
         }
-        e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync((char *)b->jacc + (size_t)b->node_off[r] * 4 * rs, 0, (size_t)N * 4 * rs,
                                               b->stream);
