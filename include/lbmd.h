@@ -359,8 +359,9 @@ lbmd_status lbmd_batch_get_particles(lbmd_batch *b, int32_t replica, double *pos
 lbmd_status lbmd_batch_get_counts(lbmd_batch *b, int32_t replica, int64_t *n_particles, int64_t *lb_step,
                                   int64_t *md_step);
 /* The autotuner's choice and its timings of the 3 candidates (64, 128, 256):
- * nodes per block of the LB kernels, threads per block of the particle
- * kernels; lb_ms and particle_ms take 3 doubles each or NULL. */
+ * nodes per work item of the LB kernels (a block has one more warp, which
+ * prefetches the items), threads per block of the particle kernels; lb_ms
+ * and particle_ms take 3 doubles each or NULL. */
 lbmd_status lbmd_batch_tuning(lbmd_batch *b, int32_t *nodes_per_block, int32_t *particle_block, double *lb_ms,
                               double *particle_ms);
 void *lbmd_batch_stream(lbmd_batch *b);
