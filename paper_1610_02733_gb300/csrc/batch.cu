@@ -239,9 +239,10 @@ __device__ __forceinline__ void fetch_item(const BLbArgs<T> &a, ItemWindow &win,
     }
 }
 
-// Asynchronous copies global -> shared memory (cp.async): a thread stages the
-// values of its node of the next item while it computes the current one, and
-// waits only for its own copies.
+// Asynchronous copies global -> shared memory (cp.async, BYTES = 4, 8 or
+// 16, both addresses aligned to BYTES): a thread stages the values of its
+// node of the next item while it computes the current one, and waits only
+// for its own copies.
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
@@ -251,6 +252,7 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most the newest committed group is still in flight
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
