@@ -168,6 +168,15 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ct.c_void_p)
 
 
+def _host_addr(a):
+    """Address of a host array: numpy array or (pinned) torch CPU tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ct.c_void_p(a.data_ptr())
+    return _ptr(a)
+
+
 def _f64(a, n=None) -> np.ndarray:
     a = np.ascontiguousarray(a, dtype=np.float64)
     if n is not None:
@@ -334,14 +343,8 @@ class LBMD:
 
     def set_particles(self, pos=None, vel=None):
         """Host arrays (numpy or pinned torch tensors, float64, 3 N each)."""
-        def addr(a):
-            if a is None:
-                return None
-            if hasattr(a, "data_ptr"):
-                return ct.c_void_p(a.data_ptr())
-            return _ptr(a)
         self._keep = (pos, vel)
-        _check(self._h, load().lbmd_set_particles(self._h, addr(pos), addr(vel)), "lbmd_set_particles")
+        _check(self._h, load().lbmd_set_particles(self._h, _host_addr(pos), _host_addr(vel)), "lbmd_set_particles")
 
     def md_substep(self):
         return lbmd_md_substep(self._h)
@@ -392,7 +395,14 @@ class LBMD:
     def n_particles(self) -> int:
         return self.counts()["n_particles"]
 
-    def particles(self):
+    def particles(self, out=None):
+        """Positions and velocities in id order as (n, 3) arrays; with out =
+        (pos, vel), caller host arrays of 3 N float64 (numpy or pinned torch
+        tensors) are filled and returned instead."""
+        if out is not None:
+            _check(self._h, load().lbmd_get_particles(self._h, _host_addr(out[0]), _host_addr(out[1])),
+                   "lbmd_get_particles")
+            return out
         n = self.n_particles
         pos = np.empty(3 * max(n, 1))
         vel = np.empty(3 * max(n, 1))
