@@ -364,6 +364,12 @@ lbmd_status lbmd_batch_get_counts(lbmd_batch *b, int32_t replica, int64_t *n_par
  * and particle_ms take 3 doubles each or NULL. */
 lbmd_status lbmd_batch_tuning(lbmd_batch *b, int32_t *nodes_per_block, int32_t *particle_block, double *lb_ms,
                               double *particle_ms);
+/* Cap on the number of blocks of the persistent LB kernels (each block works
+ * through the work items b, b + G, b + 2G, ... of a tick, G = the grid size);
+ * 0 = as many blocks as fit on the GPU at once (the default).  Results do not
+ * depend on it; a small cap leaves SMs to other work on the device.
+ * LBMD_ERR_ARG for a negative cap. */
+lbmd_status lbmd_batch_set_lb_grid(lbmd_batch *b, int32_t max_blocks);
 void *lbmd_batch_stream(lbmd_batch *b);
 const char *lbmd_batch_last_error(lbmd_batch *b);
 

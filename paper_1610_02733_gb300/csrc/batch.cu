@@ -548,6 +548,7 @@ struct lbmd_batch {
     // of the due replicas
     int nodes_per_block = 128, particle_block = 256;
     int sms = 1;
+    int lb_grid_cap = 0;  // 0: persistent LB grid as large as fits
     bool particles_tuned = false;
     int2 *work = nullptr;
     std::vector<int64_t> work_off, work_len;
@@ -708,7 +709,9 @@ unsigned lb_grid(const lbmd_batch *b, K kernel, int64_t n_items, size_t smem) {
             cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    return (unsigned)std::min<int64_t>(n_items, (int64_t)per_sm * b->sms);
+    int64_t g = std::min<int64_t>(n_items, (int64_t)per_sm * b->sms);
+    if (b->lb_grid_cap > 0) g = std::min<int64_t>(g, b->lb_grid_cap);
+    return (unsigned)g;
 }
 
 template <typename T>
@@ -1275,6 +1278,18 @@ lbmd_status lbmd_batch_tuning(lbmd_batch *b, int32_t *nodes_per_block, int32_t *
     for (int c = 0; c < 3; ++c) {
         if (lb_ms) lb_ms[c] = b->tune_ms_lb[c];
         if (particle_ms) particle_ms[c] = b->tune_ms_part[c];
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_batch_set_lb_grid(lbmd_batch *b, int32_t max_blocks) {
+    if (!b) return LBMD_ERR_ARG;
+    if (max_blocks < 0) return bfail(b, LBMD_ERR_ARG, "max_blocks must be >= 0");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->lb_grid_cap = max_blocks;
+    if (b->graph) {  // the captured period has the old grid size baked in
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
     }
     return LBMD_OK;
 }

@@ -42,7 +42,8 @@ EXPORTS = (
     "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add_particles", "lbmd_batch_run", "lbmd_batch_kinetic",
     "lbmd_batch_kinetic_device",
     "lbmd_batch_unstable", "lbmd_batch_get_populations", "lbmd_batch_set_populations", "lbmd_batch_get_particles",
-    "lbmd_batch_get_counts", "lbmd_batch_tuning", "lbmd_batch_stream", "lbmd_batch_last_error",
+    "lbmd_batch_get_counts", "lbmd_batch_tuning", "lbmd_batch_set_lb_grid", "lbmd_batch_stream",
+    "lbmd_batch_last_error",
     "lbmd_adjoint_create", "lbmd_adjoint_destroy", "lbmd_adjoint_forward", "lbmd_adjoint_backward",
     "lbmd_adjoint_last_error",
 )
@@ -146,6 +147,7 @@ def load():
     L.lbmd_batch_get_particles.argtypes = [P, i32, P, P]
     L.lbmd_batch_get_counts.argtypes = [P, i32, i64p, i64p, i64p]
     L.lbmd_batch_tuning.argtypes = [P, ct.POINTER(i32), ct.POINTER(i32), P, P]
+    L.lbmd_batch_set_lb_grid.argtypes = [P, i32]
     L.lbmd_batch_stream.restype = ct.c_void_p
     L.lbmd_batch_stream.argtypes = [P]
     L.lbmd_batch_last_error.restype = ct.c_char_p
@@ -545,6 +547,10 @@ class Batch:
                 "lbmd_batch_tuning")
         return {"nodes_per_block": nb.value, "particle_block": pb.value, "candidates": [64, 128, 256],
                 "lb_ms": lb.tolist(), "particle_ms": pt.tolist()}
+
+    def set_lb_grid(self, max_blocks: int):
+        """Cap on the blocks of the persistent LB kernels (0: as many as fit)."""
+        _bcheck(self._h, load().lbmd_batch_set_lb_grid(self._h, int(max_blocks)), "lbmd_batch_set_lb_grid")
 
     @property
     def stream(self) -> int:

@@ -123,3 +123,52 @@ def test_tuning_choice():
     t = b.tuning()
     assert t["nodes_per_block"] in (64, 128, 256) and t["particle_block"] in (64, 128, 256)
     assert all(x > 0 for x in t["lb_ms"]) and all(x > 0 for x in t["particle_ms"])
+
+
+@pytest.mark.parametrize("cap", [1, 3])
+def test_persistent_grid_cap_is_bitwise_neutral(cap):
+    # one or three blocks work through every LB item of a tick (many items
+    # per block: several windows of work entries, the header ring and the
+    # staging buffers rotate) and give bit for bit what the full grid gives
+    b_full, _ = _build("fp32")
+    b_cap, _ = _build("fp32")
+    b_cap.set_lb_grid(cap)
+    b_full.run(23)
+    b_cap.run(23)
+    for i in range(len(REPLICAS)):
+        assert b_cap.counts(i) == b_full.counts(i)
+        assert np.array_equal(b_cap.populations(i), b_full.populations(i))
+        p1, v1 = b_cap.particles(i)
+        p2, v2 = b_full.particles(i)
+        assert np.array_equal(p1, p2) and np.array_equal(v1, v2)
+
+
+def test_frozen_replica_items_are_skipped_by_a_capped_grid():
+    # a large replica that turns unstable ahead of a small stable one in the
+    # work table: one block skips the frozen replica's items window by window
+    # and the stable replica still follows its oracle
+    dims = [(24, 24, 24), (8, 6, 10)]
+    b = lbmd.Batch(dims, n_sub=[1, 1], variant=["B", "A"], zeta=[5.0, 0.5], seed=[5, 6], max_particles=[4, 4],
+                   precision="fp64", kT=KT)
+    b.set_lb_grid(1)
+    o = orc.Oracle(8, 6, 10, n_sub=1, variant=0, kT=KT, zeta=0.5, seed=6)
+    for i in range(2):
+        pos, vel = inputs.uniform_positions(4, dims[i], 30 + i), inputs.maxwell_velocities(4, 1e-3, 30 + i)
+        b.add_particles(i, pos, vel)
+        if i == 1:
+            o.add_particles(pos, vel)
+    b.run(40)
+    assert list(b.unstable()) == [1, 0]
+    _oracle_steps(o, 1, 0, 40)
+    err = np.abs(b.populations(1) - o.populations()) / W[:, None]
+    assert float(err.max()) <= TOL["fp64"]
+    pg, vg = b.particles(1)
+    po, vo = o.particles()
+    assert_vec_close(pg, po, "fp64", "stable replica positions")
+    assert_vec_close(vg, vo, "fp64", "stable replica velocities")
+
+
+def test_negative_grid_cap_is_rejected():
+    b, _ = _build("fp32")
+    with pytest.raises(lbmd.LbmdError):
+        b.set_lb_grid(-1)
