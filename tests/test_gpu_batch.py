@@ -125,13 +125,13 @@ def test_tuning_choice():
     assert all(x > 0 for x in t["lb_ms"]) and all(x > 0 for x in t["particle_ms"])
 
 
-@pytest.mark.parametrize("cap", [1, 3])
-def test_persistent_grid_cap_is_bitwise_neutral(cap):
-    # one or three blocks work through every LB item of a tick (many items
+@pytest.mark.parametrize("precision,cap", [("fp32", 1), ("fp32", 3), ("fp64", 2)])
+def test_persistent_grid_cap_is_bitwise_neutral(precision, cap):
+    # one to three blocks work through every LB item of a tick (many items
     # per block: several windows of work entries, the header ring and the
     # staging buffers rotate) and give bit for bit what the full grid gives
-    b_full, _ = _build("fp32")
-    b_cap, _ = _build("fp32")
+    b_full, _ = _build(precision)
+    b_cap, _ = _build(precision)
     b_cap.set_lb_grid(cap)
     b_full.run(23)
     b_cap.run(23)
