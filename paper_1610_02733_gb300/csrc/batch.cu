@@ -104,12 +104,14 @@ __global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
     using P = Prec<T>;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n_slots) return;
+    // the slot's record is loaded with its replica index (every slot is
+    // allocated; an unused one is simply not used)
+    const typename P::real4 R = a.pos4[p];
+    typename P::real4 V = a.vel4[p];
     const int r = a.prep[p];
     const BRep<T> &rp = a.rep[r];
     const int64_t local = p - rp.part_off;
     if (local >= rp.np || a.unstable[r]) return;
-    const typename P::real4 R = a.pos4[p];
-    typename P::real4 V = a.vel4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), rp.fd_nx, rp.fd_ny);
     uint32_t idx[8];
     T delta[8];
@@ -167,11 +169,11 @@ __global__ void __launch_bounds__(256) batch_transfer_kernel(BArgs<T> a) {
     using P = Prec<T>;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n_slots) return;
+    const typename P::real4 R = a.old4[p];
+    const typename P::real4 F = a.fc4[p];
     const int r = a.prep[p];
     const BRep<T> &rp = a.rep[r];
     if (rp.variant != LBMD_VARIANT_B || p - rp.part_off >= rp.np || a.unstable[r]) return;
-    const typename P::real4 R = a.old4[p];
-    const typename P::real4 F = a.fc4[p];
     const CellXYZ c = cell_xyz(P::cell_of(R), rp.fd_nx, rp.fd_ny);
     uint32_t idx[8];
     T delta[8];
