@@ -56,7 +56,8 @@ typedef enum lbmd_status {
     LBMD_ERR_OOM = -3,       /* device or host allocation failed */
     LBMD_ERR_SEQUENCE = -4,  /* call out of the m-substeps-then-LB-step order */
     LBMD_ERR_NONFINITE = -5, /* an observable came out NaN or infinite */
-    LBMD_ERR_CAPACITY = -6   /* more particles or bonds than reserved */
+    LBMD_ERR_CAPACITY = -6,  /* more particles or bonds than reserved */
+    LBMD_ERR_RANGE = -7      /* node momentum left the fixed-point range */
 } lbmd_status;
 
 /* Variants of the coupling: A and B (Sec. 3); C (Sec. 4): after every MD step
@@ -131,7 +132,17 @@ typedef struct lbmd_observables_t {
 /* Create a context: allocates populations (two buffers), the node field, the
  * momentum-transfer accumulator and particle storage on the current device,
  * and sets the fluid at rest, f_i = w_i rho0 (Sec. 2).
- * Errors: LBMD_ERR_ARG for invalid parameters, LBMD_ERR_OOM, LBMD_ERR_CUDA. */
+ * Momentum range: the node field holds the momentum density j (Eq. (2)) and
+ * the particles' transfers (Eqs. (7), (8)) as integers in units of
+ * 2^(e - 30) (FP32, FP16_DEV, BF16_DEV) or 2^(e - 56) (FP64) with
+ * e = ceil(log2 rho0), so that transfers add up in any order to the same
+ * bits.  Each component must stay below 2^(e + 1) (FP32) / 2^(e + 7) (FP64)
+ * in magnitude: a node velocity of 2 / 128 lattice units at rho = rho0, far
+ * beyond the lattice speed of sound (c_s^2 = 1/3) up to which an LB fluid is
+ * valid at all.  A node whose momentum reaches half of that raises a sticky
+ * range flag, which lbmd_observables reports as LBMD_ERR_RANGE.
+ * Errors: LBMD_ERR_ARG for invalid parameters (rho0 outside [2^-60, 2^60]
+ * among them), LBMD_ERR_OOM, LBMD_ERR_CUDA. */
 lbmd_status lbmd_create(const lbmd_params *params, lbmd_ctx **out);
 
 /* Free every resource of the context (synchronising).  NULL is accepted. */
@@ -227,8 +238,28 @@ lbmd_status lbmd_lb_step(lbmd_ctx *ctx);
 lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n);
 
 /* FP64 device reductions of the observables; synchronising; copies the
- * result to *out.  LBMD_ERR_NONFINITE if any of them is NaN or infinite. */
+ * result to *out.  LBMD_ERR_NONFINITE if any of them is NaN or infinite;
+ * LBMD_ERR_RANGE (out still filled) once any node's momentum density has
+ * reached half the fixed-point range since creation or the last
+ * lbmd_set_populations / lbmd_load_state (see lbmd_create): the state is no
+ * longer valid. */
 lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out);
+
+/* The post-stream moments (Eqs. (1), (2)) of a node row are computed inside
+ * the LB step's collide kernel once the 27 blocks around the row have pushed
+ * their populations; a block waits for them at most `polls` polls of 64 ns and
+ * otherwise leaves the row to a follow-up kernel, which gives the same bits.
+ * polls = -1 restores the default (2^20 polls, ~67 ms); 0 sends every row to
+ * the follow-up kernel; small values make some rows time out.  Results do not
+ * depend on it: it exists to exercise and measure the fallback.  Takes effect
+ * from the next LB step (drops the captured cycle graphs).
+ * Errors: LBMD_ERR_ARG for polls < -1. */
+lbmd_status lbmd_set_moments_wait(lbmd_ctx *ctx, int32_t polls);
+
+/* Rows (collide blocks of up to 256 nodes) whose fused moments timed out and
+ * were computed by the follow-up kernel, summed over every LB step since
+ * creation (synchronising). */
+lbmd_status lbmd_moments_fallback_rows(lbmd_ctx *ctx, int64_t *rows);
 
 /* Synchronising accessors (host arrays, id order, FP64). */
 /* populations f*_i after the last streaming step: 19 N doubles, [i][r] */
@@ -292,7 +323,10 @@ lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes);
  * call before any stream capture.  All calls on one device share that
  * device's array, and it keeps the last call's partial sums: calls that can
  * overlap on the GPU (e.g. issued on different streams) race, so the caller
- * must order them.  Errors: LBMD_ERR_ARG,
+ * must order them.  The looked-up address is kept for the life of the
+ * process: after cudaDeviceReset (or any other teardown of the device's
+ * primary context) the entry point must not be called on that device again.
+ * Errors: LBMD_ERR_ARG,
  * LBMD_ERR_CAPACITY, LBMD_ERR_CUDA (message in lbmd_last_error(NULL)). */
 lbmd_status lbmd_particle_sums_static(const double *vel, const double *mass, int64_t n, double *out, void *stream);
 

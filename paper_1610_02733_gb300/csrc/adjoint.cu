@@ -52,6 +52,7 @@ struct AdArgs {
     int64_t N;
     FastDiv fd_nx, fd_ny;
     T zeta, dt, half_dt, amp, neg_scale_dt, norm;
+    T fs, fis;  // fixed-point scale of the momentum density and its inverse
     uint32_t key0, key1;
     T g[3];
     // read by collide()
@@ -77,7 +78,7 @@ __global__ void ad_init_kernel(T *f, int64_t N, T rho0) {
 }
 
 template <typename T>
-__global__ void ad_moments_kernel(const T *f, typename Prec<T>::node4 *node, int64_t N) {
+__global__ void ad_moments_kernel(const T *f, typename Prec<T>::node4 *node, int64_t N, T fs) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
     T fl[Q];
@@ -86,7 +87,7 @@ __global__ void ad_moments_kernel(const T *f, typename Prec<T>::node4 *node, int
     T rho, jx, jy, jz;
     node_moments(fl, rho, jx, jy, jz);
     using P = Prec<T>;
-    node[r] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    node[r] = P::pack(rho, P::to_fix(jx, fs), P::to_fix(jy, fs), P::to_fix(jz, fs));
 }
 
 template <typename T>
@@ -112,9 +113,9 @@ template <typename T>
 __device__ __forceinline__ void node_force(const AdArgs<T> &a, const typename Prec<T>::node4 &n, T jx, T jy, T jz,
                                            T &Fx, T &Fy, T &Fz) {
     using P = Prec<T>;
-    Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx)) + a.g[0];
-    Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy)) + a.g[1];
-    Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz)) + a.g[2];
+    Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx, a.fs), a.fis) + a.g[0];
+    Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy, a.fs), a.fis) + a.g[1];
+    Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz, a.fs), a.fis) + a.g[2];
 }
 
 // LB step of the forward pass: collide at every node and push into fout.
@@ -156,8 +157,8 @@ __global__ void __launch_bounds__(256) ad_couple(AdArgs<T> a, typename Prec<T>::
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const typename P::node4 n = node[idx[k]];
-        const T rho = P::rho_of(n), jx = P::from_fix(P::jx_of(n)), jy = P::from_fix(P::jy_of(n)),
-                jz = P::from_fix(P::jz_of(n));
+        const T rho = P::rho_of(n), jx = P::from_fix(P::jx_of(n), a.fis), jy = P::from_fix(P::jy_of(n), a.fis),
+                jz = P::from_fix(P::jz_of(n), a.fis);
         if (rec.C) rec.C[8 * p + k] = P::make4(rho, jx, jy, jz);
         const T w = delta[k] / rho;
         ux += w * jx;
@@ -444,6 +445,7 @@ struct lbmd_adjoint {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     LbCoeffs co{};
+    FixUnit fix{};  // fixed-point unit of the momentum density (from rho0)
     double zeta = 0.0;
     bool have_forward = false;
     // device
@@ -512,7 +514,9 @@ AdArgs<T> make_args(const lbmd_adjoint *ad) {
     a.dt = (T)dt;
     a.half_dt = (T)(0.5 * dt);
     a.amp = (T)std::sqrt(2.0 * ad->zeta * p.kT / dt);
-    a.neg_scale_dt = (T)dt * -Prec<T>::SCALE;
+    a.neg_scale_dt = (T)dt * -(T)ad->fix.scale;
+    a.fs = (T)ad->fix.scale;
+    a.fis = (T)ad->fix.inv_scale;
     a.norm = (T)(1.0 / ((double)p.n_cycles * p.n_sub * std::max(1, p.n_particles)));
     a.key0 = (uint32_t)(p.seed & 0xffffffffu);
     a.key1 = (uint32_t)(p.seed >> 32);
@@ -563,7 +567,7 @@ cudaError_t run_md(lbmd_adjoint *ad, int c, bool record) {
     const AdArgs<T> a = make_args<T>(ad);
     const int np = ad->p.n_particles, m = ad->p.n_sub;
     ad_moments_kernel<T><<<nb(ad->N, 256), 256, 0, ad->stream>>>(fchk_at<T>(ad, c), static_cast<N4 *>(ad->node),
-                                                                  ad->N);
+                                                                  ad->N, (T)ad->fix.scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (np == 0) return cudaSuccess;
@@ -739,18 +743,11 @@ lbmd_status lbmd_adjoint_create(const lbmd_adjoint_params *p, lbmd_adjoint **out
     a->p = *p;
     a->N = (int64_t)p->nx * p->ny * p->nz;
     a->rs = p->precision == LBMD_FP64 ? 8 : 4;
-    LbCoeffs &co = a->co;
-    co.gamma_shear = (6.0 * p->nu - 1.0) / (6.0 * p->nu + 1.0);
-    co.gamma_bulk = p->nu_bulk < 0 ? 0.0 : (9.0 * p->nu_bulk - 1.0) / (9.0 * p->nu_bulk + 1.0);
-    co.gamma_ghost = p->gamma_ghost;
-    static const double bnorm[19] = {1.0,       1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0,
-                                     1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 9.0,
-                                     2.0 / 9.0, 2.0 / 9.0, 2.0,       4.0 / 3.0, 4.0 / 9.0};
-    for (int k = 0; k < 19; ++k) {
-        const double g = k < 4 ? 1.0 : (k == 4 ? co.gamma_bulk : (k <= 9 ? co.gamma_shear : co.gamma_ghost));
-        co.noise_amp[k] = k < 4 ? 0.0 : std::sqrt(3.0 * p->kT * bnorm[k] * (1.0 - g * g));
+    lb_coefficients(p->nu, p->nu_bulk, p->gamma_ghost, p->kT, a->co);
+    if (!fix_unit(p->rho0, p->precision == LBMD_FP64 ? Prec<double>::SCALE_LOG2 : Prec<float>::SCALE_LOG2, a->fix)) {
+        delete a;
+        return afail(nullptr, LBMD_ERR_ARG, "rho0 must lie in [2^-60, 2^60]");
     }
-    co.noisy = p->kT > 0 ? 1 : 0;
     if (p->stream) {
         a->stream = (cudaStream_t)p->stream;
     } else {

@@ -75,6 +75,7 @@ struct BArgs {
     const unsigned long long *lb_step;
     int *unstable;
     int tick;  // MD step within the period
+    T fis;     // 1 / fixed-point scale of the momentum density (shared rho0)
 };
 
 template <typename T>
@@ -89,6 +90,7 @@ struct BLbArgs {
     unsigned *items_done;  // per replica: items of the moments kernel taken so far
     int advance;           // the moments kernel advances the LB step counters
     int nodes_per_block;
+    T fs, fis;             // fixed-point scale of the momentum density and its inverse
     // members read by collide()
     T gamma_bulk, gamma_shear, gamma_ghost;
     T amp16[Q];
@@ -122,9 +124,9 @@ __global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
     for (int k = 0; k < 8; ++k) {
         const typename P::node4 n = node[idx[k]];
         const T w = delta[k] / P::rho_of(n);
-        ux += w * P::from_fix(P::jx_of(n));
-        uy += w * P::from_fix(P::jy_of(n));
-        uz += w * P::from_fix(P::jz_of(n));
+        ux += w * P::from_fix(P::jx_of(n), a.fis);
+        uy += w * P::from_fix(P::jy_of(n), a.fis);
+        uz += w * P::from_fix(P::jz_of(n), a.fis);
     }
     T Fx = -rp.zeta * (V.x - ux), Fy = -rp.zeta * (V.y - uy), Fz = -rp.zeta * (V.z - uz);
     if (rp.amp != T(0)) {
@@ -364,13 +366,13 @@ __global__ void __launch_bounds__(BATCH_LB_MAX_THREADS, sizeof(T) == 4 ? 4 : 2) 
         const N4 n = staged_node<T>(s_node + ((size_t)buf * nb + t) * sizeof(N4));
         T Fx, Fy, Fz;
         if (rp.variant == LBMD_VARIANT_B) {
-            Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx));
-            Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy));
-            Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz));
+            Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx, a.fs), a.fis);
+            Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy, a.fs), a.fis);
+            Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz, a.fs), a.fis);
         } else {
-            Fx = P::from_fix(P::jx_of(n));
-            Fy = P::from_fix(P::jy_of(n));
-            Fz = P::from_fix(P::jz_of(n));
+            Fx = P::from_fix(P::jx_of(n), a.fis);
+            Fy = P::from_fix(P::jy_of(n), a.fis);
+            Fz = P::from_fix(P::jz_of(n), a.fis);
             N4 zero;
             zero.x = zero.y = zero.z = zero.w = 0;
             a.jacc[rp.node_off + loc] = zero;
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(BATCH_LB_MAX_THREADS) batch_moments_kernel(BLb
         for (int i = 0; i < Q; ++i) fl[i] = src[i * nb];
         T rho, jx, jy, jz;
         node_moments(fl, rho, jx, jy, jz);
-        a.node[rp.node_off + loc] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+        a.node[rp.node_off + loc] = P::pack(rho, P::to_fix(jx, a.fs), P::to_fix(jy, a.fs), P::to_fix(jz, a.fs));
     };
     auto advance = [&](const BItem<T> &it) {
         if (!a.advance) return;
@@ -529,6 +531,7 @@ struct lbmd_batch {
     std::vector<uint64_t> seed;
     std::vector<int64_t> node_off, part_off;
     double rho0 = 1, nu = 1.0 / 6.0, nu_bulk = -1, gamma_ghost = 0, kT = 0;
+    FixUnit fix{};  // fixed-point unit of the momentum density (from rho0)
     int64_t n_nodes = 0, n_slots = 0;
     int64_t period = 1;
     cudaStream_t stream = nullptr;
@@ -619,7 +622,7 @@ void fill_reps(const lbmd_batch *b, std::vector<BRep<T>> &out) {
         q.dt = (T)dt;
         q.half_dt = (T)(0.5 * dt);
         q.amp = (T)std::sqrt(2.0 * b->zeta[r] * b->kT / dt);
-        q.neg_scale_dt = (T)dt * -Prec<T>::SCALE;
+        q.neg_scale_dt = (T)dt * -(T)b->fix.scale;
     }
 }
 
@@ -672,6 +675,7 @@ BArgs<T> make_bargs(lbmd_batch *b, int tick) {
     a.lb_step = b->lb_step;
     a.unstable = b->unstable;
     a.tick = tick;
+    a.fis = (T)b->fix.inv_scale;
     return a;
 }
 
@@ -690,6 +694,8 @@ BLbArgs<T> make_lbargs(lbmd_batch *b, int64_t table) {
     a.items_done = b->items_done;
     a.advance = 0;
     a.nodes_per_block = b->nodes_per_block;
+    a.fs = (T)b->fix.scale;
+    a.fis = (T)b->fix.inv_scale;
     a.gamma_bulk = (T)b->co.gamma_bulk;
     a.gamma_shear = (T)b->co.gamma_shear;
     a.gamma_ghost = (T)b->co.gamma_ghost;
@@ -924,6 +930,10 @@ lbmd_status lbmd_batch_create(const lbmd_batch_params *p, lbmd_batch **out) {
     if (!b) return bfail(nullptr, LBMD_ERR_OOM, "host allocation");
     b->R = R;
     b->precision = p->precision;
+    if (!fix_unit(p->rho0, p->precision == LBMD_FP64 ? Prec<double>::SCALE_LOG2 : Prec<float>::SCALE_LOG2, b->fix)) {
+        delete b;
+        return bfail(nullptr, LBMD_ERR_ARG, "rho0 must lie in [2^-60, 2^60]");
+    }
     b->rho0 = p->rho0;
     b->nu = p->nu;
     b->nu_bulk = p->nu_bulk;
@@ -968,19 +978,7 @@ lbmd_status lbmd_batch_create(const lbmd_batch_params *p, lbmd_batch **out) {
     b->n_slots = slots;
     b->period = period;
     // relaxation factors and noise amplitudes, as for a single box
-    LbCoeffs &co = b->co;
-    co.gamma_shear = (6.0 * p->nu - 1.0) / (6.0 * p->nu + 1.0);
-    co.gamma_bulk = p->nu_bulk < 0 ? 0.0 : (9.0 * p->nu_bulk - 1.0) / (9.0 * p->nu_bulk + 1.0);
-    co.gamma_ghost = p->gamma_ghost;
-    static const double bnorm[19] = {1.0,       1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0,
-                                     1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 9.0,
-                                     2.0 / 9.0, 2.0 / 9.0, 2.0,       4.0 / 3.0, 4.0 / 9.0};
-    const double mu = 3.0 * p->kT;
-    for (int k = 0; k < 19; ++k) {
-        const double g = k < 4 ? 1.0 : (k == 4 ? co.gamma_bulk : (k <= 9 ? co.gamma_shear : co.gamma_ghost));
-        co.noise_amp[k] = k < 4 ? 0.0 : std::sqrt(mu * bnorm[k] * (1.0 - g * g));
-    }
-    co.noisy = p->kT > 0 ? 1 : 0;
+    lb_coefficients(p->nu, p->nu_bulk, p->gamma_ghost, p->kT, b->co);
     if (p->stream) {
         b->stream = (cudaStream_t)p->stream;
     } else {

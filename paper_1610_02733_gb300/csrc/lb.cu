@@ -39,8 +39,11 @@ struct LbArgs {
     // fused post-stream moments (dataflow between collide blocks)
     uint32_t *blk_done;
     int32_t *missed, *missed_list;
+    int spin;  // polls of the wait for the neighbour blocks (0: every row to the fallback)
     int nx, ny, nz;
     int64_t N;
+    T fs, fis;            // fixed-point scale of the momentum density and its inverse
+    int32_t *range_flag;  // set when a written record reaches half the fixed-point range
     T gamma_bulk, gamma_shear, gamma_ghost;
     T amp16[Q];  // noise amplitude sqrt(mu b_k (1 - g_k^2)) times sqrt(12) 2^-16
     T g[3];
@@ -50,6 +53,17 @@ struct LbArgs {
     int variant;
 };
 
+// Range guard: a record whose momentum reaches half the fixed-point range
+// raises the context's flag (the integer sums of later transfers could wrap).
+template <typename T>
+__device__ __forceinline__ typename Prec<T>::node4 guarded_record(T rho, T jx, T jy, T jz, T fs,
+                                                                  int32_t *range_flag) {
+    using P = Prec<T>;
+    const typename P::fix ix = P::to_fix(jx, fs), iy = P::to_fix(jy, fs), iz = P::to_fix(jz, fs);
+    if (P::beyond_half(ix) | P::beyond_half(iy) | P::beyond_half(iz)) atomicOr(range_flag, 1);
+    return P::pack(rho, ix, iy, iz);
+}
+
 // Post-stream moments rho*, j* (Eqs. (1), (2)) of node (x, y, t): the node
 // record and, for an active node of the coming cycle (variant B), its
 // compact record.  The populations are read through L2 (ld.global.cg): they
@@ -57,7 +71,7 @@ struct LbArgs {
 template <typename T, typename S>
 __device__ __forceinline__ void node_moments_at(const S *f, typename Prec<T>::node4 *node, const uint2 *occw,
                                                 typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx,
-                                                int ny, T rho0, int x, int y, int t) {
+                                                int ny, T rho0, T fs, int32_t *range_flag, int x, int y, int t) {
     using P = Prec<T>;
     using St = PopStore<S, T>;
     const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)t);
@@ -66,7 +80,7 @@ __device__ __forceinline__ void node_moments_at(const S *f, typename Prec<T>::no
     for (int i = 0; i < Q; ++i) fl[i] = St::load_cg(f + (size_t)i * N + r, T(WEIGHT(i)) * rho0);
     T rho, jx, jy, jz;
     node_moments(fl, rho, jx, jy, jz);
-    const typename P::node4 rec = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    const typename P::node4 rec = guarded_record(rho, jx, jy, jz, fs, range_flag);
     node[r] = rec;
     if (occw) {
         const int sl = active_slot(occw[((size_t)y + (size_t)ny * t) * occ_words + (x >> 5)], x);
@@ -80,7 +94,10 @@ __device__ __forceinline__ void node_moments_at(const S *f, typename Prec<T>::no
 // FUSE_LAG planes (whose neighbourhood wraps to later planes), and any row
 // whose wait ran out, are left to moments_rest_kernel.
 constexpr int FUSE_LAG = 2;
-constexpr int FUSE_SPIN = 1 << 20;  // polls of 64 ns at most, then the row is left to the fallback
+// The wait polls at most ctx->fuse_spin times (64 ns apart; default
+// LBMD_DEFAULT_FUSE_SPIN, far above the few us the lag needs); a context can
+// lower it (lbmd_set_moments_wait), down to 0, where every row goes to the
+// fallback kernel.
 
 // One thread per node; grid (ceil(nx / blockDim.x), ny, nz).  The variant is
 // a run-time (warp-uniform) flag rather than a template parameter: both
@@ -106,14 +123,14 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
         // record is its compact one)
         const int sl = active_slot(a.occw[((size_t)y + (size_t)a.ny * z) * a.occ_words + (x >> 5)], x);
         const typename P::node4 n = sl >= 0 ? a.cact[sl] : a.node[r];
-        Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx));
-        Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy));
-        Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz));
+        Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx, a.fs), a.fis);
+        Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy, a.fs), a.fis);
+        Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz, a.fs), a.fis);
     } else {
         const typename P::node4 J = a.jacc[r];
-        Fx = P::from_fix(P::jx_of(J));
-        Fy = P::from_fix(P::jy_of(J));
-        Fz = P::from_fix(P::jz_of(J));
+        Fx = P::from_fix(P::jx_of(J), a.fis);
+        Fy = P::from_fix(P::jy_of(J), a.fis);
+        Fz = P::from_fix(P::jz_of(J), a.fis);
         typename P::node4 zero;
         zero.x = zero.y = zero.z = zero.w = 0;
         a.jacc[r] = zero;
@@ -157,15 +174,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
     if (t < 1) return;
     __shared__ int s_ok;
     if (threadIdx.x < 32) {
-        bool ok = true;
-        if (threadIdx.x < 27) {
+        bool ok = a.spin > 0;
+        if (ok && threadIdx.x < 27) {
             const int dx = (int)threadIdx.x % 3 - 1, dy = ((int)threadIdx.x / 3) % 3 - 1;
             const int dz = (int)threadIdx.x / 9 - 1;
             const uint32_t xb = (blockIdx.x + gx + dx) % gx, yb = (uint32_t)((y + a.ny + dy) % a.ny);
             const volatile uint32_t *flag = a.blk_done + xb + gx * (yb + gy * (uint32_t)(t + dz));
             int polls = 0;
             while (*flag != epoch) {
-                if (++polls > FUSE_SPIN) {
+                if (++polls > a.spin) {
                     ok = false;
                     break;
                 }
@@ -184,17 +201,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
         return;
     }
     if (x < a.nx)
-        node_moments_at<T, S>(a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, a.N, a.nx, a.ny, a.rho0, x, y, t);
+        node_moments_at<T, S>(a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, a.N, a.nx, a.ny, a.rho0, a.fs,
+                              a.range_flag, x, y, t);
 }
 
 // The moments the collide kernel left: node rows of plane 0 and of the last
-// FUSE_LAG planes, and the rows whose wait ran out; then the LB step counter
-// advances.
+// FUSE_LAG planes, and the rows whose wait ran out (counted into
+// missed_total); then the LB step counter advances.
 template <typename T, typename S>
 __global__ void __launch_bounds__(256)
     moments_rest_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
                         typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, int nz, T rho0,
-                        const int32_t *missed, const int32_t *missed_list, unsigned long long *lb_step) {
+                        T fs, int32_t *range_flag, const int32_t *missed, const int32_t *missed_list,
+                        unsigned long long *missed_total, unsigned long long *lb_step) {
     const int gx = (nx + (int)blockDim.x - 1) / (int)blockDim.x;
     const int rows = gx * ny;
     // boundary planes: 0 and max(1, nz - FUSE_LAG) .. nz - 1
@@ -213,18 +232,22 @@ __global__ void __launch_bounds__(256)
         }
         const int xb = b % gx, rest = b / gx, y = rest % ny, t = rest / ny;
         const int x = xb * (int)blockDim.x + (int)threadIdx.x;
-        if (x < nx) node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, x, y, t);
+        if (x < nx) node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, fs, range_flag, x, y, t);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *lb_step += 1ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *missed_total += (unsigned long long)*missed;
+        *lb_step += 1ull;
+    }
 }
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(256)
     node_moments_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
-                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, T rho0) {
+                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, T rho0, T fs,
+                        int32_t *range_flag) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
-    node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, x, blockIdx.y, blockIdx.z);
+    node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, fs, range_flag, x, blockIdx.y, blockIdx.z);
 }
 
 // Variant C (Sec. 4): the momentum transfer F = J_acc of the MD step just
@@ -236,14 +259,16 @@ __global__ void __launch_bounds__(256)
 template <typename T, typename S>
 __global__ void __launch_bounds__(256) forcing_update_kernel(S *__restrict__ f, typename Prec<T>::node4 *node,
                                                              typename Prec<T>::node4 *jacc, int64_t N, T rho0,
-                                                             T gamma_bulk, T gamma_shear) {
+                                                             T gamma_bulk, T gamma_shear, T fix_s, T fix_is,
+                                                             int32_t *range_flag) {
     using P = Prec<T>;
     using St = PopStore<S, T>;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
     const typename P::node4 J = jacc[r];
     if (P::jx_of(J) == 0 && P::jy_of(J) == 0 && P::jz_of(J) == 0) return;
-    const T Fx = P::from_fix(P::jx_of(J)), Fy = P::from_fix(P::jy_of(J)), Fz = P::from_fix(P::jz_of(J));
+    const T Fx = P::from_fix(P::jx_of(J), fix_is), Fy = P::from_fix(P::jy_of(J), fix_is),
+            Fz = P::from_fix(P::jz_of(J), fix_is);
     T fl[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) fl[i] = St::load(f + (int64_t)i * N + r, T(WEIGHT(i)) * rho0);
@@ -277,7 +302,7 @@ __global__ void __launch_bounds__(256) forcing_update_kernel(S *__restrict__ f, 
         St::store(f + (int64_t)i * N + r, fl[i], T(WEIGHT(i)) * rho0);
     }
     node_moments(fl, rho, jx, jy, jz);
-    node[r] = P::pack(rho, P::to_fix(jx), P::to_fix(jy), P::to_fix(jz));
+    node[r] = guarded_record(rho, jx, jy, jz, fix_s, range_flag);
     typename P::node4 zero;
     zero.x = zero.y = zero.z = zero.w = 0;
     jacc[r] = zero;
@@ -317,6 +342,10 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.blk_done = ctx->blk_done;
     a.missed = ctx->lb_missed;
     a.missed_list = ctx->missed_list;
+    a.spin = ctx->fuse_spin;
+    a.fs = (T)ctx->fix.scale;
+    a.fis = (T)ctx->fix.inv_scale;
+    a.range_flag = ctx->range_flag;
     a.nx = ctx->p.nx;
     a.ny = ctx->p.ny;
     a.nz = ctx->p.nz;
@@ -341,8 +370,8 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the moments the collide kernel left, on the new populations
     moments_rest_kernel<T, S><<<2 * ctx->sm_count, block, 0, ctx->stream>>>(
-        a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, ctx->N, ctx->p.nx, ctx->p.ny, ctx->p.nz, a.rho0,
-        ctx->lb_missed, ctx->missed_list, ctx->d_lb_step);
+        a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, ctx->N, ctx->p.nx, ctx->p.ny, ctx->p.nz, a.rho0, a.fs,
+        ctx->range_flag, ctx->lb_missed, ctx->missed_list, ctx->missed_total, ctx->d_lb_step);
     return cudaGetLastError();
 }
 
@@ -356,7 +385,7 @@ static cudaError_t node_moments_t(lbmd_ctx *ctx) {
         static_cast<const S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
         B ? active_words_now(ctx) : nullptr,
         static_cast<typename Prec<T>::node4 *>(B ? active_records_now(ctx) : nullptr),
-        active_words(ctx->p.nx), ctx->N, ctx->p.nx, ctx->p.ny, (T)ctx->p.rho0);
+        active_words(ctx->p.nx), ctx->N, ctx->p.nx, ctx->p.ny, (T)ctx->p.rho0, (T)ctx->fix.scale, ctx->range_flag);
     return cudaGetLastError();
 }
 
@@ -366,7 +395,7 @@ static cudaError_t forcing_update_t(lbmd_ctx *ctx) {
     forcing_update_kernel<T, S><<<blocks, 256, 0, ctx->stream>>>(
         static_cast<S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
         static_cast<typename Prec<T>::node4 *>(ctx->jacc), ctx->N, (T)ctx->p.rho0, (T)ctx->co.gamma_bulk,
-        (T)ctx->co.gamma_shear);
+        (T)ctx->co.gamma_shear, (T)ctx->fix.scale, (T)ctx->fix.inv_scale, ctx->range_flag);
     return cudaGetLastError();
 }
 

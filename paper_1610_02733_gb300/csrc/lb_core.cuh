@@ -14,6 +14,14 @@ __host__ __device__ constexpr double INV_BNORM(int k) {
                              1.5, 1.5, 1.5, 4.5, 4.5, 4.5, 0.5, 0.75, 2.25};
     return t[k];
 }
+// 1/b_k and the norms b_k of lbmd_device.cuh (which the host's noise
+// amplitudes use) are one table: checked at compile time.
+constexpr bool inv_bnorm_matches() {
+    for (int k = 0; k < Q; ++k)
+        if (BNORM(k) * INV_BNORM(k) != 1.0) return false;
+    return true;
+}
+static_assert(inv_bnorm_matches(), "INV_BNORM(k) must be 1 / BNORM(k)");
 
 // The D3Q19 order pairs every moving velocity with its opposite:
 // c_{2p+2} = -c_{2p+1}, p = 0..8.  Even modes (0, 4-9, 16-18) see only the

@@ -53,7 +53,8 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->staging,      ctx->red_partial,   ctx->red_out,       ctx->d_lb_step,
                     ctx->occw[0],      ctx->occw[1],       ctx->cact[0],       ctx->cact[1],
                     ctx->blk_done,     ctx->lb_missed,     ctx->missed_list,   ctx->nb_list,
-                    ctx->nb_count,     ctx->nb_invalid,    ctx->nb_ref4};
+                    ctx->nb_count,     ctx->nb_invalid,    ctx->nb_ref4,       ctx->range_flag,
+                    ctx->missed_total};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int i = 0; i < 4; ++i)
@@ -78,6 +79,7 @@ const char *lbmd_status_string(lbmd_status s) {
     case LBMD_ERR_SEQUENCE: return "call out of the MD/LB step sequence";
     case LBMD_ERR_NONFINITE: return "non-finite observable";
     case LBMD_ERR_CAPACITY: return "capacity exceeded";
+    case LBMD_ERR_RANGE: return "node momentum beyond the fixed-point range";
     }
     return "unknown status";
 }
@@ -100,6 +102,10 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         return fail(nullptr, LBMD_ERR_ARG, "precision must be FP32, FP64, FP16_DEV or BF16_DEV");
     if (!(p->rho0 > 0) || !(p->nu > 0) || !is_finite_d(p->rho0) || !is_finite_d(p->nu))
         return fail(nullptr, LBMD_ERR_ARG, "rho0 and nu must be positive");
+    FixUnit fix;
+    if (!fix_unit(p->rho0, p->precision == LBMD_FP64 ? lbmd::Prec<double>::SCALE_LOG2 : lbmd::Prec<float>::SCALE_LOG2,
+                  fix))
+        return fail(nullptr, LBMD_ERR_ARG, "rho0 must lie in [2^-60, 2^60]");
     if (!(p->kT >= 0) || !is_finite_d(p->kT)) return fail(nullptr, LBMD_ERR_ARG, "kT must be >= 0");
     if (!(p->zeta >= 0) || !is_finite_d(p->zeta)) return fail(nullptr, LBMD_ERR_ARG, "zeta must be >= 0");
     if (!(std::fabs(p->gamma_ghost) < 1.0)) return fail(nullptr, LBMD_ERR_ARG, "|gamma_ghost| must be < 1");
@@ -121,21 +127,10 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     ctx->p = *p;
     ctx->N = (int64_t)p->nx * p->ny * p->nz;
     ctx->dt = 1.0 / (double)p->n_sub;
-    // relaxation factors: nu = (1+g_s)/(6(1-g_s)), nu_b = (1+g_b)/(9(1-g_b))
-    LbCoeffs &co = ctx->co;
-    co.gamma_shear = (6.0 * p->nu - 1.0) / (6.0 * p->nu + 1.0);
-    co.gamma_bulk = p->nu_bulk < 0 ? 0.0 : (9.0 * p->nu_bulk - 1.0) / (9.0 * p->nu_bulk + 1.0);
-    co.gamma_ghost = p->gamma_ghost;
-    static const double bnorm[19] = {1.0,       1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 4.0 / 9.0,
-                                     1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 2.0 / 9.0,
-                                     2.0 / 9.0, 2.0 / 9.0, 2.0,       4.0 / 3.0, 4.0 / 9.0};
-    const double mu = 3.0 * p->kT;  // kT / (a^3 c_s^2)
-    for (int k = 0; k < 19; ++k) {
-        double g = k < 4 ? 1.0 : (k == 4 ? co.gamma_bulk : (k <= 9 ? co.gamma_shear : co.gamma_ghost));
-        co.noise_amp[k] = k < 4 ? 0.0 : std::sqrt(mu * bnorm[k] * (1.0 - g * g));
-    }
-    for (int d = 0; d < 3; ++d) co.body_force[d] = p->body_force[d];
-    co.noisy = p->kT > 0 ? 1 : 0;
+    ctx->fix = fix;
+    ctx->fuse_spin = LBMD_DEFAULT_FUSE_SPIN;
+    lb_coefficients(p->nu, p->nu_bulk, p->gamma_ghost, p->kT, ctx->co);
+    for (int d = 0; d < 3; ++d) ctx->co.body_force[d] = p->body_force[d];
 
     if (p->stream) {
         ctx->stream = (cudaStream_t)p->stream;
@@ -203,6 +198,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->blk_done, (size_t)n_lb_blocks * sizeof(uint32_t)},
         {(void **)&ctx->lb_missed, sizeof(int32_t)},
         {(void **)&ctx->missed_list, (size_t)n_lb_blocks * sizeof(int32_t)},
+        {(void **)&ctx->missed_total, sizeof(unsigned long long)},
+        {(void **)&ctx->range_flag, sizeof(int32_t)},
         {(void **)&ctx->bond_count, (size_t)maxp * sizeof(int32_t)},
         {(void **)&ctx->bond_partner, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(int32_t)},
         {(void **)&ctx->bond_k, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
@@ -225,6 +222,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     }
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_lb_step, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->missed_total, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->range_flag, 0, sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_count, 0, (size_t)maxp * sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_kind, 0, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE, ctx->stream);
     // no row buckets yet: every particle is spread as a migrant until the
@@ -512,8 +511,10 @@ lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
     LBMD_TRACE("lbmd_observables");
     if (!ctx || !out) return LBMD_ERR_ARG;
     double h[8];
+    int32_t range = 0;
     CK(ctx, launch_observables(ctx));
     CK(ctx, cudaMemcpyAsync(h, ctx->red_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(&range, ctx->range_flag, sizeof(range), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     out->mass = h[0];
     for (int d = 0; d < 3; ++d) {
@@ -526,6 +527,30 @@ lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
     out->md_step = ctx->md_step;
     for (int c = 0; c < 8; ++c)
         if (!is_finite_d(h[c])) return fail(ctx, LBMD_ERR_NONFINITE, "non-finite observable");
+    if (range)
+        return fail(ctx, LBMD_ERR_RANGE,
+                    "a node's momentum density reached half the fixed-point range (|u| ~ 1 at rho0): the fluid "
+                    "state is no longer valid");
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_moments_wait(lbmd_ctx *ctx, int32_t polls) {
+    if (!ctx) return LBMD_ERR_ARG;
+    if (polls < -1) return fail(ctx, LBMD_ERR_ARG, "polls must be >= -1");
+    const int v = polls < 0 ? LBMD_DEFAULT_FUSE_SPIN : polls;
+    if (v != ctx->fuse_spin) {
+        ctx->fuse_spin = v;
+        drop_cycle_graphs(ctx);  // the captured launches carry the old limit
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_moments_fallback_rows(lbmd_ctx *ctx, int64_t *rows) {
+    if (!ctx || !rows) return LBMD_ERR_ARG;
+    unsigned long long v = 0;
+    CK(ctx, cudaMemcpyAsync(&v, ctx->missed_total, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    *rows = (int64_t)v;
     return LBMD_OK;
 }
 
@@ -553,6 +578,8 @@ lbmd_status lbmd_set_populations(lbmd_ctx *ctx, const double *in) {
         CK(ctx, launch_populations_from_double(ctx, s, c, ctx->staging));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
     }
+    // a new fluid state: the range guard starts over
+    CK(ctx, cudaMemsetAsync(ctx->range_flag, 0, sizeof(int32_t), ctx->stream));
     CK(ctx, launch_node_moments(ctx, false));
     CK(ctx, launch_clear_transfer(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -795,7 +822,9 @@ lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes) {
     const unsigned long long step = (unsigned long long)h.lb_step;
     CK(ctx, cudaMemcpy(ctx->d_lb_step, &step, sizeof(step), cudaMemcpyHostToDevice));
     // node field of the restored populations (no pending transfer at a cycle
-    // boundary) and the conservative forces at the restored positions
+    // boundary) and the conservative forces at the restored positions; the
+    // range guard starts over
+    CK(ctx, cudaMemset(ctx->range_flag, 0, sizeof(int32_t)));
     CK(ctx, launch_node_moments(ctx, false));
     CK(ctx, launch_clear_transfer(ctx));
     if (ctx->np > 0 && has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));

@@ -35,10 +35,12 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstdint>
 #include <string>
 
 #include "../../include/lbmd.h"
+#include "lbmd_device.cuh"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -60,6 +62,43 @@ struct LbCoeffs {
     double body_force[3];
     int noisy;
 };
+
+// Relaxation factors and noise amplitudes of the collision operator (Sec. 2),
+// one definition for the single box, the batched replicas and the adjoint:
+// nu = (1 + g_s) / (6 (1 - g_s)), nu_b = (1 + g_b) / (9 (1 - g_b)) (g_b = 0
+// for nu_b < 0), ghost factor as given; mode k >= 4 gets the amplitude
+// sqrt(mu b_k (1 - g_k^2)) with mu = kT / (a^3 c_s^2) = 3 kT, the conserved
+// modes 0-3 none.  The body force is left to the caller.
+inline void lb_coefficients(double nu, double nu_bulk, double gamma_ghost, double kT, LbCoeffs &co) {
+    co.gamma_shear = (6.0 * nu - 1.0) / (6.0 * nu + 1.0);
+    co.gamma_bulk = nu_bulk < 0 ? 0.0 : (9.0 * nu_bulk - 1.0) / (9.0 * nu_bulk + 1.0);
+    co.gamma_ghost = gamma_ghost;
+    const double mu = 3.0 * kT;
+    for (int k = 0; k < lbmd::Q; ++k) {
+        const double g = k < 4 ? 1.0 : (k == 4 ? co.gamma_bulk : (k <= 9 ? co.gamma_shear : co.gamma_ghost));
+        co.noise_amp[k] = k < 4 ? 0.0 : std::sqrt(mu * lbmd::BNORM(k) * (1.0 - g * g));
+    }
+    for (int d = 0; d < 3; ++d) co.body_force[d] = 0.0;
+    co.noisy = kT > 0 ? 1 : 0;
+}
+
+// Unit of the fixed-point momentum density, 2^(e - scale_log2) with
+// e = ceil(log2 rho0): |j| then stays representable up to a node velocity of
+// 2 (FP32) / 128 (FP64) at rho = rho0 whatever rho0 is.  At rho0 = 1, e = 0
+// (units 2^-30 / 2^-56).  False for rho0 outside [2^-60, 2^60].
+struct FixUnit {
+    int e;
+    double scale, inv_scale;  // 2^(scale_log2 - e) and its inverse
+};
+inline bool fix_unit(double rho0, int scale_log2, FixUnit &u) {
+    if (!(rho0 >= std::ldexp(1.0, -60) && rho0 <= std::ldexp(1.0, 60))) return false;
+    int E = 0;
+    const double m = std::frexp(rho0, &E);  // rho0 = m 2^E, m in [0.5, 1)
+    u.e = m == 0.5 ? E - 1 : E;
+    u.scale = std::ldexp(1.0, scale_log2 - u.e);
+    u.inv_scale = std::ldexp(1.0, u.e - scale_log2);
+    return true;
+}
 
 struct lbmd_ctx {
     lbmd_params p;
@@ -91,6 +130,8 @@ struct lbmd_ctx {
     uint32_t *blk_done;
     int32_t *lb_missed;    // count
     int32_t *missed_list;  // collide-block ids
+    unsigned long long *missed_total;  // rows left to the fallback since creation
+    int fuse_spin;         // polls of a collide block's wait (0: no fused moments)
     int sm_count;
     int gather_warps;  // warps per block of the variant B row gather
     int32_t *bond_count, *bond_partner;
@@ -109,6 +150,10 @@ struct lbmd_ctx {
     int64_t staging_len;
     double *red_partial;  // per-block partial sums of the observables
     double *red_out;      // final sums
+    // range guard of the fixed-point momentum: set (sticky) by the kernels
+    // that write a node record whose momentum reaches half the range
+    int32_t *range_flag;
+    FixUnit fix;
     int red_blocks;
     unsigned long long *d_lb_step;  // LB step counter read by the kernels
     int64_t np, nb;
@@ -128,6 +173,11 @@ inline uint2 *active_words_now(const lbmd_ctx *c) { return c->occw[c->lb_step & 
 inline void *active_records_now(const lbmd_ctx *c) { return c->cact[c->lb_step & 1]; }
 inline uint2 *active_words_next(const lbmd_ctx *c) { return c->occw[(c->lb_step + 1) & 1]; }
 inline void *active_records_next(const lbmd_ctx *c) { return c->cact[(c->lb_step + 1) & 1]; }
+
+// Default poll limit of a collide block's wait for its neighbour blocks
+// before it leaves its row's fused moments to the follow-up kernel (64 ns per
+// poll: about 67 ms, far above the few microseconds the lag needs).
+constexpr int LBMD_DEFAULT_FUSE_SPIN = 1 << 20;
 
 // Launchers, one per kernel family; each enqueues on ctx->stream and returns
 // the launch status.

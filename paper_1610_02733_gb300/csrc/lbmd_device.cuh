@@ -4,13 +4,18 @@
 // momentum density.
 //
 // Fixed-point momentum.  The node field stores the momentum density j as a
-// signed integer multiple of 2^-30 (FP32 build) or 2^-56 (FP64 build).
-// Particle-to-fluid transfers (Eqs. (7), (8) of the paper) are added with
-// integer atomics, which are associative: the accumulated value does not
-// depend on the order in which particles are processed, so every run is
-// bitwise reproducible without a fixed particle order or colouring.  Range: |j| < 2 (FP32)
-// and |j| < 128 (FP64), far above any flow an LB fluid can carry (the
-// lattice Mach number must stay well below one).
+// signed integer multiple of the unit 2^(e - 30) (FP32 build) or 2^(e - 56)
+// (FP64 build), e = ceil(log2 rho0), the smallest power of two at or above
+// the reference density.  Particle-to-fluid transfers (Eqs. (7), (8) of the
+// paper) are added with integer atomics, which are associative: the
+// accumulated value does not depend on the order in which particles are
+// processed, so every run is bitwise reproducible without a fixed particle
+// order or colouring.  Range: |j| < 2^(e + 1) (FP32) and |j| < 2^(e + 7)
+// (FP64), i.e. a node velocity |u| = |j| / rho below 2 (FP32) / 128 (FP64)
+// at rho = rho0, far above any flow an LB fluid can carry (the lattice Mach
+// number must stay well below one).  The scale s = 1 / unit and its inverse
+// are run-time arguments of every kernel that converts (both exact powers of
+// two, so moving the scale or a sign onto a factor is exact).
 #pragma once
 
 #include <cstdint>
@@ -133,7 +138,7 @@ struct Prec;
 
 // FP32 node record (16 bytes, one int4): word 0 holds rho as float bits,
 // word 1 j_z, words 2-3 one signed 64-bit integer S = j_y 2^32 + j_x (all in
-// units of 2^-30).  The low word of S is j_x itself; the high word is j_y,
+// units of 2^(e - 30)).  The low word of S is j_x itself; the high word is j_y,
 // minus one when j_x is negative.  Because S is an ordinary integer sum, a
 // transfer (dx, dy, dz) is added with two atomics, one 64-bit add of
 // dy 2^32 + dx and one 32-bit add of dz, and the fields stay exact as long as
@@ -144,14 +149,17 @@ struct Prec<float> {
     using real4 = float4;
     using fix = int32_t;
     using node4 = int4;
-    static constexpr float SCALE = 1073741824.0f;             // 2^30
-    static constexpr float INV_SCALE = 9.313225746154785e-10f;  // 2^-30
-    __device__ static __forceinline__ fix to_fix(float v) { return __float2int_rn(v * SCALE); }
-    // to_fix(-d * dp) for ps = neg_scaled(dp): the power-of-two scale and the
-    // sign move onto dp, which is exact, so the two are bitwise equal
-    __device__ static __forceinline__ float neg_scaled(float dp) { return dp * -SCALE; }
+    static constexpr int SCALE_LOG2 = 30;  // scale at rho0 <= 1: 2^30
+    // j -> fixed point with the scale s (a power of two)
+    __device__ static __forceinline__ fix to_fix(float v, float s) { return __float2int_rn(v * s); }
+    // to_fix(-d * dp, s) for ps = -s dp: the power-of-two scale and the sign
+    // move onto dp, which is exact, so the two are bitwise equal
     __device__ static __forceinline__ fix to_fix_neg(float d, float ps) { return __float2int_rn(d * ps); }
-    __device__ static __forceinline__ float from_fix(fix v) { return (float)v * INV_SCALE; }
+    __device__ static __forceinline__ float from_fix(fix v, float inv_s) { return (float)v * inv_s; }
+    // |v| >= 2^30, half the range of a field: the range guard's test
+    __device__ static __forceinline__ bool beyond_half(fix v) {
+        return (uint32_t)v + 0x40000000u >= 0x80000000u;
+    }
     __device__ static __forceinline__ node4 pack(float rho, fix jx, fix jy, fix jz) {
         const long long S = (long long)jy * 4294967296LL + (long long)jx;
         return make_int4(__float_as_int(rho), jz, (int)(unsigned)(unsigned long long)S, (int)(S >> 32));
@@ -189,19 +197,21 @@ struct Prec<float> {
 };
 
 // FP64 node record (32 bytes): rho as double bits, then j_x, j_y, j_z as
-// signed 64-bit integers in units of 2^-56; a transfer is three atomics.
+// signed 64-bit integers in units of 2^(e - 56); a transfer is three atomics.
 template <>
 struct Prec<double> {
     using real = double;
     using real4 = D4;
     using fix = long long;
     using node4 = L4;
-    static constexpr double SCALE = 72057594037927936.0;          // 2^56
-    static constexpr double INV_SCALE = 1.3877787807814457e-17;  // 2^-56
-    __device__ static __forceinline__ fix to_fix(double v) { return __double2ll_rn(v * SCALE); }
-    __device__ static __forceinline__ double neg_scaled(double dp) { return dp * -SCALE; }
+    static constexpr int SCALE_LOG2 = 56;  // scale at rho0 <= 1: 2^56
+    __device__ static __forceinline__ fix to_fix(double v, double s) { return __double2ll_rn(v * s); }
     __device__ static __forceinline__ fix to_fix_neg(double d, double ps) { return __double2ll_rn(d * ps); }
-    __device__ static __forceinline__ double from_fix(fix v) { return (double)v * INV_SCALE; }
+    __device__ static __forceinline__ double from_fix(fix v, double inv_s) { return (double)v * inv_s; }
+    // |v| >= 2^62, half the range of a field
+    __device__ static __forceinline__ bool beyond_half(fix v) {
+        return (unsigned long long)v + 0x4000000000000000ull >= 0x8000000000000000ull;
+    }
     __device__ static __forceinline__ node4 pack(double rho, fix jx, fix jy, fix jz) {
         return L4{__double_as_longlong(rho), jx, jy, jz};
     }

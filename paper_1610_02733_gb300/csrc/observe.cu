@@ -129,14 +129,15 @@ __global__ void __launch_bounds__(RED_THREADS)
 // one warp per column: lane l adds rows l, l + 32, ... in order, then a fixed
 // butterfly combines the lanes
 template <typename T>
-__global__ void __launch_bounds__(32 * RED_COLS) observe_final_kernel(const double *partial, int rows, double *out) {
+__global__ void __launch_bounds__(32 * RED_COLS) observe_final_kernel(const double *partial, int rows, double inv_scale,
+                                                                      double *out) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double s = 0.0;
     for (int r = lane; r < rows; r += 32) s += partial[(int64_t)r * RED_COLS + c];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane != 0) return;
-    if (c >= 1 && c <= 3) s *= (double)Prec<T>::INV_SCALE;
+    if (c >= 1 && c <= 3) s *= inv_scale;  // fixed-point units -> momentum (a power of two: exact)
     out[c] = s;
 }
 
@@ -160,7 +161,8 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
         static_cast<const typename P::real4 *>(ctx->vel4[ctx->pcur]), ctx->slot_of, ctx->np, ctx->red_partial);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    observe_final_kernel<T><<<1, 32 * RED_COLS, 0, ctx->stream>>>(ctx->red_partial, B, ctx->red_out);
+    observe_final_kernel<T><<<1, 32 * RED_COLS, 0, ctx->stream>>>(ctx->red_partial, B, ctx->fix.inv_scale,
+                                                                   ctx->red_out);
     return cudaGetLastError();
 }
 
@@ -198,8 +200,8 @@ __global__ void pops_from_double_kernel(S *f, int64_t first, int64_t count, int6
 // pending transfer J_acc, for nodes [first, first + count)
 template <typename T, typename S>
 __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc,
-                                      const S *f, int64_t N, T rho0, int64_t first, int64_t count, double *dst,
-                                      int transfer_only, int variant) {
+                                      const S *f, int64_t N, T rho0, T fs, T fis, int64_t first, int64_t count,
+                                      double *dst, int transfer_only, int variant) {
     using P = Prec<T>;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
@@ -207,25 +209,25 @@ __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const
     const typename P::node4 n = node[r];
     if (!transfer_only) {
         dst[4 * t + 0] = (double)P::rho_of(n);
-        dst[4 * t + 1] = (double)P::from_fix(P::jx_of(n));
-        dst[4 * t + 2] = (double)P::from_fix(P::jy_of(n));
-        dst[4 * t + 3] = (double)P::from_fix(P::jz_of(n));
+        dst[4 * t + 1] = (double)P::from_fix(P::jx_of(n), fis);
+        dst[4 * t + 2] = (double)P::from_fix(P::jy_of(n), fis);
+        dst[4 * t + 3] = (double)P::from_fix(P::jz_of(n), fis);
         return;
     }
     if (variant != LBMD_VARIANT_B) {
         const typename P::node4 J = jacc[r];
-        dst[3 * t + 0] = (double)P::from_fix(P::jx_of(J));
-        dst[3 * t + 1] = (double)P::from_fix(P::jy_of(J));
-        dst[3 * t + 2] = (double)P::from_fix(P::jz_of(J));
+        dst[3 * t + 0] = (double)P::from_fix(P::jx_of(J), fis);
+        dst[3 * t + 1] = (double)P::from_fix(P::jy_of(J), fis);
+        dst[3 * t + 2] = (double)P::from_fix(P::jz_of(J), fis);
     } else {
         T fl[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) fl[i] = PopStore<S, T>::load(f + (int64_t)i * N + r, T(WEIGHT(i)) * rho0);
         T rho, jx, jy, jz;
         node_moments(fl, rho, jx, jy, jz);
-        dst[3 * t + 0] = (double)P::from_fix(P::jx_of(n) - P::to_fix(jx));
-        dst[3 * t + 1] = (double)P::from_fix(P::jy_of(n) - P::to_fix(jy));
-        dst[3 * t + 2] = (double)P::from_fix(P::jz_of(n) - P::to_fix(jz));
+        dst[3 * t + 0] = (double)P::from_fix(P::jx_of(n) - P::to_fix(jx, fs), fis);
+        dst[3 * t + 1] = (double)P::from_fix(P::jy_of(n) - P::to_fix(jy, fs), fis);
+        dst[3 * t + 2] = (double)P::from_fix(P::jz_of(n) - P::to_fix(jz, fs), fis);
     }
 }
 
@@ -328,7 +330,8 @@ static cudaError_t node_to_double_t(lbmd_ctx *ctx, int64_t first, int64_t count,
     node_to_double_kernel<T, S><<<nblocks(count), 256, 0, ctx->stream>>>(
         static_cast<const N4 *>(ctx->node), static_cast<const N4 *>(ctx->jacc),
         static_cast<const S *>(ctx->f[ctx->cur]),
-        ctx->N, (T)ctx->p.rho0, first, count, dst, transfer_only ? 1 : 0, ctx->p.variant);
+        ctx->N, (T)ctx->p.rho0, (T)ctx->fix.scale, (T)ctx->fix.inv_scale, first, count, dst, transfer_only ? 1 : 0,
+        ctx->p.variant);
     return cudaGetLastError();
 }
 

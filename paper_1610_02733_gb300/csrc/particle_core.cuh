@@ -71,7 +71,7 @@ __device__ __forceinline__ void advance(T &frac, int &c, T d, int n) {
 
 // The transfer -delta_k Delta P of Eqs. (7), (8) in fixed point; every
 // spreading path computes it this way (sx = F_x neg_scale_dt etc., equal to
-// neg_scaled(dt F_x) because the scale is a power of two).
+// -s dt F_x for the fixed-point scale s because s is a power of two).
 template <typename T>
 __device__ __forceinline__ void spread_to(typename Prec<T>::node4 *field, const uint32_t idx[8], const T delta[8], T sx,
                                           T sy, T sz) {

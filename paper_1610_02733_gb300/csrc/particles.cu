@@ -60,7 +60,8 @@ struct PArgs {
     FastDiv fd_nx, fd_ny;  // division by nx and ny
     int64_t np;
     T zeta, dt, half_dt, amp;
-    T neg_scale_dt;  // -dt times the fixed-point scale: neg_scaled(dt F) = F neg_scale_dt exactly
+    T neg_scale_dt;  // -dt times the fixed-point scale s: -s (dt F) = F neg_scale_dt exactly
+    T fis;           // 1 / s: fixed-point momentum -> real
     uint32_t key0, key1;
     const unsigned long long *lb_step;
     int n_sub, substep, noisy;
@@ -118,9 +119,9 @@ __device__ __forceinline__ void interp_u(const PArgs<T> &a, const CellXYZ &c, T 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const T w = (wx[h] * wy[q & 1] * wz[q >> 1]) / P::rho_of(n[h]);
-            ux += w * P::from_fix(P::jx_of(n[h]));
-            uy += w * P::from_fix(P::jy_of(n[h]));
-            uz += w * P::from_fix(P::jz_of(n[h]));
+            ux += w * P::from_fix(P::jx_of(n[h]), a.fis);
+            uy += w * P::from_fix(P::jy_of(n[h]), a.fis);
+            uz += w * P::from_fix(P::jz_of(n[h]), a.fis);
         }
     }
 }
@@ -1053,7 +1054,8 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.dt = (T)ctx->dt;
     a.half_dt = (T)(0.5 * ctx->dt);
     a.amp = (T)sqrt(2.0 * ctx->p.zeta * ctx->p.kT / ctx->dt);
-    a.neg_scale_dt = (T)ctx->dt * -P::SCALE;
+    a.neg_scale_dt = (T)ctx->dt * -(T)ctx->fix.scale;
+    a.fis = (T)ctx->fix.inv_scale;
     a.key0 = (uint32_t)(ctx->p.seed & 0xffffffffu);
     a.key1 = (uint32_t)(ctx->p.seed >> 32);
     a.lb_step = ctx->d_lb_step;

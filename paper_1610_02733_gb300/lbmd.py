@@ -23,6 +23,7 @@ LBMD_ERR_OOM = -3
 LBMD_ERR_SEQUENCE = -4
 LBMD_ERR_NONFINITE = -5
 LBMD_ERR_CAPACITY = -6
+LBMD_ERR_RANGE = -7
 VARIANT_A, VARIANT_B, VARIANT_C = 0, 1, 2
 FP32, FP64, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_DEV}
@@ -38,7 +39,7 @@ EXPORTS = (
     "lbmd_md_substep", "lbmd_lb_step", "lbmd_run_cycles", "lbmd_observables", "lbmd_get_populations",
     "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
-    "lbmd_particle_sums_static",
+    "lbmd_particle_sums_static", "lbmd_set_moments_wait", "lbmd_moments_fallback_rows",
     "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add_particles", "lbmd_batch_run", "lbmd_batch_kinetic",
     "lbmd_batch_kinetic_device",
     "lbmd_batch_unstable", "lbmd_batch_get_populations", "lbmd_batch_set_populations", "lbmd_batch_get_particles",
@@ -128,6 +129,8 @@ def load():
     L.lbmd_get_particles_device.argtypes = [P, ct.c_void_p, ct.c_void_p]
     L.lbmd_get_counts.argtypes = [P, i64p, i64p, i64p, i64p, ct.POINTER(ct.c_int32)]
     L.lbmd_particle_sums_static.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p]
+    L.lbmd_set_moments_wait.argtypes = [P, ct.c_int32]
+    L.lbmd_moments_fallback_rows.argtypes = [P, i64p]
     L.lbmd_stream.restype = ct.c_void_p
     L.lbmd_stream.argtypes = [P]
     L.lbmd_last_error.restype = ct.c_char_p
@@ -410,6 +413,17 @@ class LBMD:
         vel = np.empty(3 * max(n, 1))
         _check(self._h, load().lbmd_get_particles(self._h, _ptr(pos), _ptr(vel)), "lbmd_get_particles")
         return pos[:3 * n].reshape(n, 3), vel[:3 * n].reshape(n, 3)
+
+    def set_moments_wait(self, polls: int):
+        """Poll limit of the fused post-stream moments' wait (-1: default, 0:
+        every row to the follow-up kernel); results do not depend on it."""
+        _check(self._h, load().lbmd_set_moments_wait(self._h, int(polls)), "lbmd_set_moments_wait")
+
+    def moments_fallback_rows(self) -> int:
+        """Rows whose fused moments the follow-up kernel computed, since creation."""
+        v = ct.c_int64(0)
+        _check(self._h, load().lbmd_moments_fallback_rows(self._h, ct.byref(v)), "lbmd_moments_fallback_rows")
+        return v.value
 
     def particles_device(self, pos, vel):
         """Stream-ordered copy into caller-owned device tensors (float64, 3 N)."""

@@ -47,7 +47,7 @@ def test_params_struct_layout():
 
 
 def test_status_strings_without_gpu(lib):
-    for s in (0, -1, -2, -3, -4, -5, -6):
+    for s in (0, -1, -2, -3, -4, -5, -6, -7):
         assert lib.lbmd_status_string(s)
 
 

@@ -40,6 +40,37 @@ def test_particle_sums_static_matches_observables_twice():
         assert np.abs(got - want).max() <= 1e-12 * scale, (call, got, want)
 
 
+def test_particle_sums_static_edge_cases_and_no_allocation():
+    torch = pytest.importorskip("torch")
+    from paper_1610_02733_gb300 import inputs, lbmd
+
+    shape, n, kT = (12, 12, 12), 5000, 1e-3
+    g = lbmd.LBMD(*shape, variant="B", n_sub=2, kT=kT, zeta=1.0, seed=4, max_particles=n)
+    g.add_particles(inputs.uniform_positions(n, shape, 4), inputs.maxwell_velocities(n, kT, 4))
+    g.cycle(1)
+    vel = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    g.particles_device(None, vel)
+    # n = 0: no partial-sum block runs, the sums are zero
+    lbmd.lbmd_particle_sums_static(vel.data_ptr(), 0, 0, out.data_ptr(), g.stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), np.zeros(4))
+    # mass NULL: unit masses, as in the context
+    lbmd.lbmd_particle_sums_static(vel.data_ptr(), 0, n, out.data_ptr(), g.stream)
+    torch.cuda.synchronize()
+    ob = g.observables()
+    want = np.concatenate([ob["p_particles"], [2.0 * ob["e_kin"]]])
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-12 * np.abs(want).max()
+    # no device memory taken by a call (after the first one, which has loaded
+    # the kernels' module)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    lbmd.lbmd_particle_sums_static(vel.data_ptr(), 0, n, out.data_ptr(), g.stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    g.close()
+
+
 def test_particle_sums_static_rejects_oversize():
     from paper_1610_02733_gb300 import lbmd
     with pytest.raises(lbmd.LbmdError) as ei:
