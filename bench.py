@@ -280,6 +280,40 @@ def _variant_costs(torch, lbmd, inputs, stream, pos, vel, steps, ms_b):
     return out
 
 
+def _bead_spring_64_form(torch, lbmd, inputs, stream):
+    """The configuration of the A-versus-B cost comparison: 64^3, 64 random-walk
+    chains of 64 beads (harmonic bonds k = 30, r0 = 1, mass 1, zeta = 2),
+    kT = 1e-4, n = 10, FP32, 10^4 MD steps (1000 cycles replayed from the
+    captured cycle graph) for variants A and B; GPU time per cycle by CUDA
+    events and the extra cost of B over A (Sec. 3: 'a few percent')."""
+    shape, cycles = (64, 64, 64), 1000
+    pos, bonds = inputs.bead_spring_chains(64, 64, shape, 2)
+    vel = inputs.maxwell_velocities(pos.shape[0], KT, 2)
+    out = {"workload": "64^3 D3Q19, 64 chains x 64 beads (harmonic k=30, r0=1), zeta=2, kT=1e-4, n=10, FP32, "
+                       "10^4 MD steps"}
+    ms = {}
+    for v in ("A", "B"):
+        sim = lbmd.LBMD(*shape, variant=v, precision="fp32", n_sub=10, kT=KT, zeta=2.0, seed=SEED,
+                        max_particles=pos.shape[0], max_bonds=bonds.shape[0], stream=stream.cuda_stream)
+        sim.add_particles(pos, vel)
+        sim.add_bonds(bonds, 30.0, 1.0)
+        sim.run_cycles(20)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        sim.run_cycles(cycles)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms[v] = a.elapsed_time(b) / cycles
+        sim.close()
+    n_nodes = shape[0] * shape[1] * shape[2]
+    for v in ("A", "B"):
+        out[v] = {"ms_per_cycle": round(ms[v], 5), "value": round(n_nodes / (ms[v] * 1e-3) / 1e6, 1),
+                  "unit": "MLUPS", "particle_substeps_per_s": float("%.4g" % (pos.shape[0] * 10 / (ms[v] * 1e-3)))}
+    out["extra_vs_A"] = {"B": round(ms["B"] / ms["A"] - 1.0, 4)}
+    return out
+
+
 def _kremer_grest_form(torch, stream):
     """The paper's test system (Sec. 4): 10 Kremer-Grest chains of 256 beads in
     (20 sigma)^3, LJ units converted to lattice units, HALF_STEP integrator.
@@ -521,6 +555,7 @@ def run_gpu(args):
         line["batched_replicas"] = _batched_replicas(torch, lbmd, inputs, stream, peak)
         line["adjoint"] = _adjoint_form(torch, lbmd, inputs)
         line["kremer_grest"] = _kremer_grest_form(torch, stream)
+        line["bead_spring_64"] = _bead_spring_64_form(torch, lbmd, inputs, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -568,13 +603,60 @@ def _oracle_sample(edge: int, cycles: int):
     return dt, edge ** 3, n
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu), else what platform reports."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_full_cycles(cycles: int):
+    """The oracle's OpenMP timing build (LB node loops over all host cores,
+    particle loop serial) on the full workload: 256^3, 10^6 particles,
+    `cycles` cycles of 10 MD steps + 1 LB step."""
+    from oracle import oracle as orc
+    from paper_1610_02733_gb300 import inputs
+    o = orc.Oracle(*SHAPE, n_sub=N_SUB, variant=1, kT=KT, zeta=ZETA, seed=SEED, openmp=True)
+    o.add_particles(inputs.uniform_positions(N_PARTICLES, SHAPE, SEED), inputs.maxwell_velocities(N_PARTICLES, KT, SEED))
+    t0 = time.perf_counter()
+    o.cycle(cycles)
+    dt = time.perf_counter() - t0
+    o.close()
+    return dt
+
+
 def cpu_baseline():
+    """The FP64 oracle on the host cores: 3 full cycles of the benchmark
+    workload with its OpenMP timing build (all cores on the LB node loops,
+    particle loop serial), and a bounded single-thread sample of the plain
+    build (8 cycles of a 128^3 box at the same particle density)."""
     edge, cycles = 128, 8
     dt, nodes, n = _oracle_sample(edge, cycles)
-    return {"value": round(nodes * cycles / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "particle_substeps_per_s": float("%.4g" % (n * N_SUB * cycles / dt)),
-            "sample": "%d cycles of a %d^3 box with %d particles (same density, n=10, variant B), FP64, "
-                      "single thread, %.1f s" % (cycles, edge, n, dt)}
+    single = {"value": round(nodes * cycles / dt / 1e6, 4), "unit": "MLUPS", "cores": 1,
+              "particle_substeps_per_s": float("%.4g" % (n * N_SUB * cycles / dt)),
+              "sample": "%d cycles of a %d^3 box with %d particles (same density, n=10, variant B), FP64, "
+                        "single thread, %.1f s" % (cycles, edge, n, dt)}
+    cores = os.cpu_count() or 1
+    out = {"kind": "oracle", "cpu_model": _cpu_model(), "nproc": cores, "single_thread": single}
+    full_cycles = 3
+    try:
+        dt_full = _oracle_full_cycles(full_cycles)
+        nodes_full = SHAPE[0] * SHAPE[1] * SHAPE[2]
+        out.update({"value": round(nodes_full * full_cycles / dt_full / 1e6, 4), "unit": "MLUPS", "cores": cores,
+                    "particle_substeps_per_s": float("%.4g" % (N_PARTICLES * N_SUB * full_cycles / dt_full)),
+                    "sample": "%d full cycles of the workload (%dx%dx%d, %d particles, n=10, variant B), FP64, "
+                              "OpenMP over %d cores on the LB node loops, particle loop serial, %.1f s" % (
+                                  full_cycles, SHAPE[0], SHAPE[1], SHAPE[2], N_PARTICLES, cores, dt_full)})
+    except Exception as exc:  # no OpenMP runtime on this host
+        out.update({"value": single["value"], "unit": "MLUPS", "cores": 1, "sample": single["sample"],
+                    "all_cores": "unavailable: %s" % exc})
+    return out
 
 
 def run_reference(args):

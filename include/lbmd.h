@@ -84,14 +84,22 @@ enum { LBMD_FP32 = 0, LBMD_FP64 = 1, LBMD_FP16_DEV = 2, LBMD_BF16_DEV = 3 };
  *   kT, where START gives kT / (1 - zeta dt / 2m). */
 enum { LBMD_INTEGRATOR_START = 0, LBMD_INTEGRATOR_HALF_STEP = 1 };
 /* How variant B hands each MD step's transfers to the nodes (Eqs. (7), (8)).
- * ROWS: a gather per lattice row over the particles re-ordered by row, plus
- * atomics for the particles that left their row (few atomics; pays off for
- * many particles).  ATOMIC: every particle adds its 8 corner transfers with
- * integer atomics (one launch; pays off for few particles).  AUTO: ATOMIC
+ * ROWS: a gather per lattice row over the particles re-ordered by row, after
+ * a separate particle pass, plus atomics for the particles that left their
+ * row (few atomics; pays off for many particles).  ATOMIC: every particle
+ * adds its 8 corner transfers with integer atomics (one launch; pays off for
+ * few particles).  TILES: the whole MD step in one pass over tiles of 4 x 4
+ * lattice rows: a block stages the node records of its rows (and one more
+ * row above in y and z) in shared memory, steps the particles of its rows,
+ * sums their transfers to its rows in shared memory and hands those to the
+ * rows above to the neighbouring tile through an edge accumulator; particles
+ * that left their row go through atomics (needs the START integrator, no
+ * bonds or Lennard-Jones forces, nx <= 512, ny and nz >= 6; otherwise ROWS is
+ * used; measured slower than ROWS at 0.06 particles per node).  AUTO: ATOMIC
  * while there are fewer than LBMD_SPREAD_ATOMIC_PER_ROW particles per lattice
  * row (y, z) on average, ROWS above (measured crossover).  The transfers are
- * fixed-point integers, so all three give bitwise the same results. */
-enum { LBMD_SPREAD_AUTO = 0, LBMD_SPREAD_ROWS = 1, LBMD_SPREAD_ATOMIC = 2 };
+ * fixed-point integers, so all of them give bitwise the same results. */
+enum { LBMD_SPREAD_AUTO = 0, LBMD_SPREAD_ROWS = 1, LBMD_SPREAD_ATOMIC = 2, LBMD_SPREAD_TILES = 3 };
 #define LBMD_SPREAD_ATOMIC_PER_ROW 10
 
 typedef struct lbmd_params {
@@ -112,7 +120,7 @@ typedef struct lbmd_params {
     void *stream;          /* cudaStream_t to enqueue on (borrowed); NULL: the
                               context creates and owns a stream of its own */
     int32_t integrator;    /* LBMD_INTEGRATOR_START or LBMD_INTEGRATOR_HALF_STEP */
-    int32_t spread;        /* variant B: LBMD_SPREAD_AUTO, _ROWS or _ATOMIC */
+    int32_t spread;        /* variant B: LBMD_SPREAD_AUTO, _TILES, _ROWS or _ATOMIC */
 } lbmd_params;
 
 typedef struct lbmd_ctx lbmd_ctx;

@@ -186,6 +186,8 @@ void orc_modes(double e_out[Q * Q], double b_out[Q]) {
 }
 
 static void compute_moments(orc_state *s) {
+    /* every node on its own (a timing build may spread the loop over threads) */
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < s->n_nodes; ++r) {
         double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
         for (int i = 0; i < Q; ++i) {
@@ -346,6 +348,9 @@ static int64_t node_index(const orc_state *s, int64_t x, int64_t y, int64_t z) {
 int orc_lb_step(orc_state *s) {
     if (s->sub_done != s->p.n_sub) return ORC_ERR_SEQUENCE;
     int64_t n = s->n_nodes;
+    /* every node collides on its own and pushes to distinct targets (a timing
+     * build may spread the planes over threads; the results do not change) */
+#pragma omp parallel for schedule(static)
     for (int64_t z = 0; z < s->p.nz; ++z)
         for (int64_t y = 0; y < s->p.ny; ++y)
             for (int64_t x = 0; x < s->p.nx; ++x) {

@@ -19,6 +19,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbmd_oracle.so")
+# timing build for the all-cores CPU baseline: the same sources with OpenMP
+# (the LB node loops run over threads; the particle loop stays serial)
+_OMP_PATH = os.path.join(_BUILD, "liblbmd_oracle_omp.so")
 _SRC = os.path.join(_HERE, "lbmd_oracle.c")
 _SRCS = [_SRC, os.path.join(_HERE, "lbmd_tangent.c")]
 
@@ -26,19 +29,34 @@ ORC_OK = 0
 ORC_ERR_SEQUENCE = -4
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (plain C99, -O2, no fast-math) and return the path."""
+def _compile(path: str, extra, force: bool) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     hdr = os.path.join(_HERE, "lbmd_oracle.h")
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max([os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(hdr)])):
-        return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp] + _SRCS + ["-lm"]
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= max([os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(hdr)])):
+        return path
+    tmp = path + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-std=c99", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared"] + list(extra) + \
+          ["-o", tmp] + _SRCS + ["-lm"]
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C99, -O2, no fast-math, single thread) and
+    return the path; also the OpenMP timing build where gcc supports it."""
+    path = _compile(_LIB_PATH, [], force)
+    try:
+        build_openmp(force)
+    except (subprocess.CalledProcessError, OSError):
+        pass  # no OpenMP runtime: the all-cores baseline reports itself unavailable
+    return path
+
+
+def build_openmp(force: bool = False) -> str:
+    """The timing build: the same sources with -fopenmp (identical results)."""
+    return _compile(_OMP_PATH, ["-fopenmp"], force)
 
 
 class OrcParams(ct.Structure):
@@ -51,14 +69,15 @@ class OrcParams(ct.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ct.CDLL(build())
-        L = _lib
+def lib(openmp: bool = False):
+    """The oracle library (openmp: the timing build)."""
+    key = bool(openmp)
+    if key not in _libs:
+        L = ct.CDLL(build_openmp() if openmp else build())
+        _libs[key] = L
         P = ct.c_void_p
         dp = ct.POINTER(ct.c_double)
         L.orc_create.restype = P
@@ -100,7 +119,7 @@ def lib():
         L.tan_drag.argtypes = [P, dp]
         L.tan_get_populations.argtypes = [P, dp, dp]
         L.tan_get_particles.argtypes = [P, dp, dp, dp, dp]
-    return _lib
+    return _libs[key]
 
 
 def _dp(a: np.ndarray):
@@ -151,7 +170,8 @@ class Oracle:
     """
 
     def __init__(self, nx, ny, nz, *, n_sub=1, variant=1, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
-                 gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1, integrator=0):
+                 gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1, integrator=0,
+                 openmp=False):
         p = OrcParams()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
         p.n_sub, p.variant, p.integrator = int(n_sub), int(variant), int(integrator)
@@ -164,14 +184,15 @@ class Oracle:
         self.shape = (int(nx), int(ny), int(nz))
         self.n_nodes = int(nx) * int(ny) * int(nz)
         self.n_sub = int(n_sub)
-        h = lib().orc_create(ct.byref(p))
+        self._lib = lib(openmp)
+        h = self._lib.orc_create(ct.byref(p))
         if not h:
             raise ValueError("orc_create rejected the parameters")
         self._h = ct.c_void_p(h)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            lib().orc_destroy(self._h)
+            self._lib.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -185,14 +206,14 @@ class Oracle:
         pos = _f64(pos).reshape(-1, 3)
         vel = _f64(vel).reshape(-1, 3)
         m = None if mass is None else _f64(mass).reshape(-1)
-        rc = lib().orc_add_particles(self._h, pos.shape[0], _dp(pos), _dp(vel),
+        rc = self._lib.orc_add_particles(self._h, pos.shape[0], _dp(pos), _dp(vel),
                                      None if m is None else _dp(m))
         if rc != ORC_OK:
             raise RuntimeError("orc_add_particles: %d" % rc)
 
     def add_bonds(self, pairs, k, r0):
         pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
-        rc = lib().orc_add_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
+        rc = self._lib.orc_add_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
                                  float(k), float(r0))
         if rc != ORC_OK:
             raise RuntimeError("orc_add_bonds: %d" % rc)
@@ -200,14 +221,14 @@ class Oracle:
     def add_fene_bonds(self, pairs, k, R0):
         """FENE springs U = -(k/2) R0^2 ln(1 - (r/R0)^2) (Sec. 4)."""
         pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
-        rc = lib().orc_add_fene_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
+        rc = self._lib.orc_add_fene_bonds(self._h, pairs.shape[0], pairs.ctypes.data_as(ct.POINTER(ct.c_int64)),
                                       float(k), float(R0))
         if rc != ORC_OK:
             raise RuntimeError("orc_add_fene_bonds: %d" % rc)
 
     def set_lj(self, eps, sigma, rc):
         """Lennard-Jones between all particles, cut off (and shifted to 0) at rc (Sec. 4)."""
-        r = lib().orc_set_lj(self._h, float(eps), float(sigma), float(rc))
+        r = self._lib.orc_set_lj(self._h, float(eps), float(sigma), float(rc))
         if r != ORC_OK:
             raise RuntimeError("orc_set_lj: %d" % r)
 
@@ -216,14 +237,14 @@ class Oracle:
         n = self.n_particles
         out = np.zeros((max(n, 1), 3))
         e = np.zeros(3)
-        lib().orc_conservative_forces(self._h, _dp(out), _dp(e))
+        self._lib.orc_conservative_forces(self._h, _dp(out), _dp(e))
         return out[:n], {"harmonic": float(e[0]), "fene": float(e[1]), "lj": float(e[2])}
 
     def md_substep(self) -> int:
-        return lib().orc_md_substep(self._h)
+        return self._lib.orc_md_substep(self._h)
 
     def lb_step(self) -> int:
-        return lib().orc_lb_step(self._h)
+        return self._lib.orc_lb_step(self._h)
 
     def cycle(self, k: int = 1):
         for _ in range(k):
@@ -236,79 +257,79 @@ class Oracle:
     # accessors -------------------------------------------------------------
     def observables(self) -> dict:
         o = np.zeros(11)
-        lib().orc_observables(self._h, _dp(o))
+        self._lib.orc_observables(self._h, _dp(o))
         return {"mass": o[0], "p_fluid": o[1:4].copy(), "p_particles": o[4:7].copy(),
                 "kT_particles": o[7], "e_kin": o[8], "lb_step": int(o[9]), "md_step": int(o[10])}
 
     def populations(self) -> np.ndarray:
         out = np.zeros(19 * self.n_nodes)
-        lib().orc_get_populations(self._h, _dp(out))
+        self._lib.orc_get_populations(self._h, _dp(out))
         return out.reshape(19, self.n_nodes)
 
     def set_populations(self, f):
         f = _f64(f).reshape(-1)
         assert f.size == 19 * self.n_nodes
-        lib().orc_set_populations(self._h, _dp(f))
+        self._lib.orc_set_populations(self._h, _dp(f))
 
     def jacc(self) -> np.ndarray:
         out = np.zeros(3 * self.n_nodes)
-        lib().orc_get_jacc(self._h, _dp(out))
+        self._lib.orc_get_jacc(self._h, _dp(out))
         return out.reshape(self.n_nodes, 3)
 
     def set_jacc(self, j):
         j = _f64(j).reshape(-1)
         assert j.size == 3 * self.n_nodes
-        lib().orc_set_jacc(self._h, _dp(j))
+        self._lib.orc_set_jacc(self._h, _dp(j))
 
     def node_field(self) -> np.ndarray:
         out = np.zeros(4 * self.n_nodes)
-        lib().orc_get_node_field(self._h, _dp(out))
+        self._lib.orc_get_node_field(self._h, _dp(out))
         return out.reshape(self.n_nodes, 4)
 
     @property
     def n_particles(self) -> int:
-        return int(lib().orc_num_particles(self._h))
+        return int(self._lib.orc_num_particles(self._h))
 
     def particles(self):
         n = self.n_particles
         pos = np.zeros(3 * max(n, 1))
         vel = np.zeros(3 * max(n, 1))
-        lib().orc_get_particles(self._h, _dp(pos), _dp(vel))
+        self._lib.orc_get_particles(self._h, _dp(pos), _dp(vel))
         return pos[:3 * n].reshape(n, 3), vel[:3 * n].reshape(n, 3)
 
     def set_particles(self, pos=None, vel=None):
         n = self.n_particles
         p = None if pos is None else _f64(pos).reshape(n, 3)
         v = None if vel is None else _f64(vel).reshape(n, 3)
-        lib().orc_set_particles(self._h, None if p is None else _dp(p), None if v is None else _dp(v))
+        self._lib.orc_set_particles(self._h, None if p is None else _dp(p), None if v is None else _dp(v))
 
     def coupling_forces(self) -> np.ndarray:
         n = self.n_particles
         out = np.zeros(3 * max(n, 1))
-        lib().orc_get_coupling_forces(self._h, _dp(out))
+        self._lib.orc_get_coupling_forces(self._h, _dp(out))
         return out[:3 * n].reshape(n, 3)
 
     def counters(self):
         o = (ct.c_int64 * 3)()
-        lib().orc_counters(self._h, o)
+        self._lib.orc_counters(self._h, o)
         return int(o[0]), int(o[1]), int(o[2])
 
     def set_counters(self, lb_step, md_step):
-        lib().orc_set_counters(self._h, int(lb_step), int(md_step))
+        self._lib.orc_set_counters(self._h, int(lb_step), int(md_step))
 
     # building blocks ---------------------------------------------------------
     def collide_node(self, f, F, node=0, lb_step=0) -> np.ndarray:
         f = _f64(f).reshape(19)
         F = _f64(F).reshape(3)
         out = np.zeros(19)
-        lib().orc_collide_node(self._h, _dp(f), _dp(F), int(node), int(lb_step), _dp(out))
+        self._lib.orc_collide_node(self._h, _dp(f), _dp(F), int(node), int(lb_step), _dp(out))
         return out
 
     def trilinear(self, R):
         R = _f64(R).reshape(3)
         corner = np.zeros(8, dtype=np.int64)
         delta = np.zeros(8)
-        lib().orc_trilinear(self._h, _dp(R), corner.ctypes.data_as(ct.POINTER(ct.c_int64)), _dp(delta))
+        self._lib.orc_trilinear(self._h, _dp(R), corner.ctypes.data_as(ct.POINTER(ct.c_int64)), _dp(delta))
         return corner, delta
 
 

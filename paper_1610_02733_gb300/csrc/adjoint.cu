@@ -168,9 +168,9 @@ __global__ void __launch_bounds__(256) ad_couple(AdArgs<T> a, typename Prec<T>::
     T Fx = -a.zeta * (V.x - ux), Fy = -a.zeta * (V.y - uy), Fz = -a.zeta * (V.z - uz);
     if (a.amp != T(0)) {
         const U4 rnd = philox4x32_10(U4{(uint32_t)p, md_step, 1u, 0u}, a.key0, a.key1);
-        Fx += a.amp * unit_uniform<T>(rnd.x);
-        Fy += a.amp * unit_uniform<T>(rnd.y);
-        Fz += a.amp * unit_uniform<T>(rnd.z);
+        Fx = fma(a.amp, unit_uniform<T>(rnd.x), Fx);
+        Fy = fma(a.amp, unit_uniform<T>(rnd.y), Fy);
+        Fz = fma(a.amp, unit_uniform<T>(rnd.z), Fz);
     }
     drag[p] = Fx;
     if (rec.R) {
@@ -180,17 +180,17 @@ __global__ void __launch_bounds__(256) ad_couple(AdArgs<T> a, typename Prec<T>::
         rec.U[p] = P::make4(ux, uy, uz, T(0));
     }
     const T hm = a.half_dt * V.w;
-    V.x += hm * Fx;
-    V.y += hm * Fy;
-    V.z += hm * Fz;
+    V.x = fma(hm, Fx, V.x);
+    V.y = fma(hm, Fy, V.y);
+    V.z = fma(hm, Fz, V.z);
     T fx = R.x, fy = R.y, fz = R.z;
     int cx = c.x, cy = c.y, cz = c.z;
-    advance(fx, cx, a.dt * V.x, a.nx);
-    advance(fy, cy, a.dt * V.y, a.ny);
-    advance(fz, cz, a.dt * V.z, a.nz);
-    V.x += hm * Fx;
-    V.y += hm * Fy;
-    V.z += hm * Fz;
+    advance(fx, cx, a.dt, V.x, a.nx);
+    advance(fy, cy, a.dt, V.y, a.ny);
+    advance(fz, cz, a.dt, V.z, a.nz);
+    V.x = fma(hm, Fx, V.x);
+    V.y = fma(hm, Fy, V.y);
+    V.z = fma(hm, Fz, V.z);
     pos4[p] = P::make_pos(fx, fy, fz, cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz));
     vel4[p] = V;
     old4[p] = R;

@@ -133,22 +133,22 @@ __global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
         const uint32_t md_step =
             (uint32_t)(a.lb_step[r] * (unsigned long long)rp.n_sub + (unsigned)(a.tick % rp.n_sub));
         const U4 rnd = philox4x32_10(U4{(uint32_t)local, md_step, 1u, 0u}, rp.key0, rp.key1);
-        Fx += rp.amp * unit_uniform<T>(rnd.x);
-        Fy += rp.amp * unit_uniform<T>(rnd.y);
-        Fz += rp.amp * unit_uniform<T>(rnd.z);
+        Fx = fma(rp.amp, unit_uniform<T>(rnd.x), Fx);
+        Fy = fma(rp.amp, unit_uniform<T>(rnd.y), Fy);
+        Fz = fma(rp.amp, unit_uniform<T>(rnd.z), Fz);
     }
     const T hm = rp.half_dt * V.w;
-    V.x += hm * Fx;
-    V.y += hm * Fy;
-    V.z += hm * Fz;
+    V.x = fma(hm, Fx, V.x);
+    V.y = fma(hm, Fy, V.y);
+    V.z = fma(hm, Fz, V.z);
     T fx = R.x, fy = R.y, fz = R.z;
     int cx = c.x, cy = c.y, cz = c.z;
-    advance(fx, cx, rp.dt * V.x, rp.nx);
-    advance(fy, cy, rp.dt * V.y, rp.ny);
-    advance(fz, cz, rp.dt * V.z, rp.nz);
-    V.x += hm * Fx;
-    V.y += hm * Fy;
-    V.z += hm * Fz;
+    advance(fx, cx, rp.dt, V.x, rp.nx);
+    advance(fy, cy, rp.dt, V.y, rp.ny);
+    advance(fz, cz, rp.dt, V.z, rp.nz);
+    V.x = fma(hm, Fx, V.x);
+    V.y = fma(hm, Fy, V.y);
+    V.z = fma(hm, Fz, V.z);
     if (!(V.x * V.x + V.y * V.y + V.z * V.z <= T(BATCH_VMAX2))) {
         a.unstable[r] = 1;  // explicit friction diverged: freeze the replica
         return;

@@ -426,8 +426,10 @@ cudaError_t launch_lb_step(lbmd_ctx *ctx) {
     if (e != cudaSuccess) return e;
     if ((e = launch_nb_build(ctx)) != cudaSuccess) return e;
     if ((e = launch_active_set(ctx)) != cudaSuccess) return e;
+    if ((e = md_tile_build_table(ctx, (int)((ctx->lb_step + 1) & 1))) != cudaSuccess) return e;
     if ((e = LBMD_DISPATCH_POPS(ctx, lbmd::lb_step_t, ctx)) != cudaSuccess) return e;
     ctx->cur ^= 1;
+    ctx->rec = 0;  // the moments wrote the next set's first record buffer
     return cudaSuccess;
 }
 

@@ -54,10 +54,12 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->occw[0],      ctx->occw[1],       ctx->cact[0],       ctx->cact[1],
                     ctx->blk_done,     ctx->lb_missed,     ctx->missed_list,   ctx->nb_list,
                     ctx->nb_count,     ctx->nb_invalid,    ctx->nb_ref4,       ctx->range_flag,
-                    ctx->missed_total};
+                    ctx->missed_total, ctx->dev_error,     ctx->arow[0],       ctx->arow[1],
+                    ctx->tile_table[0], ctx->tile_table[1], ctx->edge_acc,  ctx->tile_flag,
+                    ctx->late_rows,    ctx->late_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 16; ++i)
         if (ctx->cycle_graph[i]) cudaGraphExecDestroy(ctx->cycle_graph[i]);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
 }
@@ -113,14 +115,16 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         return fail(nullptr, LBMD_ERR_ARG, "bad capacities");
     if ((int64_t)p->ny * p->nz > (int64_t)1024 * 1024)
         return fail(nullptr, LBMD_ERR_ARG, "ny * nz must not exceed 2^20 (particle re-ordering by row)");
+    if (p->ny > 65535 || p->nz > 65535)
+        return fail(nullptr, LBMD_ERR_ARG, "ny and nz must not exceed 65535 (one collide block row per (y, z))");
     if (p->nx > (p->precision == LBMD_FP64 ? 2048 : 4096))
         return fail(nullptr, LBMD_ERR_ARG, "nx must not exceed 4096 (FP32) / 2048 (FP64): row gather shared memory");
     for (int d = 0; d < 3; ++d)
         if (!is_finite_d(p->body_force[d])) return fail(nullptr, LBMD_ERR_ARG, "non-finite body force");
     if (p->integrator != LBMD_INTEGRATOR_START && p->integrator != LBMD_INTEGRATOR_HALF_STEP)
         return fail(nullptr, LBMD_ERR_ARG, "integrator must be START or HALF_STEP");
-    if (p->spread < LBMD_SPREAD_AUTO || p->spread > LBMD_SPREAD_ATOMIC)
-        return fail(nullptr, LBMD_ERR_ARG, "spread must be AUTO, ROWS or ATOMIC");
+    if (p->spread < LBMD_SPREAD_AUTO || p->spread > LBMD_SPREAD_TILES)
+        return fail(nullptr, LBMD_ERR_ARG, "spread must be AUTO, ROWS, ATOMIC or TILES");
 
     lbmd_ctx *ctx = new (std::nothrow) lbmd_ctx();
     if (!ctx) return fail(nullptr, LBMD_ERR_OOM, "host allocation");
@@ -160,6 +164,11 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     // active
     ctx->cact_cap = std::min<int64_t>(N, 8 * maxp);
     const size_t occ_bytes = (size_t)p->ny * p->nz * (size_t)((p->nx + 31) / 32) * sizeof(uint2);
+    const size_t arow_bytes = ((size_t)p->ny * p->nz + 1) * sizeof(int32_t);
+    ctx->node_bytes = node_bytes;
+    // the tiled MD step's tables and buffers, where the lattice suits it and
+    // the spread mode asks for it
+    const size_t table_bytes = md_tile_geometry(ctx) && p->spread == LBMD_SPREAD_TILES ? md_tile_table_bytes(ctx) : 0;
     // blocks of the LB collide (node kernels: rows of up to 256 nodes)
     const int bx = p->nx >= 256 ? 256 : (p->nx >= 128 ? 128 : (p->nx >= 64 ? 64 : 32));
     const int64_t n_lb_blocks = (int64_t)((p->nx + bx - 1) / bx) * p->ny * p->nz;
@@ -193,8 +202,17 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
         {(void **)&ctx->occw[0], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
         {(void **)&ctx->occw[1], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
-        {&ctx->cact[0], p->variant == LBMD_VARIANT_B ? (size_t)ctx->cact_cap * node_bytes : 0},
-        {&ctx->cact[1], p->variant == LBMD_VARIANT_B ? (size_t)ctx->cact_cap * node_bytes : 0},
+        {&ctx->cact[0], p->variant == LBMD_VARIANT_B ? (size_t)2 * ctx->cact_cap * node_bytes : 0},
+        {&ctx->cact[1], p->variant == LBMD_VARIANT_B ? (size_t)2 * ctx->cact_cap * node_bytes : 0},
+        {(void **)&ctx->arow[0], p->variant == LBMD_VARIANT_B ? arow_bytes : 0},
+        {(void **)&ctx->arow[1], p->variant == LBMD_VARIANT_B ? arow_bytes : 0},
+        {(void **)&ctx->dev_error, sizeof(int32_t)},
+        {&ctx->tile_table[0], table_bytes},
+        {&ctx->tile_table[1], table_bytes},
+        {&ctx->edge_acc, table_bytes ? (size_t)ctx->cact_cap * md_tile_edge_bytes(ctx) : 0},
+        {(void **)&ctx->tile_flag, table_bytes ? (size_t)md_tile_count(ctx) * sizeof(uint32_t) : 0},
+        {(void **)&ctx->late_rows, table_bytes ? (size_t)2 * md_tile_late_cap(ctx) * sizeof(int32_t) : 0},
+        {(void **)&ctx->late_count, table_bytes ? 2 * sizeof(int32_t) : 0},
         {(void **)&ctx->blk_done, (size_t)n_lb_blocks * sizeof(uint32_t)},
         {(void **)&ctx->lb_missed, sizeof(int32_t)},
         {(void **)&ctx->missed_list, (size_t)n_lb_blocks * sizeof(int32_t)},
@@ -224,6 +242,12 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_lb_step, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->missed_total, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->range_flag, 0, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_error, 0, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess && ctx->edge_acc)
+        e = cudaMemsetAsync(ctx->edge_acc, 0, (size_t)ctx->cact_cap * md_tile_edge_bytes(ctx), ctx->stream);
+    if (e == cudaSuccess && ctx->tile_flag)
+        e = cudaMemsetAsync(ctx->tile_flag, 0, (size_t)md_tile_count(ctx) * sizeof(uint32_t), ctx->stream);
+    if (e == cudaSuccess && ctx->late_count) e = cudaMemsetAsync(ctx->late_count, 0, 2 * sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_count, 0, (size_t)maxp * sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bond_kind, 0, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE, ctx->stream);
     // no row buckets yet: every particle is spread as a migrant until the
@@ -235,6 +259,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     // no active nodes until the first re-ordering
     for (int s = 0; s < 2 && e == cudaSuccess; ++s)
         if (ctx->occw[s]) e = cudaMemsetAsync(ctx->occw[s], 0, occ_bytes, ctx->stream);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+        if (ctx->arow[s]) e = cudaMemsetAsync(ctx->arow[s], 0, arow_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->blk_done, 0, (size_t)n_lb_blocks * sizeof(uint32_t), ctx->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b)
         e = cudaMemsetAsync(ctx->fcons4[b], 0, (size_t)maxp * 4 * rs, ctx->stream);
@@ -262,6 +288,14 @@ lbmd_status lbmd_destroy(lbmd_ctx *ctx) {
     free_all(ctx);
     delete ctx;
     return LBMD_OK;
+}
+
+static void drop_cycle_graphs(lbmd_ctx *ctx) {
+    for (int i = 0; i < 16; ++i)
+        if (ctx->cycle_graph[i]) {
+            cudaGraphExecDestroy(ctx->cycle_graph[i]);
+            ctx->cycle_graph[i] = nullptr;
+        }
 }
 
 // The LJ neighbour lists, allocated when LJ forces are first switched on.
@@ -329,22 +363,15 @@ lbmd_status lbmd_add_particles(lbmd_ctx *ctx, int64_t n, const double *pos, cons
     CK(ctx, cudaMemsetAsync((char *)ctx->fc4[ctx->pcur] + ctx->np * 4 * rs, 0, n * 4 * rs, ctx->stream));
     ctx->np += n;
     CK(ctx, invalidate_nb_lists(ctx));
+    // re-order now, so that every particle sits in the row bucket of its cell
+    // (the MD kernels of variant B walk the buckets; the active nodes stay
+    // those of the last LB step until the next one)
+    CK(ctx, launch_sort_particles(ctx));
+    CK(ctx, md_tile_build_table(ctx, (int)(ctx->lb_step & 1)));
     if (has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 4; ++i)
-        if (ctx->cycle_graph[i]) {
-            cudaGraphExecDestroy(ctx->cycle_graph[i]);
-            ctx->cycle_graph[i] = nullptr;
-        }
+    drop_cycle_graphs(ctx);
     return LBMD_OK;
-}
-
-static void drop_cycle_graphs(lbmd_ctx *ctx) {
-    for (int i = 0; i < 4; ++i)
-        if (ctx->cycle_graph[i]) {
-            cudaGraphExecDestroy(ctx->cycle_graph[i]);
-            ctx->cycle_graph[i] = nullptr;
-        }
 }
 
 static lbmd_status add_bonds_of_kind(lbmd_ctx *ctx, int64_t nb, const int64_t *pairs, double k, double r0,
@@ -474,33 +501,43 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
     if (!ctx || n < 0) return LBMD_ERR_ARG;
     if (ctx->sub_done != 0) return fail(ctx, LBMD_ERR_SEQUENCE, "run_cycles must start at a cycle boundary");
     for (int64_t c = 0; c < n; ++c) {
-        const int parity = ctx->cur | (int)((ctx->lb_step & 1) << 1);
-        if (!ctx->cycle_graph[parity]) {
-            // capture one cycle starting from this population buffer
+        // the launches of a cycle depend on the buffer state it starts from
+        const int key = ctx->cur | (int)((ctx->lb_step & 1) << 1) | (ctx->pcur << 2) | (ctx->pv << 3);
+        if (!ctx->cycle_graph[key]) {
+            // capture one cycle starting from this state
             cudaGraph_t g = nullptr;
             CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
-            const int cur0 = ctx->cur, pcur0 = ctx->pcur;
+            const int cur0 = ctx->cur, pcur0 = ctx->pcur, pv0 = ctx->pv, rec0 = ctx->rec;
             for (int s = 0; s < ctx->p.n_sub && e == cudaSuccess; ++s) e = launch_md_substep(ctx, s);
             if (e == cudaSuccess) e = launch_lb_step(ctx);
-            ctx->cur = cur0;  // the launchers flipped the buffers during capture
+            // the launchers flipped the buffers during capture: keep the state
+            // the cycle leaves, then restore the starting one
+            ctx->cycle_post[key][0] = ctx->cur;
+            ctx->cycle_post[key][1] = ctx->pcur;
+            ctx->cycle_post[key][2] = ctx->pv;
+            ctx->cur = cur0;
             ctx->pcur = pcur0;
+            ctx->pv = pv0;
+            ctx->rec = rec0;
             cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
             if (e != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
                 return cuda_fail(ctx, e, "capture");
             }
             if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&ctx->cycle_graph[parity], g, 0);
+            e = cudaGraphInstantiate(&ctx->cycle_graph[key], g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) {
-                ctx->cycle_graph[parity] = nullptr;
+                ctx->cycle_graph[key] = nullptr;
                 return cuda_fail(ctx, e, "cudaGraphInstantiate");
             }
         }
-        CK(ctx, cudaGraphLaunch(ctx->cycle_graph[parity], ctx->stream));
-        ctx->cur ^= 1;
-        ctx->pcur ^= 1;
+        CK(ctx, cudaGraphLaunch(ctx->cycle_graph[key], ctx->stream));
+        ctx->cur = ctx->cycle_post[key][0];
+        ctx->pcur = ctx->cycle_post[key][1];
+        ctx->pv = ctx->cycle_post[key][2];
+        ctx->rec = 0;
         ctx->lb_step += 1;
         ctx->md_step += ctx->p.n_sub;
     }
@@ -511,11 +548,14 @@ lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
     LBMD_TRACE("lbmd_observables");
     if (!ctx || !out) return LBMD_ERR_ARG;
     double h[8];
-    int32_t range = 0;
+    int32_t range = 0, dev_error = 0;
     CK(ctx, launch_observables(ctx));
     CK(ctx, cudaMemcpyAsync(h, ctx->red_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(&range, ctx->range_flag, sizeof(range), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(&dev_error, ctx->dev_error, sizeof(dev_error), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (dev_error)
+        return fail(ctx, LBMD_ERR_CUDA, "a kernel's bounded wait for its own bulk copies gave up: results are invalid");
     out->mass = h[0];
     for (int d = 0; d < 3; ++d) {
         out->p_fluid[d] = h[1 + d];
@@ -732,8 +772,8 @@ lbmd_status lbmd_save_state(lbmd_ctx *ctx, void *buf, int64_t bytes) {
     CK(ctx, cudaMemcpy(o, ctx->f[ctx->cur], (size_t)19 * ctx->N * pop_size(ctx), cudaMemcpyDeviceToHost));
     o += L.pops;
     if (np) {
-        CK(ctx, cudaMemcpy(o, ctx->pos4[b], rb, cudaMemcpyDeviceToHost));
-        CK(ctx, cudaMemcpy(o + rb, ctx->vel4[b], rb, cudaMemcpyDeviceToHost));
+        CK(ctx, cudaMemcpy(o, pos_now(ctx), rb, cudaMemcpyDeviceToHost));
+        CK(ctx, cudaMemcpy(o + rb, vel_now(ctx), rb, cudaMemcpyDeviceToHost));
         CK(ctx, cudaMemcpy(o + 2 * rb, ctx->fc4[b], rb, cudaMemcpyDeviceToHost));
         o += L.recs;
         CK(ctx, cudaMemcpy(o, ctx->pid[b], np * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -787,8 +827,8 @@ lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes) {
     CK(ctx, cudaMemcpy(ctx->f[ctx->cur], in, (size_t)19 * ctx->N * pop_size(ctx), cudaMemcpyHostToDevice));
     in += L.pops;
     if (np) {
-        CK(ctx, cudaMemcpy(ctx->pos4[b], in, rb, cudaMemcpyHostToDevice));
-        CK(ctx, cudaMemcpy(ctx->vel4[b], in + rb, rb, cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(pos_now(ctx), in, rb, cudaMemcpyHostToDevice));
+        CK(ctx, cudaMemcpy(vel_now(ctx), in + rb, rb, cudaMemcpyHostToDevice));
         CK(ctx, cudaMemcpy(ctx->fc4[b], in + 2 * rb, rb, cudaMemcpyHostToDevice));
         in += L.recs;
         CK(ctx, cudaMemcpy(ctx->pid[b], pid.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -827,6 +867,9 @@ lbmd_status lbmd_load_state(lbmd_ctx *ctx, const void *buf, int64_t bytes) {
     CK(ctx, cudaMemset(ctx->range_flag, 0, sizeof(int32_t)));
     CK(ctx, launch_node_moments(ctx, false));
     CK(ctx, launch_clear_transfer(ctx));
+    // every particle into the row bucket of its cell (see lbmd_add_particles)
+    if (ctx->np > 0) CK(ctx, launch_sort_particles(ctx));
+    CK(ctx, md_tile_build_table(ctx, (int)(ctx->lb_step & 1)));
     if (ctx->np > 0 && has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     drop_cycle_graphs(ctx);

@@ -15,8 +15,9 @@
 //   transfers).  Results do not depend on the order: every per-particle
 //   quantity is keyed by the particle id, and transfers are integer sums.
 //   pos4[2]     per slot: fractional position in its cell (x, y, z) and the
-//               linear cell index (two buffers: the re-ordering copies).
-//   vel4[2]     per slot: velocity (x, y, z) and 1 / mass.
+//               linear cell index (two buffers, current one pv: the
+//               re-ordering and the tiled variant-B MD step write the other).
+//   vel4[2]     per slot: velocity (x, y, z) and 1 / mass (same buffers).
 //   fcons4[2]   per slot: bond force at the current positions.
 //   pid[2]      per slot: particle id.   slot_of: per id, its slot.
 //   fc4         per slot: coupling force F of the current MD step.
@@ -28,10 +29,14 @@
 //   occw        variant B: the active nodes (corners of the particles' cells
 //               at the last re-ordering), per row and 32-node word the bits
 //               and the compact slot of the word's first active node.
-//   cact        variant B: compact node records of the active nodes.  For an
-//               active node the compact record, not `node`, is current
-//               between LB updates; `node` is brought up to date from it only
-//               for the observables and the host accessors.
+//   cact        variant B: compact node records of the active nodes, two
+//               buffers per active set (the current one `rec`; the tiled MD
+//               step reads one and writes the other).  For an active node
+//               the compact record, not `node`, is current between LB
+//               updates; `node` is brought up to date from it only for the
+//               observables and the host accessors.
+//   arow        variant B, per active set: compact slot of every row's first
+//               record (rows + 1 entries, the last the total).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -109,7 +114,8 @@ struct lbmd_ctx {
     void *f[2];
     void *node;
     void *jacc;
-    int pcur;  // index of the particle buffers in use
+    int pcur;  // index of the particle buffers in use (ids, forces)
+    int pv;    // index of the position / velocity buffers in use
     void *pos4[2], *vel4[2], *fcons4[2];
     int32_t *pid[2];
     int32_t *slot_of;
@@ -123,8 +129,17 @@ struct lbmd_ctx {
     // s & 1 (built at the end of cycle s - 1); the LB step of cycle s reads
     // set s & 1 and writes the new moments into set (s + 1) & 1
     uint2 *occw[2];      // (ny * nz) x active_words(nx) words
-    void *cact[2];       // compact node records, cact_cap of them
+    void *cact[2];       // compact node records: two buffers of cact_cap each
+    int32_t *arow[2];    // first compact slot of every row, ny * nz + 1 entries
+    void *tile_table[2]; // per active set: the tiled MD step's table of every tile (md_tile.cu)
+    void *edge_acc;      // tiled MD step: transfers into the rows above each tile, per compact slot (zero
+                         // between MD steps)
+    uint32_t *tile_flag; // tiled MD step: per tile, the MD step (+ 1) whose particles are done
+    int32_t *late_rows;  // tiled MD step: rows left to the follow-up, two lists by MD-step parity
+    int32_t *late_count;
     int64_t cact_cap;
+    size_t node_bytes;   // bytes of one node record
+    int rec;             // record buffer of the current set in use (0 after every LB step)
     // LB collide with fused post-stream moments: per collide block the LB step
     // (+1) it last pushed, and the rows whose moments the fallback computes
     uint32_t *blk_done;
@@ -153,6 +168,7 @@ struct lbmd_ctx {
     // range guard of the fixed-point momentum: set (sticky) by the kernels
     // that write a node record whose momentum reaches half the range
     int32_t *range_flag;
+    int32_t *dev_error;  // set by a kernel whose bounded wait gave up
     FixUnit fix;
     int red_blocks;
     unsigned long long *d_lb_step;  // LB step counter read by the kernels
@@ -161,18 +177,28 @@ struct lbmd_ctx {
     int sub_done;
     LbCoeffs co;
     double dt;
-    // one captured cycle per (population buffer, LB step parity); the two
-    // flip together, so two of the four are used
-    cudaGraphExec_t cycle_graph[4];
+    // captured cycles, keyed by the buffer state at the start of the cycle
+    // (population buffer, LB step parity, particle buffers, position buffer),
+    // each with the buffer state it leaves
+    cudaGraphExec_t cycle_graph[16];
+    int cycle_post[16][3];  // cur, pcur, pv after the cycle
     std::string err;
 };
 
 // The active-node set the MD steps of the current LB cycle use, and the one
 // the coming LB step fills.
 inline uint2 *active_words_now(const lbmd_ctx *c) { return c->occw[c->lb_step & 1]; }
-inline void *active_records_now(const lbmd_ctx *c) { return c->cact[c->lb_step & 1]; }
+inline void *active_records_now(const lbmd_ctx *c) {
+    return static_cast<char *>(c->cact[c->lb_step & 1]) + (size_t)c->rec * c->cact_cap * c->node_bytes;
+}
+// the other record buffer of the current set (written by the tiled MD step)
+inline void *active_records_other(const lbmd_ctx *c) {
+    return static_cast<char *>(c->cact[c->lb_step & 1]) + (size_t)(c->rec ^ 1) * c->cact_cap * c->node_bytes;
+}
 inline uint2 *active_words_next(const lbmd_ctx *c) { return c->occw[(c->lb_step + 1) & 1]; }
 inline void *active_records_next(const lbmd_ctx *c) { return c->cact[(c->lb_step + 1) & 1]; }
+inline void *pos_now(const lbmd_ctx *c) { return c->pos4[c->pv]; }
+inline void *vel_now(const lbmd_ctx *c) { return c->vel4[c->pv]; }
 
 // Default poll limit of a collide block's wait for its neighbour blocks
 // before it leaves its row's fused moments to the follow-up kernel (64 ns per
@@ -205,6 +231,16 @@ cudaError_t launch_sort_particles(lbmd_ctx *ctx);
 cudaError_t launch_active_set(lbmd_ctx *ctx);
 cudaError_t launch_active_sync(lbmd_ctx *ctx);
 cudaError_t setup_particle_kernels(lbmd_ctx *ctx);
+// the tiled variant-B MD step (md_tile.cu)
+bool md_tile_geometry(const lbmd_ctx *ctx);
+int md_tile_count(const lbmd_ctx *ctx);
+size_t md_tile_table_bytes(const lbmd_ctx *ctx);
+size_t md_tile_edge_bytes(const lbmd_ctx *ctx);
+int md_tile_late_cap(const lbmd_ctx *ctx);
+cudaError_t md_tile_build_table(lbmd_ctx *ctx, int set);
+bool md_tile_supported(const lbmd_ctx *ctx);
+bool md_tile_expected_to_fit(const lbmd_ctx *ctx);
+cudaError_t md_tile_setup_kernels(lbmd_ctx *ctx);
 
 // message returned by lbmd_last_error(NULL) (calls without a context)
 void lbmd_set_global_error(const std::string &msg);

@@ -158,7 +158,7 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     observe_particles_kernel<T><<<B, RED_THREADS, 0, ctx->stream>>>(
-        static_cast<const typename P::real4 *>(ctx->vel4[ctx->pcur]), ctx->slot_of, ctx->np, ctx->red_partial);
+        static_cast<const typename P::real4 *>(vel_now(ctx)), ctx->slot_of, ctx->np, ctx->red_partial);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     observe_final_kernel<T><<<1, 32 * RED_COLS, 0, ctx->stream>>>(ctx->red_partial, B, ctx->fix.inv_scale,
@@ -376,12 +376,12 @@ cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t c
     const int assign = set_mass ? 1 : 0;  // only lbmd_add_particles sets masses
     if (ctx->p.precision == LBMD_FP64)
         particles_from_double_kernel<double><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<Prec<double>::real4 *>(ctx->pos4[b]), static_cast<Prec<double>::real4 *>(ctx->vel4[b]),
+            static_cast<Prec<double>::real4 *>(pos_now(ctx)), static_cast<Prec<double>::real4 *>(vel_now(ctx)),
             ctx->pid[b], ctx->slot_of, first, count, pos, vel, mass, set_pos, set_vel, set_mass, assign, ctx->p.nx,
             ctx->p.ny, ctx->p.nz);
     else
         particles_from_double_kernel<float><<<nblocks(count), 256, 0, ctx->stream>>>(
-            static_cast<Prec<float>::real4 *>(ctx->pos4[b]), static_cast<Prec<float>::real4 *>(ctx->vel4[b]),
+            static_cast<Prec<float>::real4 *>(pos_now(ctx)), static_cast<Prec<float>::real4 *>(vel_now(ctx)),
             ctx->pid[b], ctx->slot_of, first, count, pos, vel, mass, set_pos, set_vel, set_mass, assign, ctx->p.nx,
             ctx->p.ny, ctx->p.nz);
     return cudaGetLastError();
@@ -389,16 +389,15 @@ cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t c
 
 cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel) {
     if (ctx->np <= 0) return cudaSuccess;
-    const int b = ctx->pcur;
     if (ctx->p.precision == LBMD_FP64)
         particles_to_double_kernel<double><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
-            static_cast<const Prec<double>::real4 *>(ctx->pos4[b]),
-            static_cast<const Prec<double>::real4 *>(ctx->vel4[b]), ctx->slot_of, ctx->np, pos, vel, ctx->p.nx,
+            static_cast<const Prec<double>::real4 *>(pos_now(ctx)),
+            static_cast<const Prec<double>::real4 *>(vel_now(ctx)), ctx->slot_of, ctx->np, pos, vel, ctx->p.nx,
             ctx->p.ny);
     else
         particles_to_double_kernel<float><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
-            static_cast<const Prec<float>::real4 *>(ctx->pos4[b]),
-            static_cast<const Prec<float>::real4 *>(ctx->vel4[b]),
+            static_cast<const Prec<float>::real4 *>(pos_now(ctx)),
+            static_cast<const Prec<float>::real4 *>(vel_now(ctx)),
             ctx->slot_of, ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
     return cudaGetLastError();
 }

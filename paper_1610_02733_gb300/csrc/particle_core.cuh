@@ -50,10 +50,13 @@ __device__ __forceinline__ void corner_rows(const CellXYZ &c, int ny, int nz, ui
     rows[3] = (uint32_t)y1 + (uint32_t)ny * (uint32_t)z1;
 }
 
-// Move a fractional coordinate by d and carry whole cells into the index.
+// Move a fractional coordinate by dt v and carry whole cells into the index.
+// The drift frac + dt v is one explicit fused multiply-add, so every kernel
+// that moves particles rounds it the same way whatever the compiler would
+// contract.
 template <typename T>
-__device__ __forceinline__ void advance(T &frac, int &c, T d, int n) {
-    T x = frac + d;
+__device__ __forceinline__ void advance(T &frac, int &c, T dt, T v, int n) {
+    T x = fma(dt, v, frac);
     T s = floor(x);
     x -= s;
     if (x >= T(1)) {  // a tiny negative offset rounded up to the next node

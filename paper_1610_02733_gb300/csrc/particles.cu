@@ -37,158 +37,17 @@
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
 #include "particle_core.cuh"
+#include "particle_step.cuh"
+
+// the tiled variant-B MD step (md_tile.cu)
+namespace lbmd {
+template <typename T>
+struct PArgs;
+}
+template <typename T>
+cudaError_t md_tile_step(lbmd_ctx *ctx, const lbmd::PArgs<T> &a);
 
 namespace lbmd {
-
-template <typename T>
-struct PArgs {
-    using P = Prec<T>;
-    typename P::real4 *pos4, *vel4, *fc4, *old4, *fcons4;
-    const int32_t *pid, *slot_of;
-    typename P::node4 *node, *jacc;
-    const int32_t *bond_count, *bond_partner;
-    const double *bond_k, *bond_r0;
-    const uint8_t *bond_kind;
-    T lj_eps24, lj_sig2, lj_rc2;  // Lennard-Jones: 24 eps, sigma^2, r_cut^2
-    float lj_filter2;             // (r_cut + rounding margin of FP32 absolute positions)^2
-    // LJ Verlet lists (null when LJ is off)
-    const int32_t *nb_list, *nb_count;
-    int32_t *nb_invalid;
-    const typename P::real4 *nb_ref4;  // positions at the list build, per id
-    T nb_half_skin2;                   // (skin / 2)^2: a larger move since the build voids the lists
-    int nx, ny, nz;
-    FastDiv fd_nx, fd_ny;  // division by nx and ny
-    int64_t np;
-    T zeta, dt, half_dt, amp;
-    T neg_scale_dt;  // -dt times the fixed-point scale s: -s (dt F) = F neg_scale_dt exactly
-    T fis;           // 1 / s: fixed-point momentum -> real
-    uint32_t key0, key1;
-    const unsigned long long *lb_step;
-    int n_sub, substep, noisy;
-    int mig_par;  // parity of the MD step (lb_step n_sub + substep): which migrant list is filled
-    int variant;
-    // variant B row-gather spreading and active nodes
-    const int32_t *row_start, *slot_row;
-    const uint2 *occw;
-    typename P::node4 *cact;
-    int occ_words;
-    int32_t *migrant_slot, *migrant_count;  // two lists of np_cap slots, two counters
-    int b_atomic;      // variant B spreads every particle with atomics (no row gather, no migrant lists)
-    int kick_spreads;  // ... and the bond / pair kernel does it, after every particle has read the nodes
-    int64_t np_cap;
-};
-
-// Variant B: the records of corners 2q, 2q+1 (nodes x0 and x0 + 1 of row
-// `row`): compact record of an active node, node field entry otherwise.
-template <typename T>
-__device__ __forceinline__ void corner_pair(const PArgs<T> &a, uint32_t row, int x0, int x1,
-                                            typename Prec<T>::node4 &n0, typename Prec<T>::node4 &n1) {
-    const uint2 *wr = a.occw + (size_t)row * (uint32_t)a.occ_words;
-    const uint2 w0 = wr[x0 >> 5];
-    const uint2 w1 = (x1 >> 5) == (x0 >> 5) ? w0 : wr[x1 >> 5];
-    const int s0 = active_slot(w0, x0), s1 = active_slot(w1, x1);
-    const size_t r0 = (size_t)row * (uint32_t)a.nx;
-    n0 = s0 >= 0 ? a.cact[s0] : a.node[r0 + x0];
-    n1 = s1 >= 0 ? a.cact[s1] : a.node[r0 + x1];
-}
-
-// Fluid velocity at a particle in cell c with fractional offsets (fx, fy, fz),
-// Eq. (5): corners k = ox + 2 oy + 4 oz = 0..7 with weights delta_k = wx wy wz;
-// variant B reads an active corner's compact record.
-template <typename T>
-__device__ __forceinline__ void interp_u(const PArgs<T> &a, const CellXYZ &c, T fx, T fy, T fz, T &ux, T &uy,
-                                         T &uz) {
-    using P = Prec<T>;
-    ux = T(0);
-    uy = T(0);
-    uz = T(0);
-    uint32_t rows[4];
-    corner_rows(c, a.ny, a.nz, rows);
-    const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
-    const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        typename P::node4 n[2];
-        if (a.variant == LBMD_VARIANT_B) {
-            corner_pair(a, rows[q], c.x, x1, n[0], n[1]);
-        } else {
-            const size_t r0 = (size_t)rows[q] * (uint32_t)a.nx;
-            n[0] = a.node[r0 + c.x];
-            n[1] = a.node[r0 + x1];
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const T w = (wx[h] * wy[q & 1] * wz[q >> 1]) / P::rho_of(n[h]);
-            ux += w * P::from_fix(P::jx_of(n[h]), a.fis);
-            uy += w * P::from_fix(P::jy_of(n[h]), a.fis);
-            uz += w * P::from_fix(P::jz_of(n[h]), a.fis);
-        }
-    }
-}
-
-// Coupling force of Eq. (4) without the conservative part: friction against
-// the interpolated fluid velocity plus the random force of Philox(id, s, 1, 0).
-template <typename T>
-__device__ __forceinline__ void coupling_force(const PArgs<T> &a, int64_t p, const typename Prec<T>::real4 &V, T ux,
-                                               T uy, T uz, T &Fx, T &Fy, T &Fz) {
-    Fx = -a.zeta * (V.x - ux);
-    Fy = -a.zeta * (V.y - uy);
-    Fz = -a.zeta * (V.z - uz);
-    if (a.noisy) {
-        const uint32_t md_step = (uint32_t)((*a.lb_step) * (unsigned long long)a.n_sub + (unsigned)a.substep);
-        const U4 r = philox4x32_10(U4{(uint32_t)a.pid[p], md_step, 1u, 0u}, a.key0, a.key1);
-        Fx += a.amp * unit_uniform<T>(r.x);
-        Fy += a.amp * unit_uniform<T>(r.y);
-        Fz += a.amp * unit_uniform<T>(r.z);
-    }
-}
-
-// Newton's third law for the particle in slot p whose transfer -delta_k dt F
-// belongs to the nodes around position R (cell c): variants A and C add it to
-// J_acc at once (nothing reads J_acc during the MD step; C then moves it into
-// the populations, forcing_update_kernel); variant B keeps R for the row
-// gather, and a particle whose cell row is no longer the row bucket it was
-// sorted into is listed as a migrant (two lists alternating with the parity
-// of the MD step).
-template <typename T>
-__device__ __forceinline__ void hand_over(const PArgs<T> &a, int64_t p, const typename Prec<T>::real4 &R,
-                                          const CellXYZ &c, T Fx, T Fy, T Fz) {
-    using P = Prec<T>;
-    if (a.variant != LBMD_VARIANT_B) {
-        uint32_t idx[8];
-        T delta[8];
-        corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
-        spread_to<T>(a.jacc, idx, delta, Fx * a.neg_scale_dt, Fy * a.neg_scale_dt, Fz * a.neg_scale_dt);
-    } else {
-        a.old4[p] = R;
-        if (a.b_atomic) return;
-        const int32_t srow = a.slot_row[p];
-        if (srow < 0 || (uint32_t)P::cell_of(R) - (uint32_t)srow * (uint32_t)a.nx >= (uint32_t)a.nx) {
-            a.migrant_slot[(int64_t)a.mig_par * a.np_cap + atomicAdd(a.migrant_count + a.mig_par, 1)] = (int32_t)p;
-        }
-    }
-}
-
-// Cell offset d (partner minus particle, |d| < n) to its periodic image
-// nearest to zero, in [-n/2, n/2].
-__device__ __forceinline__ int nearest_image(int d, int n) {
-    const int h = n >> 1;
-    return d > h ? d - n : (d < -h ? d + n : d);
-}
-
-// LJ Verlet lists: a particle that moved more than half the skin since the
-// lists were built voids them (flag read by the pair kernel of this step).
-template <typename T>
-__device__ __forceinline__ void check_list_skin(const PArgs<T> &a, int64_t p, const CellXYZ &cn, T fx, T fy, T fz) {
-    using P = Prec<T>;
-    if (!a.nb_ref4 || *a.nb_invalid) return;
-    const typename P::real4 S = a.nb_ref4[a.pid[p]];
-    const CellXYZ d = cell_xyz(P::cell_of(S), a.fd_nx, a.fd_ny);
-    const T dx = T(nearest_image(cn.x - d.x, a.nx)) + (fx - S.x);
-    const T dy = T(nearest_image(cn.y - d.y, a.ny)) + (fy - S.y);
-    const T dz = T(nearest_image(cn.z - d.z, a.nz)) + (fz - S.z);
-    if (dx * dx + dy * dy + dz * dz > a.nb_half_skin2) atomicOr(a.nb_invalid, 1);
-}
 
 // One MD step, coupling force from the start of the step (integrator START):
 // F = -zeta (v - u(R)) + F_rand with R, v of the beginning of the step
@@ -219,18 +78,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PAr
         Gy += Fc.y;
         Gz += Fc.z;
     }
-    V.x += hm * Gx;
-    V.y += hm * Gy;
-    V.z += hm * Gz;
+    V.x = fma(hm, Gx, V.x);
+    V.y = fma(hm, Gy, V.y);
+    V.z = fma(hm, Gz, V.z);
     T fx = R.x, fy = R.y, fz = R.z;
     int cx = c.x, cy = c.y, cz = c.z;
-    advance(fx, cx, a.dt * V.x, a.nx);
-    advance(fy, cy, a.dt * V.y, a.ny);
-    advance(fz, cz, a.dt * V.z, a.nz);
+    advance(fx, cx, a.dt, V.x, a.nx);
+    advance(fy, cy, a.dt, V.y, a.ny);
+    advance(fz, cz, a.dt, V.z, a.nz);
     if (!BONDS) {
-        V.x += hm * Fx;
-        V.y += hm * Fy;
-        V.z += hm * Fz;
+        V.x = fma(hm, Fx, V.x);
+        V.y = fma(hm, Fy, V.y);
+        V.z = fma(hm, Fz, V.z);
     }
     if (BONDS) check_list_skin(a, p, CellXYZ{cx, cy, cz}, fx, fy, fz);
     a.pos4[p] = P::make_pos(fx, fy, fz, cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz));
@@ -260,23 +119,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_half_kerne
         G.y += Fc.y;
         G.z += Fc.z;
     }
-    V.x += hm * G.x;
-    V.y += hm * G.y;
-    V.z += hm * G.z;
+    V.x = fma(hm, G.x, V.x);
+    V.y = fma(hm, G.y, V.y);
+    V.z = fma(hm, G.z, V.z);
     T fx = R.x, fy = R.y, fz = R.z;
     CellXYZ cn = c;
-    advance(fx, cn.x, a.dt * V.x, a.nx);
-    advance(fy, cn.y, a.dt * V.y, a.ny);
-    advance(fz, cn.z, a.dt * V.z, a.nz);
+    advance(fx, cn.x, a.dt, V.x, a.nx);
+    advance(fy, cn.y, a.dt, V.y, a.ny);
+    advance(fz, cn.z, a.dt, V.z, a.nz);
     const typename P::real4 Rn = P::make_pos(fx, fy, fz, cn.x + (int64_t)a.nx * (cn.y + (int64_t)a.ny * cn.z));
     if (BONDS) check_list_skin(a, p, cn, fx, fy, fz);
     T ux, uy, uz, Fx, Fy, Fz;
     interp_u(a, cn, fx, fy, fz, ux, uy, uz);
     coupling_force(a, p, V, ux, uy, uz, Fx, Fy, Fz);
     if (!BONDS) {
-        V.x += hm * Fx;
-        V.y += hm * Fy;
-        V.z += hm * Fz;
+        V.x = fma(hm, Fx, V.x);
+        V.y = fma(hm, Fy, V.y);
+        V.z = fma(hm, Fz, V.z);
     }
     a.pos4[p] = Rn;
     a.vel4[p] = V;
@@ -428,50 +287,9 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) spread_rows_kernel(PArgs<T>
 }
 
 // Variant B: the migrants of this MD step, spread with atomics once the row
-// gather is done (into the compact record of an active corner, the node
-// field entry of an inactive one).  With `all`, every particle is spread this
-// way and the row gather does not run (LBMD_SPREAD_ATOMIC).
-template <typename T>
-__device__ __forceinline__ void spread_corner_atomic(const PArgs<T> &a, int64_t p, int k) {
-    using P = Prec<T>;
-    const typename P::real4 R = a.old4[p];
-    const typename P::real4 F = a.fc4[p];
-    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
-    const int ox = k & 1, oy = (k >> 1) & 1, oz = k >> 2;
-    const int xn = ox ? (c.x + 1 == a.nx ? 0 : c.x + 1) : c.x;
-    const int yn = oy ? (c.y + 1 == a.ny ? 0 : c.y + 1) : c.y;
-    const int zn = oz ? (c.z + 1 == a.nz ? 0 : c.z + 1) : c.z;
-    const T delta = (ox ? R.x : T(1) - R.x) * (oy ? R.y : T(1) - R.y) * (oz ? R.z : T(1) - R.z);
-    const uint32_t row = (uint32_t)yn + (uint32_t)a.ny * (uint32_t)zn;
-    const int sl = active_slot(a.occw[(size_t)row * (uint32_t)a.occ_words + (xn >> 5)], xn);
-    typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[(size_t)row * (uint32_t)a.nx + xn];
-    const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
-    P::add_transfer(rec, P::to_fix_neg(delta, sx), P::to_fix_neg(delta, sy), P::to_fix_neg(delta, sz));
-}
-
-// All 8 corner transfers of the particle in slot p (position and force read
-// and the cell decoded once).
-template <typename T>
-__device__ __forceinline__ void spread_particle_atomic(const PArgs<T> &a, int64_t p) {
-    using P = Prec<T>;
-    const typename P::real4 R = a.old4[p];
-    const typename P::real4 F = a.fc4[p];
-    const CellXYZ c = cell_xyz(P::cell_of(R), a.fd_nx, a.fd_ny);
-    uint32_t idx[8], rows[4];
-    T delta[8];
-    corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
-    corner_rows(c, a.ny, a.nz, rows);
-    const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
-    const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int xn = (k & 1) ? x1 : c.x;
-        const int sl = active_slot(a.occw[(size_t)rows[k >> 1] * (uint32_t)a.occ_words + (xn >> 5)], xn);
-        typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[idx[k]];
-        P::add_transfer(rec, P::to_fix_neg(delta[k], sx), P::to_fix_neg(delta[k], sy), P::to_fix_neg(delta[k], sz));
-    }
-}
-
+// gather is done (spread_particle_atomic, particle_step.cuh).  With `all`,
+// every particle is spread this way and the row gather does not run
+// (LBMD_SPREAD_ATOMIC).
 template <typename T>
 __global__ void __launch_bounds__(256) migrant_spread_kernel(PArgs<T> a, int all) {
     using P = Prec<T>;
@@ -551,9 +369,9 @@ __global__ void __launch_bounds__(256) bond_kick_kernel(PArgs<T> a) {
         typename P::real4 V = a.vel4[p];
         const typename P::real4 Fc = a.fc4[p];
         const T hm = a.half_dt * V.w;
-        V.x += hm * (Fx + Fc.x);
-        V.y += hm * (Fy + Fc.y);
-        V.z += hm * (Fz + Fc.z);
+        V.x = fma(hm, Fx + Fc.x, V.x);
+        V.y = fma(hm, Fy + Fc.y, V.y);
+        V.z = fma(hm, Fz + Fc.z, V.z);
         a.vel4[p] = V;
         // variant B, all atomics: every particle has read the nodes (couple
         // kernel), so the transfers can go in now
@@ -712,9 +530,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_kick_kernel(PArgs<T> a) {
         typename P::real4 V = a.vel4[p];
         const typename P::real4 Fc = a.fc4[p];
         const T hm = a.half_dt * V.w;
-        V.x += hm * (Fx + Fc.x);
-        V.y += hm * (Fy + Fc.y);
-        V.z += hm * (Fz + Fc.z);
+        V.x = fma(hm, Fx + Fc.x, V.x);
+        V.y = fma(hm, Fy + Fc.y, V.y);
+        V.z = fma(hm, Fz + Fc.z, V.z);
         a.vel4[p] = V;
     }
 }
@@ -963,7 +781,7 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS)
 // within chunks of 1024 rows): the first slot of every row, added to the
 // in-row slots of its words.
 __global__ void __launch_bounds__(1024) active_finalize_kernel(const int32_t *row_offset, const int32_t *chunk_total,
-                                                               int64_t n_rows, uint2 *occw, int W) {
+                                                               int64_t n_rows, uint2 *occw, int W, int32_t *arow) {
     int32_t before;
     const int32_t v = (int)threadIdx.x < (int)blockIdx.x ? chunk_total[threadIdx.x] : 0;
     block_exclusive_scan(v, &before);  // total of the first blockIdx.x chunks
@@ -972,6 +790,12 @@ __global__ void __launch_bounds__(1024) active_finalize_kernel(const int32_t *ro
     const uint32_t b = (uint32_t)(before + row_offset[i]);
     uint2 *wr = occw + (size_t)i * W;
     for (int w = 0; w < W; ++w) wr[w].y += b;
+    // the row's first compact slot; the last row also closes the table
+    arow[i] = (int32_t)b;
+    if (i == n_rows - 1) {
+        const uint2 last = wr[W - 1];
+        arow[n_rows] = (int32_t)(last.y + __popc(last.x));
+    }
 }
 
 // Node field entries of the active nodes brought up to date from their
@@ -1005,7 +829,9 @@ static cudaError_t setup_t(lbmd_ctx *ctx) {
     const size_t smem = gather_smem_bytes<T>(ctx, warps);
     if (smem > (size_t)200 * 1024) return cudaErrorInvalidValue;
     ctx->gather_warps = warps;
-    return cudaFuncSetAttribute(spread_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(spread_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return md_tile_setup_kernels(ctx);
 }
 
 template <typename T>
@@ -1013,8 +839,8 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     using P = Prec<T>;
     const int b = ctx->pcur;
     PArgs<T> a;
-    a.pos4 = static_cast<typename P::real4 *>(ctx->pos4[b]);
-    a.vel4 = static_cast<typename P::real4 *>(ctx->vel4[b]);
+    a.pos4 = static_cast<typename P::real4 *>(pos_now(ctx));
+    a.vel4 = static_cast<typename P::real4 *>(vel_now(ctx));
     a.fcons4 = static_cast<typename P::real4 *>(ctx->fcons4[b]);
     a.pid = ctx->pid[b];
     a.slot_of = ctx->slot_of;
@@ -1089,7 +915,19 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
                                ctx->np < (int64_t)LBMD_SPREAD_ATOMIC_PER_ROW * ctx->p.ny * ctx->p.nz));
     a.b_atomic = atomic ? 1 : 0;
     a.kick_spreads = atomic && cons ? 1 : 0;
+    // the tiled step only on request: at the benchmark density it measured
+    // slower than the separate particle pass and row gather
+    const bool tiles = !atomic && md_tile_supported(ctx) && ctx->p.spread == LBMD_SPREAD_TILES;
     cudaError_t e;
+    if (tiles) {
+        // the whole MD step in one pass over tiles of rows (new positions,
+        // velocities and records into the other buffers) and a short
+        // follow-up (transfers across the periodic wrap, listed particles)
+        if ((e = md_tile_step<T>(ctx, a)) != cudaSuccess) return e;
+        ctx->pv ^= 1;
+        ctx->rec ^= 1;
+        return cudaSuccess;
+    }
     if (ctx->p.integrator == LBMD_INTEGRATOR_HALF_STEP) {
         if (cons)
             couple_half_kernel<T, true><<<blocks, 256, 0, ctx->stream>>>(a);
@@ -1146,12 +984,13 @@ template <typename T>
 static cudaError_t sort_t(lbmd_ctx *ctx) {
     using R4 = typename Prec<T>::real4;
     const int b = ctx->pcur, o = b ^ 1;
+    const int v = ctx->pv, vo = v ^ 1;  // position / velocity buffers
     const int64_t rows = (int64_t)ctx->p.ny * ctx->p.nz;
     cudaError_t e = cudaMemsetAsync(ctx->row_count, 0, (size_t)rows * sizeof(int32_t), ctx->stream);
     if (e != cudaSuccess) return e;
     if (ctx->np > 0) {
         const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
-        sort_count_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<const R4 *>(ctx->pos4[b]), ctx->np,
+        sort_count_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<const R4 *>(ctx->pos4[v]), ctx->np,
                                                                 make_fastdiv((uint32_t)ctx->p.nx), ctx->row_count,
                                                                 ctx->sort_rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1162,15 +1001,16 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
                                                                  ctx->row_start, (int32_t)ctx->np);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sort_scatter_kernel<T><<<blocks, 256, 0, ctx->stream>>>(
-            static_cast<const R4 *>(ctx->pos4[b]), static_cast<const R4 *>(ctx->vel4[b]),
+            static_cast<const R4 *>(ctx->pos4[v]), static_cast<const R4 *>(ctx->vel4[v]),
             static_cast<const R4 *>(ctx->fcons4[b]), static_cast<const R4 *>(ctx->fc4[b]), ctx->pid[b],
-            static_cast<R4 *>(ctx->pos4[o]), static_cast<R4 *>(ctx->vel4[o]), static_cast<R4 *>(ctx->fcons4[o]),
+            static_cast<R4 *>(ctx->pos4[vo]), static_cast<R4 *>(ctx->vel4[vo]), static_cast<R4 *>(ctx->fcons4[o]),
             static_cast<R4 *>(ctx->fc4[o]), ctx->pid[o], ctx->slot_of, ctx->slot_row, ctx->row_start,
             ctx->sort_rank, ctx->np, make_fastdiv((uint32_t)ctx->p.nx), has_cons(ctx) ? 1 : 0,
             ctx->p.integrator == LBMD_INTEGRATOR_HALF_STEP ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ctx->pcur = o;
+    ctx->pv = vo;
     return cudaSuccess;
 }
 
@@ -1179,17 +1019,22 @@ static cudaError_t active_set_t(lbmd_ctx *ctx) {
     const int64_t rows = (int64_t)ctx->p.ny * ctx->p.nz;
     const int W = active_words(ctx->p.nx);
     uint2 *occw = active_words_next(ctx);  // built for the coming LB cycle
-    if (ctx->np == 0) return cudaMemsetAsync(occw, 0, (size_t)rows * W * sizeof(uint2), ctx->stream);
+    int32_t *arow = ctx->arow[(ctx->lb_step + 1) & 1];
+    if (ctx->np == 0) {
+        cudaError_t e = cudaMemsetAsync(occw, 0, (size_t)rows * W * sizeof(uint2), ctx->stream);
+        if (e != cudaSuccess) return e;
+        return cudaMemsetAsync(arow, 0, (size_t)(rows + 1) * sizeof(int32_t), ctx->stream);
+    }
     const unsigned blocks = (unsigned)((rows + GATHER_WARPS - 1) / GATHER_WARPS);
     active_rows_kernel<T><<<blocks, 32 * GATHER_WARPS, GATHER_WARPS * W * sizeof(uint32_t), ctx->stream>>>(
-        static_cast<const typename Prec<T>::real4 *>(ctx->pos4[ctx->pcur]), ctx->row_start, ctx->p.nx,
+        static_cast<const typename Prec<T>::real4 *>(pos_now(ctx)), ctx->row_start, ctx->p.nx,
         make_fastdiv((uint32_t)ctx->p.ny), ctx->p.nz, W, occw, ctx->row_count, (int)rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int n_chunks = (int)((rows + 1023) / 1024);
     sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    active_finalize_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, ctx->chunk_total, rows, occw, W);
+    active_finalize_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, ctx->chunk_total, rows, occw, W, arow);
     return cudaGetLastError();
 }
 

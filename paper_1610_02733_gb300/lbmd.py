@@ -29,8 +29,8 @@ FP32, FP64, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_DEV}
 INTEGRATOR_START, INTEGRATOR_HALF_STEP = 0, 1
 INTEGRATORS = {"start": INTEGRATOR_START, "half_step": INTEGRATOR_HALF_STEP}
-SPREAD_AUTO, SPREAD_ROWS, SPREAD_ATOMIC = 0, 1, 2
-SPREADS = {"auto": SPREAD_AUTO, "rows": SPREAD_ROWS, "atomic": SPREAD_ATOMIC}
+SPREAD_AUTO, SPREAD_ROWS, SPREAD_ATOMIC, SPREAD_TILES = 0, 1, 2, 3
+SPREADS = {"auto": SPREAD_AUTO, "rows": SPREAD_ROWS, "atomic": SPREAD_ATOMIC, "tiles": SPREAD_TILES}
 
 # every symbol include/lbmd.h declares
 EXPORTS = (
@@ -268,7 +268,7 @@ class LBMD:
     state, FP32 arithmetic); ``variant`` is ``"A"``, ``"B"`` or ``"C"``;
     ``integrator`` is ``"start"`` (coupling force from the start of the MD
     step, Eq. (6)) or ``"half_step"`` (from the half-step velocity after the
-    drift); ``spread`` (variant B) is ``"auto"``, ``"rows"`` or ``"atomic"``
+    drift); ``spread`` (variant B) is ``"auto"``, ``"tiles"``, ``"rows"`` or ``"atomic"``
     (the path that hands the transfers to the nodes; bitwise the same
     results).
     """
