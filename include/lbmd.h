@@ -69,8 +69,21 @@ enum { LBMD_VARIANT_A = 0, LBMD_VARIANT_B = 1, LBMD_VARIANT_C = 2 };
  * in that precision.  FP16_DEV / BF16_DEV: populations stored as deviations
  * f_i - w_i rho0 in FP16 / BF16 (round to nearest), everything else and all
  * arithmetic as in FP32; the rounding of the stored deviations breaks exact
- * mass conservation at the level of their last bit. */
-enum { LBMD_FP32 = 0, LBMD_FP64 = 1, LBMD_FP16_DEV = 2, LBMD_BF16_DEV = 3 };
+ * mass conservation at the level of their last bit.  FP16_DEV_SR /
+ * BF16_DEV_SR: the same storage, but the collision rounds each stored
+ * deviation stochastically (up with probability equal to its distance from
+ * the grid value below, in units of the grid step, resolved to 2^-16), with 16
+ * bits of Philox4x32-10 under the context's seed: counter (node r, LB step,
+ * 2, i / 8), word (i / 2) mod 4, low half for even i, for population i of the
+ * post-collision state of node r.  Variants A and B only. */
+enum {
+    LBMD_FP32 = 0,
+    LBMD_FP64 = 1,
+    LBMD_FP16_DEV = 2,
+    LBMD_BF16_DEV = 3,
+    LBMD_FP16_DEV_SR = 4,
+    LBMD_BF16_DEV_SR = 5
+};
 /* Where velocity Verlet evaluates the coupling force of Eq. (4).
  * START (default, the reading of Eq. (6): R, v and F_rand of the beginning of
  *   the MD step): F_c from R, v at the start of the step, used in both
@@ -106,7 +119,7 @@ typedef struct lbmd_params {
     int32_t nx, ny, nz;    /* lattice nodes per axis (periodic), each >= 2 */
     int32_t n_sub;         /* m = tau_LB / dt: MD steps per LB step, >= 1 (Sec. 3) */
     int32_t variant;       /* LBMD_VARIANT_A, _B (Sec. 3) or _C (Sec. 4) */
-    int32_t precision;     /* LBMD_FP32, LBMD_FP64, LBMD_FP16_DEV or LBMD_BF16_DEV */
+    int32_t precision;     /* LBMD_FP32, LBMD_FP64, LBMD_FP16_DEV, LBMD_BF16_DEV or their _SR forms */
     double rho0;           /* initial fluid density; the fluid starts at rest */
     double nu;             /* kinematic shear viscosity, > 0 */
     double nu_bulk;        /* bulk viscosity; < 0 selects relaxation factor 0 */

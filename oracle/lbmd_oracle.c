@@ -804,3 +804,59 @@ void orc_set_counters(orc_state *s, int64_t lb_step, int64_t md_step) {
 }
 
 int64_t orc_num_particles(const orc_state *s) { return s->np; }
+
+/* ------------------------------------------------------------------------ */
+/* Reduced-precision population storage (an extension of the method, not in */
+/* the paper): the stored deviation of a population from its rest value is  */
+/* rounded onto a binary floating-point grid with p significand bits and    */
+/* minimum normal exponent emin (FP16: p = 11, emin = -14; BF16: p = 8,     */
+/* emin = -126), written out from the definition of such a grid.  Finite    */
+/* range assumed (the deviations are far below the largest finite value).   */
+/* ------------------------------------------------------------------------ */
+
+/* x rounded onto the grid: to nearest, ties to the even neighbour
+ * (stochastic = 0), or stochastically with 16 random bits r (stochastic = 1):
+ * away from zero when r < 2^16 frac, frac = the distance of |x| above the
+ * grid value below it in units of the grid step there. */
+double orc_round_storage(double x, int p, int emin, uint32_t r, int stochastic) {
+    if (x == 0.0) return x;
+    double a = fabs(x);
+    int e;
+    frexp(a, &e); /* a = m 2^e, 1/2 <= m < 1: the leading bit has exponent e - 1 */
+    int E = e - 1 < emin ? emin : e - 1;
+    double step = ldexp(1.0, E - (p - 1)); /* spacing of the grid around a */
+    double q = a / step;                   /* exact: step is a power of two */
+    double lo = floor(q), frac = q - lo;
+    int up;
+    if (stochastic)
+        up = (double)(r & 0xffffu) < frac * 65536.0;
+    else
+        up = frac > 0.5 || (frac == 0.5 && fmod(lo, 2.0) == 1.0);
+    double y = (lo + (double)up) * step;
+    return x < 0.0 ? -y : y;
+}
+
+/* The 16 random bits of population i of node `node`'s post-collision state
+ * in LB step `lb_step`: Philox4x32-10 under the seed, counter (node, lb_step,
+ * 2, i / 8), word (i / 2) mod 4, low half for even i. */
+void orc_sr_bits(uint64_t seed, uint32_t node, uint32_t lb_step, uint32_t out[Q]) {
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t ctr[4], w[4];
+    for (int i = 0; i < Q; ++i) {
+        if (i % 8 == 0) {
+            ctr[0] = node; ctr[1] = lb_step; ctr[2] = 2u; ctr[3] = (uint32_t)(i / 8);
+            orc_philox4x32_10(ctr, key, w);
+        }
+        uint32_t word = w[(i / 2) % 4];
+        out[i] = (i % 2 == 0) ? (word & 0xffffu) : (word >> 16);
+    }
+}
+
+/* Vector forms for the tests. */
+void orc_round_storage_n(int64_t n, const double *x, int p, int emin, const uint32_t *r, int stochastic,
+                         double *out) {
+    for (int64_t k = 0; k < n; ++k) out[k] = orc_round_storage(x[k], p, emin, r ? r[k] : 0u, stochastic);
+}
+void orc_sr_bits_n(uint64_t seed, int64_t n, const uint32_t *nodes, uint32_t lb_step, uint32_t *out) {
+    for (int64_t k = 0; k < n; ++k) orc_sr_bits(seed, nodes[k], lb_step, out + Q * k);
+}

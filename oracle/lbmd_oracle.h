@@ -70,6 +70,16 @@ void orc_collide_node(const orc_state *s, const double f[19], const double F[3],
                       double fout[19]);
 void orc_trilinear(const orc_state *s, const double R[3], int64_t corner[8], double delta[8]);
 
+/* Reduced-precision storage of the populations (not part of the paper's
+ * method): rounding onto a binary grid (p significand bits, minimum normal
+ * exponent emin) to nearest or stochastically with 16 random bits, and the
+ * random bits of each population of a node's post-collision state. */
+double orc_round_storage(double x, int p, int emin, uint32_t r, int stochastic);
+void orc_sr_bits(uint64_t seed, uint32_t node, uint32_t lb_step, uint32_t out[19]);
+void orc_round_storage_n(int64_t n, const double *x, int p, int emin, const uint32_t *r, int stochastic,
+                         double *out);
+void orc_sr_bits_n(uint64_t seed, int64_t n, const uint32_t *nodes, uint32_t lb_step, uint32_t *out);
+
 /* Forward-mode derivative (tangent) of the oracle's step for the mean
  * particle drag along x, ideal particles of mass 1 (lbmd_tangent.c). */
 typedef struct tan_state tan_state;

@@ -110,6 +110,10 @@ def lib(openmp: bool = False):
         L.orc_modes.argtypes = [dp, dp]
         L.orc_collide_node.argtypes = [P, dp, dp, ct.c_uint32, ct.c_uint32, dp]
         L.orc_trilinear.argtypes = [P, dp, ct.POINTER(ct.c_int64), dp]
+        L.orc_round_storage.restype = ct.c_double
+        L.orc_round_storage.argtypes = [ct.c_double, ct.c_int, ct.c_int, ct.c_uint32, ct.c_int]
+        L.orc_round_storage_n.argtypes = [ct.c_int64, dp, ct.c_int, ct.c_int, u32p, ct.c_int, dp]
+        L.orc_sr_bits_n.argtypes = [ct.c_uint64, ct.c_int64, u32p, ct.c_uint32, u32p]
         L.tan_create.restype = P
         L.tan_create.argtypes = [ct.POINTER(OrcParams)]
         L.tan_destroy.argtypes = [P]
@@ -144,6 +148,38 @@ def uniform_unit(x: int) -> float:
 
 def uniform_unit16(h: int) -> float:
     return lib().orc_uniform_unit16(int(h) & 0xFFFFFFFF)
+
+
+# Binary grids of the reduced-precision population storage: (significand
+# bits p, minimum normal exponent emin).
+STORAGE_FORMATS = {"fp16": (11, -14), "bf16": (8, -126)}
+
+
+def round_storage(x, fmt, r=None):
+    """x rounded onto the FP16 / BF16 grid: to nearest (ties to even) when r
+    is None, else stochastically with the 16-bit random numbers r (one per
+    element)."""
+    x = _f64(x)
+    p, emin = STORAGE_FORMATS[fmt]
+    out = np.empty_like(x)
+    rp = None
+    if r is not None:
+        r = np.ascontiguousarray(np.broadcast_to(r, x.shape), dtype=np.uint32)
+        rp = r.ctypes.data_as(ct.POINTER(ct.c_uint32))
+    lib().orc_round_storage_n(x.size, _dp(x), p, emin, rp, 0 if r is None else 1, _dp(out))
+    return out
+
+
+def sr_bits(seed, nodes, lb_step):
+    """The 16-bit random numbers of the stochastic rounding: array (len(nodes),
+    19), population i of node nodes[k]'s post-collision state in LB step
+    lb_step."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint32)
+    out = np.empty((nodes.size, 19), dtype=np.uint32)
+    u32p = ct.POINTER(ct.c_uint32)
+    lib().orc_sr_bits_n(int(seed), nodes.size, nodes.ctypes.data_as(u32p), int(lb_step) & 0xFFFFFFFF,
+                        out.ctypes.data_as(u32p))
+    return out
 
 
 def d3q19():

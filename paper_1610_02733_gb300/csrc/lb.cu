@@ -35,6 +35,7 @@ struct LbArgs {
     const typename Prec<T>::node4 *cact;   // variant B: their compact records
     const uint2 *occw_new;                 // variant B: active nodes of the next cycle
     typename Prec<T>::node4 *cact_new;     // ... whose records the fused moments write
+    typename Prec<T>::node4 *cact_new2;    // variant A: the same records again (the next cycle's accumulator)
     int occ_words;
     // fused post-stream moments (dataflow between collide blocks)
     uint32_t *blk_done;
@@ -70,8 +71,9 @@ __device__ __forceinline__ typename Prec<T>::node4 guarded_record(T rho, T jx, T
 // were written by other blocks of the same kernel.
 template <typename T, typename S>
 __device__ __forceinline__ void node_moments_at(const S *f, typename Prec<T>::node4 *node, const uint2 *occw,
-                                                typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx,
-                                                int ny, T rho0, T fs, int32_t *range_flag, int x, int y, int t) {
+                                                typename Prec<T>::node4 *cact, typename Prec<T>::node4 *cact2,
+                                                int occ_words, int64_t N, int nx, int ny, T rho0, T fs,
+                                                int32_t *range_flag, int x, int y, int t) {
     using P = Prec<T>;
     using St = PopStore<S, T>;
     const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)t);
@@ -84,7 +86,10 @@ __device__ __forceinline__ void node_moments_at(const S *f, typename Prec<T>::no
     node[r] = rec;
     if (occw) {
         const int sl = active_slot(occw[((size_t)y + (size_t)ny * t) * occ_words + (x >> 5)], x);
-        if (sl >= 0) cact[sl] = rec;
+        if (sl >= 0) {
+            cact[sl] = rec;
+            if (cact2) cact2[sl] = rec;
+        }
     }
 }
 
@@ -117,15 +122,28 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
     T rho, jx, jy, jz;
     node_moments(f, rho, jx, jy, jz);
     T Fx, Fy, Fz;
-    if (a.variant == LBMD_VARIANT_B) {
-        // node j = fix(j*) + sum of fixed-point transfers: the difference is
-        // exactly the accumulated transfer J_acc (an active node's current
-        // record is its compact one)
-        const int sl = active_slot(a.occw[((size_t)y + (size_t)a.ny * z) * a.occ_words + (x >> 5)], x);
+    const int sl = a.occw ? active_slot(a.occw[((size_t)y + (size_t)a.ny * z) * a.occ_words + (x >> 5)], x) : -1;
+    if (sl >= 0 || a.variant == LBMD_VARIANT_B) {
+        // the record j = fix(j*) + sum of fixed-point transfers: the
+        // difference is exactly the accumulated transfer J_acc (an active
+        // node's record is its compact one -- variant A: the accumulating
+        // copy; B: an inactive node's is the node field)
         const typename P::node4 n = sl >= 0 ? a.cact[sl] : a.node[r];
         Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx, a.fs), a.fis);
         Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy, a.fs), a.fis);
         Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz, a.fs), a.fis);
+    } else if (a.occw) {
+        // variant A, inactive node: J_acc holds what migrants handed over
+        // (rarely anything; cleared only where set)
+        const typename P::node4 J = a.jacc[r];
+        Fx = P::from_fix(P::jx_of(J), a.fis);
+        Fy = P::from_fix(P::jy_of(J), a.fis);
+        Fz = P::from_fix(P::jz_of(J), a.fis);
+        if ((P::jx_of(J) | P::jy_of(J) | P::jz_of(J)) != 0) {
+            typename P::node4 zero;
+            zero.x = zero.y = zero.z = zero.w = 0;
+            a.jacc[r] = zero;
+        }
     } else {
         const typename P::node4 J = a.jacc[r];
         Fx = P::from_fix(P::jx_of(J), a.fis);
@@ -144,11 +162,26 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z == a.nz - 1 ? 0 : z + 1;
     const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
+    if constexpr (St::stochastic) {
+        // stochastic rounding of the stored deviations: 16 random bits per
+        // population from Philox stream 2 of (node, LB step), population i
+        // from call i / 8, word (i / 2) mod 4, low half for even i
+        U4 rb{0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const uint32_t t = (uint32_t)X[CX(i) + 1] +
-                           (uint32_t)a.nx * ((uint32_t)Y[CY(i) + 1] + (uint32_t)a.ny * (uint32_t)Z[CZ(i) + 1]);
-        St::store(a.fout + (size_t)i * a.N + t, f[i], T(WEIGHT(i)) * a.rho0);
+        for (int i = 0; i < Q; ++i) {
+            if ((i & 7) == 0) rb = philox4x32_10(U4{r, (uint32_t)step, 2u, (uint32_t)(i >> 3)}, a.key0, a.key1);
+            const uint32_t w = ((i >> 1) & 3) == 0 ? rb.x : ((i >> 1) & 3) == 1 ? rb.y : ((i >> 1) & 3) == 2 ? rb.z : rb.w;
+            const uint32_t t = (uint32_t)X[CX(i) + 1] +
+                               (uint32_t)a.nx * ((uint32_t)Y[CY(i) + 1] + (uint32_t)a.ny * (uint32_t)Z[CZ(i) + 1]);
+            St::store_sr(a.fout + (size_t)i * a.N + t, f[i], T(WEIGHT(i)) * a.rho0, (i & 1) ? w >> 16 : w & 0xffffu);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t t = (uint32_t)X[CX(i) + 1] +
+                               (uint32_t)a.nx * ((uint32_t)Y[CY(i) + 1] + (uint32_t)a.ny * (uint32_t)Z[CZ(i) + 1]);
+            St::store(a.fout + (size_t)i * a.N + t, f[i], T(WEIGHT(i)) * a.rho0);
+        }
     }
 }
 
@@ -201,8 +234,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
         return;
     }
     if (x < a.nx)
-        node_moments_at<T, S>(a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, a.N, a.nx, a.ny, a.rho0, a.fs,
-                              a.range_flag, x, y, t);
+        node_moments_at<T, S>(a.fout, a.node, a.occw_new, a.cact_new, a.cact_new2, a.occ_words, a.N, a.nx, a.ny,
+                              a.rho0, a.fs, a.range_flag, x, y, t);
 }
 
 // The moments the collide kernel left: node rows of plane 0 and of the last
@@ -211,7 +244,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
 template <typename T, typename S>
 __global__ void __launch_bounds__(256)
     moments_rest_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
-                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, int nz, T rho0,
+                        typename Prec<T>::node4 *cact, typename Prec<T>::node4 *cact2, int occ_words, int64_t N,
+                        int nx, int ny, int nz, T rho0,
                         T fs, int32_t *range_flag, const int32_t *missed, const int32_t *missed_list,
                         unsigned long long *missed_total, unsigned long long *lb_step) {
     const int gx = (nx + (int)blockDim.x - 1) / (int)blockDim.x;
@@ -232,7 +266,8 @@ __global__ void __launch_bounds__(256)
         }
         const int xb = b % gx, rest = b / gx, y = rest % ny, t = rest / ny;
         const int x = xb * (int)blockDim.x + (int)threadIdx.x;
-        if (x < nx) node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, fs, range_flag, x, y, t);
+        if (x < nx)
+            node_moments_at<T, S>(f, node, occw, cact, cact2, occ_words, N, nx, ny, rho0, fs, range_flag, x, y, t);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *missed_total += (unsigned long long)*missed;
@@ -243,11 +278,12 @@ __global__ void __launch_bounds__(256)
 template <typename T, typename S>
 __global__ void __launch_bounds__(256)
     node_moments_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
-                        typename Prec<T>::node4 *cact, int occ_words, int64_t N, int nx, int ny, T rho0, T fs,
-                        int32_t *range_flag) {
+                        typename Prec<T>::node4 *cact, typename Prec<T>::node4 *cact2, int occ_words, int64_t N,
+                        int nx, int ny, T rho0, T fs, int32_t *range_flag) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
-    node_moments_at<T, S>(f, node, occw, cact, occ_words, N, nx, ny, rho0, fs, range_flag, x, blockIdx.y, blockIdx.z);
+    node_moments_at<T, S>(f, node, occw, cact, cact2, occ_words, N, nx, ny, rho0, fs, range_flag, x, blockIdx.y,
+                          blockIdx.z);
 }
 
 // Variant C (Sec. 4): the momentum transfer F = J_acc of the MD step just
@@ -333,11 +369,13 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.rho0 = (T)ctx->p.rho0;
     a.node = static_cast<typename Prec<T>::node4 *>(ctx->node);
     a.jacc = static_cast<typename Prec<T>::node4 *>(ctx->jacc);
-    const bool B = ctx->p.variant == LBMD_VARIANT_B;
+    const bool B = compact_nodes(ctx);  // variants A and B
     a.occw = B ? active_words_now(ctx) : nullptr;
-    a.cact = static_cast<const typename Prec<T>::node4 *>(B ? active_records_now(ctx) : nullptr);
+    a.cact = static_cast<const typename Prec<T>::node4 *>(B ? active_records_acc(ctx) : nullptr);
     a.occw_new = B ? active_words_next(ctx) : nullptr;
     a.cact_new = static_cast<typename Prec<T>::node4 *>(B ? active_records_next(ctx) : nullptr);
+    a.cact_new2 = static_cast<typename Prec<T>::node4 *>(B ? active_records_copy(ctx, (int)((ctx->lb_step + 1) & 1))
+                                                           : nullptr);
     a.occ_words = active_words(ctx->p.nx);
     a.blk_done = ctx->blk_done;
     a.missed = ctx->lb_missed;
@@ -370,7 +408,8 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the moments the collide kernel left, on the new populations
     moments_rest_kernel<T, S><<<2 * ctx->sm_count, block, 0, ctx->stream>>>(
-        a.fout, a.node, a.occw_new, a.cact_new, a.occ_words, ctx->N, ctx->p.nx, ctx->p.ny, ctx->p.nz, a.rho0, a.fs,
+        a.fout, a.node, a.occw_new, a.cact_new, a.cact_new2, a.occ_words, ctx->N, ctx->p.nx, ctx->p.ny, ctx->p.nz,
+        a.rho0, a.fs,
         ctx->range_flag, ctx->lb_missed, ctx->missed_list, ctx->missed_total, ctx->d_lb_step);
     return cudaGetLastError();
 }
@@ -380,11 +419,12 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
 template <typename T, typename S>
 static cudaError_t node_moments_t(lbmd_ctx *ctx) {
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
-    const bool B = ctx->p.variant == LBMD_VARIANT_B;
+    const bool B = compact_nodes(ctx);  // variants A and B
     node_moments_kernel<T, S><<<grid, block, 0, ctx->stream>>>(
         static_cast<const S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
         B ? active_words_now(ctx) : nullptr,
         static_cast<typename Prec<T>::node4 *>(B ? active_records_now(ctx) : nullptr),
+        static_cast<typename Prec<T>::node4 *>(B ? active_records_copy(ctx, (int)(ctx->lb_step & 1)) : nullptr),
         active_words(ctx->p.nx), ctx->N, ctx->p.nx, ctx->p.ny, (T)ctx->p.rho0, (T)ctx->fix.scale, ctx->range_flag);
     return cudaGetLastError();
 }
@@ -411,11 +451,13 @@ static cudaError_t init_equilibrium_t(lbmd_ctx *ctx) {
 
 // population storage per precision: FP32 and FP64 plain, FP16 / BF16 as
 // deviations with FP32 arithmetic
-#define LBMD_DISPATCH_POPS(ctx, FN, ...)                                                   \
-    ((ctx)->p.precision == LBMD_FP64       ? FN<double, double>(__VA_ARGS__)               \
-     : (ctx)->p.precision == LBMD_FP16_DEV ? FN<float, __half>(__VA_ARGS__)                \
-     : (ctx)->p.precision == LBMD_BF16_DEV ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
-                                           : FN<float, float>(__VA_ARGS__))
+#define LBMD_DISPATCH_POPS(ctx, FN, ...)                                                      \
+    ((ctx)->p.precision == LBMD_FP64          ? FN<double, double>(__VA_ARGS__)               \
+     : (ctx)->p.precision == LBMD_FP16_DEV    ? FN<float, __half>(__VA_ARGS__)                \
+     : (ctx)->p.precision == LBMD_BF16_DEV    ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
+     : (ctx)->p.precision == LBMD_FP16_DEV_SR ? FN<float, lbmd::half_sr>(__VA_ARGS__)         \
+     : (ctx)->p.precision == LBMD_BF16_DEV_SR ? FN<float, lbmd::bf16_sr>(__VA_ARGS__)         \
+                                              : FN<float, float>(__VA_ARGS__))
 
 // One LB update: re-order the particles by row and build the active nodes of
 // the coming cycle (variant B; the particles do not move during the LB

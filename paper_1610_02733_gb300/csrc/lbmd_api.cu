@@ -100,8 +100,10 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (p->n_sub < 1) return fail(nullptr, LBMD_ERR_ARG, "n_sub must be >= 1");
     if (p->variant != LBMD_VARIANT_A && p->variant != LBMD_VARIANT_B && p->variant != LBMD_VARIANT_C)
         return fail(nullptr, LBMD_ERR_ARG, "variant must be A (0), B (1) or C (2)");
-    if (p->precision < LBMD_FP32 || p->precision > LBMD_BF16_DEV)
-        return fail(nullptr, LBMD_ERR_ARG, "precision must be FP32, FP64, FP16_DEV or BF16_DEV");
+    if (p->precision < LBMD_FP32 || p->precision > LBMD_BF16_DEV_SR)
+        return fail(nullptr, LBMD_ERR_ARG, "precision must be FP32, FP64, FP16_DEV, BF16_DEV or an _SR form");
+    if ((p->precision == LBMD_FP16_DEV_SR || p->precision == LBMD_BF16_DEV_SR) && p->variant == LBMD_VARIANT_C)
+        return fail(nullptr, LBMD_ERR_ARG, "stochastic rounding of the stored populations needs variant A or B");
     if (!(p->rho0 > 0) || !(p->nu > 0) || !is_finite_d(p->rho0) || !is_finite_d(p->nu))
         return fail(nullptr, LBMD_ERR_ARG, "rho0 and nu must be positive");
     FixUnit fix;
@@ -165,6 +167,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     ctx->cact_cap = std::min<int64_t>(N, 8 * maxp);
     const size_t occ_bytes = (size_t)p->ny * p->nz * (size_t)((p->nx + 31) / 32) * sizeof(uint2);
     const size_t arow_bytes = ((size_t)p->ny * p->nz + 1) * sizeof(int32_t);
+    const bool compact = compact_nodes(ctx);  // variants A and B: compact records of the active nodes
     ctx->node_bytes = node_bytes;
     // the tiled MD step's tables and buffers, where the lattice suits it and
     // the spread mode asks for it
@@ -199,13 +202,13 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->migrant_count, 2 * sizeof(int32_t)},
         {&ctx->fc4[0], (size_t)maxp * 4 * rs},
         {&ctx->fc4[1], (size_t)maxp * 4 * rs},
-        {&ctx->old4, p->variant == LBMD_VARIANT_B ? (size_t)maxp * 4 * rs : 0},
-        {(void **)&ctx->occw[0], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
-        {(void **)&ctx->occw[1], p->variant == LBMD_VARIANT_B ? occ_bytes : 0},
-        {&ctx->cact[0], p->variant == LBMD_VARIANT_B ? (size_t)2 * ctx->cact_cap * node_bytes : 0},
-        {&ctx->cact[1], p->variant == LBMD_VARIANT_B ? (size_t)2 * ctx->cact_cap * node_bytes : 0},
-        {(void **)&ctx->arow[0], p->variant == LBMD_VARIANT_B ? arow_bytes : 0},
-        {(void **)&ctx->arow[1], p->variant == LBMD_VARIANT_B ? arow_bytes : 0},
+        {&ctx->old4, compact ? (size_t)maxp * 4 * rs : 0},
+        {(void **)&ctx->occw[0], compact ? occ_bytes : 0},
+        {(void **)&ctx->occw[1], compact ? occ_bytes : 0},
+        {&ctx->cact[0], compact ? (size_t)2 * ctx->cact_cap * node_bytes : 0},
+        {&ctx->cact[1], compact ? (size_t)2 * ctx->cact_cap * node_bytes : 0},
+        {(void **)&ctx->arow[0], compact ? arow_bytes : 0},
+        {(void **)&ctx->arow[1], compact ? arow_bytes : 0},
         {(void **)&ctx->dev_error, sizeof(int32_t)},
         {&ctx->tile_table[0], table_bytes},
         {&ctx->tile_table[1], table_bytes},

@@ -197,6 +197,24 @@ inline void *active_records_other(const lbmd_ctx *c) {
 }
 inline uint2 *active_words_next(const lbmd_ctx *c) { return c->occw[(c->lb_step + 1) & 1]; }
 inline void *active_records_next(const lbmd_ctx *c) { return c->cact[(c->lb_step + 1) & 1]; }
+// Variants A and B keep the node records of the active nodes in compact
+// arrays (variant C updates the populations every MD step instead).  Variant
+// A reads the frozen records (first buffer of the set) and accumulates the
+// transfers in the set's second buffer, which starts as a copy of the first;
+// variant B reads and updates one buffer.
+inline bool compact_nodes(const lbmd_ctx *c) { return c->p.variant != LBMD_VARIANT_C; }
+// the records the MD steps add transfers to (and the LB step reads)
+inline void *active_records_acc(const lbmd_ctx *c) {
+    return c->p.variant == LBMD_VARIANT_A
+               ? static_cast<char *>(c->cact[c->lb_step & 1]) + (size_t)c->cact_cap * c->node_bytes
+               : active_records_now(c);
+}
+// variant A: the second buffer of a set, which the moments fill with the same
+// records as the first (null for B)
+inline void *active_records_copy(const lbmd_ctx *c, int set) {
+    return c->p.variant == LBMD_VARIANT_A ? static_cast<char *>(c->cact[set]) + (size_t)c->cact_cap * c->node_bytes
+                                          : nullptr;
+}
 inline void *pos_now(const lbmd_ctx *c) { return c->pos4[c->pv]; }
 inline void *vel_now(const lbmd_ctx *c) { return c->vel4[c->pv]; }
 

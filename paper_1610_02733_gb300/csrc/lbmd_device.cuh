@@ -244,9 +244,11 @@ struct Prec<double> {
 // ---------------------------------------------------------------------------
 // Population storage.  FP32 / FP64 store f_i itself.  The reduced-precision
 // forms store the deviation from the rest equilibrium, f_i - w_i rho0, as FP16
-// or BF16 (rounded to nearest) and do all arithmetic in FP32: the deviations
-// are small (thermal and flow perturbations), so the 11- or 8-bit significand
-// is spent on them rather than on the constant w_i rho0.
+// or BF16 and do all arithmetic in FP32: the deviations are small (thermal
+// and flow perturbations), so the 11- or 8-bit significand is spent on them
+// rather than on the constant w_i rho0.  The collision's stores round the
+// deviation to nearest (FP16 / BF16) or stochastically (the _SR forms below);
+// every other store (initial and user-given states) rounds to nearest.
 // ---------------------------------------------------------------------------
 template <typename S, typename T>
 struct PopStore {  // plain storage: S == T
@@ -254,6 +256,40 @@ struct PopStore {  // plain storage: S == T
     __device__ static __forceinline__ T load_cg(const S *p, T /*base*/) { return __ldcg(p); }
     __device__ static __forceinline__ void store(S *p, T v, T /*base*/) { *p = v; }
     static constexpr bool deviation = false;
+    static constexpr bool stochastic = false;
+};
+
+// Stochastic rounding of x onto the FP16 / BF16 grid with 16 random bits r:
+// with lo the grid value next to x towards zero and hi the next one away from
+// zero, the result is hi when r < 2^16 (|x| - |lo|) / (|hi| - |lo|), else lo
+// (Forsythe 1959; Connolly, Higham & Mary, SIAM J. Sci. Comput. 43 (2021)):
+// unbiased, E[result] = x up to 2^-16 of a grid step.  For an FP32 x the
+// fraction times 2^16 is exact, so the comparison is exact.
+__device__ __forceinline__ __nv_bfloat16 bf16_round_stochastic(float x, uint32_t r) {
+    // BF16 is the top half of FP32: the dropped 16 bits are the fraction
+    const uint32_t bits = __float_as_uint(x), mag = bits & 0x7fffffffu;
+    const uint32_t up = r < (mag & 0xffffu) ? 1u : 0u;
+    return __ushort_as_bfloat16((unsigned short)(((bits >> 16) & 0x8000u) | ((mag >> 16) + up)));
+}
+__device__ __forceinline__ __half fp16_round_stochastic(float x, uint32_t r) {
+    const float a = fabsf(x);
+    const unsigned short lo = __half_as_ushort(__float2half_rz(a));  // towards zero, subnormals included
+    const float lo_f = __half2float(__ushort_as_half(lo));
+    // the grid step above lo (a power of two: the divisions below are exact)
+    const float step = __half2float(__ushort_as_half((unsigned short)(lo + 1))) - lo_f;
+    const float t = (a - lo_f) / step * 65536.0f;  // a - lo_f is exact (Sterbenz)
+    const unsigned short up = (lo < 0x7bffu && (float)r < t) ? 1 : 0;
+    const unsigned short sign = (unsigned short)((__float_as_uint(x) >> 16) & 0x8000u);
+    return __ushort_as_half((unsigned short)(sign | (lo + up)));
+}
+
+// Storage tags of the stochastically rounded forms (same bits as __half /
+// __nv_bfloat16).
+struct half_sr {
+    unsigned short u;
+};
+struct bf16_sr {
+    unsigned short u;
 };
 template <>
 struct PopStore<__half, float> {
@@ -263,6 +299,7 @@ struct PopStore<__half, float> {
     }
     __device__ static __forceinline__ void store(__half *p, float v, float base) { *p = __float2half_rn(v - base); }
     static constexpr bool deviation = true;
+    static constexpr bool stochastic = false;
 };
 template <>
 struct PopStore<__nv_bfloat16, float> {
@@ -276,6 +313,42 @@ struct PopStore<__nv_bfloat16, float> {
         *p = __float2bfloat16_rn(v - base);
     }
     static constexpr bool deviation = true;
+    static constexpr bool stochastic = false;
+};
+template <>
+struct PopStore<half_sr, float> {
+    __device__ static __forceinline__ float load(const half_sr *p, float base) {
+        return base + __half2float(__ushort_as_half(p->u));
+    }
+    __device__ static __forceinline__ float load_cg(const half_sr *p, float base) {
+        return base + __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __forceinline__ void store(half_sr *p, float v, float base) {
+        p->u = __half_as_ushort(__float2half_rn(v - base));
+    }
+    // r: 16 random bits
+    __device__ static __forceinline__ void store_sr(half_sr *p, float v, float base, uint32_t r) {
+        p->u = __half_as_ushort(fp16_round_stochastic(v - base, r));
+    }
+    static constexpr bool deviation = true;
+    static constexpr bool stochastic = true;
+};
+template <>
+struct PopStore<bf16_sr, float> {
+    __device__ static __forceinline__ float load(const bf16_sr *p, float base) {
+        return base + __bfloat162float(__ushort_as_bfloat16(p->u));
+    }
+    __device__ static __forceinline__ float load_cg(const bf16_sr *p, float base) {
+        return base + __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __forceinline__ void store(bf16_sr *p, float v, float base) {
+        p->u = __bfloat16_as_ushort(__float2bfloat16_rn(v - base));
+    }
+    __device__ static __forceinline__ void store_sr(bf16_sr *p, float v, float base, uint32_t r) {
+        p->u = __bfloat16_as_ushort(bf16_round_stochastic(v - base, r));
+    }
+    static constexpr bool deviation = true;
+    static constexpr bool stochastic = true;
 };
 
 // Hydrodynamic moments rho = sum f_i, j = sum f_i c_i (Eqs. (1), (2)).  One

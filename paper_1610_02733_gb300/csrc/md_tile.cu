@@ -752,7 +752,7 @@ cudaError_t md_tile_step(lbmd_ctx *ctx, const lbmd::PArgs<T> &a) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     lbmd::PArgs<T> m = a;
-    m.cact = t.cact_out;
+    m.cact = m.cact_acc = t.cact_out;  // the listed particles spread into the new records
     lbmd::md_tile_finish_kernel<T><<<ctx->sm_count, 256, 0, ctx->stream>>>(m, t, ctx->arow[ctx->lb_step & 1],
                                                                          ctx->cact_cap);
     return cudaGetLastError();

@@ -151,10 +151,12 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
             static_cast<const typename P::node4 *>(ctx->node), nullptr, active_words_now(ctx),
             static_cast<const typename P::node4 *>(active_records_now(ctx)), active_words(ctx->p.nx), fnx, ctx->N,
             ctx->red_partial);
-    else
+    else  // variant A: the accumulating records of the active nodes (j* + J_acc), J_acc elsewhere; C: J_acc
         observe_nodes_kernel<T, LBMD_VARIANT_A><<<B, RED_THREADS, 0, ctx->stream>>>(
             static_cast<const typename P::node4 *>(ctx->node), static_cast<const typename P::node4 *>(ctx->jacc),
-            nullptr, nullptr, 0, fnx, ctx->N, ctx->red_partial);
+            compact_nodes(ctx) ? active_words_now(ctx) : nullptr,
+            static_cast<const typename P::node4 *>(compact_nodes(ctx) ? active_records_acc(ctx) : nullptr),
+            active_words(ctx->p.nx), fnx, ctx->N, ctx->red_partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     observe_particles_kernel<T><<<B, RED_THREADS, 0, ctx->stream>>>(
@@ -169,13 +171,15 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
 // ---------------------------------------------------------------------------
 // Conversions for the host accessors.
 // ---------------------------------------------------------------------------
-// populations [first, first + count) of the flat array f[i * N + r]
-__device__ __forceinline__ double pop_base(int64_t flat, int64_t N, double rho0) {
+// populations [first, first + count) of the flat array f[i * N + r]; the
+// base of the deviation storage w_i rho0 formed as the collision forms it
+template <typename T>
+__device__ __forceinline__ T pop_base(int64_t flat, int64_t N, double rho0) {
     const int i = (int)(flat / N);
     double w = 1.0 / 36.0;
     if (i == 0) w = 1.0 / 3.0;
     else if (i <= 6) w = 1.0 / 18.0;
-    return w * rho0;
+    return T(w) * T(rho0);
 }
 
 template <typename T, typename S>
@@ -184,7 +188,7 @@ __global__ void pops_to_double_kernel(const S *f, int64_t first, int64_t count, 
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     const int64_t k = first + t;
-    dst[t] = (double)PopStore<S, T>::load(f + k, (T)pop_base(k, N, rho0));
+    dst[t] = (double)PopStore<S, T>::load(f + k, pop_base<T>(k, N, rho0));
 }
 
 template <typename T, typename S>
@@ -193,13 +197,14 @@ __global__ void pops_from_double_kernel(S *f, int64_t first, int64_t count, int6
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     const int64_t k = first + t;
-    PopStore<S, T>::store(f + k, (T)src[t], (T)pop_base(k, N, rho0));
+    PopStore<S, T>::store(f + k, (T)src[t], pop_base<T>(k, N, rho0));
 }
 
 // node field (rho, j seen by the particles) or, with transfer_only, the
 // pending transfer J_acc, for nodes [first, first + count)
 template <typename T, typename S>
 __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc,
+                                      const uint2 *occw, const typename Prec<T>::node4 *cacc, int W, int nx,
                                       const S *f, int64_t N, T rho0, T fs, T fis, int64_t first, int64_t count,
                                       double *dst, int transfer_only, int variant) {
     using P = Prec<T>;
@@ -214,7 +219,14 @@ __global__ void node_to_double_kernel(const typename Prec<T>::node4 *node, const
         dst[4 * t + 3] = (double)P::from_fix(P::jz_of(n), fis);
         return;
     }
-    if (variant != LBMD_VARIANT_B) {
+    const int sl = occw ? active_slot(occw[(size_t)(r / nx) * W + ((r % nx) >> 5)], (int)(r % nx)) : -1;
+    if (sl >= 0 && variant == LBMD_VARIANT_A) {
+        // variant A, active node: the accumulating record minus the frozen one
+        const typename P::node4 c = cacc[sl];
+        dst[3 * t + 0] = (double)P::from_fix(P::jx_of(c) - P::jx_of(n), fis);
+        dst[3 * t + 1] = (double)P::from_fix(P::jy_of(c) - P::jy_of(n), fis);
+        dst[3 * t + 2] = (double)P::from_fix(P::jz_of(c) - P::jz_of(n), fis);
+    } else if (variant != LBMD_VARIANT_B) {
         const typename P::node4 J = jacc[r];
         dst[3 * t + 0] = (double)P::from_fix(P::jx_of(J), fis);
         dst[3 * t + 1] = (double)P::from_fix(P::jy_of(J), fis);
@@ -329,17 +341,20 @@ static cudaError_t node_to_double_t(lbmd_ctx *ctx, int64_t first, int64_t count,
     using N4 = typename Prec<T>::node4;
     node_to_double_kernel<T, S><<<nblocks(count), 256, 0, ctx->stream>>>(
         static_cast<const N4 *>(ctx->node), static_cast<const N4 *>(ctx->jacc),
-        static_cast<const S *>(ctx->f[ctx->cur]),
-        ctx->N, (T)ctx->p.rho0, (T)ctx->fix.scale, (T)ctx->fix.inv_scale, first, count, dst, transfer_only ? 1 : 0,
-        ctx->p.variant);
+        compact_nodes(ctx) ? active_words_now(ctx) : nullptr,
+        static_cast<const N4 *>(compact_nodes(ctx) ? active_records_acc(ctx) : nullptr), active_words(ctx->p.nx),
+        ctx->p.nx, static_cast<const S *>(ctx->f[ctx->cur]), ctx->N, (T)ctx->p.rho0, (T)ctx->fix.scale,
+        (T)ctx->fix.inv_scale, first, count, dst, transfer_only ? 1 : 0, ctx->p.variant);
     return cudaGetLastError();
 }
 
-#define LBMD_DISPATCH_POPS(ctx, FN, ...)                                                   \
-    ((ctx)->p.precision == LBMD_FP64       ? FN<double, double>(__VA_ARGS__)               \
-     : (ctx)->p.precision == LBMD_FP16_DEV ? FN<float, __half>(__VA_ARGS__)                \
-     : (ctx)->p.precision == LBMD_BF16_DEV ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
-                                           : FN<float, float>(__VA_ARGS__))
+#define LBMD_DISPATCH_POPS(ctx, FN, ...)                                                      \
+    ((ctx)->p.precision == LBMD_FP64          ? FN<double, double>(__VA_ARGS__)               \
+     : (ctx)->p.precision == LBMD_FP16_DEV    ? FN<float, __half>(__VA_ARGS__)                \
+     : (ctx)->p.precision == LBMD_BF16_DEV    ? FN<float, __nv_bfloat16>(__VA_ARGS__)         \
+     : (ctx)->p.precision == LBMD_FP16_DEV_SR ? FN<float, lbmd::half_sr>(__VA_ARGS__)         \
+     : (ctx)->p.precision == LBMD_BF16_DEV_SR ? FN<float, lbmd::bf16_sr>(__VA_ARGS__)         \
+                                              : FN<float, float>(__VA_ARGS__))
 
 cudaError_t launch_populations_to_double(lbmd_ctx *ctx, int64_t first, int64_t count, double *dst) {
     if (count <= 0) return cudaSuccess;

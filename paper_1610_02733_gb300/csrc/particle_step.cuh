@@ -41,7 +41,9 @@ struct PArgs {
     // variant B row-gather spreading and active nodes
     const int32_t *row_start, *slot_row;
     const uint2 *occw;
-    typename P::node4 *cact;
+    typename P::node4 *cact;          // the active nodes' records the MD step reads
+    typename P::node4 *cact_acc;      // ... and the ones it adds transfers to (variant A: a second buffer)
+    typename P::node4 *inactive_acc;  // where transfers to inactive nodes go (A: J_acc, B: the node field)
     int occ_words;
     int32_t *migrant_slot, *migrant_count;  // two lists of np_cap slots, two counters
     int b_atomic;      // variant B spreads every particle with atomics (no row gather, no migrant lists)
@@ -101,7 +103,7 @@ __device__ __forceinline__ void interp_u(const PArgs<T> &a, const CellXYZ &c, T 
     corner_rows(c, a.ny, a.nz, rows);
     const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
     interp_u_from(fx, fy, fz, a.fis, ux, uy, uz, [&](int q, typename P::node4 &n0, typename P::node4 &n1) {
-        if (a.variant == LBMD_VARIANT_B) {
+        if (a.occw) {  // variants A and B: an active corner's compact record
             corner_pair(a, rows[q], c.x, x1, n0, n1);
         } else {
             const size_t r0 = (size_t)rows[q] * (uint32_t)a.nx;
@@ -144,17 +146,17 @@ __device__ __forceinline__ void coupling_force(const PArgs<T> &a, int64_t p, con
 }
 
 // Newton's third law for the particle in slot p whose transfer -delta_k dt F
-// belongs to the nodes around position R (cell c): variants A and C add it to
-// J_acc at once (nothing reads J_acc during the MD step; C then moves it into
-// the populations, forcing_update_kernel); variant B keeps R for the row
-// gather, and a particle whose cell row is no longer the row bucket it was
-// sorted into is listed as a migrant (two lists alternating with the parity
-// of the MD step).
+// belongs to the nodes around position R (cell c): variant C adds it to
+// J_acc at once (forcing_update_kernel then moves it into the populations);
+// variants A and B keep R for the row gather (which adds the transfers to the
+// compact records: B's own, A's second buffer), and a particle whose cell row
+// is no longer the row bucket it was sorted into is listed as a migrant (two
+// lists alternating with the parity of the MD step).
 template <typename T>
 __device__ __forceinline__ void hand_over(const PArgs<T> &a, int64_t p, const typename Prec<T>::real4 &R,
                                           const CellXYZ &c, T Fx, T Fy, T Fz) {
     using P = Prec<T>;
-    if (a.variant != LBMD_VARIANT_B) {
+    if (a.variant == LBMD_VARIANT_C) {
         uint32_t idx[8];
         T delta[8];
         corners(c, R.x, R.y, R.z, a.nx, a.ny, a.nz, idx, delta);
@@ -208,7 +210,7 @@ __device__ __forceinline__ void spread_corner_atomic(const PArgs<T> &a, int64_t 
     const T delta = (ox ? R.x : T(1) - R.x) * (oy ? R.y : T(1) - R.y) * (oz ? R.z : T(1) - R.z);
     const uint32_t row = (uint32_t)yn + (uint32_t)a.ny * (uint32_t)zn;
     const int sl = active_slot(a.occw[(size_t)row * (uint32_t)a.occ_words + (xn >> 5)], xn);
-    typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[(size_t)row * (uint32_t)a.nx + xn];
+    typename P::node4 *rec = sl >= 0 ? &a.cact_acc[sl] : &a.inactive_acc[(size_t)row * (uint32_t)a.nx + xn];
     const T sx = F.x * a.neg_scale_dt, sy = F.y * a.neg_scale_dt, sz = F.z * a.neg_scale_dt;
     P::add_transfer(rec, P::to_fix_neg(delta, sx), P::to_fix_neg(delta, sy), P::to_fix_neg(delta, sz));
 }
@@ -231,7 +233,7 @@ __device__ __forceinline__ void spread_particle_atomic(const PArgs<T> &a, int64_
     for (int k = 0; k < 8; ++k) {
         const int xn = (k & 1) ? x1 : c.x;
         const int sl = active_slot(a.occw[(size_t)rows[k >> 1] * (uint32_t)a.occ_words + (xn >> 5)], xn);
-        typename P::node4 *rec = sl >= 0 ? &a.cact[sl] : &a.node[idx[k]];
+        typename P::node4 *rec = sl >= 0 ? &a.cact_acc[sl] : &a.inactive_acc[idx[k]];
         P::add_transfer(rec, P::to_fix_neg(delta[k], sx), P::to_fix_neg(delta[k], sy), P::to_fix_neg(delta[k], sz));
     }
 }

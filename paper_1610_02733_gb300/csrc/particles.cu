@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_kernel(PAr
     if (BONDS) check_list_skin(a, p, CellXYZ{cx, cy, cz}, fx, fy, fz);
     a.pos4[p] = P::make_pos(fx, fy, fz, cx + (int64_t)a.nx * (cy + (int64_t)a.ny * cz));
     a.vel4[p] = V;
-    if (BONDS || a.variant == LBMD_VARIANT_B) a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
+    if (BONDS || a.variant != LBMD_VARIANT_C) a.fc4[p] = P::make4(Fx, Fy, Fz, T(0));
     hand_over(a, p, R, c, Fx, Fy, Fz);
 }
 
@@ -144,17 +144,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_half_kerne
 }
 
 
-// Variant B, atomic-free: one warp per node row (y, z), four rows per block,
+// Variants A and B, atomic-free: one warp per node row (y, z), four rows per block,
 // rows in reverse order (the couple kernel touched the high rows last).  The
 // row's nodes get transfers only from particles in the four cell rows
 // (y - oy, z - oz), oy, oz in {0, 1}; with the particles bucketed by cell
 // row, the warp reads those buckets and adds each particle's two
 // contributions to this row (nodes x and x + 1, weight delta_k as in
 // Eq. (5)) as fixed-point integers in shared memory, one entry per active
-// node of the row; then it updates the row's compact records with plain
-// loads and stores (no other warp writes them).  A contribution to an
-// inactive node goes to the node field with atomics.  Particles that left
-// their bucket's row are skipped here and spread by migrant_spread_kernel.
+// node of the row; then it updates the row's compact records (variant A:
+// the accumulating second buffer) with plain loads and stores (no other warp
+// writes them).  A contribution to an inactive node goes with atomics to the
+// node field (B) or J_acc (A).  Particles that left their bucket's row are
+// skipped here and spread by migrant_spread_kernel.
 constexpr int GATHER_WARPS = 4;  // warps per block (fewer for very long rows)
 
 // Shared-memory sums of the row gather: 3 per active node (odd stride, so
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) spread_rows_kernel(PArgs<T>
     const int cnt = (int)last.y - base + __popc(last.x);
     acc_clear(acc, cnt, lane);
     __syncwarp();
-    N4 *rowp = a.node + (size_t)a.nx * nrow;
+    N4 *rowp = a.inactive_acc + (size_t)a.nx * nrow;
     // entries in passes of 64, two per lane, both loaded before either is used
     for (int t0 = 0; t0 < total; t0 += 64) {
         typename P::real4 Rv[2], Fv[2];
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) spread_rows_kernel(PArgs<T>
     }
     __syncwarp();
     // write-back in passes of 128 nodes, the four records loaded together
-    N4 *crec = a.cact + base;
+    N4 *crec = a.cact_acc + base;
     for (int k0 = 0; k0 < cnt; k0 += 128) {
         N4 rec[4];
 #pragma unroll
@@ -899,6 +900,8 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.kick_spreads = 0;
     a.occw = active_words_now(ctx);
     a.cact = static_cast<typename P::node4 *>(active_records_now(ctx));
+    a.cact_acc = static_cast<typename P::node4 *>(active_records_acc(ctx));
+    a.inactive_acc = ctx->p.variant == LBMD_VARIANT_A ? a.jacc : a.node;
     a.occ_words = active_words(ctx->p.nx);
     return a;
 }
@@ -909,7 +912,7 @@ static cudaError_t md_substep_t(lbmd_ctx *ctx, int substep) {
     PArgs<T> a = make_pargs<T>(ctx, substep);
     const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
     const bool cons = has_cons(ctx);
-    const bool B = ctx->p.variant == LBMD_VARIANT_B;
+    const bool B = compact_nodes(ctx);  // variants A and B: spreading into the compact records
     const bool atomic = B && (ctx->p.spread == LBMD_SPREAD_ATOMIC ||
                               (ctx->p.spread == LBMD_SPREAD_AUTO &&
                                ctx->np < (int64_t)LBMD_SPREAD_ATOMIC_PER_ROW * ctx->p.ny * ctx->p.nz));
@@ -1065,7 +1068,7 @@ static cudaError_t nb_build_t(lbmd_ctx *ctx) {
 }  // namespace lbmd
 
 cudaError_t launch_active_set(lbmd_ctx *ctx) {
-    if (ctx->p.variant != LBMD_VARIANT_B) return cudaSuccess;
+    if (!compact_nodes(ctx)) return cudaSuccess;
     return ctx->p.precision == LBMD_FP64 ? lbmd::active_set_t<double>(ctx) : lbmd::active_set_t<float>(ctx);
 }
 

@@ -25,8 +25,9 @@ LBMD_ERR_NONFINITE = -5
 LBMD_ERR_CAPACITY = -6
 LBMD_ERR_RANGE = -7
 VARIANT_A, VARIANT_B, VARIANT_C = 0, 1, 2
-FP32, FP64, FP16_DEV, BF16_DEV = 0, 1, 2, 3
-PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_DEV}
+FP32, FP64, FP16_DEV, BF16_DEV, FP16_DEV_SR, BF16_DEV_SR = 0, 1, 2, 3, 4, 5
+PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_DEV, "fp16dev_sr": FP16_DEV_SR,
+              "bf16dev_sr": BF16_DEV_SR}
 INTEGRATOR_START, INTEGRATOR_HALF_STEP = 0, 1
 INTEGRATORS = {"start": INTEGRATOR_START, "half_step": INTEGRATOR_HALF_STEP}
 SPREAD_AUTO, SPREAD_ROWS, SPREAD_ATOMIC, SPREAD_TILES = 0, 1, 2, 3
@@ -265,7 +266,9 @@ class LBMD:
     Keyword arguments are the fields of ``lbmd_params`` (lattice units,
     a = tau_LB = 1).  ``precision`` is ``"fp32"``, ``"fp64"``, ``"fp16dev"`` or
     ``"bf16dev"`` (populations stored as FP16 / BF16 deviations from the rest
-    state, FP32 arithmetic); ``variant`` is ``"A"``, ``"B"`` or ``"C"``;
+    state, FP32 arithmetic), or ``"fp16dev_sr"`` / ``"bf16dev_sr"`` (the same,
+    the collision rounding the stored deviations stochastically); ``variant``
+    is ``"A"``, ``"B"`` or ``"C"``;
     ``integrator`` is ``"start"`` (coupling force from the start of the MD
     step, Eq. (6)) or ``"half_step"`` (from the half-step velocity after the
     drift); ``spread`` (variant B) is ``"auto"``, ``"tiles"``, ``"rows"`` or ``"atomic"``

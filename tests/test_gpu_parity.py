@@ -228,13 +228,15 @@ def test_variant_c_several_cycles(precision):
 
 @pytest.mark.parametrize("integrator", ["start", "half_step"])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_variant_b_spread_paths_agree_bitwise(precision, integrator):
+@pytest.mark.parametrize("variant", ["A", "B"])
+def test_variant_b_spread_paths_agree_bitwise(precision, integrator, variant):
     # the row gather (+ migrant atomics) and the all-atomic path hand over the
-    # same fixed-point transfers: bitwise equal, and equal to the oracle
+    # same fixed-point transfers (variant A: into the accumulating copy of the
+    # frozen records): bitwise equal, and equal to the oracle
     shape, n = (24, 20, 18), 3000
     runs = {}
     for spread in ("rows", "atomic"):
-        o, g = pair(shape, precision=precision, variant="B", n_sub=5, kT=1e-4, zeta=1.5, seed=41, max_particles=n,
+        o, g = pair(shape, precision=precision, variant=variant, n_sub=5, kT=1e-4, zeta=1.5, seed=41, max_particles=n,
                     integrator=integrator, spread=spread)
         pos, vel = inputs.uniform_positions(n, shape, 41), inputs.maxwell_velocities(n, 1e-4, 41)
         g.add_particles(pos, vel)
