@@ -169,6 +169,39 @@ def _time_form(torch, lbmd, inputs, stream, precision, steps, pos, vel):
     return ms, lb_ms
 
 
+ACCURACY_CYCLES = 100  # 1000 MD steps at m = 10
+ACCURACY_FORMS = ("fp32", "fp16dev", "fp16dev_sr", "bf16dev", "bf16dev_sr")
+
+
+def _precision_accuracy(lbmd, inputs, stream, pos, vel):
+    """Per-observable errors of the storage forms on the benchmark workload
+    over 1000 MD steps, each from the same initial state and Philox streams:
+    the mass against N rho0, the total (fluid + particle) momentum against
+    that of the initial particles (both conserved exactly in exact
+    arithmetic), in units of the particles' thermal momentum sqrt(N_p m kT),
+    and the particle temperature against the FP32 run."""
+    import numpy as np
+
+    n_nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    p0 = np.asarray(vel).sum(axis=0)
+    p_scale = float(np.sqrt(N_PARTICLES * KT))
+    out = {"workload": WORKLOAD.replace(", FP32", "") + ", %d MD steps" % (ACCURACY_CYCLES * N_SUB)}
+    for prec in ACCURACY_FORMS:
+        sim = lbmd.LBMD(*SHAPE, variant="B", precision=prec, n_sub=N_SUB, kT=KT, zeta=ZETA, seed=SEED,
+                        max_particles=N_PARTICLES, stream=stream.cuda_stream)
+        sim.add_particles(pos, vel)
+        sim.run_cycles(ACCURACY_CYCLES)
+        ob = sim.observables()
+        sim.close()
+        row = {"mass_rel": float("%.3g" % abs(ob["mass"] / (n_nodes * 1.0) - 1.0)),
+               "momentum_rel": float("%.3g" % (np.linalg.norm(ob["p_fluid"] + ob["p_particles"] - p0) / p_scale)),
+               "kT_particles": float("%.6g" % ob["kT_particles"])}
+        if prec != "fp32":
+            row["kT_rel_vs_fp32"] = float("%.3g" % abs(ob["kT_particles"] / out["fp32"]["kT_particles"] - 1.0))
+        out[prec] = row
+    return out
+
+
 BATCH_REPLICAS, BATCH_MD_STEPS, BATCH_SAMPLE = 512, 2000, 10
 
 
@@ -542,7 +575,7 @@ def run_gpu(args):
         # the reduced-precision storage forms on the same workload, against
         # this plain FP32 path (algorithmic LB bytes 2 x 19 x 2 B per node)
         forms = {}
-        for prec in ("fp16dev", "bf16dev"):
+        for prec in ("fp16dev", "bf16dev", "fp16dev_sr", "bf16dev_sr"):
             ms, lb_ms = _time_form(torch, lbmd, inputs, stream, prec, min(args.steps, 50), pos0, vel0)
             lb_bytes = 2 * 19 * 2 * n_nodes
             forms[prec] = {"value": round(whole_job_rate(n_nodes, world, ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
@@ -551,6 +584,7 @@ def run_gpu(args):
                            "lb_step_speedup_vs_fp32": round(lb_avg_ms / lb_ms, 3),
                            "lb_roofline_frac": round(lb_bytes / (lb_ms * 1e-3) / 1e9 / peak, 4)}
         line["precision_forms"] = forms
+        line["precision_accuracy"] = _precision_accuracy(lbmd, inputs, stream, pos0, vel0)
         line["variants"] = _variant_costs(torch, lbmd, inputs, stream, pos0, vel0, min(args.steps, 30), ms_per_step)
         line["batched_replicas"] = _batched_replicas(torch, lbmd, inputs, stream, peak)
         line["adjoint"] = _adjoint_form(torch, lbmd, inputs)
@@ -699,7 +733,7 @@ def main():
                     help="non-cubic lattice (profiling of smaller cases with 256-node rows)")
     ap.add_argument("--particles", type=int, default=1_000_000)
     ap.add_argument("--kT", type=float, default=1e-4, help="temperature (profiling: 0 switches the noise off)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev", "fp16dev_sr", "bf16dev_sr"],
                     help="population storage of the timed workload (profiling)")
     ap.add_argument("--only-form", default=None, choices=["batched_replicas"],
                     help="run only this form and print its JSON object (profiling)")

@@ -67,9 +67,10 @@ typedef enum lbmd_status {
 enum { LBMD_VARIANT_A = 0, LBMD_VARIANT_B = 1, LBMD_VARIANT_C = 2 };
 /* Storage and arithmetic.  FP32 / FP64: populations, node field and particles
  * in that precision.  FP16_DEV / BF16_DEV: populations stored as deviations
- * f_i - w_i rho0 in FP16 / BF16 (round to nearest), everything else and all
- * arithmetic as in FP32; the rounding of the stored deviations breaks exact
- * mass conservation at the level of their last bit.  FP16_DEV_SR /
+ * f_i - w_i rho0 in FP16 / BF16 (round to nearest), everything else as in
+ * FP32, the LB arithmetic on the deviations (the mass moment is their sum);
+ * the rounding of the stored deviations breaks exact mass and momentum
+ * conservation at the level of their last bit (a random walk).  FP16_DEV_SR /
  * BF16_DEV_SR: the same storage, but the collision rounds each stored
  * deviation stochastically (up with probability equal to its distance from
  * the grid value below, in units of the grid step, resolved to 2^-16), with 16
@@ -281,6 +282,17 @@ lbmd_status lbmd_set_moments_wait(lbmd_ctx *ctx, int32_t polls);
  * were computed by the follow-up kernel, summed over every LB step since
  * creation (synchronising). */
 lbmd_status lbmd_moments_fallback_rows(lbmd_ctx *ctx, int64_t *rows);
+
+/* Variant A (Sec. 3): where the MD steps of a cycle read the node velocities
+ * frozen at the last LB step.  on = 1: a copy of the active nodes' compact
+ * records, made by the post-stream moments (the transfers then go to the
+ * records themselves); on = 0: the node field.  Results are the same bit for
+ * bit; the default is the node field while it takes at most a quarter of the
+ * device's L2 cache (its scattered reads stay on chip), the copy above.
+ * Only at a cycle boundary; no effect for variants B and C.
+ * Errors: LBMD_ERR_ARG (on not 0 or 1), LBMD_ERR_SEQUENCE (MD steps of the
+ * cycle done), LBMD_ERR_CUDA. */
+lbmd_status lbmd_set_frozen_copy(lbmd_ctx *ctx, int32_t on);
 
 /* Synchronising accessors (host arrays, id order, FP64). */
 /* populations f*_i after the last streaming step: 19 N doubles, [i][r] */

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) ad_collide_push(const T *fin, T *fout, co
     T rho, jx, jy, jz, Fx, Fy, Fz;
     node_moments(f, rho, jx, jy, jz);
     node_force(a, node[r], jx, jy, jz, Fx, Fy, Fz);
-    collide<T, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, (uint32_t)r, step);
+    collide<T, RELAX_FULL>(f, rho, rho, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, (uint32_t)r, step);
 #pragma unroll
     for (int i = 0; i < Q; ++i) fout[(int64_t)i * a.N + neighbour(a, x, y, z, i)] = f[i];
 }

@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(BATCH_LB_MAX_THREADS, sizeof(T) == 4 ? 4 : 2) 
             zero.x = zero.y = zero.z = zero.w = 0;
             a.jacc[rp.node_off + loc] = zero;
         }
-        collide<T, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, rp.key0, rp.key1, u, (uint32_t)step);
+        collide<T, RELAX_FULL>(f, rho, rho, jx, jy, jz, Fx, Fy, Fz, a, rp.key0, rp.key1, u, (uint32_t)step);
         const int nx = rp.nx, ny = rp.ny, nz = rp.nz;
         const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
         const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;

@@ -28,14 +28,14 @@ template <typename T, typename S>
 struct LbArgs {
     const S *__restrict__ fin;
     S *__restrict__ fout;
-    T rho0;  // reference density of the deviation storage
+    T rho_base;  // deviation storage: sum_i of the stored rest values w_i rho0
     typename Prec<T>::node4 *node;
     typename Prec<T>::node4 *jacc;
     const uint2 *occw;                     // variant B: active nodes of this cycle
     const typename Prec<T>::node4 *cact;   // variant B: their compact records
     const uint2 *occw_new;                 // variant B: active nodes of the next cycle
     typename Prec<T>::node4 *cact_new;     // ... whose records the fused moments write
-    typename Prec<T>::node4 *cact_new2;    // variant A: the same records again (the next cycle's accumulator)
+    typename Prec<T>::node4 *cact_new2;    // variant A with a frozen copy: the same records again
     int occ_words;
     // fused post-stream moments (dataflow between collide blocks)
     uint32_t *blk_done;
@@ -72,16 +72,16 @@ __device__ __forceinline__ typename Prec<T>::node4 guarded_record(T rho, T jx, T
 template <typename T, typename S>
 __device__ __forceinline__ void node_moments_at(const S *f, typename Prec<T>::node4 *node, const uint2 *occw,
                                                 typename Prec<T>::node4 *cact, typename Prec<T>::node4 *cact2,
-                                                int occ_words, int64_t N, int nx, int ny, T rho0, T fs,
+                                                int occ_words, int64_t N, int nx, int ny, T rho_base, T fs,
                                                 int32_t *range_flag, int x, int y, int t) {
     using P = Prec<T>;
     using St = PopStore<S, T>;
     const uint32_t r = (uint32_t)x + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)t);
     T fl[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fl[i] = St::load_cg(f + (size_t)i * N + r, T(WEIGHT(i)) * rho0);
-    T rho, jx, jy, jz;
-    node_moments(fl, rho, jx, jy, jz);
+    for (int i = 0; i < Q; ++i) fl[i] = St::arith_cg(f + (size_t)i * N + r);
+    T rho, rho_m, jx, jy, jz;
+    pop_moments<St::deviation>(fl, rho_base, rho, rho_m, jx, jy, jz);
     const typename P::node4 rec = guarded_record(rho, jx, jy, jz, fs, range_flag);
     node[r] = rec;
     if (occw) {
@@ -118,9 +118,9 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
     const uint32_t r = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     T f[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = St::load(a.fin + (size_t)i * a.N + r, T(WEIGHT(i)) * a.rho0);
-    T rho, jx, jy, jz;
-    node_moments(f, rho, jx, jy, jz);
+    for (int i = 0; i < Q; ++i) f[i] = St::arith(a.fin + (size_t)i * a.N + r);
+    T rho, rho_m, jx, jy, jz;
+    pop_moments<St::deviation>(f, a.rho_base, rho, rho_m, jx, jy, jz);
     T Fx, Fy, Fz;
     const int sl = a.occw ? active_slot(a.occw[((size_t)y + (size_t)a.ny * z) * a.occ_words + (x >> 5)], x) : -1;
     if (sl >= 0 || a.variant == LBMD_VARIANT_B) {
@@ -156,7 +156,7 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
     Fx += a.g[0];
     Fy += a.g[1];
     Fz += a.g[2];
-    collide<T, RELAX_FULL>(f, rho, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, r, (uint32_t)step);
+    collide<T, RELAX_FULL>(f, rho, rho_m, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, r, (uint32_t)step);
 
     const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
@@ -173,14 +173,14 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
             const uint32_t w = ((i >> 1) & 3) == 0 ? rb.x : ((i >> 1) & 3) == 1 ? rb.y : ((i >> 1) & 3) == 2 ? rb.z : rb.w;
             const uint32_t t = (uint32_t)X[CX(i) + 1] +
                                (uint32_t)a.nx * ((uint32_t)Y[CY(i) + 1] + (uint32_t)a.ny * (uint32_t)Z[CZ(i) + 1]);
-            St::store_sr(a.fout + (size_t)i * a.N + t, f[i], T(WEIGHT(i)) * a.rho0, (i & 1) ? w >> 16 : w & 0xffffu);
+            St::store_arith_sr(a.fout + (size_t)i * a.N + t, f[i], (i & 1) ? w >> 16 : w & 0xffffu);
         }
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const uint32_t t = (uint32_t)X[CX(i) + 1] +
                                (uint32_t)a.nx * ((uint32_t)Y[CY(i) + 1] + (uint32_t)a.ny * (uint32_t)Z[CZ(i) + 1]);
-            St::store(a.fout + (size_t)i * a.N + t, f[i], T(WEIGHT(i)) * a.rho0);
+            St::store_arith(a.fout + (size_t)i * a.N + t, f[i]);
         }
     }
 }
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(L
     }
     if (x < a.nx)
         node_moments_at<T, S>(a.fout, a.node, a.occw_new, a.cact_new, a.cact_new2, a.occ_words, a.N, a.nx, a.ny,
-                              a.rho0, a.fs, a.range_flag, x, y, t);
+                              a.rho_base, a.fs, a.range_flag, x, y, t);
 }
 
 // The moments the collide kernel left: node rows of plane 0 and of the last
@@ -245,8 +245,7 @@ template <typename T, typename S>
 __global__ void __launch_bounds__(256)
     moments_rest_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
                         typename Prec<T>::node4 *cact, typename Prec<T>::node4 *cact2, int occ_words, int64_t N,
-                        int nx, int ny, int nz, T rho0,
-                        T fs, int32_t *range_flag, const int32_t *missed, const int32_t *missed_list,
+                        int nx, int ny, int nz, T rho_base, T fs, int32_t *range_flag, const int32_t *missed, const int32_t *missed_list,
                         unsigned long long *missed_total, unsigned long long *lb_step) {
     const int gx = (nx + (int)blockDim.x - 1) / (int)blockDim.x;
     const int rows = gx * ny;
@@ -267,7 +266,8 @@ __global__ void __launch_bounds__(256)
         const int xb = b % gx, rest = b / gx, y = rest % ny, t = rest / ny;
         const int x = xb * (int)blockDim.x + (int)threadIdx.x;
         if (x < nx)
-            node_moments_at<T, S>(f, node, occw, cact, cact2, occ_words, N, nx, ny, rho0, fs, range_flag, x, y, t);
+            node_moments_at<T, S>(f, node, occw, cact, cact2, occ_words, N, nx, ny, rho_base, fs, range_flag, x, y,
+                                  t);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *missed_total += (unsigned long long)*missed;
@@ -279,10 +279,10 @@ template <typename T, typename S>
 __global__ void __launch_bounds__(256)
     node_moments_kernel(const S *__restrict__ f, typename Prec<T>::node4 *node, const uint2 *occw,
                         typename Prec<T>::node4 *cact, typename Prec<T>::node4 *cact2, int occ_words, int64_t N,
-                        int nx, int ny, T rho0, T fs, int32_t *range_flag) {
+                        int nx, int ny, T rho_base, T fs, int32_t *range_flag) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
-    node_moments_at<T, S>(f, node, occw, cact, cact2, occ_words, N, nx, ny, rho0, fs, range_flag, x, blockIdx.y,
+    node_moments_at<T, S>(f, node, occw, cact, cact2, occ_words, N, nx, ny, rho_base, fs, range_flag, x, blockIdx.y,
                           blockIdx.z);
 }
 
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256)
 // and J_acc is cleared.  Nodes without a transfer are left as they are.
 template <typename T, typename S>
 __global__ void __launch_bounds__(256) forcing_update_kernel(S *__restrict__ f, typename Prec<T>::node4 *node,
-                                                             typename Prec<T>::node4 *jacc, int64_t N, T rho0,
+                                                             typename Prec<T>::node4 *jacc, int64_t N, T rho_base,
                                                              T gamma_bulk, T gamma_shear, T fix_s, T fix_is,
                                                              int32_t *range_flag) {
     using P = Prec<T>;
@@ -307,9 +307,9 @@ __global__ void __launch_bounds__(256) forcing_update_kernel(S *__restrict__ f, 
             Fz = P::from_fix(P::jz_of(J), fix_is);
     T fl[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fl[i] = St::load(f + (int64_t)i * N + r, T(WEIGHT(i)) * rho0);
-    T rho, jx, jy, jz;
-    node_moments(fl, rho, jx, jy, jz);
+    for (int i = 0; i < Q; ++i) fl[i] = St::arith(f + (int64_t)i * N + r);
+    T rho, rho_m, jx, jy, jz;
+    pop_moments<St::deviation>(fl, rho_base, rho, rho_m, jx, jy, jz);
     const T ir = T(1) / rho;
     const T ux = (jx + T(0.5) * Fx) * ir, uy = (jy + T(0.5) * Fy) * ir, uz = (jz + T(0.5) * Fz) * ir;
     const T uF = ux * Fx + uy * Fy + uz * Fz;
@@ -335,9 +335,9 @@ __global__ void __launch_bounds__(256) forcing_update_kernel(S *__restrict__ f, 
             if (e != 0) acc += T(e) * dm[k] * T(INV_BNORM(k));
         }
         fl[i] += T(WEIGHT(i)) * acc;
-        St::store(f + (int64_t)i * N + r, fl[i], T(WEIGHT(i)) * rho0);
+        St::store_arith(f + (int64_t)i * N + r, fl[i]);
     }
-    node_moments(fl, rho, jx, jy, jz);
+    pop_moments<St::deviation>(fl, rho_base, rho, rho_m, jx, jy, jz);
     node[r] = guarded_record(rho, jx, jy, jz, fix_s, range_flag);
     typename P::node4 zero;
     zero.x = zero.y = zero.z = zero.w = 0;
@@ -361,12 +361,23 @@ static dim3 node_grid(const lbmd_ctx *ctx, dim3 block) {
     return dim3((ctx->p.nx + block.x - 1) / block.x, ctx->p.ny, ctx->p.nz);
 }
 
+// Deviation storage: the density of the stored rest values, sum_i b_i with
+// b_i = w_i rho0 formed in T as the kernels form it (0 for the plain forms,
+// whose arithmetic is on the populations themselves).
+template <typename T, typename S>
+static T rest_density(const lbmd_ctx *ctx) {
+    if (!PopStore<S, T>::deviation) return T(0);
+    double sum = 0.0;
+    for (int i = 0; i < Q; ++i) sum += (double)(T(WEIGHT(i)) * (T)ctx->p.rho0);
+    return (T)sum;
+}
+
 template <typename T, typename S>
 static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     LbArgs<T, S> a;
     a.fin = static_cast<const S *>(ctx->f[ctx->cur]);
     a.fout = static_cast<S *>(ctx->f[ctx->cur ^ 1]);
-    a.rho0 = (T)ctx->p.rho0;
+    a.rho_base = rest_density<T, S>(ctx);
     a.node = static_cast<typename Prec<T>::node4 *>(ctx->node);
     a.jacc = static_cast<typename Prec<T>::node4 *>(ctx->jacc);
     const bool B = compact_nodes(ctx);  // variants A and B
@@ -374,8 +385,7 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.cact = static_cast<const typename Prec<T>::node4 *>(B ? active_records_acc(ctx) : nullptr);
     a.occw_new = B ? active_words_next(ctx) : nullptr;
     a.cact_new = static_cast<typename Prec<T>::node4 *>(B ? active_records_next(ctx) : nullptr);
-    a.cact_new2 = static_cast<typename Prec<T>::node4 *>(B ? active_records_copy(ctx, (int)((ctx->lb_step + 1) & 1))
-                                                           : nullptr);
+    a.cact_new2 = static_cast<typename Prec<T>::node4 *>(active_records_copy(ctx, (int)((ctx->lb_step + 1) & 1)));
     a.occ_words = active_words(ctx->p.nx);
     a.blk_done = ctx->blk_done;
     a.missed = ctx->lb_missed;
@@ -409,8 +419,8 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     // the moments the collide kernel left, on the new populations
     moments_rest_kernel<T, S><<<2 * ctx->sm_count, block, 0, ctx->stream>>>(
         a.fout, a.node, a.occw_new, a.cact_new, a.cact_new2, a.occ_words, ctx->N, ctx->p.nx, ctx->p.ny, ctx->p.nz,
-        a.rho0, a.fs,
-        ctx->range_flag, ctx->lb_missed, ctx->missed_list, ctx->missed_total, ctx->d_lb_step);
+        a.rho_base,
+        a.fs, ctx->range_flag, ctx->lb_missed, ctx->missed_list, ctx->missed_total, ctx->d_lb_step);
     return cudaGetLastError();
 }
 
@@ -424,8 +434,9 @@ static cudaError_t node_moments_t(lbmd_ctx *ctx) {
         static_cast<const S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
         B ? active_words_now(ctx) : nullptr,
         static_cast<typename Prec<T>::node4 *>(B ? active_records_now(ctx) : nullptr),
-        static_cast<typename Prec<T>::node4 *>(B ? active_records_copy(ctx, (int)(ctx->lb_step & 1)) : nullptr),
-        active_words(ctx->p.nx), ctx->N, ctx->p.nx, ctx->p.ny, (T)ctx->p.rho0, (T)ctx->fix.scale, ctx->range_flag);
+        static_cast<typename Prec<T>::node4 *>(active_records_copy(ctx, (int)(ctx->lb_step & 1))),
+        active_words(ctx->p.nx), ctx->N, ctx->p.nx, ctx->p.ny, rest_density<T, S>(ctx), (T)ctx->fix.scale,
+        ctx->range_flag);
     return cudaGetLastError();
 }
 
@@ -434,7 +445,7 @@ static cudaError_t forcing_update_t(lbmd_ctx *ctx) {
     const unsigned blocks = (unsigned)((ctx->N + 255) / 256);
     forcing_update_kernel<T, S><<<blocks, 256, 0, ctx->stream>>>(
         static_cast<S *>(ctx->f[ctx->cur]), static_cast<typename Prec<T>::node4 *>(ctx->node),
-        static_cast<typename Prec<T>::node4 *>(ctx->jacc), ctx->N, (T)ctx->p.rho0, (T)ctx->co.gamma_bulk,
+        static_cast<typename Prec<T>::node4 *>(ctx->jacc), ctx->N, rest_density<T, S>(ctx), (T)ctx->co.gamma_bulk,
         (T)ctx->co.gamma_shear, (T)ctx->fix.scale, (T)ctx->fix.inv_scale, ctx->range_flag);
     return cudaGetLastError();
 }

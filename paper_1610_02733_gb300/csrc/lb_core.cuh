@@ -32,7 +32,12 @@ static_assert(inv_bnorm_matches(), "INV_BNORM(k) must be 1 / BNORM(k)");
 __host__ __device__ constexpr bool EVEN_MODE(int k) { return k == 0 || (k >= 4 && k <= 9) || k >= 16; }
 
 // MRT collision with forcing and noise at one node; f holds f* on entry and
-// f' on exit.
+// f' on exit -- or, for a deviation storage form, f* - b and f' - b with b the
+// stored rest values (see PopStore): the collision is linear in the moments,
+// and the mass mode takes rho_m (the density, or its part sum_i (f*_i - b_i)),
+// while u, the equilibria and the noise amplitudes take the density rho.  With
+// sum_i w_i = 1 and sum_i w_i e_k(c_i) = 0 for k > 0 the deviations then keep
+// their sum, so the mass is conserved up to the rounding of small numbers.
 // 1/rho and sqrt(rho): IEEE in FP64; in FP32 both from one reciprocal square
 // root (at most a few ulp, far below the FP32 path's tolerance)
 __device__ __forceinline__ void rho_factors(double rho, double &inv, double &sq) {
@@ -60,8 +65,8 @@ __device__ __forceinline__ double centred16(uint32_t h, double) { return (double
 // amp16[Q] and noisy (the single-box and the batched kernels); the Philox
 // key (key0, key1) and counters (node, step) come as arguments.
 template <typename T, bool RELAX_FULL, typename A>
-__device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T Fy, T Fz, const A &a, uint32_t key0,
-                                        uint32_t key1, uint32_t node, uint32_t step) {
+__device__ __forceinline__ void collide(T f[Q], T rho, T rho_m, T jx, T jy, T jz, T Fx, T Fy, T Fz, const A &a,
+                                        uint32_t key0, uint32_t key1, uint32_t node, uint32_t step) {
     T inv_rho, sr;
     rho_factors(rho, inv_rho, sr);
     const T ux = (jx + T(0.5) * Fx) * inv_rho;
@@ -101,7 +106,7 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T jx, T jy, T jz, T Fx, T
     meq[9] = rho * uy * uz;
 
     T mp[Q];
-    mp[0] = rho;
+    mp[0] = rho_m;
     mp[1] = jx + Fx;
     mp[2] = jy + Fy;
     mp[3] = jz + Fz;

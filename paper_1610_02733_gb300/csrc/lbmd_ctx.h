@@ -149,6 +149,7 @@ struct lbmd_ctx {
     int fuse_spin;         // polls of a collide block's wait (0: no fused moments)
     int sm_count;
     int gather_warps;  // warps per block of the variant B row gather
+    bool a_frozen_copy;  // variant A: interpolate from a frozen copy of the compact records (else the node field)
     int32_t *bond_count, *bond_partner;
     double *bond_k, *bond_r0;
     uint8_t *bond_kind;  // LBMD_BOND_HARMONIC or LBMD_BOND_FENE per (id, bond)
@@ -198,22 +199,25 @@ inline void *active_records_other(const lbmd_ctx *c) {
 inline uint2 *active_words_next(const lbmd_ctx *c) { return c->occw[(c->lb_step + 1) & 1]; }
 inline void *active_records_next(const lbmd_ctx *c) { return c->cact[(c->lb_step + 1) & 1]; }
 // Variants A and B keep the node records of the active nodes in compact
-// arrays (variant C updates the populations every MD step instead).  Variant
-// A reads the frozen records (first buffer of the set) and accumulates the
-// transfers in the set's second buffer, which starts as a copy of the first;
-// variant B reads and updates one buffer.
+// arrays, which the MD steps add their transfers to (variant C updates the
+// populations every MD step instead).  Variant B's MD steps also read them.
+// Variant A's read the node velocities as the LB step left them: from the
+// node field, which nobody writes between LB steps in A (transfers to
+// inactive nodes go to J_acc), or -- when the node field is too large for the
+// L2 cache, where its scattered reads cost more than a copy -- from the first
+// buffer of the set, the transfers then going to the second buffer, which the
+// moments fill with the same records.
 inline bool compact_nodes(const lbmd_ctx *c) { return c->p.variant != LBMD_VARIANT_C; }
+inline bool a_copy(const lbmd_ctx *c) { return c->p.variant == LBMD_VARIANT_A && c->a_frozen_copy; }
 // the records the MD steps add transfers to (and the LB step reads)
 inline void *active_records_acc(const lbmd_ctx *c) {
-    return c->p.variant == LBMD_VARIANT_A
-               ? static_cast<char *>(c->cact[c->lb_step & 1]) + (size_t)c->cact_cap * c->node_bytes
-               : active_records_now(c);
+    return a_copy(c) ? static_cast<char *>(c->cact[c->lb_step & 1]) + (size_t)c->cact_cap * c->node_bytes
+                     : active_records_now(c);
 }
-// variant A: the second buffer of a set, which the moments fill with the same
-// records as the first (null for B)
+// the second buffer of set `set`, which the moments fill with the same records
+// as the first (null unless variant A keeps a frozen copy)
 inline void *active_records_copy(const lbmd_ctx *c, int set) {
-    return c->p.variant == LBMD_VARIANT_A ? static_cast<char *>(c->cact[set]) + (size_t)c->cact_cap * c->node_bytes
-                                          : nullptr;
+    return a_copy(c) ? static_cast<char *>(c->cact[set]) + (size_t)c->cact_cap * c->node_bytes : nullptr;
 }
 inline void *pos_now(const lbmd_ctx *c) { return c->pos4[c->pv]; }
 inline void *vel_now(const lbmd_ctx *c) { return c->vel4[c->pv]; }

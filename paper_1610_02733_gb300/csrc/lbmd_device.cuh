@@ -250,11 +250,23 @@ struct Prec<double> {
 // deviation to nearest (FP16 / BF16) or stochastically (the _SR forms below);
 // every other store (initial and user-given states) rounds to nearest.
 // ---------------------------------------------------------------------------
+//
+// The kernels do their arithmetic on what is stored: f_i itself for the
+// plain forms, the deviation for the reduced ones (arith / arith_cg /
+// store_arith), so that the mass moment of a deviation form is the FP32 sum of
+// small deviations rather than of values near w_i rho0 -- the FP32 sum of the
+// latter rounds the same way at every node of a near-uniform fluid, and the
+// collision would write that rounding back into the populations every step.
+// load / store convert to and from the population itself (host accessors,
+// initial state).
 template <typename S, typename T>
 struct PopStore {  // plain storage: S == T
     __device__ static __forceinline__ T load(const S *p, T /*base*/) { return *p; }
     __device__ static __forceinline__ T load_cg(const S *p, T /*base*/) { return __ldcg(p); }
     __device__ static __forceinline__ void store(S *p, T v, T /*base*/) { *p = v; }
+    __device__ static __forceinline__ T arith(const S *p) { return *p; }
+    __device__ static __forceinline__ T arith_cg(const S *p) { return __ldcg(p); }
+    __device__ static __forceinline__ void store_arith(S *p, T v) { *p = v; }
     static constexpr bool deviation = false;
     static constexpr bool stochastic = false;
 };
@@ -275,10 +287,13 @@ __device__ __forceinline__ __half fp16_round_stochastic(float x, uint32_t r) {
     const float a = fabsf(x);
     const unsigned short lo = __half_as_ushort(__float2half_rz(a));  // towards zero, subnormals included
     const float lo_f = __half2float(__ushort_as_half(lo));
-    // the grid step above lo (a power of two: the divisions below are exact)
+    // the grid step above lo, a power of two 2^k (k >= -24), and 2^16 / step
+    // = 2^(16 - k) built from its exponent field: the product below is exact
     const float step = __half2float(__ushort_as_half((unsigned short)(lo + 1))) - lo_f;
-    const float t = (a - lo_f) / step * 65536.0f;  // a - lo_f is exact (Sterbenz)
-    const unsigned short up = (lo < 0x7bffu && (float)r < t) ? 1 : 0;
+    const float t = (a - lo_f) * __uint_as_float(0x87000000u - __float_as_uint(step));  // a - lo_f exact (Sterbenz)
+    // r < t with r < 2^16 as the float 2^23 + r - 2^23 (exact, no conversion)
+    const float rf = __uint_as_float(0x4B000000u | r) - 8388608.0f;
+    const unsigned short up = (lo < 0x7bffu && rf < t) ? 1 : 0;
     const unsigned short sign = (unsigned short)((__float_as_uint(x) >> 16) & 0x8000u);
     return __ushort_as_half((unsigned short)(sign | (lo + up)));
 }
@@ -298,6 +313,11 @@ struct PopStore<__half, float> {
         return base + __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
     }
     __device__ static __forceinline__ void store(__half *p, float v, float base) { *p = __float2half_rn(v - base); }
+    __device__ static __forceinline__ float arith(const __half *p) { return __half2float(*p); }
+    __device__ static __forceinline__ float arith_cg(const __half *p) {
+        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __forceinline__ void store_arith(__half *p, float d) { *p = __float2half_rn(d); }
     static constexpr bool deviation = true;
     static constexpr bool stochastic = false;
 };
@@ -312,6 +332,11 @@ struct PopStore<__nv_bfloat16, float> {
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v, float base) {
         *p = __float2bfloat16_rn(v - base);
     }
+    __device__ static __forceinline__ float arith(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ float arith_cg(const __nv_bfloat16 *p) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __forceinline__ void store_arith(__nv_bfloat16 *p, float d) { *p = __float2bfloat16_rn(d); }
     static constexpr bool deviation = true;
     static constexpr bool stochastic = false;
 };
@@ -326,9 +351,16 @@ struct PopStore<half_sr, float> {
     __device__ static __forceinline__ void store(half_sr *p, float v, float base) {
         p->u = __half_as_ushort(__float2half_rn(v - base));
     }
+    __device__ static __forceinline__ float arith(const half_sr *p) { return __half2float(__ushort_as_half(p->u)); }
+    __device__ static __forceinline__ float arith_cg(const half_sr *p) {
+        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __forceinline__ void store_arith(half_sr *p, float d) {
+        p->u = __half_as_ushort(__float2half_rn(d));
+    }
     // r: 16 random bits
-    __device__ static __forceinline__ void store_sr(half_sr *p, float v, float base, uint32_t r) {
-        p->u = __half_as_ushort(fp16_round_stochastic(v - base, r));
+    __device__ static __forceinline__ void store_arith_sr(half_sr *p, float d, uint32_t r) {
+        p->u = __half_as_ushort(fp16_round_stochastic(d, r));
     }
     static constexpr bool deviation = true;
     static constexpr bool stochastic = true;
@@ -344,8 +376,17 @@ struct PopStore<bf16_sr, float> {
     __device__ static __forceinline__ void store(bf16_sr *p, float v, float base) {
         p->u = __bfloat16_as_ushort(__float2bfloat16_rn(v - base));
     }
-    __device__ static __forceinline__ void store_sr(bf16_sr *p, float v, float base, uint32_t r) {
-        p->u = __bfloat16_as_ushort(bf16_round_stochastic(v - base, r));
+    __device__ static __forceinline__ float arith(const bf16_sr *p) {
+        return __bfloat162float(__ushort_as_bfloat16(p->u));
+    }
+    __device__ static __forceinline__ float arith_cg(const bf16_sr *p) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+    }
+    __device__ static __forceinline__ void store_arith(bf16_sr *p, float d) {
+        p->u = __bfloat16_as_ushort(__float2bfloat16_rn(d));
+    }
+    __device__ static __forceinline__ void store_arith_sr(bf16_sr *p, float d, uint32_t r) {
+        p->u = __bfloat16_as_ushort(bf16_round_stochastic(d, r));
     }
     static constexpr bool deviation = true;
     static constexpr bool stochastic = true;
@@ -362,6 +403,16 @@ __device__ __forceinline__ void node_moments(const T f[Q], T &rho, T &jx, T &jy,
     jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
     jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) + (f[17] - f[18]);
     jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) + (f[15] - f[16]) + (f[18] - f[17]);
+}
+
+// The same from the values the arithmetic works on (PopStore::arith): rho_m
+// is their sum (the density itself, or, for a deviation form, the density
+// minus rho_base = sum_i of the stored rest values) and rho the density.
+// The rest values of opposite velocities are equal, so j is the same sum.
+template <bool DEV, typename T>
+__device__ __forceinline__ void pop_moments(const T f[Q], T rho_base, T &rho, T &rho_m, T &jx, T &jy, T &jz) {
+    node_moments(f, rho_m, jx, jy, jz);
+    rho = DEV ? rho_base + rho_m : rho_m;
 }
 
 // ---------------------------------------------------------------------------

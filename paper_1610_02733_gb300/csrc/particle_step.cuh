@@ -41,9 +41,10 @@ struct PArgs {
     // variant B row-gather spreading and active nodes
     const int32_t *row_start, *slot_row;
     const uint2 *occw;
-    typename P::node4 *cact;          // the active nodes' records the MD step reads
-    typename P::node4 *cact_acc;      // ... and the ones it adds transfers to (variant A: a second buffer)
+    typename P::node4 *cact;          // the active nodes' records (variant A with a frozen copy: the frozen ones)
+    typename P::node4 *cact_acc;      // ... the ones the transfers go to (the same unless A keeps a frozen copy)
     typename P::node4 *inactive_acc;  // where transfers to inactive nodes go (A: J_acc, B: the node field)
+    int interp_compact;               // interpolate from cact (B; A with a frozen copy), else the node field
     int occ_words;
     int32_t *migrant_slot, *migrant_count;  // two lists of np_cap slots, two counters
     int b_atomic;      // variant B spreads every particle with atomics (no row gather, no migrant lists)
@@ -103,7 +104,7 @@ __device__ __forceinline__ void interp_u(const PArgs<T> &a, const CellXYZ &c, T 
     corner_rows(c, a.ny, a.nz, rows);
     const int x1 = c.x + 1 == a.nx ? 0 : c.x + 1;
     interp_u_from(fx, fy, fz, a.fis, ux, uy, uz, [&](int q, typename P::node4 &n0, typename P::node4 &n1) {
-        if (a.occw) {  // variants A and B: an active corner's compact record
+        if (a.interp_compact) {  // an active corner's compact record
             corner_pair(a, rows[q], c.x, x1, n0, n1);
         } else {
             const size_t r0 = (size_t)rows[q] * (uint32_t)a.nx;
@@ -149,7 +150,7 @@ __device__ __forceinline__ void coupling_force(const PArgs<T> &a, int64_t p, con
 // belongs to the nodes around position R (cell c): variant C adds it to
 // J_acc at once (forcing_update_kernel then moves it into the populations);
 // variants A and B keep R for the row gather (which adds the transfers to the
-// compact records: B's own, A's second buffer), and a particle whose cell row
+// compact records, cact_acc), and a particle whose cell row
 // is no longer the row bucket it was sorted into is listed as a migrant (two
 // lists alternating with the parity of the MD step).
 template <typename T>

@@ -151,9 +151,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) couple_half_kerne
 // row, the warp reads those buckets and adds each particle's two
 // contributions to this row (nodes x and x + 1, weight delta_k as in
 // Eq. (5)) as fixed-point integers in shared memory, one entry per active
-// node of the row; then it updates the row's compact records (variant A:
-// the accumulating second buffer) with plain loads and stores (no other warp
-// writes them).  A contribution to an inactive node goes with atomics to the
+// node of the row; then it updates the row's compact records with plain
+// loads and stores (no other warp writes them).  A contribution to an inactive node goes with atomics to the
 // node field (B) or J_acc (A).  Particles that left their bucket's row are
 // skipped here and spread by migrant_spread_kernel.
 constexpr int GATHER_WARPS = 4;  // warps per block (fewer for very long rows)
@@ -901,6 +900,7 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.occw = active_words_now(ctx);
     a.cact = static_cast<typename P::node4 *>(active_records_now(ctx));
     a.cact_acc = static_cast<typename P::node4 *>(active_records_acc(ctx));
+    a.interp_compact = ctx->p.variant == LBMD_VARIANT_B || a_copy(ctx) ? 1 : 0;
     a.inactive_acc = ctx->p.variant == LBMD_VARIANT_A ? a.jacc : a.node;
     a.occ_words = active_words(ctx->p.nx);
     return a;

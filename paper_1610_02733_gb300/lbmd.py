@@ -40,7 +40,7 @@ EXPORTS = (
     "lbmd_md_substep", "lbmd_lb_step", "lbmd_run_cycles", "lbmd_observables", "lbmd_get_populations",
     "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
-    "lbmd_particle_sums_static", "lbmd_set_moments_wait", "lbmd_moments_fallback_rows",
+    "lbmd_particle_sums_static", "lbmd_set_moments_wait", "lbmd_moments_fallback_rows", "lbmd_set_frozen_copy",
     "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add_particles", "lbmd_batch_run", "lbmd_batch_kinetic",
     "lbmd_batch_kinetic_device",
     "lbmd_batch_unstable", "lbmd_batch_get_populations", "lbmd_batch_set_populations", "lbmd_batch_get_particles",
@@ -132,6 +132,7 @@ def load():
     L.lbmd_particle_sums_static.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p]
     L.lbmd_set_moments_wait.argtypes = [P, ct.c_int32]
     L.lbmd_moments_fallback_rows.argtypes = [P, i64p]
+    L.lbmd_set_frozen_copy.argtypes = [P, ct.c_int32]
     L.lbmd_stream.restype = ct.c_void_p
     L.lbmd_stream.argtypes = [P]
     L.lbmd_last_error.restype = ct.c_char_p
@@ -421,6 +422,12 @@ class LBMD:
         """Poll limit of the fused post-stream moments' wait (-1: default, 0:
         every row to the follow-up kernel); results do not depend on it."""
         _check(self._h, load().lbmd_set_moments_wait(self._h, int(polls)), "lbmd_set_moments_wait")
+
+    def set_frozen_copy(self, on: bool):
+        """Variant A: read the frozen node velocities from a copy of the
+        compact records (True) or the node field (False); same results.  Only
+        at a cycle boundary."""
+        _check(self._h, load().lbmd_set_frozen_copy(self._h, 1 if on else 0), "lbmd_set_frozen_copy")
 
     def moments_fallback_rows(self) -> int:
         """Rows whose fused moments the follow-up kernel computed, since creation."""

@@ -48,3 +48,60 @@ def assert_vec_close(got, want, precision, what):
     tol = {"fp32": 1e-5, "fp64": 1e-12}[precision]
     assert err <= tol, "%s: max error %.3e of scale %.3e > %.0e" % (what, err, scale, tol)
     return err
+
+
+# Reduced-precision storage: grid of the stored deviation and whether the
+# collision rounds it stochastically.
+STORAGE = {"fp16dev": ("fp16", False), "bf16dev": ("bf16", False), "fp16dev_sr": ("fp16", True),
+           "bf16dev_sr": ("bf16", True)}
+
+D3Q19_C = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 0],
+                    [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1], [-1, 0, 1], [0, 1, 1],
+                    [0, -1, -1], [0, 1, -1], [0, -1, 1]])
+
+
+def storage_base32(rho0=1.0):
+    """The FP32 rest value w_i rho0 the deviations are taken from."""
+    return (W.astype(np.float32) * np.float32(rho0)).astype(np.float32)
+
+
+def expected_readback(post, i, src, precision, seed, lb_step, rho0=1.0):
+    """What the GPU reads back for population i whose exact (oracle)
+    post-collision value at source node src is `post`: the deviation from
+    the FP32 rest value rounded by the oracle onto the storage grid (to
+    nearest, or stochastically with the Philox bits of (src, lb_step)), then
+    added back to the rest value in FP32.  Returns (value, grid step of the
+    exact deviation, distance of the exact deviation from the nearest point
+    where the rounding decision changes: the rounding threshold, or a grid
+    value)."""
+    fmt, sr = STORAGE[precision]
+    post, i, src = np.asarray(post, dtype=np.float64), np.asarray(i), np.asarray(src, dtype=np.uint32)
+    base = storage_base32(rho0)[i]
+    dev = post - base.astype(np.float64)
+    r16 = orc.sr_bits(seed, src, lb_step)[np.arange(src.size), i] if sr else None
+    stored = orc.round_storage(dev, fmt, r16)
+    value = (base + stored.astype(np.float32)).astype(np.float64)
+    p, emin = orc.STORAGE_FORMATS[fmt]
+    a = np.abs(dev)
+    expo = np.maximum(np.floor(np.log2(np.maximum(a, 1e-300))), emin)
+    step = np.exp2(expo - (p - 1))
+    frac = a / step - np.floor(a / step)
+    thr = r16 / 65536.0 if sr else 0.5
+    dist = np.minimum(np.abs(frac - thr), np.minimum(frac, 1.0 - frac)) * step
+    return value, step, dist
+
+
+def assert_rounded_like_oracle(got, want, step, dist, ulps=16):
+    """The GPU value equals the oracle's rounded value except where the FP32
+    collision's error (below `ulps` units in the last place of the FP32
+    population) can put the deviation on the other side of a rounding
+    decision: there they differ by one grid step (two across a binade), or,
+    for a deviation so small that its grid is finer than the FP32 error, by
+    that error.  Returns the fraction of bit-identical values."""
+    eps = ulps * np.spacing(np.abs(want).astype(np.float32)).astype(np.float64)
+    diff = np.abs(got - want)
+    assert (diff <= 2.0 * step + eps).all(), float((diff / (2.0 * step + eps)).max())
+    off = diff > 0.0
+    near = dist <= eps
+    assert np.all(near[off]), "%d values rounded the other way far from a threshold" % int(np.sum(off & ~near))
+    return float(np.mean(~off))

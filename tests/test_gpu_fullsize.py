@@ -11,7 +11,7 @@ oracle computes from its own state.
 import numpy as np
 import pytest
 
-from paper_1610_02733_gb300 import inputs
+from paper_1610_02733_gb300 import inputs, lbmd
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +76,39 @@ def test_lb_step_full_size_sampled(states):
     # mass and total momentum after the full cycle (FP32 storage)
     assert abs(ob["mass"] / 256 ** 3 - 1.0) < 1e-6
     del f_before
+
+
+@pytest.mark.parametrize("precision", ["fp16dev", "fp16dev_sr", "bf16dev", "bf16dev_sr"])
+def test_reduced_precision_lb_step_full_size_sampled(states, precision):
+    # the same workload with the populations stored as FP16 / BF16 deviations
+    # (the fluid at rest is exact there, so the MD phase is the FP32 one):
+    # after the first LB step every stored value at a sample of nodes is the
+    # oracle's post-collision value rounded onto the storage grid -- to
+    # nearest, or stochastically with the same Philox bits
+    from gpu_common import D3Q19_C, W, assert_rounded_like_oracle, expected_readback
+    o, _ = states
+    g = lbmd.LBMD(*SHAPE, variant="B", precision=precision, n_sub=N_SUB, kT=1e-4, zeta=1.0, seed=1,
+                  max_particles=NP)
+    g.add_particles(inputs.uniform_positions(NP, SHAPE, 1), inputs.maxwell_velocities(NP, 1e-4, 1))
+    g.cycle(1)
+    fg = g.populations()
+    g.close()
+    L = np.array(SHAPE)
+    rng = np.random.default_rng(5)
+    sample = np.vstack([rng.integers(0, 256, size=(300, 3)), [[0, 0, 0], [255, 255, 255], [255, 0, 128]]])
+    J = o.jacc()
+    post, idx, src, got = [], [], [], []
+    for r in sample:
+        ridx = int(r[0] + 256 * (r[1] + 256 * r[2]))
+        for i in range(19):
+            s = (r - D3Q19_C[i]) % L
+            sidx = int(s[0] + 256 * (s[1] + 256 * s[2]))
+            post.append(o.collide_node(W * 1.0, J[sidx], node=sidx, lb_step=0)[i])
+            idx.append(i)
+            src.append(sidx)
+            got.append(fg[i, ridx])
+    idx = np.array(idx)
+    want, step, dist = expected_readback(post, idx, src, precision, seed=1, lb_step=0)
+    exact = assert_rounded_like_oracle(np.array(got), want, step, dist)
+    assert exact > 0.9, exact
+    print("%s: %.4f of the sampled populations bit-identical to the oracle's rounding" % (precision, exact))

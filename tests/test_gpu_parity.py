@@ -114,16 +114,20 @@ def test_bonded_chains_several_cycles(precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_variants_a_and_b_coincide_bitwise_at_m_equal_one(precision):
+    # variant A both with the node field and with the frozen copy of the
+    # compact records as the source of its frozen node velocities
     shape, n = (12, 10, 8), 50
     runs = {}
-    for variant in ("A", "B"):
+    for variant, copy in (("A", False), ("A", True), ("B", False)):
         o, g = pair(shape, precision=precision, variant=variant, n_sub=1, kT=1e-3, zeta=1.5, seed=9,
                     max_particles=n)
+        g.set_frozen_copy(copy)
         g.add_particles(inputs.uniform_positions(n, shape, 2), inputs.maxwell_velocities(n, 1e-3, 2))
         g.cycle(5)
-        runs[variant] = (g.populations(), *g.particles())
-    for a, b in zip(runs["A"], runs["B"]):
-        np.testing.assert_array_equal(a, b)
+        runs[variant, copy] = (g.populations(), *g.particles())
+    for key in (("A", False), ("A", True)):
+        for a, b in zip(runs[key], runs["B", False]):
+            np.testing.assert_array_equal(a, b)
 
 
 def test_repeat_runs_and_graph_replay_are_bitwise_identical():
@@ -231,25 +235,34 @@ def test_variant_c_several_cycles(precision):
 @pytest.mark.parametrize("variant", ["A", "B"])
 def test_variant_b_spread_paths_agree_bitwise(precision, integrator, variant):
     # the row gather (+ migrant atomics) and the all-atomic path hand over the
-    # same fixed-point transfers (variant A: into the accumulating copy of the
-    # frozen records): bitwise equal, and equal to the oracle
+    # same fixed-point transfers into the compact records: bitwise equal, and
+    # equal to the oracle; variant A also with its frozen node velocities
+    # from a copy of the records instead of the node field (switched at a
+    # cycle boundary in the middle of the run, both ways)
     shape, n = (24, 20, 18), 3000
     runs = {}
-    for spread in ("rows", "atomic"):
+    modes = [("rows", None), ("atomic", None)]
+    if variant == "A":
+        modes += [("rows", (True, False)), ("atomic", (False, True))]
+    for spread, copies in modes:
         o, g = pair(shape, precision=precision, variant=variant, n_sub=5, kT=1e-4, zeta=1.5, seed=41, max_particles=n,
                     integrator=integrator, spread=spread)
         pos, vel = inputs.uniform_positions(n, shape, 41), inputs.maxwell_velocities(n, 1e-4, 41)
         g.add_particles(pos, vel)
-        g.cycle(2)
-        runs[spread] = (g.populations(), *g.particles())
-    for a, b in zip(runs["rows"], runs["atomic"]):
-        np.testing.assert_array_equal(a, b)
+        for c in range(2):
+            if copies is not None:
+                g.set_frozen_copy(copies[c])
+            g.cycle(1)
+        runs[spread, copies] = (g.populations(), *g.particles())
+    for key in runs:
+        for a, b in zip(runs[key], runs["rows", None]):
+            np.testing.assert_array_equal(a, b)
     o.add_particles(pos, vel)
     o.cycle(2)
-    assert_pops_close(runs["rows"][0], o.populations(), precision)
+    assert_pops_close(runs["rows", None][0], o.populations(), precision)
     po, vo = o.particles()
-    assert np.abs(_periodic_diff(runs["rows"][1], po, shape)).max() <= TOL[precision] * max(shape)
-    assert_vec_close(runs["rows"][2], vo, precision, "velocities")
+    assert np.abs(_periodic_diff(runs["rows", None][1], po, shape)).max() <= TOL[precision] * max(shape)
+    assert_vec_close(runs["rows", None][2], vo, precision, "velocities")
 
 
 def test_unstable_friction_step_rejected():
@@ -280,3 +293,20 @@ def test_longest_rows(precision, nx):
     with pytest.raises(lbmd.LbmdError):
         lbmd.LBMD(nx + 1 if precision == "fp32" else nx * 2 + 1, 2, 2, precision=precision)
 
+
+
+def test_frozen_copy_arguments():
+    g = lbmd.LBMD(8, 8, 8, variant="A", n_sub=2, max_particles=4)
+    with pytest.raises(lbmd.LbmdError) as e:
+        lbmd._check(g._h, lbmd.load().lbmd_set_frozen_copy(g._h, 2), "lbmd_set_frozen_copy")
+    assert e.value.status == lbmd.LBMD_ERR_ARG
+    g.add_particles(np.ones((1, 3)), np.zeros((1, 3)))
+    g.md_substep()
+    with pytest.raises(lbmd.LbmdError) as e:
+        g.set_frozen_copy(True)
+    assert e.value.status == lbmd.LBMD_ERR_SEQUENCE
+    g.md_substep()
+    g.lb_step()
+    g.set_frozen_copy(True)
+    g.set_frozen_copy(False)
+    g.close()
