@@ -310,3 +310,38 @@ def test_frozen_copy_arguments():
     g.set_frozen_copy(True)
     g.set_frozen_copy(False)
     g.close()
+
+
+@pytest.mark.parametrize("variant", ["A", "B"])
+def test_calls_between_the_last_md_step_and_the_lb_step(variant):
+    # reading the state between the last MD step of a cycle and the LB step
+    # changes nothing; replacing the particles there gives the same bits as
+    # replacing them at the cycle boundary (the LB step then re-orders the
+    # new particles, instead of the next cycle treating them as having left
+    # their rows): the active set only decides where the fixed-point
+    # transfers are summed
+    shape, n, n_sub = (24, 20, 18), 3000, 3
+    pos, vel = inputs.uniform_positions(n, shape, 5), inputs.maxwell_velocities(n, 1e-4, 5)
+    pos2, vel2 = inputs.uniform_positions(n, shape, 6), inputs.maxwell_velocities(n, 1e-4, 6)
+    runs = {}
+    for mode in ("plain", "read", "set_before", "set_after"):
+        g = lbmd.LBMD(*shape, variant=variant, n_sub=n_sub, kT=1e-4, zeta=1.5, seed=17, max_particles=n)
+        g.add_particles(pos, vel)
+        g.cycle(1)
+        for _ in range(n_sub):
+            g.md_substep()
+        if mode == "read":
+            g.particles()
+            g.observables()
+        if mode == "set_before":
+            g.set_particles(pos2, vel2)
+        g.lb_step()
+        if mode == "set_after":
+            g.set_particles(pos2, vel2)
+        g.run_cycles(2)
+        runs[mode] = (g.populations(), *g.particles())
+        g.close()
+    for a, b in zip(runs["read"], runs["plain"]):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(runs["set_before"], runs["set_after"]):
+        np.testing.assert_array_equal(a, b)
