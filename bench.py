@@ -143,6 +143,25 @@ def _setup_gpu(torch, lbmd, inputs, seed_offset=0):
     return sim, stream, pos, vel
 
 
+def _plain_lb_form(torch, lbmd, stream, peak, steps=50):
+    """The LB step alone: 256^3 D3Q19, no particles, kT = 1e-4, FP32 -- the
+    LB kernel's roofline without the coupling (152 B/node)."""
+    sim = lbmd.LBMD(*SHAPE, variant="B", precision="fp32", n_sub=1, kT=KT, seed=SEED, stream=stream.cuda_stream)
+    sim.run_cycles(5)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    sim.run_cycles(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sim.close()
+    ms = a.elapsed_time(b) / steps
+    n_nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    return {"workload": "256^3 D3Q19, no particles, kT=1e-4, FP32 (an empty MD step and one LB step per cycle)",
+            "value": round(n_nodes / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "ms_per_step": round(ms, 4),
+            "roofline_frac": round(LB_BYTES_PER_NODE * n_nodes / (ms * 1e-3) / 1e9 / peak, 4)}
+
+
 def _time_form(torch, lbmd, inputs, stream, precision, steps, pos, vel):
     """Cycle time of the same workload with another population storage form."""
     sim = lbmd.LBMD(*SHAPE, variant="B", precision=precision, n_sub=N_SUB, kT=KT, zeta=ZETA, seed=SEED,
@@ -540,6 +559,11 @@ def run_gpu(args):
                "algorithmic_bytes": md_alg, "ms": round(md_step_ms, 4), "peak_source": peak_kind}
     for r in (lb_roof, md_roof):
         r["frac"] = round(r["achieved"] / peak, 4)
+        if r["traffic"]:
+            # the ncu DRAM bytes over the same time, and their ratio to the
+            # algorithmic bytes (the implementation's overhead)
+            r["dram_frac"] = round(r["traffic"] / (r["ms"] * 1e-3) / 1e9 / peak, 4)
+            r["overhead"] = round(r["traffic"] / r["algorithmic_bytes"], 3)
     dominant = md_roof if md_ms > lb_avg_ms else lb_roof
     line = {
         "metric": METRIC,
@@ -590,6 +614,7 @@ def run_gpu(args):
         line["adjoint"] = _adjoint_form(torch, lbmd, inputs)
         line["kremer_grest"] = _kremer_grest_form(torch, stream)
         line["bead_spring_64"] = _bead_spring_64_form(torch, lbmd, inputs, stream)
+        line["plain_lb"] = _plain_lb_form(torch, lbmd, stream, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -665,6 +690,41 @@ def _oracle_full_cycles(cycles: int):
     return dt
 
 
+def _oracle_small_configs():
+    """The oracle (OpenMP timing build, all host cores on the LB node loops)
+    on BASELINE's first configuration in full -- 8^3, 10 particles, FP64,
+    m = 5, 1000 MD steps, variants A and B -- and on 10 cycles (100 MD steps)
+    of its second, 64^3 with 64 chains of 64 beads (harmonic k = 30, r0 = 1,
+    zeta = 2, m = 10, variants A and B)."""
+    from oracle import oracle as orc
+    from paper_1610_02733_gb300 import inputs
+    out = {}
+    for v, name in ((0, "A"), (1, "B")):
+        o = orc.Oracle(8, 8, 8, n_sub=5, variant=v, kT=1e-4, zeta=1.0, seed=1, openmp=True)
+        o.add_particles(inputs.uniform_positions(10, (8, 8, 8), 1), inputs.maxwell_velocities(10, 1e-4, 1))
+        t0 = time.perf_counter()
+        o.cycle(200)
+        dt = time.perf_counter() - t0
+        o.close()
+        out["c1_" + name] = {"value": round(512 * 200 / dt / 1e6, 4), "unit": "MLUPS", "s": round(dt, 3),
+                             "sample": "8^3, 10 particles, m=5, 1000 MD steps, FP64 (the whole configuration)"}
+    shape = (64, 64, 64)
+    pos, bonds = inputs.bead_spring_chains(64, 64, shape, 2)
+    vel = inputs.maxwell_velocities(pos.shape[0], KT, 2)
+    for v, name in ((0, "A"), (1, "B")):
+        o = orc.Oracle(*shape, n_sub=10, variant=v, kT=KT, zeta=2.0, seed=2, openmp=True)
+        o.add_particles(pos, vel)
+        o.add_bonds(bonds, 30.0, 1.0)
+        t0 = time.perf_counter()
+        o.cycle(10)
+        dt = time.perf_counter() - t0
+        o.close()
+        out["c2_" + name] = {"value": round(64 ** 3 * 10 / dt / 1e6, 4), "unit": "MLUPS",
+                             "particle_substeps_per_s": float("%.4g" % (pos.shape[0] * 100 / dt)), "s": round(dt, 3),
+                             "sample": "10 cycles (100 MD steps) of 64^3 with 64 chains x 64 beads, m=10, FP64"}
+    return out
+
+
 def cpu_baseline():
     """The FP64 oracle on the host cores: 3 full cycles of the benchmark
     workload with its OpenMP timing build (all cores on the LB node loops,
@@ -690,6 +750,10 @@ def cpu_baseline():
     except Exception as exc:  # no OpenMP runtime on this host
         out.update({"value": single["value"], "unit": "MLUPS", "cores": 1, "sample": single["sample"],
                     "all_cores": "unavailable: %s" % exc})
+    try:
+        out["other_configs"] = _oracle_small_configs()
+    except Exception as exc:
+        out["other_configs"] = "unavailable: %s" % exc
     return out
 
 

@@ -114,6 +114,20 @@ enum { LBMD_INTEGRATOR_START = 0, LBMD_INTEGRATOR_HALF_STEP = 1 };
  * row (y, z) on average, ROWS above (measured crossover).  The transfers are
  * fixed-point integers, so all of them give bitwise the same results. */
 enum { LBMD_SPREAD_AUTO = 0, LBMD_SPREAD_ROWS = 1, LBMD_SPREAD_ATOMIC = 2, LBMD_SPREAD_TILES = 3 };
+/* Distribution of the random numbers of the thermal noise (fluid modes,
+ * Sec. 2) and of the particles' random force (Eq. (4)); both have zero mean
+ * and unit variance, which is all the fluctuation-dissipation balance needs.
+ * UNIFORM (default): sqrt(12) (u - 1/2) from 16 (fluid) or 32 (particles)
+ * bits of Philox4x32-10, no transcendental function, so any two
+ * implementations agree to rounding.  GAUSS: standard normal variates by the
+ * Box-Muller transform of pairs of Philox words (u = (h + 1/2) 2^-24 from the
+ * top 24 bits h of a word; r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2)),
+ * evaluated with the device's log and sincospi; the fluid takes four Philox
+ * calls per node, counter (node, LB step, 0, q), q = 0..3, variates in mode
+ * order k = 4..18, two per word pair; a particle takes one, (id, MD step, 1,
+ * 0), words (x, y) and (z, w) for its three components.  GAUSS needs FP32 or
+ * FP64 storage (LBMD_ERR_ARG otherwise). */
+enum { LBMD_NOISE_UNIFORM = 0, LBMD_NOISE_GAUSS = 1 };
 #define LBMD_SPREAD_ATOMIC_PER_ROW 10
 
 typedef struct lbmd_params {
@@ -135,6 +149,7 @@ typedef struct lbmd_params {
                               context creates and owns a stream of its own */
     int32_t integrator;    /* LBMD_INTEGRATOR_START or LBMD_INTEGRATOR_HALF_STEP */
     int32_t spread;        /* variant B: LBMD_SPREAD_AUTO, _TILES, _ROWS or _ATOMIC */
+    int32_t noise;         /* LBMD_NOISE_UNIFORM or LBMD_NOISE_GAUSS */
 } lbmd_params;
 
 typedef struct lbmd_ctx lbmd_ctx;

@@ -158,6 +158,20 @@ double orc_uniform_unit16(uint32_t h) {
     return sqrt(12.0) * (u - 0.5);
 }
 
+/* Two 32-bit Philox words -> two independent standard normal variates by the
+ * Box-Muller transform (Box & Muller, Ann. Math. Stat. 29 (1958) 610): the
+ * top 24 bits of each word give u = (h + 1/2) 2^-24 in (0, 1), and with
+ * r = sqrt(-2 ln u1) the pair is (r cos 2 pi u2, r sin 2 pi u2).  Used for
+ * every noise term when the Gaussian option is selected. */
+void orc_box_muller(uint32_t w1, uint32_t w2, double out[2]) {
+    const double two_pi = 6.283185307179586476925286766559;
+    double u1 = ((double)(w1 >> 8) + 0.5) * (1.0 / 16777216.0);
+    double u2 = ((double)(w2 >> 8) + 0.5) * (1.0 / 16777216.0);
+    double r = sqrt(-2.0 * log(u1));
+    out[0] = r * cos(two_pi * u2);
+    out[1] = r * sin(two_pi * u2);
+}
+
 static void key_of(const orc_state *s, uint32_t key[2]) {
     key[0] = (uint32_t)(s->p.seed & 0xffffffffu);
     key[1] = (uint32_t)(s->p.seed >> 32);
@@ -312,12 +326,22 @@ void orc_collide_node(const orc_state *s, const double f[Q], const double F[3],
         uint32_t key[2], ctr[4], out[4];
         double xi[16];
         key_of(s, key);
-        for (uint32_t q = 0; q < 2; ++q) {
-            ctr[0] = node; ctr[1] = lb_step; ctr[2] = 0u; ctr[3] = q;
-            orc_philox4x32_10(ctr, key, out);
-            for (int t = 0; t < 4; ++t) {
-                xi[8 * q + 2 * t] = orc_uniform_unit16(out[t] & 0xffffu);
-                xi[8 * q + 2 * t + 1] = orc_uniform_unit16(out[t] >> 16);
+        if (s->p.noise == 1) {
+            /* normal variates: four Philox calls, two Box-Muller pairs each */
+            for (uint32_t q = 0; q < 4; ++q) {
+                ctr[0] = node; ctr[1] = lb_step; ctr[2] = 0u; ctr[3] = q;
+                orc_philox4x32_10(ctr, key, out);
+                orc_box_muller(out[0], out[1], xi + 4 * q);
+                orc_box_muller(out[2], out[3], xi + 4 * q + 2);
+            }
+        } else {
+            for (uint32_t q = 0; q < 2; ++q) {
+                ctr[0] = node; ctr[1] = lb_step; ctr[2] = 0u; ctr[3] = q;
+                orc_philox4x32_10(ctr, key, out);
+                for (int t = 0; t < 4; ++t) {
+                    xi[8 * q + 2 * t] = orc_uniform_unit16(out[t] & 0xffffu);
+                    xi[8 * q + 2 * t + 1] = orc_uniform_unit16(out[t] >> 16);
+                }
             }
         }
         double mu = 3.0 * s->p.kT;
@@ -559,8 +583,15 @@ static void coupling_forces(orc_state *s, double dt, int64_t *corner, double *de
         }
         uint32_t ctr[4] = {(uint32_t)p, (uint32_t)s->md_step, 1u, 0u}, out[4];
         orc_philox4x32_10(ctr, key, out);
+        double xi[4];
+        if (s->p.noise == 1) {
+            orc_box_muller(out[0], out[1], xi);
+            orc_box_muller(out[2], out[3], xi + 2);
+        } else {
+            for (int a = 0; a < 3; ++a) xi[a] = orc_uniform_unit(out[a]);
+        }
         for (int a = 0; a < 3; ++a) {
-            double frand = s->p.kT > 0.0 ? amp * orc_uniform_unit(out[a]) : 0.0;
+            double frand = s->p.kT > 0.0 ? amp * xi[a] : 0.0;
             s->fc[3 * p + a] = -s->p.zeta * (s->vel[3 * p + a] - uR[a]) + frand;
         }
     }

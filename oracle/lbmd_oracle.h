@@ -32,6 +32,7 @@ typedef struct orc_params {
     double zeta;          /* particle friction coefficient of Eq. (4) */
     double body_force[3]; /* uniform force density on the fluid */
     uint64_t seed;        /* Philox key */
+    int32_t noise;        /* 0: uniform variates sqrt(12) (u - 1/2); 1: normal variates (Box-Muller) */
 } orc_params;
 
 typedef struct orc_state orc_state;
@@ -64,6 +65,7 @@ int64_t orc_num_particles(const orc_state *s);
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform_unit(uint32_t x);
 double orc_uniform_unit16(uint32_t h);
+void orc_box_muller(uint32_t w1, uint32_t w2, double out[2]);
 void orc_d3q19(int32_t c_out[19 * 3], double w_out[19]);
 void orc_modes(double e_out[19 * 19], double b_out[19]);
 void orc_collide_node(const orc_state *s, const double f[19], const double F[3], uint32_t node, uint32_t lb_step,

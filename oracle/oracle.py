@@ -65,7 +65,7 @@ class OrcParams(ct.Structure):
         ("n_sub", ct.c_int32), ("variant", ct.c_int32), ("integrator", ct.c_int32),
         ("rho0", ct.c_double), ("nu", ct.c_double), ("nu_bulk", ct.c_double),
         ("gamma_ghost", ct.c_double), ("kT", ct.c_double), ("zeta", ct.c_double),
-        ("body_force", ct.c_double * 3), ("seed", ct.c_uint64),
+        ("body_force", ct.c_double * 3), ("seed", ct.c_uint64), ("noise", ct.c_int32),
     ]
 
 
@@ -106,6 +106,7 @@ def lib(openmp: bool = False):
         L.orc_uniform_unit.argtypes = [ct.c_uint32]
         L.orc_uniform_unit16.restype = ct.c_double
         L.orc_uniform_unit16.argtypes = [ct.c_uint32]
+        L.orc_box_muller.argtypes = [ct.c_uint32, ct.c_uint32, dp]
         L.orc_d3q19.argtypes = [ct.POINTER(ct.c_int32), dp]
         L.orc_modes.argtypes = [dp, dp]
         L.orc_collide_node.argtypes = [P, dp, dp, ct.c_uint32, ct.c_uint32, dp]
@@ -144,6 +145,14 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def uniform_unit(x: int) -> float:
     return lib().orc_uniform_unit(int(x) & 0xFFFFFFFF)
+
+
+def box_muller(w1: int, w2: int):
+    """The two standard normal variates of the Gaussian noise option from two
+    32-bit Philox words."""
+    out = np.zeros(2)
+    lib().orc_box_muller(int(w1) & 0xFFFFFFFF, int(w2) & 0xFFFFFFFF, _dp(out))
+    return out
 
 
 def uniform_unit16(h: int) -> float:
@@ -203,12 +212,15 @@ class Oracle:
     tau_LB = 1), ``n_sub`` = m MD steps per LB step, ``variant`` 0 = A, 1 = B, 2 = C,
     ``integrator`` 0 = coupling force from the start of the MD step (Eq. (6)),
     1 = from the half-step velocity after the drift (see orc_md_substep).
+    ``noise``: 0 / "uniform" (unit-variance uniform variates), 1 / "gauss"
+    (standard normal variates by Box-Muller).
     """
 
     def __init__(self, nx, ny, nz, *, n_sub=1, variant=1, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
                  gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1, integrator=0,
-                 openmp=False):
+                 noise=0, openmp=False):
         p = OrcParams()
+        p.noise = {"uniform": 0, "gauss": 1}.get(noise, noise)
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
         p.n_sub, p.variant, p.integrator = int(n_sub), int(variant), int(integrator)
         p.rho0, p.nu, p.nu_bulk, p.gamma_ghost = float(rho0), float(nu), float(nu_bulk), float(gamma_ghost)

@@ -47,6 +47,7 @@ struct LbArgs {
     int32_t *range_flag;  // set when a written record reaches half the fixed-point range
     T gamma_bulk, gamma_shear, gamma_ghost;
     T amp16[Q];  // noise amplitude sqrt(mu b_k (1 - g_k^2)) times sqrt(12) 2^-16
+    T ampg[Q];   // the amplitude itself (normal variates)
     T g[3];
     uint32_t key0, key1;
     const unsigned long long *lb_step;
@@ -110,7 +111,7 @@ constexpr int FUSE_LAG = 2;
 // agree bit for bit, as the paper's algorithmic equivalence requires.
 // Collide node (x, y, z) and push its post-collision populations to the
 // neighbours r + c_i in the other buffer.
-template <typename T, typename S, bool RELAX_FULL>
+template <typename T, typename S, bool RELAX_FULL, bool GAUSS>
 __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, int y, int z,
                                                   unsigned long long step) {
     using P = Prec<T>;
@@ -156,7 +157,8 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
     Fx += a.g[0];
     Fy += a.g[1];
     Fz += a.g[2];
-    collide<T, RELAX_FULL>(f, rho, rho_m, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, r, (uint32_t)step);
+    collide<T, RELAX_FULL, LbArgs<T, S>, GAUSS>(f, rho, rho_m, jx, jy, jz, Fx, Fy, Fz, a, a.key0, a.key1, r,
+                                                (uint32_t)step);
 
     const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y == a.ny - 1 ? 0 : y + 1;
@@ -185,14 +187,14 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
     }
 }
 
-template <typename T, typename S, bool RELAX_FULL>
+template <typename T, typename S, bool RELAX_FULL, bool GAUSS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3) lb_collide_push(LbArgs<T, S> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     // the step counter, read before the fallback kernel advances it; it also
     // tags the blocks that have pushed
     const unsigned long long step = *a.lb_step;
-    if (x < a.nx) collide_push_node<T, S, RELAX_FULL>(a, x, y, z, step);
+    if (x < a.nx) collide_push_node<T, S, RELAX_FULL, GAUSS>(a, x, y, z, step);
 
     // fused post-stream moments: publish this block, then compute the
     // moments of the block FUSE_LAG planes back once its neighbourhood is in
@@ -401,7 +403,10 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     a.gamma_bulk = (T)ctx->co.gamma_bulk;
     a.gamma_shear = (T)ctx->co.gamma_shear;
     a.gamma_ghost = (T)ctx->co.gamma_ghost;
-    for (int k = 0; k < Q; ++k) a.amp16[k] = (T)(ctx->co.noise_amp[k] * 3.4641016151377544 * 1.52587890625e-05);
+    for (int k = 0; k < Q; ++k) {
+        a.amp16[k] = (T)(ctx->co.noise_amp[k] * 3.4641016151377544 * 1.52587890625e-05);
+        a.ampg[k] = (T)ctx->co.noise_amp[k];
+    }
     for (int d = 0; d < 3; ++d) a.g[d] = (T)ctx->co.body_force[d];
     a.key0 = (uint32_t)(ctx->p.seed & 0xffffffffu);
     a.key1 = (uint32_t)(ctx->p.seed >> 32);
@@ -411,10 +416,23 @@ static cudaError_t lb_step_t(lbmd_ctx *ctx) {
     const dim3 block = node_block(ctx), grid = node_grid(ctx, block);
     cudaError_t e = cudaMemsetAsync(ctx->lb_missed, 0, sizeof(int32_t), ctx->stream);
     if (e != cudaSuccess) return e;
-    if (ctx->co.gamma_bulk == 0.0 && ctx->co.gamma_ghost == 0.0)
-        lb_collide_push<T, S, true><<<grid, block, 0, ctx->stream>>>(a);
-    else
-        lb_collide_push<T, S, false><<<grid, block, 0, ctx->stream>>>(a);
+    const bool full = ctx->co.gamma_bulk == 0.0 && ctx->co.gamma_ghost == 0.0;
+    // normal variates: a kernel instance of its own (FP32 / FP64 storage),
+    // so that the default one keeps its registers
+    if constexpr (!PopStore<S, T>::deviation) {
+        if (ctx->p.noise == LBMD_NOISE_GAUSS) {
+            if (full)
+                lb_collide_push<T, S, true, true><<<grid, block, 0, ctx->stream>>>(a);
+            else
+                lb_collide_push<T, S, false, true><<<grid, block, 0, ctx->stream>>>(a);
+        }
+    }
+    if (ctx->p.noise != LBMD_NOISE_GAUSS) {
+        if (full)
+            lb_collide_push<T, S, true, false><<<grid, block, 0, ctx->stream>>>(a);
+        else
+            lb_collide_push<T, S, false, false><<<grid, block, 0, ctx->stream>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the moments the collide kernel left, on the new populations
     moments_rest_kernel<T, S><<<2 * ctx->sm_count, block, 0, ctx->stream>>>(

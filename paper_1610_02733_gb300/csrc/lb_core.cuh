@@ -62,9 +62,10 @@ __device__ __forceinline__ double centred16(uint32_t h, double) { return (double
 // bulk and ghost modes relax fully, m'_k = m^eq_k exactly, and their moments
 // m_k need not be computed (gamma (m - m^eq) is +-0 for finite m).
 // A: any struct with the members gamma_bulk, gamma_shear, gamma_ghost,
-// amp16[Q] and noisy (the single-box and the batched kernels); the Philox
-// key (key0, key1) and counters (node, step) come as arguments.
-template <typename T, bool RELAX_FULL, typename A>
+// amp16[Q] and noisy (the single-box, batched and adjoint kernels), and for
+// GAUSS (normal variates) ampg[Q]; the Philox key (key0, key1) and counters
+// (node, step) come as arguments.
+template <typename T, bool RELAX_FULL, typename A, bool GAUSS = false>
 __device__ __forceinline__ void collide(T f[Q], T rho, T rho_m, T jx, T jy, T jz, T Fx, T Fy, T Fz, const A &a,
                                         uint32_t key0, uint32_t key1, uint32_t node, uint32_t step) {
     T inv_rho, sr;
@@ -127,7 +128,24 @@ __device__ __forceinline__ void collide(T f[Q], T rho, T rho_m, T jx, T jy, T jz
     mp[8] += fs * T(0.5) * (ux * Fz + uz * Fx);
     mp[9] += fs * T(0.5) * (uy * Fz + uz * Fy);
 
-    if (a.noisy) {
+    if constexpr (GAUSS) {
+        if (a.noisy) {
+            // 15 normal variates from four Philox calls, a Box-Muller pair
+            // per two words, in mode order k = 4..18
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                const U4 r = philox4x32_10(U4{node, step, 0u, q}, key0, key1);
+                T g[4];
+                box_muller(r.x, r.y, g[0], g[1]);
+                box_muller(r.z, r.w, g[2], g[3]);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int k = 4 + 4 * (int)q + t;
+                    if (k < Q) mp[k] += (a.ampg[k] * sr) * g[t];
+                }
+            }
+        }
+    } else if (a.noisy) {
         // 15 variates from two Philox calls: two 16-bit halves per 32-bit
         // word, low half first, in mode order k = 4..18.  The variate
         // sqrt(12) ((h + 1/2) 2^-16 - 1/2) is (h - 32767.5) times

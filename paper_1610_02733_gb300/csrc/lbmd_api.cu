@@ -125,6 +125,10 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         if (!is_finite_d(p->body_force[d])) return fail(nullptr, LBMD_ERR_ARG, "non-finite body force");
     if (p->integrator != LBMD_INTEGRATOR_START && p->integrator != LBMD_INTEGRATOR_HALF_STEP)
         return fail(nullptr, LBMD_ERR_ARG, "integrator must be START or HALF_STEP");
+    if (p->noise != LBMD_NOISE_UNIFORM && p->noise != LBMD_NOISE_GAUSS)
+        return fail(nullptr, LBMD_ERR_ARG, "noise must be LBMD_NOISE_UNIFORM or LBMD_NOISE_GAUSS");
+    if (p->noise == LBMD_NOISE_GAUSS && p->precision != LBMD_FP32 && p->precision != LBMD_FP64)
+        return fail(nullptr, LBMD_ERR_ARG, "normal variates need FP32 or FP64 storage");
     if (p->spread < LBMD_SPREAD_AUTO || p->spread > LBMD_SPREAD_TILES)
         return fail(nullptr, LBMD_ERR_ARG, "spread must be AUTO, ROWS, ATOMIC or TILES");
 

@@ -112,6 +112,29 @@ __device__ __forceinline__ float unit_uniform_f(uint32_t x) {
     const float centred = (float)(int32_t)(x ^ 0x80000000u) + 0.5f;
     return centred * (3.4641016151377544f * 2.3283064365386963e-10f);
 }
+// Two 32-bit Philox words -> two independent standard normal variates
+// (Box & Muller, Ann. Math. Stat. 29 (1958) 610): u = (h + 1/2) 2^-24 from the
+// top 24 bits h of each word (exact in FP32), r = sqrt(-2 ln u1), and the pair
+// (r cos 2 pi u2, r sin 2 pi u2) from the device's log and sincospi.
+__device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, float &a, float &b) {
+    const float u1 = ((float)(w1 >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float u2 = ((float)(w2 >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    a = r * cs;
+    b = r * sn;
+}
+__device__ __forceinline__ void box_muller(uint32_t w1, uint32_t w2, double &a, double &b) {
+    const double u1 = ((double)(w1 >> 8) + 0.5) * 5.9604644775390625e-8;
+    const double u2 = ((double)(w2 >> 8) + 0.5) * 5.9604644775390625e-8;
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    a = r * cs;
+    b = r * sn;
+}
+
 template <typename T>
 __device__ __forceinline__ T unit_uniform(uint32_t x);
 template <>

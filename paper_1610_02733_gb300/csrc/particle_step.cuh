@@ -47,6 +47,7 @@ struct PArgs {
     int interp_compact;               // interpolate from cact (B; A with a frozen copy), else the node field
     int occ_words;
     int32_t *migrant_slot, *migrant_count;  // two lists of np_cap slots, two counters
+    int gauss;         // normal variates (Box-Muller) for the random force
     int b_atomic;      // variant B spreads every particle with atomics (no row gather, no migrant lists)
     int kick_spreads;  // ... and the bond / pair kernel does it, after every particle has read the nodes
     int64_t np_cap;
@@ -127,9 +128,18 @@ __device__ __forceinline__ void coupling_force_id(const PArgs<T> &a, uint32_t id
     Fz = -a.zeta * (V.z - uz);
     if (a.noisy) {
         const U4 r = philox4x32_10(U4{id, md_step, 1u, 0u}, a.key0, a.key1);
-        Fx = fma(a.amp, unit_uniform<T>(r.x), Fx);
-        Fy = fma(a.amp, unit_uniform<T>(r.y), Fy);
-        Fz = fma(a.amp, unit_uniform<T>(r.z), Fz);
+        T g0, g1, g2, g3;
+        if (a.gauss) {  // normal variates: Box-Muller pairs (x, y) and (z, w)
+            box_muller(r.x, r.y, g0, g1);
+            box_muller(r.z, r.w, g2, g3);
+        } else {
+            g0 = unit_uniform<T>(r.x);
+            g1 = unit_uniform<T>(r.y);
+            g2 = unit_uniform<T>(r.z);
+        }
+        Fx = fma(a.amp, g0, Fx);
+        Fy = fma(a.amp, g1, Fy);
+        Fz = fma(a.amp, g2, Fz);
     }
 }
 

@@ -889,6 +889,7 @@ static PArgs<T> make_pargs(lbmd_ctx *ctx, int substep) {
     a.substep = substep;
     a.mig_par = (int)((ctx->lb_step * ctx->p.n_sub + substep) & 1);
     a.noisy = ctx->p.kT > 0.0 ? 1 : 0;
+    a.gauss = ctx->p.noise == LBMD_NOISE_GAUSS ? 1 : 0;
     a.variant = ctx->p.variant;
     a.row_start = ctx->row_start;
     a.slot_row = ctx->slot_row;

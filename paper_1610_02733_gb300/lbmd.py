@@ -32,6 +32,8 @@ INTEGRATOR_START, INTEGRATOR_HALF_STEP = 0, 1
 INTEGRATORS = {"start": INTEGRATOR_START, "half_step": INTEGRATOR_HALF_STEP}
 SPREAD_AUTO, SPREAD_ROWS, SPREAD_ATOMIC, SPREAD_TILES = 0, 1, 2, 3
 SPREADS = {"auto": SPREAD_AUTO, "rows": SPREAD_ROWS, "atomic": SPREAD_ATOMIC, "tiles": SPREAD_TILES}
+NOISE_UNIFORM, NOISE_GAUSS = 0, 1
+NOISES = {"uniform": NOISE_UNIFORM, "gauss": NOISE_GAUSS}
 
 # every symbol include/lbmd.h declares
 EXPORTS = (
@@ -59,7 +61,7 @@ class LbmdParams(ct.Structure):
         ("gamma_ghost", ct.c_double), ("kT", ct.c_double), ("zeta", ct.c_double),
         ("body_force", ct.c_double * 3), ("seed", ct.c_uint64),
         ("max_particles", ct.c_int64), ("max_bonds", ct.c_int64), ("stream", ct.c_void_p),
-        ("integrator", ct.c_int32), ("spread", ct.c_int32),
+        ("integrator", ct.c_int32), ("spread", ct.c_int32), ("noise", ct.c_int32),
     ]
 
 
@@ -245,7 +247,7 @@ def lbmd_particle_sums_static(vel_ptr: int, mass_ptr, n: int, out_ptr: int, stre
 
 def make_params(nx, ny, nz, *, n_sub=1, variant=VARIANT_B, precision=FP32, rho0=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
                 gamma_ghost=0.0, kT=0.0, zeta=1.0, body_force=(0.0, 0.0, 0.0), seed=1, max_particles=0,
-                max_bonds=0, stream=None, integrator="start", spread="auto") -> LbmdParams:
+                max_bonds=0, stream=None, integrator="start", spread="auto", noise="uniform") -> LbmdParams:
     p = LbmdParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.n_sub, p.variant, p.precision = int(n_sub), int(variant), int(precision)
@@ -258,6 +260,7 @@ def make_params(nx, ny, nz, *, n_sub=1, variant=VARIANT_B, precision=FP32, rho0=
     p.stream = stream
     p.integrator = INTEGRATORS[integrator] if isinstance(integrator, str) else int(integrator)
     p.spread = SPREADS[spread] if isinstance(spread, str) else int(spread)
+    p.noise = NOISES[noise] if isinstance(noise, str) else int(noise)
     return p
 
 
@@ -272,7 +275,8 @@ class LBMD:
     is ``"A"``, ``"B"`` or ``"C"``;
     ``integrator`` is ``"start"`` (coupling force from the start of the MD
     step, Eq. (6)) or ``"half_step"`` (from the half-step velocity after the
-    drift); ``spread`` (variant B) is ``"auto"``, ``"tiles"``, ``"rows"`` or ``"atomic"``
+    drift); ``noise`` is ``"uniform"`` (default) or ``"gauss"`` (normal
+    variates by Box-Muller); ``spread`` (variant B) is ``"auto"``, ``"tiles"``, ``"rows"`` or ``"atomic"``
     (the path that hands the transfers to the nodes; bitwise the same
     results).
     """

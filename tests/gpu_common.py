@@ -12,13 +12,14 @@ TOL = {"fp32": 1e-5, "fp64": 1e-12}
 
 def pair(shape, *, precision="fp32", variant="B", n_sub=1, kT=0.0, zeta=1.0, nu=1.0 / 6.0, nu_bulk=-1.0,
          gamma_ghost=0.0, body_force=(0.0, 0.0, 0.0), seed=1, rho0=1.0, max_particles=0, max_bonds=0,
-         integrator="start", spread="auto"):
+         integrator="start", spread="auto", noise="uniform"):
     o = orc.Oracle(*shape, n_sub=n_sub, variant={"A": 0, "B": 1, "C": 2}[variant], rho0=rho0, nu=nu, nu_bulk=nu_bulk,
                    gamma_ghost=gamma_ghost, kT=kT, zeta=zeta, body_force=body_force, seed=seed,
-                   integrator={"start": 0, "half_step": 1}[integrator])
+                   integrator={"start": 0, "half_step": 1}[integrator], noise=noise)
     g = lbmd.LBMD(*shape, variant=variant, precision=precision, n_sub=n_sub, rho0=rho0, nu=nu, nu_bulk=nu_bulk,
                   gamma_ghost=gamma_ghost, kT=kT, zeta=zeta, body_force=body_force, seed=seed,
-                  max_particles=max_particles, max_bonds=max_bonds, integrator=integrator, spread=spread)
+                  max_particles=max_particles, max_bonds=max_bonds, integrator=integrator, spread=spread,
+                  noise=noise)
     return o, g
 
 

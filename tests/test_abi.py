@@ -41,7 +41,8 @@ def test_params_struct_layout():
     assert P.seed.offset == 24 + 9 * 8
     assert P.stream.offset == 24 + 12 * 8
     assert P.integrator.offset == 24 + 13 * 8
-    assert ct.sizeof(P) == 24 + 14 * 8
+    assert P.spread.offset == 24 + 13 * 8 + 4 and P.noise.offset == 24 + 14 * 8
+    assert ct.sizeof(P) == 24 + 15 * 8  # three int32 at the end, padded to 8 bytes
     O = lbmd.LbmdObservables
     assert O.lb_step.offset == 9 * 8 and ct.sizeof(O) == 11 * 8
 
