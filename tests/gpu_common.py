@@ -42,6 +42,16 @@ def assert_pops_close(got, want, precision, rho0=1.0):
     return worst
 
 
+def assert_pops_close_per_value(got, want, precision):
+    """Element by element, relative to each value itself: the check the
+    parity tolerance states, used where no population comes near zero (kT
+    up to 1e-4, moderate flows)."""
+    err = np.abs(got - want) / np.abs(want)
+    worst = float(err.max())
+    assert worst <= TOL[precision], "max per-value relative population error %.3e > %.0e" % (worst, TOL[precision])
+    return worst
+
+
 def assert_vec_close(got, want, precision, what):
     """Particle or node vectors: relative to the largest magnitude present."""
     scale = max(float(np.abs(want).max()), 1e-300)
