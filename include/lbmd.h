@@ -330,6 +330,38 @@ lbmd_status lbmd_get_particles(lbmd_ctx *ctx, double *pos, double *vel);
  * device arrays of 3 N doubles (either may be NULL).  Enqueue only. */
 lbmd_status lbmd_get_particles_device(lbmd_ctx *ctx, double *pos, double *vel);
 
+/* Asynchronous host accessors, for a caller that streams particle data in
+ * and out while the cycles run (the paper has no counterpart).  Each call only
+ * enqueues: the copies run on two streams of the context's own (one up, one
+ * down), through two device staging buffers per direction used in turn, and
+ * are ordered against the cycles on the context's stream by events, so an
+ * upload overlaps the cycle before it and a download the cycle after it.
+ * Results and checks equal those of the synchronising calls.
+ *   lbmd_set_particles_async: as lbmd_set_particles; the host arrays are read
+ *     after the call returns, so they must stay unchanged until
+ *     lbmd_synchronize (or until a later synchronising call) -- pinned host
+ *     memory, or the copy from pageable memory is made before returning.
+ *   lbmd_get_particles_async: as lbmd_get_particles, at the point of the
+ *     call in the context's stream order; pos / vel are written after the
+ *     call returns and hold the values after lbmd_synchronize.
+ *   lbmd_observables_async: as lbmd_observables, at the point of the call;
+ *     *out is filled, and its checks (LBMD_ERR_RANGE, LBMD_ERR_NONFINITE,
+ *     LBMD_ERR_CUDA for a device error) are reported, by lbmd_synchronize --
+ *     or by the observables call after next, which reuses its slot and
+ *     reports the checks of the one it completes; out must stay valid until
+ *     then.
+ *   lbmd_synchronize: waits for everything enqueued on the context's streams,
+ *     completes the queued observables (oldest first) and returns the first
+ *     failed check among them, else LBMD_OK.
+ * The streams, events, 4 staging buffers of 6 max_particles doubles and 160 B
+ * of pinned host memory are created on the first asynchronous call and freed
+ * with the context.  Errors: LBMD_ERR_ARG, LBMD_ERR_CAPACITY, LBMD_ERR_OOM,
+ * LBMD_ERR_CUDA. */
+lbmd_status lbmd_set_particles_async(lbmd_ctx *ctx, const double *pos, const double *vel);
+lbmd_status lbmd_get_particles_async(lbmd_ctx *ctx, double *pos, double *vel);
+lbmd_status lbmd_observables_async(lbmd_ctx *ctx, lbmd_observables_t *out);
+lbmd_status lbmd_synchronize(lbmd_ctx *ctx);
+
 /* Counters and sizes. */
 lbmd_status lbmd_get_counts(lbmd_ctx *ctx, int64_t *n_particles, int64_t *n_bonds, int64_t *lb_step,
                             int64_t *md_step, int32_t *substeps_done);

@@ -59,6 +59,16 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->late_rows,    ctx->late_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->stage_in[b]) cudaFree(ctx->stage_in[b]);
+        if (ctx->stage_out[b]) cudaFree(ctx->stage_out[b]);
+        for (cudaEvent_t ev : {ctx->in_ready[b], ctx->in_done[b], ctx->out_ready[b], ctx->out_done[b], ctx->obs_done[b]})
+            if (ev) cudaEventDestroy(ev);
+    }
+    if (ctx->obs_ready) cudaEventDestroy(ctx->obs_ready);
+    if (ctx->obs_host) cudaFreeHost(ctx->obs_host);
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+    if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
     for (int i = 0; i < 16; ++i)
         if (ctx->cycle_graph[i]) cudaGraphExecDestroy(ctx->cycle_graph[i]);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -238,7 +248,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->bond_kind, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE},
         {(void **)&ctx->staging, (size_t)ctx->staging_len * sizeof(double)},
         {(void **)&ctx->red_partial, (size_t)ctx->red_blocks * 8 * sizeof(double)},
-        {(void **)&ctx->red_out, 8 * sizeof(double)},
+        {(void **)&ctx->red_out, 10 * sizeof(double)},
         {(void **)&ctx->d_lb_step, sizeof(unsigned long long)},
     };
     for (auto &a : allocs) {
@@ -560,14 +570,13 @@ lbmd_status lbmd_run_cycles(lbmd_ctx *ctx, int64_t n) {
 lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
     LBMD_TRACE("lbmd_observables");
     if (!ctx || !out) return LBMD_ERR_ARG;
-    double h[8];
-    int32_t range = 0, dev_error = 0;
+    double h[10];  // 8 sums, the range flag, the device error flag
+    if (ctx->async_ready)  // queued downloads still read the sums
+        for (int s = 0; s < 2; ++s) CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->obs_done[s], 0));
     CK(ctx, launch_observables(ctx));
     CK(ctx, cudaMemcpyAsync(h, ctx->red_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(&range, ctx->range_flag, sizeof(range), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(&dev_error, ctx->dev_error, sizeof(dev_error), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    if (dev_error)
+    if (h[9] != 0.0)
         return fail(ctx, LBMD_ERR_CUDA, "a kernel's bounded wait for its own bulk copies gave up: results are invalid");
     out->mass = h[0];
     for (int d = 0; d < 3; ++d) {
@@ -580,7 +589,7 @@ lbmd_status lbmd_observables(lbmd_ctx *ctx, lbmd_observables_t *out) {
     out->md_step = ctx->md_step;
     for (int c = 0; c < 8; ++c)
         if (!is_finite_d(h[c])) return fail(ctx, LBMD_ERR_NONFINITE, "non-finite observable");
-    if (range)
+    if (h[8] != 0.0)
         return fail(ctx, LBMD_ERR_RANGE,
                     "a node's momentum density reached half the fixed-point range (|u| ~ 1 at rho0): the fluid "
                     "state is no longer valid");
@@ -693,6 +702,148 @@ lbmd_status lbmd_get_particles(lbmd_ctx *ctx, double *pos, double *vel) {
     if (vel) CK(ctx, cudaMemcpyAsync(vel, dvel, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     return LBMD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// the asynchronous accessors' streams, events and buffers, on first use
+lbmd_status async_init(lbmd_ctx *ctx) {
+    if (ctx->async_ready) return LBMD_OK;
+    const size_t n6 = (size_t)6 * (size_t)std::max<int64_t>(ctx->p.max_particles, 1);
+    if (!ctx->up_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
+    if (!ctx->down_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        for (cudaEvent_t *ev : {&ctx->in_ready[b], &ctx->in_done[b], &ctx->out_ready[b], &ctx->out_done[b],
+                                &ctx->obs_done[b]})
+            if (!*ev) CK(ctx, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+        if (!ctx->stage_in[b]) CK(ctx, cudaMalloc(&ctx->stage_in[b], n6 * sizeof(double)));
+        if (!ctx->stage_out[b]) CK(ctx, cudaMalloc(&ctx->stage_out[b], n6 * sizeof(double)));
+    }
+    if (!ctx->obs_ready) CK(ctx, cudaEventCreateWithFlags(&ctx->obs_ready, cudaEventDisableTiming));
+    if (!ctx->obs_host) CK(ctx, cudaHostAlloc((void **)&ctx->obs_host, 2 * 10 * sizeof(double), cudaHostAllocDefault));
+    ctx->async_ready = true;
+    return LBMD_OK;
+}
+
+// the observables of queued slot `s` (whose download is complete) into the
+// caller's structure, with the checks of lbmd_observables
+lbmd_status finalise_observables(lbmd_ctx *ctx, int s) {
+    lbmd_observables_t *out = ctx->obs_out[s];
+    ctx->obs_out[s] = nullptr;
+    const double *h = ctx->obs_host + 10 * s;
+    out->mass = h[0];
+    for (int d = 0; d < 3; ++d) {
+        out->p_fluid[d] = h[1 + d];
+        out->p_particles[d] = h[4 + d];
+    }
+    out->e_kin = 0.5 * h[7];
+    out->kT_particles = ctx->obs_np[s] > 0 ? h[7] / (3.0 * (double)ctx->obs_np[s]) : 0.0;
+    out->lb_step = ctx->obs_lb[s];
+    out->md_step = ctx->obs_md[s];
+    if (h[9] != 0.0)
+        return fail(ctx, LBMD_ERR_CUDA, "a kernel's bounded wait for its own bulk copies gave up: results are invalid");
+    for (int c = 0; c < 8; ++c)
+        if (!is_finite_d(h[c])) return fail(ctx, LBMD_ERR_NONFINITE, "non-finite observable");
+    if (h[8] != 0.0)
+        return fail(ctx, LBMD_ERR_RANGE,
+                    "a node's momentum density reached half the fixed-point range (|u| ~ 1 at rho0): the fluid "
+                    "state is no longer valid");
+    return LBMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbmd_status lbmd_set_particles_async(lbmd_ctx *ctx, const double *pos, const double *vel) {
+    LBMD_TRACE("lbmd_set_particles_async");
+    if (!ctx) return LBMD_ERR_ARG;
+    const int64_t n = ctx->np;
+    if (n == 0 || (!pos && !vel)) return LBMD_OK;
+    if (n > ctx->p.max_particles) return fail(ctx, LBMD_ERR_CAPACITY, "more particles than max_particles");
+    const lbmd_status st = async_init(ctx);
+    if (st != LBMD_OK) return st;
+    const int b = ctx->in_idx;
+    ctx->in_idx ^= 1;
+    double *dpos = ctx->stage_in[b], *dvel = ctx->stage_in[b] + 3 * n;
+    // the upload waits only for the conversion that last read this staging
+    // buffer, so it can run beside the work already enqueued
+    CK(ctx, cudaStreamWaitEvent(ctx->up_stream, ctx->in_done[b], 0));
+    if (pos) CK(ctx, cudaMemcpyAsync(dpos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->up_stream));
+    if (vel) CK(ctx, cudaMemcpyAsync(dvel, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->up_stream));
+    CK(ctx, cudaEventRecord(ctx->in_ready[b], ctx->up_stream));
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready[b], 0));
+    CK(ctx, launch_particles_from_double(ctx, 0, n, dpos, dvel, nullptr, pos != nullptr, vel != nullptr, false));
+    CK(ctx, cudaEventRecord(ctx->in_done[b], ctx->stream));
+    if (pos) CK(ctx, invalidate_nb_lists(ctx));
+    if (pos && has_cons(ctx)) CK(ctx, launch_bond_forces_only(ctx));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_particles_async(lbmd_ctx *ctx, double *pos, double *vel) {
+    LBMD_TRACE("lbmd_get_particles_async");
+    if (!ctx) return LBMD_ERR_ARG;
+    const int64_t n = ctx->np;
+    if (n == 0 || (!pos && !vel)) return LBMD_OK;
+    if (n > ctx->p.max_particles) return fail(ctx, LBMD_ERR_CAPACITY, "more particles than max_particles");
+    const lbmd_status st = async_init(ctx);
+    if (st != LBMD_OK) return st;
+    const int b = ctx->out_idx;
+    ctx->out_idx ^= 1;
+    double *dpos = ctx->stage_out[b], *dvel = ctx->stage_out[b] + 3 * n;
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->out_done[b], 0));  // its last download has read it
+    CK(ctx, launch_particles_to_double(ctx, pos ? dpos : nullptr, vel ? dvel : nullptr));
+    CK(ctx, cudaEventRecord(ctx->out_ready[b], ctx->stream));
+    CK(ctx, cudaStreamWaitEvent(ctx->down_stream, ctx->out_ready[b], 0));
+    if (pos) CK(ctx, cudaMemcpyAsync(pos, dpos, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->down_stream));
+    if (vel) CK(ctx, cudaMemcpyAsync(vel, dvel, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->down_stream));
+    CK(ctx, cudaEventRecord(ctx->out_done[b], ctx->down_stream));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_observables_async(lbmd_ctx *ctx, lbmd_observables_t *out) {
+    LBMD_TRACE("lbmd_observables_async");
+    if (!ctx || !out) return LBMD_ERR_ARG;
+    lbmd_status st = async_init(ctx);
+    if (st != LBMD_OK) return st;
+    const int s = ctx->obs_next, prev = s ^ 1;
+    ctx->obs_next ^= 1;
+    if (ctx->obs_out[s]) {  // the slot's previous observables: complete it first
+        CK(ctx, cudaEventSynchronize(ctx->obs_done[s]));
+        st = finalise_observables(ctx, s);
+    }
+    // the reduction overwrites the sums the previous slot's download reads
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->obs_done[prev], 0));
+    CK(ctx, launch_observables(ctx));
+    CK(ctx, cudaEventRecord(ctx->obs_ready, ctx->stream));
+    CK(ctx, cudaStreamWaitEvent(ctx->down_stream, ctx->obs_ready, 0));
+    double *h = ctx->obs_host + 10 * s;
+    CK(ctx, cudaMemcpyAsync(h, ctx->red_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, ctx->down_stream));
+    CK(ctx, cudaEventRecord(ctx->obs_done[s], ctx->down_stream));
+    ctx->obs_out[s] = out;
+    ctx->obs_np[s] = ctx->np;
+    ctx->obs_lb[s] = ctx->lb_step;
+    ctx->obs_md[s] = ctx->md_step;
+    return st;
+}
+
+lbmd_status lbmd_synchronize(lbmd_ctx *ctx) {
+    LBMD_TRACE("lbmd_synchronize");
+    if (!ctx) return LBMD_ERR_ARG;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!ctx->async_ready) return LBMD_OK;
+    CK(ctx, cudaStreamSynchronize(ctx->up_stream));
+    CK(ctx, cudaStreamSynchronize(ctx->down_stream));
+    lbmd_status st = LBMD_OK;
+    for (int k = 0; k < 2; ++k) {  // oldest first
+        const int s = (ctx->obs_next + k) & 1;
+        if (!ctx->obs_out[s]) continue;
+        const lbmd_status r = finalise_observables(ctx, s);
+        if (st == LBMD_OK) st = r;
+    }
+    return st;
 }
 
 lbmd_status lbmd_get_particles_device(lbmd_ctx *ctx, double *pos, double *vel) {

@@ -165,7 +165,7 @@ struct lbmd_ctx {
     double *staging;   // device staging buffer for host <-> device conversions
     int64_t staging_len;
     double *red_partial;  // per-block partial sums of the observables
-    double *red_out;      // final sums
+    double *red_out;      // final sums (8), then the range and device error flags
     // range guard of the fixed-point momentum: set (sticky) by the kernels
     // that write a node record whose momentum reaches half the range
     int32_t *range_flag;
@@ -178,6 +178,20 @@ struct lbmd_ctx {
     int sub_done;
     LbCoeffs co;
     double dt;
+    // the asynchronous accessors (created on first use): uploads and
+    // downloads on streams of their own through two device staging buffers
+    // each, ordered against the context's stream by events
+    bool async_ready;
+    cudaStream_t up_stream, down_stream;
+    cudaEvent_t in_ready[2], in_done[2], out_ready[2], out_done[2], obs_ready, obs_done[2];
+    double *stage_in[2], *stage_out[2];
+    int in_idx, out_idx;
+    // queued observables: raw sums and flags in pinned host memory, and the
+    // caller's structure they are finalised into (two slots, used in turn)
+    double *obs_host;  // per slot: 8 sums, then the range flag and the device error flag
+    lbmd_observables_t *obs_out[2];
+    int64_t obs_np[2], obs_lb[2], obs_md[2];
+    int obs_next;
     // captured cycles, keyed by the buffer state at the start of the cycle
     // (population buffer, LB step parity, particle buffers, position buffer),
     // each with the buffer state it leaves

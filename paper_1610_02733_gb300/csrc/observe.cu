@@ -127,11 +127,17 @@ __global__ void __launch_bounds__(RED_THREADS)
 }
 
 // one warp per column: lane l adds rows l, l + 32, ... in order, then a fixed
-// butterfly combines the lanes
+// butterfly combines the lanes; out[8], out[9] take the range and device
+// error flags as they stand at this point of the stream order
 template <typename T>
 __global__ void __launch_bounds__(32 * RED_COLS) observe_final_kernel(const double *partial, int rows, double inv_scale,
-                                                                      double *out) {
+                                                                      const int32_t *range_flag,
+                                                                      const int32_t *dev_error, double *out) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        out[RED_COLS] = (double)*range_flag;
+        out[RED_COLS + 1] = (double)*dev_error;
+    }
     double s = 0.0;
     for (int r = lane; r < rows; r += 32) s += partial[(int64_t)r * RED_COLS + c];
 #pragma unroll
@@ -164,7 +170,7 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     observe_final_kernel<T><<<1, 32 * RED_COLS, 0, ctx->stream>>>(ctx->red_partial, B, ctx->fix.inv_scale,
-                                                                   ctx->red_out);
+                                                                   ctx->range_flag, ctx->dev_error, ctx->red_out);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,7 @@ EXPORTS = (
     "lbmd_md_substep", "lbmd_lb_step", "lbmd_run_cycles", "lbmd_observables", "lbmd_get_populations",
     "lbmd_set_populations", "lbmd_get_node_field", "lbmd_get_transfer", "lbmd_get_particles",
     "lbmd_get_particles_device", "lbmd_get_counts", "lbmd_stream", "lbmd_last_error", "lbmd_status_string",
+    "lbmd_set_particles_async", "lbmd_get_particles_async", "lbmd_observables_async", "lbmd_synchronize",
     "lbmd_particle_sums_static", "lbmd_set_moments_wait", "lbmd_moments_fallback_rows", "lbmd_set_frozen_copy",
     "lbmd_batch_create", "lbmd_batch_destroy", "lbmd_batch_add_particles", "lbmd_batch_run", "lbmd_batch_kinetic",
     "lbmd_batch_kinetic_device",
@@ -130,6 +131,10 @@ def load():
         getattr(L, name).argtypes = [P, ct.c_void_p]
     L.lbmd_get_particles.argtypes = [P, ct.c_void_p, ct.c_void_p]
     L.lbmd_get_particles_device.argtypes = [P, ct.c_void_p, ct.c_void_p]
+    L.lbmd_set_particles_async.argtypes = [P, ct.c_void_p, ct.c_void_p]
+    L.lbmd_get_particles_async.argtypes = [P, ct.c_void_p, ct.c_void_p]
+    L.lbmd_observables_async.argtypes = [P, ct.POINTER(LbmdObservables)]
+    L.lbmd_synchronize.argtypes = [P]
     L.lbmd_get_counts.argtypes = [P, i64p, i64p, i64p, i64p, ct.POINTER(ct.c_int32)]
     L.lbmd_particle_sums_static.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p]
     L.lbmd_set_moments_wait.argtypes = [P, ct.c_int32]
@@ -230,11 +235,15 @@ def lbmd_run_cycles(h, n: int):
     return _check(h, load().lbmd_run_cycles(h, int(n)), "lbmd_run_cycles")
 
 
+def observables_dict(o: LbmdObservables) -> dict:
+    return {"mass": o.mass, "p_fluid": np.array(list(o.p_fluid)), "p_particles": np.array(list(o.p_particles)),
+            "kT_particles": o.kT_particles, "e_kin": o.e_kin, "lb_step": o.lb_step, "md_step": o.md_step}
+
+
 def lbmd_observables(h) -> dict:
     o = LbmdObservables()
     _check(h, load().lbmd_observables(h, ct.byref(o)), "lbmd_observables")
-    return {"mass": o.mass, "p_fluid": np.array(list(o.p_fluid)), "p_particles": np.array(list(o.p_particles)),
-            "kT_particles": o.kT_particles, "e_kin": o.e_kin, "lb_step": o.lb_step, "md_step": o.md_step}
+    return observables_dict(o)
 
 
 def lbmd_particle_sums_static(vel_ptr: int, mass_ptr, n: int, out_ptr: int, stream=None):
@@ -288,6 +297,7 @@ class LBMD:
         self.shape = (int(nx), int(ny), int(nz))
         self.n_nodes = int(nx) * int(ny) * int(nz)
         self.n_sub = self.params.n_sub
+        self._pending = []  # host objects the asynchronous accessors still use
         self._h = lbmd_create(self.params)
 
     @property
@@ -421,6 +431,37 @@ class LBMD:
         vel = np.empty(3 * max(n, 1))
         _check(self._h, load().lbmd_get_particles(self._h, _ptr(pos), _ptr(vel)), "lbmd_get_particles")
         return pos[:3 * n].reshape(n, 3), vel[:3 * n].reshape(n, 3)
+
+    # asynchronous accessors: enqueue only; host arrays stay in use until synchronize()
+    def set_particles_async(self, pos=None, vel=None):
+        """Enqueue an upload of host arrays (pinned torch tensors or numpy,
+        float64, 3 N each), which must stay unchanged until synchronize()."""
+        self._pending.append((pos, vel))
+        _check(self._h, load().lbmd_set_particles_async(self._h, _host_addr(pos), _host_addr(vel)),
+               "lbmd_set_particles_async")
+
+    def particles_async(self, pos, vel):
+        """Enqueue a download of the positions and velocities at this point of
+        the stream order into host arrays of 3 N float64 (either may be None),
+        filled once synchronize() returns."""
+        self._pending.append((pos, vel))
+        _check(self._h, load().lbmd_get_particles_async(self._h, _host_addr(pos), _host_addr(vel)),
+               "lbmd_get_particles_async")
+
+    def observables_async(self) -> LbmdObservables:
+        """Enqueue the observables at this point of the stream order; the
+        returned structure is filled (observables_dict() reads it) once
+        synchronize() returns, which also reports its checks."""
+        o = LbmdObservables()
+        self._pending.append(o)
+        _check(self._h, load().lbmd_observables_async(self._h, ct.byref(o)), "lbmd_observables_async")
+        return o
+
+    def synchronize(self):
+        """Wait for all enqueued work and complete the queued observables."""
+        st = load().lbmd_synchronize(self._h)
+        self._pending = []
+        _check(self._h, st, "lbmd_synchronize")
 
     def set_moments_wait(self, polls: int):
         """Poll limit of the fused post-stream moments' wait (-1: default, 0:
