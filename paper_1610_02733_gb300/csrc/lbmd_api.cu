@@ -247,7 +247,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {(void **)&ctx->bond_r0, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE * sizeof(double)},
         {(void **)&ctx->bond_kind, (size_t)maxp * LBMD_MAX_BONDS_PER_PARTICLE},
         {(void **)&ctx->staging, (size_t)ctx->staging_len * sizeof(double)},
-        {(void **)&ctx->red_partial, (size_t)ctx->red_blocks * 8 * sizeof(double)},
+        {(void **)&ctx->red_partial, (size_t)ctx->red_blocks * 8 * sizeof(double) + 16},  // + arrival counter
         {(void **)&ctx->red_out, 10 * sizeof(double)},
         {(void **)&ctx->d_lb_step, sizeof(unsigned long long)},
     };
@@ -266,6 +266,8 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->missed_total, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->range_flag, 0, sizeof(int32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_error, 0, sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctx->red_partial, 0, (size_t)ctx->red_blocks * 8 * sizeof(double) + 16, ctx->stream);
     if (e == cudaSuccess && ctx->edge_acc)
         e = cudaMemsetAsync(ctx->edge_acc, 0, (size_t)ctx->cact_cap * md_tile_edge_bytes(ctx), ctx->stream);
     if (e == cudaSuccess && ctx->tile_flag)

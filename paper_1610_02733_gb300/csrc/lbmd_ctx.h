@@ -164,7 +164,7 @@ struct lbmd_ctx {
     void *nb_ref4;
     double *staging;   // device staging buffer for host <-> device conversions
     int64_t staging_len;
-    double *red_partial;  // per-block partial sums of the observables
+    double *red_partial;  // per-block partial sums of the observables, then an arrival counter
     double *red_out;      // final sums (8), then the range and device error flags
     // range guard of the fixed-point momentum: set (sticky) by the kernels
     // that write a node record whose momentum reaches half the range

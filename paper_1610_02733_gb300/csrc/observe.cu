@@ -2,13 +2,21 @@
 // between the device storage and the FP64 host arrays of the C ABI.
 //
 // Observables (mass, fluid momentum incl. pending transfers, particle
-// momentum, sum of m v^2): every thread accumulates a fixed strided subset in
-// double precision, each block reduces in a fixed tree order into one row of
-// a partial-sum table, and a single block adds the rows in order.  The grid
-// size is fixed per context, so the sums are bitwise reproducible.
+// momentum, sum of m v^2): every thread accumulates a fixed strided subset,
+// each block reduces in a fixed tree order into one row of a partial-sum
+// table in double precision, and a single block adds the rows in order.  The
+// grid size is fixed per context, so the sums are bitwise reproducible.
+//
+// The FP64 pipes of this GPU issue a small fraction of the FP32 / integer
+// rate, so the per-element work of the FP32 forms avoids them: the mass and
+// the fluid momentum are summed in 64-bit integers (fixed point) up to the
+// block totals, the particle sums in pairs of FP32 values, and FP32 values
+// become doubles through their bit fields (exact, integer pipes).  Doubles
+// are added only per block and in the final reduction.
 #include "lbmd_ctx.h"
 #include "lbmd_device.cuh"
 #include "particle_core.cuh"
+#include "convert.cuh"
 
 namespace lbmd {
 
@@ -34,75 +42,243 @@ __device__ __forceinline__ void block_reduce_store(double v[NV], double *row) {
     }
 }
 
-// Momentum sums in fixed-point units: FP32 records hold 32-bit integers,
-// whose per-thread sums are exact in 64-bit integers (and exact again as
-// doubles, being far below 2^53); FP64 records (56 fraction bits) are summed
-// in doubles.
+__device__ __forceinline__ double to_double(float v) { return exact_double(v); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double cell_plus_fraction(uint32_t x, double f) { return (double)x + f; }
+
+// Fixed-order block reduction of NV 64-bit integers: a butterfly within each
+// warp, then thread 0 adds the warps' totals in warp order (integer sums are
+// exact, so the order only matters for the doubles beside them).
+template <int NV>
+__device__ __forceinline__ void block_sum_ll(long long v[NV]) {
+    __shared__ long long sh[RED_THREADS / 32][NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) sh[threadIdx.x >> 5][c] = v[c];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            long long t = 0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) t += sh[w][c];
+            v[c] = t;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Fluid sums.  FP64 records: rho and the fixed-point momentum (56 fraction
+// bits) are added in doubles.  FP32 records: the momentum components are
+// 32-bit fixed-point integers, added exactly in 64-bit integers; the density
+// is added in 64-bit integers too, in units of 2^-u, u = 40 - e
+// (e = ceil(log2 rho0)): every density of at least 2^(e - 17) is a whole
+// number of units, so those sums are exact, and smaller ones lose their parts
+// below one unit (2^(e - 40)).  Densities of 2^(e + 4) and more, infinite or
+// NaN (an unstable fluid) go to a double sum beside it, which keeps them
+// visible to the non-finite check; the integer terms stay below 2^44, so a
+// block's totals fit 64 bits while it adds fewer than 2^19 nodes.
+// ---------------------------------------------------------------------------
 template <typename T>
-struct MomentumSum {
-    using type = double;
+struct FluidSums {
+    using P = Prec<T>;
+    double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+    __device__ __forceinline__ void add(const typename P::node4 &n, int) {
+        rho += P::rho_of(n);
+        add_j(n);
+    }
+    __device__ __forceinline__ void add_j(const typename P::node4 &n) {
+        jx += (double)P::jx_of(n);
+        jy += (double)P::jy_of(n);
+        jz += (double)P::jz_of(n);
+    }
+    __device__ __forceinline__ void store(double *row, double) {
+        double v[4] = {rho, jx, jy, jz};
+        block_reduce_store<4>(v, row);
+    }
 };
 template <>
-struct MomentumSum<float> {
-    using type = long long;
+struct FluidSums<float> {
+    using P = Prec<float>;
+    long long q[4] = {0, 0, 0, 0};  // rho in units of 2^-u, then j in fixed-point units
+    double big = 0.0;
+    __device__ __forceinline__ void add(const P::node4 &n, int u) {
+        const uint32_t b = __float_as_uint(P::rho_of(n));
+        const int ex = (int)((b >> 23) & 0xffu);
+        const int sh = ex - 150 + u;  // a normal density is m 2^(ex - 150), m < 2^24
+        if (ex == 0xff || sh > 20) {
+            big += (double)P::rho_of(n);
+        } else if (ex != 0 && sh > -24) {
+            const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+            const long long t = sh >= 0 ? (m << sh) : (m >> -sh);
+            q[0] += (b >> 31) ? -t : t;
+        }
+        add_j(n);
+    }
+    __device__ __forceinline__ void add_j(const P::node4 &n) {
+        q[1] += (long long)P::jx_of(n);
+        q[2] += (long long)P::jy_of(n);
+        q[3] += (long long)P::jz_of(n);
+    }
+    __device__ __forceinline__ void store(double *row, double unit) {
+        double bsum = 0.0;
+        if (__syncthreads_or(big != 0.0)) {  // rare: a fluid far from rho0
+            double v[1] = {big};
+            block_reduce_store<1>(v, row);
+            __syncthreads();
+            bsum = row[0];
+        }
+        block_sum_ll<4>(q);
+        if (threadIdx.x == 0) {
+            row[0] = (double)q[0] * unit + bsum;
+            row[1] = (double)q[1];
+            row[2] = (double)q[2];
+            row[3] = (double)q[3];
+        }
+    }
 };
 
 // Variant B keeps the records of the active nodes in their compact array
 // during a cycle: a node's current record is found through the active words
-// (occw non-null), so no copy back is needed first.
+// (occw non-null), so no copy back is needed first.  Every thread issues the
+// loads of U nodes before it adds any (memory-level parallelism), and the
+// active-word lookups run one pass ahead of the record loads that depend on
+// them, so a pass waits on one round trip to memory, not two.
 template <typename T, int VARIANT>
-__global__ void __launch_bounds__(RED_THREADS)
-    observe_nodes_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc,
-                         const uint2 *occw, const typename Prec<T>::node4 *cact, int W, FastDiv fnx, int64_t N,
-                         double *partial) {
+__device__ __forceinline__ void observe_nodes(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc,
+                                              const uint2 *occw, const typename Prec<T>::node4 *cact, int W,
+                                              FastDiv fnx, int64_t N, int mass_u, double mass_unit, double *row) {
     using P = Prec<T>;
-    using M = typename MomentumSum<T>::type;
-    double rho = 0.0;
-    M jx = 0, jy = 0, jz = 0;
+    constexpr int U = VARIANT == LBMD_VARIANT_A ? (sizeof(T) == 8 ? 2 : 4) : (sizeof(T) == 8 ? 4 : 6);
+    FluidSums<T> acc;
     const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-    // four nodes per pass, all loaded before use (memory-level parallelism)
-    for (int64_t r0 = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; r0 < N; r0 += 4 * stride) {
-        typename P::node4 n[4], J[4];
+    // active-word lookups of the pass starting at r0 (slot -1: inactive or beyond N)
+    auto lookup = [&](int64_t r0, uint2 wd[U], int x[U]) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = r0 + u * stride;
+            x[u] = -1;
+            if (!occw || r >= N) continue;
+            const uint32_t row = fdiv((uint32_t)r, fnx);
+            x[u] = (int)((uint32_t)r - row * fnx.d);
+            wd[u] = occw[(size_t)row * W + (x[u] >> 5)];
+        }
+    };
+    int64_t r0 = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x;
+    uint2 wd[U];
+    int x[U];
+    lookup(r0, wd, x);
+    for (; r0 < N; r0 += U * stride) {
+        int sl[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) sl[u] = x[u] >= 0 ? active_slot(wd[u], x[u]) : -1;
+        typename P::node4 n[U], J[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
             const int64_t r = r0 + u * stride;
             if (r >= N) continue;
-            if (occw) {
-                const uint32_t row = fdiv((uint32_t)r, fnx);
-                const int x = (int)((uint32_t)r - row * fnx.d);
-                const int sl = active_slot(occw[(size_t)row * W + (x >> 5)], x);
-                n[u] = sl >= 0 ? cact[sl] : node[r];
-            } else {
-                n[u] = node[r];
-            }
+            n[u] = sl[u] >= 0 ? cact[sl[u]] : node[r];
             if (VARIANT == LBMD_VARIANT_A) J[u] = jacc[r];
         }
+        lookup(r0 + U * stride, wd, x);  // the next pass's words, in flight with this pass's records
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             if (r0 + u * stride >= N) continue;
-            rho += (double)P::rho_of(n[u]);
-            jx += (M)P::jx_of(n[u]);
-            jy += (M)P::jy_of(n[u]);
-            jz += (M)P::jz_of(n[u]);
-            if (VARIANT == LBMD_VARIANT_A) {
-                jx += (M)P::jx_of(J[u]);
-                jy += (M)P::jy_of(J[u]);
-                jz += (M)P::jz_of(J[u]);
-            }
+            acc.add(n[u], mass_u);
+            if (VARIANT == LBMD_VARIANT_A) acc.add_j(J[u]);
         }
     }
     // momenta stay in fixed-point units until the final scaling
-    double v[4] = {rho, (double)jx, (double)jy, (double)jz};
-    block_reduce_store<4>(v, partial + (int64_t)blockIdx.x * RED_COLS);
+    acc.store(row, mass_unit);
 }
+
+// ---------------------------------------------------------------------------
+// Particle sums (momentum m v and m v^2).  FP64 velocities: doubles.  FP32
+// velocities: every thread keeps each sum as an unevaluated pair hi + lo of
+// FP32 values -- hi the running sum, lo the exact rounding errors of its
+// additions (Knuth's two-sum) and of the products (FMA) -- about 44
+// significant bits, on the FP32 pipes; m = 1/w is the pair of the rounded
+// reciprocal and its residual.  A block combines the pairs in a fixed order
+// and stores hi + lo as a double.
+// ---------------------------------------------------------------------------
+struct FF {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(hi, x);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add(float x, float err) {
+        add(x);
+        lo = __fadd_rn(lo, err);
+    }
+};
+
+template <typename T>
+struct ParticleSums {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    __device__ __forceinline__ void add(const typename Prec<T>::real4 &V) {
+        const double m = V.w == T(1) ? 1.0 : 1.0 / (double)V.w;
+        v[0] += m * V.x;
+        v[1] += m * V.y;
+        v[2] += m * V.z;
+        v[3] += m * (V.x * V.x + V.y * V.y + V.z * V.z);
+    }
+    __device__ __forceinline__ void store(double *row) { block_reduce_store<4>(v, row); }
+};
+template <>
+struct ParticleSums<float> {
+    FF s[4];
+    __device__ __forceinline__ void add(const Prec<float>::real4 &V) {
+        const float mh = __frcp_rn(V.w);                                   // m = 1/w = mh + ml
+        const float ml = __fmul_rn(__fmaf_rn(-mh, V.w, 1.0f), mh);
+        const float c[3] = {V.x, V.y, V.z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float mv = __fmul_rn(mh, c[d]);                          // m v = mv + mve
+            const float mve = __fmaf_rn(ml, c[d], __fmaf_rn(mh, c[d], -mv));
+            s[d].add(mv, mve);
+            const float q = __fmul_rn(mv, c[d]);                           // m v^2 = q + qe
+            s[3].add(q, __fmaf_rn(mve, c[d], __fmaf_rn(mv, c[d], -q)));
+        }
+    }
+    __device__ __forceinline__ void store(double *row) {
+        __shared__ float sh[RED_THREADS / 32][4][2];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float h = __shfl_xor_sync(0xffffffffu, s[c].hi, off);
+                const float l = __shfl_xor_sync(0xffffffffu, s[c].lo, off);
+                s[c].add(h, l);
+            }
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sh[threadIdx.x >> 5][c][0] = s[c].hi;
+                sh[threadIdx.x >> 5][c][1] = s[c].lo;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                FF t;
+                for (int w = 0; w < RED_THREADS / 32; ++w) t.add(sh[w][c][0], sh[w][c][1]);
+                row[c] = exact_double(t.hi) + exact_double(t.lo);
+            }
+    }
+};
 
 // particles are visited in id order (not slot order), so the sums do not
 // depend on how the particles are currently arranged
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS)
-    observe_particles_kernel(const typename Prec<T>::real4 *vel4, const int32_t *slot_of, int64_t np,
-                             double *partial) {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+__device__ __forceinline__ void observe_particles(const typename Prec<T>::real4 *vel4, const int32_t *slot_of,
+                                                  int64_t np, double *row) {
+    ParticleSums<T> acc;
     const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
     for (int64_t id0 = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; id0 < np; id0 += 4 * stride) {
         typename Prec<T>::real4 Vs[4];
@@ -113,38 +289,61 @@ __global__ void __launch_bounds__(RED_THREADS)
         for (int u = 0; u < 4; ++u)
             if (sl[u] >= 0) Vs[u] = vel4[sl[u]];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (sl[u] < 0) continue;
-            const double m = 1.0 / (double)Vs[u].w;
-            const double vx = Vs[u].x, vy = Vs[u].y, vz = Vs[u].z;
-            v[0] += m * vx;
-            v[1] += m * vy;
-            v[2] += m * vz;
-            v[3] += m * (vx * vx + vy * vy + vz * vz);
-        }
+        for (int u = 0; u < 4; ++u)
+            if (sl[u] >= 0) acc.add(Vs[u]);
     }
-    block_reduce_store<4>(v, partial + (int64_t)blockIdx.x * RED_COLS + 4);
+    acc.store(row);
 }
 
-// one warp per column: lane l adds rows l, l + 32, ... in order, then a fixed
-// butterfly combines the lanes; out[8], out[9] take the range and device
-// error flags as they stand at this point of the stream order
-template <typename T>
-__global__ void __launch_bounds__(32 * RED_COLS) observe_final_kernel(const double *partial, int rows, double inv_scale,
-                                                                      const int32_t *range_flag,
-                                                                      const int32_t *dev_error, double *out) {
-    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// The observables in one launch: every block adds its share of the nodes and
+// of the particles into its row of the partial-sum table; the last block to
+// finish (an arrival counter behind the table, zero between launches) adds
+// the rows in order -- one warp per column, lane l taking rows l, l + 32, ...
+// (loads issued four rows ahead), then a fixed butterfly -- and writes the
+// sums, then the range and device error flags as they stand at this point of
+// the stream order, to out[0..9].
+static_assert(RED_THREADS == 32 * RED_COLS, "the last block has one warp per column");
+template <typename T, int VARIANT>
+__global__ void __launch_bounds__(RED_THREADS, 4)
+    observe_kernel(const typename Prec<T>::node4 *node, const typename Prec<T>::node4 *jacc, const uint2 *occw,
+                   const typename Prec<T>::node4 *cact, int W, FastDiv fnx, int64_t N, int mass_u,
+                   double mass_unit, const typename Prec<T>::real4 *vel4, const int32_t *slot_of, int64_t np,
+                   double *partial, double inv_scale, const int32_t *range_flag, const int32_t *dev_error,
+                   double *out) {
+    double *row = partial + (int64_t)blockIdx.x * RED_COLS;
+    observe_nodes<T, VARIANT>(node, jacc, occw, cact, W, fnx, N, mass_u, mass_unit, row);
+    observe_particles<T>(vel4, slot_of, np, row + 4);
+    unsigned *arrive = reinterpret_cast<unsigned *>(partial + (int64_t)gridDim.x * RED_COLS);
+    __shared__ int last;
     if (threadIdx.x == 0) {
-        out[RED_COLS] = (double)*range_flag;
-        out[RED_COLS + 1] = (double)*dev_error;
+        __threadfence();  // this block's row before its arrival
+        last = atomicAdd(arrive, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows = (int)gridDim.x;
     double s = 0.0;
-    for (int r = lane; r < rows; r += 32) s += partial[(int64_t)r * RED_COLS + c];
+    int r = lane;
+    for (; r + 96 < rows; r += 128) {
+        double a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = __ldcg(&partial[(int64_t)(r + 32 * k) * RED_COLS + c]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s += a[k];
+    }
+    for (; r < rows; r += 32) s += __ldcg(&partial[(int64_t)r * RED_COLS + c]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane != 0) return;
     if (c >= 1 && c <= 3) s *= inv_scale;  // fixed-point units -> momentum (a power of two: exact)
     out[c] = s;
+    if (c == 0) {
+        out[RED_COLS] = (double)*range_flag;
+        out[RED_COLS + 1] = (double)*dev_error;
+        *arrive = 0u;
+    }
 }
 
 template <typename T>
@@ -152,25 +351,22 @@ static cudaError_t observables_t(lbmd_ctx *ctx) {
     using P = Prec<T>;
     const int B = ctx->red_blocks;
     const FastDiv fnx = make_fastdiv((uint32_t)ctx->p.nx);
+    const int mass_u = 40 - ctx->fix.e;  // the FP32 mass sum's unit 2^-mass_u
+    const double mass_unit = std::ldexp(1.0, -mass_u);
+    const auto *vel = static_cast<const typename P::real4 *>(vel_now(ctx));
     if (ctx->p.variant == LBMD_VARIANT_B)
-        observe_nodes_kernel<T, LBMD_VARIANT_B><<<B, RED_THREADS, 0, ctx->stream>>>(
+        observe_kernel<T, LBMD_VARIANT_B><<<B, RED_THREADS, 0, ctx->stream>>>(
             static_cast<const typename P::node4 *>(ctx->node), nullptr, active_words_now(ctx),
             static_cast<const typename P::node4 *>(active_records_now(ctx)), active_words(ctx->p.nx), fnx, ctx->N,
-            ctx->red_partial);
+            mass_u, mass_unit, vel, ctx->slot_of, ctx->np, ctx->red_partial, ctx->fix.inv_scale, ctx->range_flag,
+            ctx->dev_error, ctx->red_out);
     else  // variant A: the accumulating records of the active nodes (j* + J_acc), J_acc elsewhere; C: J_acc
-        observe_nodes_kernel<T, LBMD_VARIANT_A><<<B, RED_THREADS, 0, ctx->stream>>>(
+        observe_kernel<T, LBMD_VARIANT_A><<<B, RED_THREADS, 0, ctx->stream>>>(
             static_cast<const typename P::node4 *>(ctx->node), static_cast<const typename P::node4 *>(ctx->jacc),
             compact_nodes(ctx) ? active_words_now(ctx) : nullptr,
             static_cast<const typename P::node4 *>(compact_nodes(ctx) ? active_records_acc(ctx) : nullptr),
-            active_words(ctx->p.nx), fnx, ctx->N, ctx->red_partial);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    observe_particles_kernel<T><<<B, RED_THREADS, 0, ctx->stream>>>(
-        static_cast<const typename P::real4 *>(vel_now(ctx)), ctx->slot_of, ctx->np, ctx->red_partial);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    observe_final_kernel<T><<<1, 32 * RED_COLS, 0, ctx->stream>>>(ctx->red_partial, B, ctx->fix.inv_scale,
-                                                                   ctx->range_flag, ctx->dev_error, ctx->red_out);
+            active_words(ctx->p.nx), fnx, ctx->N, mass_u, mass_unit, vel, ctx->slot_of, ctx->np, ctx->red_partial,
+            ctx->fix.inv_scale, ctx->range_flag, ctx->dev_error, ctx->red_out);
     return cudaGetLastError();
 }
 
@@ -279,12 +475,12 @@ __global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, type
         src = first + t;
         p = slot_of[src];
     }
-    if (set_pos) pos4[p] = pos_from_double<T>(pos + 3 * src, nx, ny, nz);
+    if (set_pos) pos4[p] = pos_from_host<T>(pos + 3 * src, nx, ny, nz);
     typename P::real4 V = vel4[p];
     if (set_vel) {
-        V.x = (T)vel[3 * src + 0];
-        V.y = (T)vel[3 * src + 1];
-        V.z = (T)vel[3 * src + 2];
+        V.x = to_storage(vel[3 * src + 0], T());
+        V.y = to_storage(vel[3 * src + 1], T());
+        V.z = to_storage(vel[3 * src + 2], T());
     }
     if (set_mass) V.w = (T)(1.0 / (mass ? mass[src] : 1.0));
     vel4[p] = V;
@@ -306,15 +502,15 @@ __global__ void particles_to_double_kernel(const typename Prec<T>::real4 *pos4, 
         const uint32_t cell = (uint32_t)P::cell_of(R);  // < nx ny nz <= 2^32
         const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
         const uint32_t z = cell / nxy, rem = cell - z * nxy, y = rem / (uint32_t)nx, x = rem - y * (uint32_t)nx;
-        pos[3 * id + 0] = (double)x + (double)R.x;
-        pos[3 * id + 1] = (double)y + (double)R.y;
-        pos[3 * id + 2] = (double)z + (double)R.z;
+        pos[3 * id + 0] = cell_plus_fraction(x, R.x);
+        pos[3 * id + 1] = cell_plus_fraction(y, R.y);
+        pos[3 * id + 2] = cell_plus_fraction(z, R.z);
     }
     if (vel) {
         const typename P::real4 V = vel4[p];
-        vel[3 * id + 0] = (double)V.x;
-        vel[3 * id + 1] = (double)V.y;
-        vel[3 * id + 2] = (double)V.z;
+        vel[3 * id + 0] = to_double(V.x);
+        vel[3 * id + 1] = to_double(V.y);
+        vel[3 * id + 2] = to_double(V.z);
     }
 }
 
