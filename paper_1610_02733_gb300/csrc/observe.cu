@@ -489,19 +489,21 @@ __global__ void particles_from_double_kernel(typename Prec<T>::real4 *pos4, type
 // device state -> FP64 arrays in id order
 template <typename T>
 __global__ void particles_to_double_kernel(const typename Prec<T>::real4 *pos4, const typename Prec<T>::real4 *vel4,
-                                           const int32_t *slot_of, int64_t np, double *pos, double *vel, int nx,
-                                           int ny) {
+                                           const int32_t *slot_of, int64_t np, double *pos, double *vel, FastDiv fnx,
+                                           FastDiv fny) {
     using P = Prec<T>;
     // one thread per id: the FP64 host arrays are written in order
-    // (coalesced), the device records read from their slots
+    // (coalesced), the device records read from their slots (writing in slot
+    // order instead, with coalesced reads and scattered 24-byte writes, made
+    // the download and the cycle after it slower)
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= np) return;
     const int64_t p = slot_of[id];
     if (pos) {
         const typename P::real4 R = pos4[p];
         const uint32_t cell = (uint32_t)P::cell_of(R);  // < nx ny nz <= 2^32
-        const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
-        const uint32_t z = cell / nxy, rem = cell - z * nxy, y = rem / (uint32_t)nx, x = rem - y * (uint32_t)nx;
+        const uint32_t row = fdiv(cell, fnx), z = fdiv(row, fny);
+        const uint32_t x = cell - row * fnx.d, y = row - z * fny.d;
         pos[3 * id + 0] = cell_plus_fraction(x, R.x);
         pos[3 * id + 1] = cell_plus_fraction(y, R.y);
         pos[3 * id + 2] = cell_plus_fraction(z, R.z);
@@ -606,15 +608,14 @@ cudaError_t launch_particles_from_double(lbmd_ctx *ctx, int64_t first, int64_t c
 
 cudaError_t launch_particles_to_double(lbmd_ctx *ctx, double *pos, double *vel) {
     if (ctx->np <= 0) return cudaSuccess;
+    const FastDiv fnx = make_fastdiv((uint32_t)ctx->p.nx), fny = make_fastdiv((uint32_t)ctx->p.ny);
     if (ctx->p.precision == LBMD_FP64)
         particles_to_double_kernel<double><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
             static_cast<const Prec<double>::real4 *>(pos_now(ctx)),
-            static_cast<const Prec<double>::real4 *>(vel_now(ctx)), ctx->slot_of, ctx->np, pos, vel, ctx->p.nx,
-            ctx->p.ny);
+            static_cast<const Prec<double>::real4 *>(vel_now(ctx)), ctx->slot_of, ctx->np, pos, vel, fnx, fny);
     else
         particles_to_double_kernel<float><<<nblocks(ctx->np), 256, 0, ctx->stream>>>(
             static_cast<const Prec<float>::real4 *>(pos_now(ctx)),
-            static_cast<const Prec<float>::real4 *>(vel_now(ctx)),
-            ctx->slot_of, ctx->np, pos, vel, ctx->p.nx, ctx->p.ny);
+            static_cast<const Prec<float>::real4 *>(vel_now(ctx)), ctx->slot_of, ctx->np, pos, vel, fnx, fny);
     return cudaGetLastError();
 }
