@@ -656,7 +656,10 @@ def _source_hash(files):
 def _profiled_traffic(unit):
     """DRAM bytes (read + write) per launch of `unit` from the ncu summary in
     profiles/traffic.json; None unless the kernel sources still hash to the
-    value recorded with the capture."""
+    value recorded with the capture, and for any workload but the benchmark's
+    (the figures are for 256^3 / 10^6 particles, FP32, kT = 1e-4)."""
+    if (SHAPE, N_PARTICLES, KT, PRECISION) != ((256, 256, 256), 1_000_000, 1e-4, "fp32"):
+        return None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             d = json.load(fh)[unit]

@@ -17,13 +17,27 @@ namespace lbmd {
 // hardware conversion.
 // ---------------------------------------------------------------------------
 
+// The hardware conversions for the rare inputs outside the bit-field paths,
+// as volatile PTX so that the compiler keeps them inside their branches
+// instead of evaluating them for every element on the FP64 pipe.
+__device__ __forceinline__ double hw_f32_to_f64(float v) {
+    double r;
+    asm volatile("cvt.f64.f32 %0, %1;" : "=d"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float hw_f64_to_f32(double v) {
+    float r;
+    asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(r) : "d"(v));
+    return r;
+}
+
 // FP32 -> FP64 (exact): exponent re-biased by 1023 - 127, the 23 fraction
 // bits moved to the top of the 52.
 __device__ __forceinline__ double exact_double(float v) {
     const uint32_t b = __float_as_uint(v);
     const uint32_t ex = (b >> 23) & 0xffu;
     if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-    if (ex == 0u || ex == 0xffu) return (double)v;
+    if (ex == 0u || ex == 0xffu) return hw_f32_to_f64(v);
     const uint32_t hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
     return __hiloint2double((int)hi, (int)(b << 29));
 }
@@ -36,6 +50,9 @@ __device__ __forceinline__ double exact_double(uint32_t x) {
     return __longlong_as_double((long long)(((uint64_t)(e + 1023) << 52) | frac));
 }
 
+// the FP64 add for a subnormal offset (out of line: kept off the common path)
+static __device__ __noinline__ double cell_plus_subnormal(uint32_t x, float f) { return (double)x + (double)f; }
+
 // x + f rounded to nearest even as an FP64 value, for an integer x and an
 // FP32 f in [0, 1): the 53-bit significand is x's bits followed by the
 // leading fraction bits of f, rounded on the bits of f below them.
@@ -44,7 +61,7 @@ __device__ __forceinline__ double cell_plus_fraction(uint32_t x, float f) {
     if (fb == 0u) return exact_double(x);
     if (x == 0u) return exact_double(f);
     const int ex = (int)(fb >> 23);
-    if (ex == 0) return exact_double(x) + (double)f;  // subnormal offset: FP64 add
+    if (ex == 0) return cell_plus_subnormal(x, f);
     const uint64_t m = (fb & 0x7fffffu) | 0x800000u;  // f = m 2^(ex - 150)
     const int b = 32 - __clz(x);                       // x + f lies in [2^(b-1), 2^b]
     const int s = 97 - ex + b;                         // m's bits below the significand's last
@@ -90,7 +107,7 @@ __device__ __forceinline__ float round_to_float(double v) {
     const uint64_t b = (uint64_t)__double_as_longlong(v);
     const int ex = (int)((b >> 52) & 0x7ffu);
     if ((b << 1) == 0ull) return __uint_as_float((uint32_t)(b >> 32));  // signed zero
-    if (ex < 897 || ex > 1150) return (float)v;  // subnormal or overflowing result, non-finite input
+    if (ex < 897 || ex > 1150) return hw_f64_to_f32(v);  // subnormal or overflowing result, non-finite input
     const uint64_t mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
     return __uint_as_float((uint32_t)(b >> 32 & 0x80000000u) | fixed_to_float_bits(mant, 1075 - ex));
 }
@@ -98,6 +115,25 @@ __device__ __forceinline__ float round_to_float(double v) {
 // an FP64 value in the storage precision (rounded to nearest even)
 __device__ __forceinline__ float to_storage(double v, float) { return round_to_float(v); }
 __device__ __forceinline__ double to_storage(double v, double) { return v; }
+
+// one coordinate by the FP64 form of pos_from_double (out of line: kept off
+// the common path)
+static __device__ __noinline__ void pos_coord_fp64(double x, int L, uint32_t &fbits, uint32_t &c) {
+    const double Ld = (double)L;
+    if (!(x >= 0.0 && x < Ld)) {
+        x -= Ld * floor(x / Ld);
+        if (x >= Ld) x -= Ld;
+    }
+    double fl = floor(x);
+    float f = (float)(x - fl);
+    if (f >= 1.0f) {
+        f = 0.0f;
+        fl += 1.0;
+        if (fl >= Ld) fl = 0.0;
+    }
+    fbits = __float_as_uint(f);
+    c = (uint32_t)(int64_t)fl;
+}
 
 // pos_from_double for FP32 storage on the integer pipes: for 0 <= x < L the integer
 // part and the fraction bits are read off the binary64 fields and the
@@ -132,23 +168,7 @@ __device__ __forceinline__ Prec<float>::real4 pos_from_double_fp32(const double 
             }
             ok = ok && c < (uint32_t)L[d];
         }
-        if (!ok) {  // outside the box or a subnormal offset: the FP64 form
-            double x = x3[d];
-            const double Ld = (double)L[d];
-            if (!(x >= 0.0 && x < Ld)) {
-                x -= Ld * floor(x / Ld);
-                if (x >= Ld) x -= Ld;
-            }
-            double fl = floor(x);
-            float f = (float)(x - fl);
-            if (f >= 1.0f) {
-                f = 0.0f;
-                fl += 1.0;
-                if (fl >= Ld) fl = 0.0;
-            }
-            fbits = __float_as_uint(f);
-            c = (uint32_t)(int64_t)fl;
-        }
+        if (!ok) pos_coord_fp64(x3[d], L[d], fbits, c);  // outside the box or a subnormal offset
         fr[d] = __uint_as_float(fbits);
         cl[d] = (int64_t)c;
     }
