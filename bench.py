@@ -628,6 +628,13 @@ def run_gpu(args):
                            "speedup_vs_fp32": round(ms_per_step / ms, 3),
                            "lb_step_speedup_vs_fp32": round(lb_avg_ms / lb_ms, 3),
                            "lb_roofline_frac": round(lb_bytes / (lb_ms * 1e-3) / 1e9 / peak, 4)}
+        # the FP64 storage form (the verification precision): its cost on
+        # this GPU, whose FP64 pipes issue 2 FMA per SM per clock
+        ms, lb_ms = _time_form(torch, lbmd, inputs, stream, "fp64", 3, pos0, vel0)
+        forms["fp64"] = {"value": round(whole_job_rate(n_nodes, world, ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                         "ms_per_step": round(ms, 3), "lb_step_ms": round(lb_ms, 3),
+                         "slowdown_vs_fp32": round(ms / ms_per_step, 2),
+                         "lb_roofline_frac": round(2 * 19 * 8 * n_nodes / (lb_ms * 1e-3) / 1e9 / peak, 4)}
         line["precision_forms"] = forms
         line["precision_accuracy"] = _precision_accuracy(lbmd, inputs, stream, pos0, vel0)
         line["variants"] = _variant_costs(torch, lbmd, inputs, stream, pos0, vel0, min(args.steps, 30), ms_per_step)

@@ -116,3 +116,34 @@ def test_observables_equal_exact_sums_of_the_stored_values(masses):
     pf = [_fsum(nf[:, 1 + d]) for d in range(3)]
     np.testing.assert_allclose(o["p_fluid"], pf, rtol=0, atol=1e-14 * _fsum(np.abs(nf[:, 1:])))
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_mass_sum_far_from_rho0_and_non_finite_fluid(precision):
+    # densities beyond the FP32 form's fixed-point mass range (>= 2^(e + 4))
+    # are added beside it in double precision; a NaN density makes the
+    # observables non-finite, reported by both the synchronising and the
+    # queued observables
+    shape = (24, 10, 8)
+    g = lbmd.LBMD(*shape, variant="B", precision=precision, kT=0.0)
+    rest = g.populations()
+    f = rest.copy()
+    f[:, 17] *= 5000.0  # a node at rest with 5000 rho0
+    f[:, 400] *= 40.0
+    g.set_populations(f)
+    o = g.observables()
+    nf = g.node_field()
+    assert abs(o["mass"] - _fsum(nf[:, 0])) <= 1e-13 * o["mass"]
+    assert abs(o["mass"] / _fsum(f) - 1.0) <= (1e-6 if precision == "fp32" else 1e-13)
+    f[3, 55] = np.nan
+    g.set_populations(f)
+    with pytest.raises(lbmd.LbmdError) as e:
+        g.observables()
+    assert e.value.status == lbmd.LBMD_ERR_NONFINITE
+    g.observables_async()
+    with pytest.raises(lbmd.LbmdError) as e:
+        g.synchronize()
+    assert e.value.status == lbmd.LBMD_ERR_NONFINITE
+    g.set_populations(rest)
+    g.observables()
+    g.close()
