@@ -1,5 +1,6 @@
 // convert.cuh -- exact conversions between the FP64 host arrays of the C ABI
-// and the FP32 device storage, on the integer pipes (bit-field arithmetic).
+// and the FP32 device storage, on the integer pipes (bit-field arithmetic),
+// and the FP32-pair sums of the particle moments.
 #pragma once
 
 #include "lbmd_device.cuh"
@@ -173,6 +174,73 @@ __device__ __forceinline__ Prec<float>::real4 pos_from_double_fp32(const double 
         cl[d] = (int64_t)c;
     }
     return Prec<float>::make_pos(fr[0], fr[1], fr[2], cl[0] + (int64_t)nx * (cl[1] + (int64_t)ny * cl[2]));
+}
+
+// ---------------------------------------------------------------------------
+// Sums of FP32 values kept as unevaluated pairs hi + lo of FP32 values -- hi
+// the running sum, lo the exact rounding errors of its additions (Knuth's
+// two-sum) and of the products (FMA) -- about 44 significant bits on the
+// FP32 pipes, for the particle sums of the FP32 forms.
+// ---------------------------------------------------------------------------
+struct FF {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(hi, x);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add(float x, float err) {
+        add(x);
+        lo = __fadd_rn(lo, err);
+    }
+};
+
+// m v (three components, s[0..2]) and m v^2 (s[3]) of one particle with
+// velocity (vx, vy, vz) and w = 1/m; m as the pair of the rounded reciprocal
+// and its residual
+__device__ __forceinline__ void add_particle_moments(FF s[4], float vx, float vy, float vz, float w) {
+    const float mh = __frcp_rn(w);
+    const float ml = __fmul_rn(__fmaf_rn(-mh, w, 1.0f), mh);
+    const float c[3] = {vx, vy, vz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float mv = __fmul_rn(mh, c[d]);  // m v = mv + mve
+        const float mve = __fmaf_rn(ml, c[d], __fmaf_rn(mh, c[d], -mv));
+        s[d].add(mv, mve);
+        const float q = __fmul_rn(mv, c[d]);  // m v^2 = q + qe
+        s[3].add(q, __fmaf_rn(mve, c[d], __fmaf_rn(mv, c[d], -q)));
+    }
+}
+
+// The block's totals of NV pairs in a fixed order (a butterfly within each
+// warp, then the warps in order), as doubles in thread 0's out[]
+template <int THREADS, int NV>
+__device__ __forceinline__ void ff_block_sum(FF s[NV], double out[NV]) {
+    __shared__ float sh[THREADS / 32][NV][2];
+#pragma unroll
+    for (int c = 0; c < NV; ++c)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float h = __shfl_xor_sync(0xffffffffu, s[c].hi, off);
+            const float l = __shfl_xor_sync(0xffffffffu, s[c].lo, off);
+            s[c].add(h, l);
+        }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            sh[threadIdx.x >> 5][c][0] = s[c].hi;
+            sh[threadIdx.x >> 5][c][1] = s[c].lo;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            FF t;
+            for (int w = 0; w < THREADS / 32; ++w) t.add(sh[w][c][0], sh[w][c][1]);
+            out[c] = exact_double(t.hi) + exact_double(t.lo);
+        }
 }
 
 template <typename T>

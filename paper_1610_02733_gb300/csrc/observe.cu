@@ -203,21 +203,6 @@ __device__ __forceinline__ void observe_nodes(const typename Prec<T>::node4 *nod
 // reciprocal and its residual.  A block combines the pairs in a fixed order
 // and stores hi + lo as a double.
 // ---------------------------------------------------------------------------
-struct FF {
-    float hi = 0.0f, lo = 0.0f;
-    __device__ __forceinline__ void add(float x) {
-        const float s = __fadd_rn(hi, x);
-        const float bb = __fsub_rn(s, hi);
-        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-        hi = s;
-        lo = __fadd_rn(lo, e);
-    }
-    __device__ __forceinline__ void add(float x, float err) {
-        add(x);
-        lo = __fadd_rn(lo, err);
-    }
-};
-
 template <typename T>
 struct ParticleSums {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -232,44 +217,14 @@ struct ParticleSums {
 };
 template <>
 struct ParticleSums<float> {
-    FF s[4];
-    __device__ __forceinline__ void add(const Prec<float>::real4 &V) {
-        const float mh = __frcp_rn(V.w);                                   // m = 1/w = mh + ml
-        const float ml = __fmul_rn(__fmaf_rn(-mh, V.w, 1.0f), mh);
-        const float c[3] = {V.x, V.y, V.z};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float mv = __fmul_rn(mh, c[d]);                          // m v = mv + mve
-            const float mve = __fmaf_rn(ml, c[d], __fmaf_rn(mh, c[d], -mv));
-            s[d].add(mv, mve);
-            const float q = __fmul_rn(mv, c[d]);                           // m v^2 = q + qe
-            s[3].add(q, __fmaf_rn(mve, c[d], __fmaf_rn(mv, c[d], -q)));
-        }
-    }
+    FF s[4];  // m v_x, m v_y, m v_z, m v^2
+    __device__ __forceinline__ void add(const Prec<float>::real4 &V) { add_particle_moments(s, V.x, V.y, V.z, V.w); }
     __device__ __forceinline__ void store(double *row) {
-        __shared__ float sh[RED_THREADS / 32][4][2];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const float h = __shfl_xor_sync(0xffffffffu, s[c].hi, off);
-                const float l = __shfl_xor_sync(0xffffffffu, s[c].lo, off);
-                s[c].add(h, l);
-            }
-        if ((threadIdx.x & 31) == 0)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                sh[threadIdx.x >> 5][c][0] = s[c].hi;
-                sh[threadIdx.x >> 5][c][1] = s[c].lo;
-            }
-        __syncthreads();
+        double v[4];
+        ff_block_sum<RED_THREADS, 4>(s, v);
         if (threadIdx.x == 0)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                FF t;
-                for (int w = 0; w < RED_THREADS / 32; ++w) t.add(sh[w][c][0], sh[w][c][1]);
-                row[c] = exact_double(t.hi) + exact_double(t.lo);
-            }
+            for (int c = 0; c < 4; ++c) row[c] = v[c];
     }
 };
 

@@ -172,3 +172,19 @@ def test_negative_grid_cap_is_rejected():
     b, _ = _build("fp32")
     with pytest.raises(lbmd.LbmdError):
         b.set_lb_grid(-1)
+
+
+def test_kinetic_sums_fp32():
+    # FP32 velocities are summed as FP32 pairs (~44 bits): against exact sums
+    # of the stored values
+    import math
+    b, _ = _build("fp32")
+    b.run(10)
+    k = b.kinetic()
+    for i, r in enumerate(REPLICAS):
+        _, v = b.particles(i)
+        assert k[i, 4] == r[5]
+        e2 = math.fsum((v ** 2).ravel())
+        assert abs(k[i, 0] - e2) <= 1e-12 * max(1e-30, e2)
+        for d in range(3):
+            assert abs(k[i, 1 + d] - math.fsum(v[:, d])) <= 1e-12 * max(1e-30, math.fsum(np.abs(v[:, d])))
