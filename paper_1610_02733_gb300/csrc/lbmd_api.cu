@@ -56,7 +56,7 @@ void free_all(lbmd_ctx *ctx) {
                     ctx->nb_count,     ctx->nb_invalid,    ctx->nb_ref4,       ctx->range_flag,
                     ctx->missed_total, ctx->dev_error,     ctx->arow[0],       ctx->arow[1],
                     ctx->tile_table[0], ctx->tile_table[1], ctx->edge_acc,  ctx->tile_flag,
-                    ctx->late_rows,    ctx->late_count};
+                    ctx->late_rows,    ctx->late_count, ctx->ccw};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int b = 0; b < 2; ++b) {
@@ -229,6 +229,7 @@ lbmd_status lbmd_create(const lbmd_params *p, lbmd_ctx **out) {
         {&ctx->cact[1], compact ? (size_t)2 * ctx->cact_cap * node_bytes : 0},
         {(void **)&ctx->arow[0], compact ? arow_bytes : 0},
         {(void **)&ctx->arow[1], compact ? arow_bytes : 0},
+        {(void **)&ctx->ccw, compact ? occ_bytes / 2 : 0},
         {(void **)&ctx->dev_error, sizeof(int32_t)},
         {&ctx->tile_table[0], table_bytes},
         {&ctx->tile_table[1], table_bytes},

@@ -37,6 +37,9 @@
 //               observables and the host accessors.
 //   arow        variant B, per active set: compact slot of every row's first
 //               record (rows + 1 entries, the last the total).
+//   ccw         per cell row and 32-cell word, the cells that hold a particle
+//               at the last re-ordering (marked while counting the rows; the
+//               active words are built from them).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -129,6 +132,7 @@ struct lbmd_ctx {
     // s & 1 (built at the end of cycle s - 1); the LB step of cycle s reads
     // set s & 1 and writes the new moments into set (s + 1) & 1
     uint2 *occw[2];      // (ny * nz) x active_words(nx) words
+    uint32_t *ccw;       // (ny * nz) x active_words(nx): cells holding a particle, per cell row (re-ordering)
     void *cact[2];       // compact node records: two buffers of cact_cap each
     int32_t *arow[2];    // first compact slot of every row, ny * nz + 1 entries
     void *tile_table[2]; // per active set: the tiled MD step's table of every tile (md_tile.cu)

@@ -635,13 +635,49 @@ __global__ void nb_validate_kernel(int32_t *invalid) { *invalid = 0; }
 // ---------------------------------------------------------------------------
 // Re-ordering by lattice row.
 // ---------------------------------------------------------------------------
+// Every particle's rank within its cell row and, with ccw, its cell marked in
+// the row's occupancy words.  The particles come mostly in row order (the
+// order of the last re-ordering), so the valid lanes of a warp form runs of
+// equal rows (and of equal occupancy words): each run takes its ranks with one
+// atomic on the row's count, and ORs its cells into a word with one atomic.
+// The order within a row is free: every later sum is order-independent.
 template <typename T>
 __global__ void __launch_bounds__(256)
-    sort_count_kernel(const typename Prec<T>::real4 *pos4, int64_t np, FastDiv fnx, int32_t *row_count, int32_t *rank) {
+    sort_count_kernel(const typename Prec<T>::real4 *pos4, int64_t np, FastDiv fnx, int32_t *row_count, int32_t *rank,
+                      uint32_t *ccw, int W) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned act = __ballot_sync(0xffffffffu, p < np);  // a prefix of the warp's lanes
     if (p >= np) return;
-    const uint32_t row = fdiv((uint32_t)Prec<T>::cell_of(pos4[p]), fnx);
-    rank[p] = atomicAdd(&row_count[row], 1);
+    const int lane = (int)(threadIdx.x & 31), nvalid = __popc(act);
+    const unsigned upto = 0xffffffffu >> (31 - lane);  // lanes 0..lane
+    const uint32_t cell = (uint32_t)Prec<T>::cell_of(pos4[p]);
+    const uint32_t row = fdiv(cell, fnx);
+    // runs of equal rows: the run's first lane takes the ranks
+    const uint32_t row_prev = __shfl_up_sync(act, row, 1);
+    const unsigned heads = __ballot_sync(act, lane == 0 || row_prev != row);
+    const int head = 31 - __clz((int)(heads & upto));
+    const unsigned after = heads & ~upto;
+    const int next = after ? __ffs((int)after) - 1 : nvalid;
+    int base = 0;
+    if (lane == head) base = atomicAdd(&row_count[row], next - head);
+    base = __shfl_sync(act, base, head);
+    rank[p] = base + (lane - head);
+    if (ccw) {
+        const uint32_t cx = cell - row * fnx.d;
+        const unsigned long long key = (unsigned long long)row * (unsigned)W + (cx >> 5);
+        const unsigned long long key_prev = __shfl_up_sync(act, key, 1);
+        const unsigned kheads = __ballot_sync(act, lane == 0 || key_prev != key);
+        const unsigned kafter = kheads & ~upto;
+        const int knext = kafter ? __ffs((int)kafter) - 1 : nvalid;
+        // the run's cells ORed towards its first lane (segmented, log steps)
+        uint32_t bits = 1u << (cx & 31);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_down_sync(act, bits, off);
+            if (lane + off < knext) bits |= o;
+        }
+        if (kheads & (1u << lane)) atomicOr(&ccw[key], bits);
+    }
 }
 
 // Block-wide exclusive scan of one value per thread (1024 threads).
@@ -722,79 +758,82 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// Active nodes (variant B), rebuilt after each re-ordering.
+// Active nodes (variants A and B), rebuilt after each re-ordering.
 // ---------------------------------------------------------------------------
-// Level 0: one warp per node row marks nodes x and x + 1 of every particle in
-// the four cell rows with corners in this row, then stores the row's words
-// with the in-row slot of each word's first active node, and the row's count.
-template <typename T>
-__global__ void __launch_bounds__(32 * GATHER_WARPS)
-    active_rows_kernel(const typename Prec<T>::real4 *pos4, const int32_t *row_start, int nx, FastDiv fny, int nz,
-                       int W, uint2 *occw, int32_t *row_count, int n_rows) {
-    extern __shared__ uint32_t bits_smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *bits = bits_smem + (size_t)warp * W;
-    const int nrow = blockIdx.x * GATHER_WARPS + warp;
-    if (nrow >= n_rows) return;
+// Level 0: node x of row (y, z) is active when a particle's cell has it as a
+// corner, i.e. when cell x or x - 1 (periodic) of one of the four cell rows
+// (y - oy, z - oz), oy, oz in {0, 1}, holds a particle.  A group of L lanes
+// (L = min(32, W rounded up to a power of two)) builds one row's words from
+// the cell-occupancy words ccw, with the in-row slot of each word's first
+// active node (a scan over the group), and the row's count.
+__global__ void __launch_bounds__(256)
+    active_rows_kernel(const uint32_t *ccw, int nx, FastDiv fny, int nz, int W, int L, uint2 *occw, int32_t *row_count,
+                       int n_rows) {
+    const int lane = (int)(threadIdx.x & 31);
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nrow = gwarp * (32 / L) + lane / L, sub = lane % L;
+    const bool valid = nrow < n_rows;
     const int ny = (int)fny.d;
-    const int z = (int)fdiv((uint32_t)nrow, fny), y = nrow - z * ny;
-    for (int w = lane; w < W; w += 32) bits[w] = 0u;
-    // the four cell rows (y - oy, z - oz) as one run of entries, as in
-    // spread_rows_kernel
-    const int ym = y == 0 ? ny - 1 : y - 1, zm = z == 0 ? nz - 1 : z - 1;
-    const int c0 = y + ny * z, c1 = ym + ny * z, c2 = y + ny * zm, c3 = ym + ny * zm;
-    const int lo0 = row_start[c0], lo1 = row_start[c1], lo2 = row_start[c2], lo3 = row_start[c3];
-    const int e1 = row_start[c0 + 1] - lo0;
-    const int e2 = e1 + row_start[c1 + 1] - lo1;
-    const int e3 = e2 + row_start[c2 + 1] - lo2;
-    const int total = e3 + row_start[c3 + 1] - lo3;
-    __syncwarp();
-    for (int t = lane; t < total; t += 32) {
-        const bool b1 = t >= e1, b2 = t >= e2, b3 = t >= e3;
-        const int slot0 = b3 ? lo3 - e3 : b2 ? lo2 - e2 : b1 ? lo1 - e1 : lo0;
-        const int crow = b3 ? c3 : b2 ? c2 : b1 ? c1 : c0;
-        // freshly re-ordered: every particle's cell lies in its bucket's row
-        const int cx = (int)((uint32_t)Prec<T>::cell_of(pos4[slot0 + t]) - (uint32_t)crow * (uint32_t)nx);
-        const int x1 = cx + 1 == nx ? 0 : cx + 1;
-        atomicOr(&bits[cx >> 5], 1u << (cx & 31));
-        atomicOr(&bits[x1 >> 5], 1u << (x1 & 31));
+    int cr[4] = {0, 0, 0, 0};
+    if (valid) {
+        const int z = (int)fdiv((uint32_t)nrow, fny), y = nrow - z * ny;
+        const int ym = y == 0 ? ny - 1 : y - 1, zm = z == 0 ? nz - 1 : z - 1;
+        cr[0] = y + ny * z;
+        cr[1] = ym + ny * z;
+        cr[2] = y + ny * zm;
+        cr[3] = ym + ny * zm;
     }
-    __syncwarp();
+    const int last = nx - 1;
+    const uint32_t tail_mask = (nx & 31) ? ((1u << (nx & 31)) - 1u) : 0xffffffffu;
     int carry = 0;
-    for (int w0 = 0; w0 < W; w0 += 32) {
-        const int w = w0 + lane;
-        const uint32_t b = w < W ? bits[w] : 0u;
-        const int c = __popc(b);
-        int incl = c;
+    for (int w0 = 0; w0 < W; w0 += L) {  // uniform over the warp
+        const int w = w0 + sub;
+        uint32_t a = 0u;
+        if (valid && w < W) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t *cw = ccw + (size_t)cr[c] * W;
+                const uint32_t b = cw[w];
+                // cell x - 1 of bit x: the previous word's top bit, or (w = 0)
+                // the periodic neighbour x = nx - 1
+                const uint32_t in = w > 0 ? (cw[w - 1] >> 31) : ((cw[last >> 5] >> (last & 31)) & 1u);
+                a |= b | (b << 1) | in;
+            }
+            if (w == W - 1) a &= tail_mask;
+        }
+        const int cnt = __popc(a);
+        int incl = cnt;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
+            const int v = __shfl_up_sync(0xffffffffu, incl, off, L);
+            if (off < L && sub >= off) incl += v;
         }
-        if (w < W) occw[(size_t)nrow * W + w] = make_uint2(b, (uint32_t)(carry + incl - c));
-        carry += __shfl_sync(0xffffffffu, incl, 31);
+        if (valid && w < W) occw[(size_t)nrow * W + w] = make_uint2(a, (uint32_t)(carry + incl - cnt));
+        carry += __shfl_sync(0xffffffffu, incl, L - 1, L);
     }
-    if (lane == 0) row_count[nrow] = carry;
+    if (valid && sub == 0) row_count[nrow] = carry;
 }
 
 // Level 2 (after sort_chunk_scan_kernel turned the row counts into offsets
-// within chunks of 1024 rows): the first slot of every row, added to the
-// in-row slots of its words.
+// within chunks of 1024 rows): the first slot of every row added to the
+// in-row slots of its words, one word per thread; block (c, s) takes slice s
+// of chunk c's words.
+constexpr int FINALIZE_SLICES = 4;
 __global__ void __launch_bounds__(1024) active_finalize_kernel(const int32_t *row_offset, const int32_t *chunk_total,
                                                                int64_t n_rows, uint2 *occw, int W, int32_t *arow) {
     int32_t before;
     const int32_t v = (int)threadIdx.x < (int)blockIdx.x ? chunk_total[threadIdx.x] : 0;
     block_exclusive_scan(v, &before);  // total of the first blockIdx.x chunks
-    const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-    if (i >= n_rows) return;
-    const uint32_t b = (uint32_t)(before + row_offset[i]);
-    uint2 *wr = occw + (size_t)i * W;
-    for (int w = 0; w < W; ++w) wr[w].y += b;
-    // the row's first compact slot; the last row also closes the table
-    arow[i] = (int32_t)b;
-    if (i == n_rows - 1) {
-        const uint2 last = wr[W - 1];
-        arow[n_rows] = (int32_t)(last.y + __popc(last.x));
+    const int64_t r0 = (int64_t)blockIdx.x * 1024, r1 = r0 + 1024 < n_rows ? r0 + 1024 : n_rows;
+    const int64_t w_end = r1 * W;
+    for (int64_t i = r0 * W + (int64_t)blockIdx.y * 1024 + threadIdx.x; i < w_end; i += FINALIZE_SLICES * 1024) {
+        const int64_t row = i / W;
+        const uint32_t b = (uint32_t)(before + row_offset[row]);
+        uint2 wd = occw[i];
+        wd.y += b;
+        occw[i] = wd;
+        if (i == row * W) arow[row] = (int32_t)b;  // the row's first compact slot
+        if (row == n_rows - 1 && i == w_end - 1) arow[n_rows] = (int32_t)(wd.y + __popc(wd.x));  // closes the table
     }
 }
 
@@ -990,13 +1029,17 @@ static cudaError_t sort_t(lbmd_ctx *ctx) {
     const int b = ctx->pcur, o = b ^ 1;
     const int v = ctx->pv, vo = v ^ 1;  // position / velocity buffers
     const int64_t rows = (int64_t)ctx->p.ny * ctx->p.nz;
+    const int W = active_words(ctx->p.nx);
     cudaError_t e = cudaMemsetAsync(ctx->row_count, 0, (size_t)rows * sizeof(int32_t), ctx->stream);
     if (e != cudaSuccess) return e;
+    if (ctx->ccw && ctx->np > 0 &&
+        (e = cudaMemsetAsync(ctx->ccw, 0, (size_t)rows * W * sizeof(uint32_t), ctx->stream)) != cudaSuccess)
+        return e;
     if (ctx->np > 0) {
         const unsigned blocks = (unsigned)((ctx->np + 255) / 256);
         sort_count_kernel<T><<<blocks, 256, 0, ctx->stream>>>(static_cast<const R4 *>(ctx->pos4[v]), ctx->np,
                                                                 make_fastdiv((uint32_t)ctx->p.nx), ctx->row_count,
-                                                                ctx->sort_rank);
+                                                                ctx->sort_rank, ctx->ccw, W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int n_chunks = (int)((rows + 1023) / 1024);
         sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
@@ -1029,16 +1072,20 @@ static cudaError_t active_set_t(lbmd_ctx *ctx) {
         if (e != cudaSuccess) return e;
         return cudaMemsetAsync(arow, 0, (size_t)(rows + 1) * sizeof(int32_t), ctx->stream);
     }
-    const unsigned blocks = (unsigned)((rows + GATHER_WARPS - 1) / GATHER_WARPS);
-    active_rows_kernel<T><<<blocks, 32 * GATHER_WARPS, GATHER_WARPS * W * sizeof(uint32_t), ctx->stream>>>(
-        static_cast<const typename Prec<T>::real4 *>(pos_now(ctx)), ctx->row_start, ctx->p.nx,
-        make_fastdiv((uint32_t)ctx->p.ny), ctx->p.nz, W, occw, ctx->row_count, (int)rows);
+    int L = 1;
+    while (L < W && L < 32) L <<= 1;
+    const int64_t warps = (rows + (32 / L) - 1) / (32 / L);
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
+    active_rows_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->ccw, ctx->p.nx, make_fastdiv((uint32_t)ctx->p.ny),
+                                                        ctx->p.nz, W, L, occw, ctx->row_count, (int)rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int n_chunks = (int)((rows + 1023) / 1024);
     sort_chunk_scan_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, rows, ctx->chunk_total);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    active_finalize_kernel<<<n_chunks, 1024, 0, ctx->stream>>>(ctx->row_count, ctx->chunk_total, rows, occw, W, arow);
+    active_finalize_kernel<<<dim3(n_chunks, FINALIZE_SLICES), 1024, 0, ctx->stream>>>(ctx->row_count,
+                                                                                      ctx->chunk_total, rows, occw,
+                                                                                      W, arow);
     return cudaGetLastError();
 }
 
