@@ -224,7 +224,7 @@ def _precision_accuracy(lbmd, inputs, stream, pos, vel):
 BATCH_REPLICAS, BATCH_MD_STEPS, BATCH_SAMPLE = 512, 2000, 10
 
 
-def _batched_replicas(torch, lbmd, inputs, stream, peak):
+def _batched_replicas(torch, lbmd, inputs, stream, peak, schedule="period_graph", edges=(12, 16, 24, 32)):
     """The batched form: 512 independent replica boxes (cubic edges from
     {12, 16, 24, 32}, 1-400 ideal particles, zeta in [0.5, 5], m in {1, 5,
     10}, variants alternating A and B, kT = 1e-4, FP32), 2000 MD steps
@@ -234,7 +234,7 @@ def _batched_replicas(torch, lbmd, inputs, stream, peak):
     the replicas flagged unstable (explicit friction, zeta dt / m >~ 2)."""
     import numpy as np
 
-    cfg = inputs.replica_configs(BATCH_REPLICAS, SEED)
+    cfg = inputs.replica_configs(BATCH_REPLICAS, SEED, edges=edges)
     R = BATCH_REPLICAS
     b = lbmd.Batch(cfg["dims"], n_sub=cfg["n_sub"], variant=cfg["variant"], zeta=cfg["zeta"],
                    seed=np.arange(R, dtype=np.uint64) + np.uint64(SEED * 1000), max_particles=cfg["n_particles"],
@@ -243,7 +243,8 @@ def _batched_replicas(torch, lbmd, inputs, stream, peak):
         n = int(cfg["n_particles"][r])
         b.add_particles(r, inputs.uniform_positions(n, cfg["dims"][r], SEED + r),
                         inputs.maxwell_velocities(n, KT, SEED + r))
-    b.run(10)  # tunes the particle kernels and captures the period graph
+    b.set_schedule(schedule)
+    b.run(10)  # tunes the particle kernels and captures the graph
     n_samples = BATCH_MD_STEPS // BATCH_SAMPLE + 1
     kin = torch.empty((n_samples, R, 5), dtype=torch.float64, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -291,10 +292,13 @@ def _batched_replicas(torch, lbmd, inputs, stream, peak):
                    "median_drift_per_1000_steps": round(float(np.median(slope[sel])), 4),
                    "by_zeta_dt": byb}
     tune = b.tuning()
+    tune["persistent"] = b.persistent_tuning()
     b.close()
     return {
-        "workload": "512 replica boxes, edges {12,16,24,32}, 1-400 ideal particles, zeta in [0.5, 5], "
-                    "m in {1,5,10}, variants A/B alternating, kT=1e-4, FP32, 2000 MD steps",
+        "schedule": schedule,
+        "workload": "512 replica boxes, edges {%s}, 1-400 ideal particles, zeta in [0.5, 5], "
+                    "m in {1,5,10}, variants A/B alternating, kT=1e-4, FP32, 2000 MD steps"
+                    % ",".join(str(e) for e in edges),
         "value": round(node_updates / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
         "particle_substeps_per_s": float("%.4g" % (psteps / (ms * 1e-3))),
         "ms_total": round(ms, 2), "lb_node_updates": node_updates,
@@ -639,6 +643,9 @@ def run_gpu(args):
         line["precision_accuracy"] = _precision_accuracy(lbmd, inputs, stream, pos0, vel0)
         line["variants"] = _variant_costs(torch, lbmd, inputs, stream, pos0, vel0, min(args.steps, 30), ms_per_step)
         line["batched_replicas"] = _batched_replicas(torch, lbmd, inputs, stream, peak)
+        pers = _batched_replicas(torch, lbmd, inputs, stream, peak, "persistent")
+        line["batched_replicas"]["persistent"] = {k: pers[k] for k in ("ms_total", "value", "unit", "roofline_frac")}
+        line["batched_replicas"]["persistent"]["cluster_blocks"] = pers["tuning"]["persistent"]["cluster_blocks"]
         line["adjoint"] = _adjoint_form(torch, lbmd, inputs)
         line["kremer_grest"] = _kremer_grest_form(torch, stream)
         line["bead_spring_64"] = _bead_spring_64_form(torch, lbmd, inputs, stream)
@@ -832,6 +839,10 @@ def main():
                     help="population storage of the timed workload (profiling)")
     ap.add_argument("--only-form", default=None, choices=["batched_replicas"],
                     help="run only this form and print its JSON object (profiling)")
+    ap.add_argument("--schedule", default="period_graph", choices=["period_graph", "persistent"],
+                    help="schedule of the batched form with --only-form")
+    ap.add_argument("--edges", type=int, nargs="+", default=[12, 16, 24, 32],
+                    help="replica box edges of the batched form with --only-form")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     global SHAPE, N_PARTICLES, WORKLOAD, KT, PRECISION
@@ -851,7 +862,8 @@ def main():
     if args.only_form == "batched_replicas":
         import torch
         from paper_1610_02733_gb300 import inputs, lbmd
-        out = _batched_replicas(torch, lbmd, inputs, torch.cuda.Stream(), _peaks()[0])
+        out = _batched_replicas(torch, lbmd, inputs, torch.cuda.Stream(), _peaks()[0], args.schedule,
+                                tuple(args.edges))
         print(json.dumps(out))
         return
     run_gpu(args)

@@ -418,9 +418,10 @@ lbmd_status lbmd_particle_sums_static(const double *vel, const double *mass, int
  * (shared: rho0, nu, nu_bulk, gamma_ghost, kT; no body force, no bonds).  The
  * paper's temperature experiment (Sec. 4: particle temperature against zeta,
  * m and dt in variants A and B) needs many such boxes.  Every replica makes
- * one MD step per "tick" and its LB step after every m_r-th tick; the
- * P = lcm(m_r) ticks of a period are captured once into a CUDA graph and
- * replayed.  Block sizes are chosen by timing candidates on the batch
+ * one MD step per "tick" and its LB step after every m_r-th tick; by
+ * default the P = lcm(m_r) ticks of a period are captured once into a CUDA
+ * graph and replayed (lbmd_batch_set_schedule selects one persistent launch
+ * per call instead).  Block sizes are chosen by timing candidates on the batch
  * (lbmd_batch_tuning).  Explicit friction is unstable for zeta dt / m >~ 2:
  * a replica whose particle speed exceeds 1 (lattice units) or stops being
  * finite is flagged unstable and frozen rather than clamped
@@ -484,6 +485,33 @@ lbmd_status lbmd_batch_tuning(lbmd_batch *b, int32_t *nodes_per_block, int32_t *
  * depend on it; a small cap leaves SMs to other work on the device.
  * LBMD_ERR_ARG for a negative cap. */
 lbmd_status lbmd_batch_set_lb_grid(lbmd_batch *b, int32_t max_blocks);
+/* Schedule of lbmd_batch_run (Sec. 4's many-replica experiment; the paper
+ * itself steps one box at a time).
+ *   LBMD_BATCH_PERIOD_GRAPH (the default): per tick, one kernel per phase over
+ *     every replica (particles, variant-B transfers, collide and moments of
+ *     the due replicas); a period of lcm(m_r) ticks is captured in a CUDA
+ *     graph and replayed.
+ *   LBMD_BATCH_PERSISTENT: one launch per call, captured in a CUDA graph (one
+ *     graph per distinct md_steps): a grid of thread-block clusters of
+ *     cluster_blocks blocks of 256 threads, as many clusters as fit on the
+ *     GPU; each cluster takes replicas one at a time, heaviest first, and
+ *     runs all md_steps MD steps of the replica it holds, with cluster
+ *     barriers between the phases of a tick.  No replica waits for another.
+ * Both schedules run every node and particle through the same functions
+ * and give the same results bit for bit, except for a replica flagged
+ * unstable, whose frozen state differs (persistent: it stops at its
+ * cluster's next barrier).  cluster_blocks: 0 = the autotuner's choice (timed
+ * at creation over 1, 2, 4, 8 and 16 blocks on the rest state), else 1, 2, 4, 8
+ * or 16 (16: a non-portable cluster size, where the device allows it).
+ * Enqueued work is finished first (synchronising).  LBMD_ERR_ARG for an
+ * unknown schedule or cluster size. */
+#define LBMD_BATCH_PERIOD_GRAPH 0
+#define LBMD_BATCH_PERSISTENT 1
+lbmd_status lbmd_batch_set_schedule(lbmd_batch *b, int32_t schedule, int32_t cluster_blocks);
+/* The persistent schedule's tuned cluster size and its timings (ms of one
+ * period on the rest state) for 1, 2, 4, 8 and 16 blocks per cluster (ms: 5
+ * doubles or NULL; 0 for a size that does not fit on the device). */
+lbmd_status lbmd_batch_persistent_tuning(lbmd_batch *b, int32_t *cluster_blocks, double *ms);
 void *lbmd_batch_stream(lbmd_batch *b);
 const char *lbmd_batch_last_error(lbmd_batch *b);
 

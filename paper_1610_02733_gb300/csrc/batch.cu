@@ -98,23 +98,33 @@ struct BLbArgs {
     int noisy;
 };
 
-// One MD step of every particle: interpolation (Eq. (5)), friction and
-// random force (Eq. (4)), velocity Verlet with the force held over the step;
-// variant A hands the transfer straight to the accumulator, variant B keeps
-// the start position and the force for batch_transfer_kernel.
-template <typename T>
-__global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
+// Node records read through L2 only (ld.global.cg), for data that other
+// blocks of the same launch write.
+__device__ __forceinline__ int4 load_cg(const int4 *p) { return __ldcg(p); }
+__device__ __forceinline__ L4 load_cg(const L4 *p) {
+    const longlong2 a = __ldcg(reinterpret_cast<const longlong2 *>(p));
+    const longlong2 b = __ldcg(reinterpret_cast<const longlong2 *>(p) + 1);
+    L4 n;
+    n.x = a.x;
+    n.y = a.y;
+    n.z = b.x;
+    n.w = b.y;
+    return n;
+}
+
+// One MD step of the particle in slot p (replica r, index `local` within
+// it): interpolation (Eq. (5)), friction and random force (Eq. (4)) with the
+// Philox counter of the replica's MD step lb_step m_r + cyc (cyc: the MD step
+// within the replica's LB cycle), velocity Verlet with the force held over
+// the step; variant A hands the transfer straight to the accumulator,
+// variant B keeps the start position and the force for the transfer.  Shared
+// by both schedules of lbmd_batch_run, so that they do the same arithmetic.
+template <typename T, bool CG = false>
+__device__ __forceinline__ void batch_couple_particle(const BArgs<T> &a, int64_t p, int r, const BRep<T> &rp,
+                                                      int64_t local, unsigned long long lb_step, int cyc) {
     using P = Prec<T>;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n_slots) return;
-    // the slot's record is loaded with its replica index (every slot is
-    // allocated; an unused one is simply not used)
     const typename P::real4 R = a.pos4[p];
     typename P::real4 V = a.vel4[p];
-    const int r = a.prep[p];
-    const BRep<T> &rp = a.rep[r];
-    const int64_t local = p - rp.part_off;
-    if (local >= rp.np || a.unstable[r]) return;
     const CellXYZ c = cell_xyz(P::cell_of(R), rp.fd_nx, rp.fd_ny);
     uint32_t idx[8];
     T delta[8];
@@ -123,16 +133,15 @@ __global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
     T ux = T(0), uy = T(0), uz = T(0);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const typename P::node4 n = node[idx[k]];
+        const typename P::node4 n = CG ? load_cg(node + idx[k]) : node[idx[k]];
         const T w = delta[k] / P::rho_of(n);
-        ux += w * P::from_fix(P::jx_of(n), a.fis);
-        uy += w * P::from_fix(P::jy_of(n), a.fis);
-        uz += w * P::from_fix(P::jz_of(n), a.fis);
+        ux = fma(w, P::from_fix(P::jx_of(n), a.fis), ux);
+        uy = fma(w, P::from_fix(P::jy_of(n), a.fis), uy);
+        uz = fma(w, P::from_fix(P::jz_of(n), a.fis), uz);
     }
     T Fx = -rp.zeta * (V.x - ux), Fy = -rp.zeta * (V.y - uy), Fz = -rp.zeta * (V.z - uz);
     if (rp.amp != T(0)) {
-        const uint32_t md_step =
-            (uint32_t)(a.lb_step[r] * (unsigned long long)rp.n_sub + (unsigned)(a.tick % rp.n_sub));
+        const uint32_t md_step = (uint32_t)(lb_step * (unsigned long long)rp.n_sub + (unsigned)cyc);
         const U4 rnd = philox4x32_10(U4{(uint32_t)local, md_step, 1u, 0u}, rp.key0, rp.key1);
         Fx = fma(rp.amp, unit_uniform<T>(rnd.x), Fx);
         Fy = fma(rp.amp, unit_uniform<T>(rnd.y), Fy);
@@ -165,24 +174,45 @@ __global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
     }
 }
 
-// Variant B: the transfers of the MD step (Eqs. (7), (8)), once every
-// particle has read the node field.
+// Variant B: the transfers of the particle in slot p (Eqs. (7), (8)), once
+// every particle of its replica has read the node field.
 template <typename T>
-__global__ void __launch_bounds__(256) batch_transfer_kernel(BArgs<T> a) {
+__device__ __forceinline__ void batch_transfer_particle(const BArgs<T> &a, int64_t p, const BRep<T> &rp) {
     using P = Prec<T>;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n_slots) return;
     const typename P::real4 R = a.old4[p];
     const typename P::real4 F = a.fc4[p];
-    const int r = a.prep[p];
-    const BRep<T> &rp = a.rep[r];
-    if (rp.variant != LBMD_VARIANT_B || p - rp.part_off >= rp.np || a.unstable[r]) return;
     const CellXYZ c = cell_xyz(P::cell_of(R), rp.fd_nx, rp.fd_ny);
     uint32_t idx[8];
     T delta[8];
     corners(c, R.x, R.y, R.z, rp.nx, rp.ny, rp.nz, idx, delta);
     spread_to<T>(a.node + rp.node_off, idx, delta, F.x * rp.neg_scale_dt, F.y * rp.neg_scale_dt,
                  F.z * rp.neg_scale_dt);
+}
+
+// One MD step of every particle (per-tick schedule).
+template <typename T>
+__global__ void __launch_bounds__(256) batch_couple_kernel(BArgs<T> a) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n_slots) return;
+    // the slot's replica (every slot is allocated; an unused one is simply
+    // not used)
+    const int r = a.prep[p];
+    const BRep<T> &rp = a.rep[r];
+    const int64_t local = p - rp.part_off;
+    if (local >= rp.np || a.unstable[r]) return;
+    batch_couple_particle(a, p, r, rp, local, a.lb_step[r], a.tick % rp.n_sub);
+}
+
+// Variant B: the transfers of the MD step (per-tick schedule), once every
+// particle has read the node field.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_transfer_kernel(BArgs<T> a) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n_slots) return;
+    const int r = a.prep[p];
+    const BRep<T> &rp = a.rep[r];
+    if (rp.variant != LBMD_VARIANT_B || p - rp.part_off >= rp.np || a.unstable[r]) return;
+    batch_transfer_particle(a, p, rp);
 }
 
 // The LB kernels walk their work table with persistent blocks: block b takes
@@ -321,6 +351,62 @@ __device__ __forceinline__ typename Prec<T>::node4 staged_node(const unsigned ch
     return n;
 }
 
+// Collide node `loc` of replica rp at its LB step `step` (Eq. (3): moments,
+// the transfer of the cycle from the node record (B) or the accumulator
+// (A), MRT collision with noise) from its populations f and record n, and
+// push the result to the neighbours in the other buffer.  Shared by both
+// schedules of lbmd_batch_run.
+template <typename T, bool RELAX_FULL>
+__device__ __forceinline__ void batch_collide_node(const BLbArgs<T> &a, const BRep<T> &rp, unsigned long long step,
+                                                   int64_t loc, T (&f)[Q], const typename Prec<T>::node4 &n) {
+    using P = Prec<T>;
+    using N4 = typename P::node4;
+    const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
+    T *__restrict__ fout = ((step & 1ull) ? a.f0 : a.f1) + 19 * rp.node_off;
+    const uint32_t u = (uint32_t)loc;
+    const uint32_t row = fdiv(u, rp.fd_nx);
+    const int x = (int)(u - row * rp.fd_nx.d);
+    const int z = (int)fdiv(row, rp.fd_ny);
+    const int y = (int)(row - (uint32_t)z * rp.fd_ny.d);
+    T rho, jx, jy, jz;
+    node_moments(f, rho, jx, jy, jz);
+    T Fx, Fy, Fz;
+    if (rp.variant == LBMD_VARIANT_B) {
+        Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx, a.fs), a.fis);
+        Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy, a.fs), a.fis);
+        Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz, a.fs), a.fis);
+    } else {
+        Fx = P::from_fix(P::jx_of(n), a.fis);
+        Fy = P::from_fix(P::jy_of(n), a.fis);
+        Fz = P::from_fix(P::jz_of(n), a.fis);
+        N4 zero;
+        zero.x = zero.y = zero.z = zero.w = 0;
+        a.jacc[rp.node_off + loc] = zero;
+    }
+    collide<T, RELAX_FULL>(f, rho, rho, jx, jy, jz, Fx, Fy, Fz, a, rp.key0, rp.key1, u, (uint32_t)step);
+    const int nx = rp.nx, ny = rp.ny, nz = rp.nz;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int64_t d = (int64_t)X[CX(i) + 1] + (int64_t)nx * (Y[CY(i) + 1] + (int64_t)ny * Z[CZ(i) + 1]);
+        fout[(int64_t)i * N + d] = f[i];
+    }
+}
+
+// Post-stream moments (Eqs. (1), (2)) of node `loc` of replica rp from its
+// populations fl -> node field.  Shared by both schedules.
+template <typename T>
+__device__ __forceinline__ void batch_moments_node(const BLbArgs<T> &a, const BRep<T> &rp, int64_t loc,
+                                                   const T (&fl)[Q]) {
+    using P = Prec<T>;
+    T rho, jx, jy, jz;
+    node_moments(fl, rho, jx, jy, jz);
+    a.node[rp.node_off + loc] = P::pack(rho, P::to_fix(jx, a.fs), P::to_fix(jy, a.fs), P::to_fix(jz, a.fs));
+}
+
 // LB collide and push of the due replicas (Eq. (3)) on the nodes
 // [first, first + nodes_per_block) of each item.  Staged per node: the 19
 // populations and the node record (variant B) or the transfer accumulator
@@ -351,44 +437,12 @@ __global__ void __launch_bounds__(BATCH_LB_MAX_THREADS, sizeof(T) == 4 ? 4 : 2) 
         const BRep<T> &rp = it.rep;
         const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
         if (loc >= N) return;
-        const unsigned long long step = it.step;
-        T *__restrict__ fout = ((step & 1ull) ? a.f0 : a.f1) + 19 * rp.node_off;
-        const uint32_t u = (uint32_t)loc;
-        const uint32_t row = fdiv(u, rp.fd_nx);
-        const int x = (int)(u - row * rp.fd_nx.d);
-        const int z = (int)fdiv(row, rp.fd_ny);
-        const int y = (int)(row - (uint32_t)z * rp.fd_ny.d);
         const T *src = s_pop + (size_t)buf * Q * nb + t;
         T f[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i] = src[i * nb];
-        T rho, jx, jy, jz;
-        node_moments(f, rho, jx, jy, jz);
         const N4 n = staged_node<T>(s_node + ((size_t)buf * nb + t) * sizeof(N4));
-        T Fx, Fy, Fz;
-        if (rp.variant == LBMD_VARIANT_B) {
-            Fx = P::from_fix(P::jx_of(n) - P::to_fix(jx, a.fs), a.fis);
-            Fy = P::from_fix(P::jy_of(n) - P::to_fix(jy, a.fs), a.fis);
-            Fz = P::from_fix(P::jz_of(n) - P::to_fix(jz, a.fs), a.fis);
-        } else {
-            Fx = P::from_fix(P::jx_of(n), a.fis);
-            Fy = P::from_fix(P::jy_of(n), a.fis);
-            Fz = P::from_fix(P::jz_of(n), a.fis);
-            N4 zero;
-            zero.x = zero.y = zero.z = zero.w = 0;
-            a.jacc[rp.node_off + loc] = zero;
-        }
-        collide<T, RELAX_FULL>(f, rho, rho, jx, jy, jz, Fx, Fy, Fz, a, rp.key0, rp.key1, u, (uint32_t)step);
-        const int nx = rp.nx, ny = rp.ny, nz = rp.nz;
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-        const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int64_t d = (int64_t)X[CX(i) + 1] + (int64_t)nx * (Y[CY(i) + 1] + (int64_t)ny * Z[CZ(i) + 1]);
-            fout[(int64_t)i * N + d] = f[i];
-        }
+        batch_collide_node<T, RELAX_FULL>(a, rp, it.step, loc, f, n);
     };
     for_items(a, issue, body, [](const BItem<T> &) {});
 }
@@ -420,9 +474,7 @@ __global__ void __launch_bounds__(BATCH_LB_MAX_THREADS) batch_moments_kernel(BLb
         T fl[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) fl[i] = src[i * nb];
-        T rho, jx, jy, jz;
-        node_moments(fl, rho, jx, jy, jz);
-        a.node[rp.node_off + loc] = P::pack(rho, P::to_fix(jx, a.fs), P::to_fix(jy, a.fs), P::to_fix(jz, a.fs));
+        batch_moments_node(a, rp, loc, fl);
     };
     auto advance = [&](const BItem<T> &it) {
         if (!a.advance) return;
@@ -434,6 +486,145 @@ __global__ void __launch_bounds__(BATCH_LB_MAX_THREADS) batch_moments_kernel(BLb
         }
     };
     for_items(a, issue, body, advance);
+}
+
+// Persistent schedule (LBMD_BATCH_PERSISTENT).  One launch runs the `ticks`
+// MD steps of a lbmd_batch_run call for every replica.  The grid is a set of
+// thread-block clusters (as many as fit on the GPU at once); a cluster takes
+// replicas one at a time from a queue (heaviest first) and runs all the
+// ticks of the replica it holds, separating the phases of a tick with cluster
+// barriers (hardware barriers of blocks that the GPU schedules together, so
+// no wait can hang): the particles' MD step, [barrier], the variant-B
+// transfers, [barrier], and when the replica's LB step is due the collide and
+// push, [barrier], the post-stream moments, [barrier].  Replicas are
+// independent, so nothing synchronises the whole grid: a cluster that holds a
+// small replica simply takes the next one.  Every node and particle goes
+// through the same per-node and per-particle functions as in the per-tick
+// schedule.
+template <typename T>
+struct BPersist {
+    BArgs<T> p;             // particle arrays (p.tick unused)
+    BLbArgs<T> l;           // LB arrays and collision constants (work table unused)
+    const int32_t *order;   // replicas, heaviest first
+    int R;
+    int ticks;              // MD steps of this launch
+    int cluster;            // blocks per cluster
+    long long *tick0;       // first MD step of the launch; the last cluster to finish advances it
+    unsigned *queue;        // [0]: next index into order, [1]: clusters done (both zeroed before the launch)
+    int32_t *taken;         // per cluster, two slots by iteration parity: the index it took
+};
+
+// barrier of all threads of the cluster; release / acquire at cluster scope
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// The replica r's ticks by one cluster (tc: thread within the cluster, CT:
+// threads of the cluster).  Particle i of the replica stays with thread
+// i mod CT for the whole launch (its own writes feed its next MD step);
+// nodes, populations and records that other blocks write are read through
+// L2.  A replica flagged unstable stops at the next barrier of its cluster.
+template <typename T, bool RELAX_FULL>
+__device__ __forceinline__ void persistent_replica(const BPersist<T> &q, int r, long long t0, int64_t tc, int64_t CT) {
+    using P = Prec<T>;
+    using N4 = typename P::node4;
+    const BRep<T> &rp = q.l.rep[r];
+    if (__ldcg(q.p.unstable + r)) return;
+    unsigned long long step = __ldcg(q.l.lb_step + r);
+    const int64_t N = (int64_t)rp.nx * rp.ny * rp.nz;
+    const int64_t np = rp.np;
+    const bool B = rp.variant == LBMD_VARIANT_B;
+    const int m = rp.n_sub;
+    int cyc = (int)(t0 % (long long)m);
+    for (int k = 0; k < q.ticks; ++k) {
+        for (int64_t i = tc; i < np; i += CT) batch_couple_particle<T, true>(q.p, rp.part_off + i, r, rp, i, step, cyc);
+        const bool due = cyc == m - 1;
+        if (B || due) {
+            cluster_barrier();
+            if (__ldcg(q.p.unstable + r)) break;
+        }
+        if (B) {
+            for (int64_t i = tc; i < np; i += CT) batch_transfer_particle(q.p, rp.part_off + i, rp);
+            cluster_barrier();
+        }
+        if (due) {
+            const T *fin = ((step & 1ull) ? q.l.f1 : q.l.f0) + 19 * rp.node_off;
+            const N4 *rec = (B ? q.l.node : q.l.jacc) + rp.node_off;
+#ifdef PERSIST_PREFETCH
+            {
+                T fn[Q];
+                N4 nn;
+                if (tc < N) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) fn[i] = __ldcg(fin + (int64_t)i * N + tc);
+                    nn = load_cg(rec + tc);
+                }
+                for (int64_t loc = tc; loc < N; loc += CT) {
+                    T f[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) f[i] = fn[i];
+                    const N4 n = nn;
+                    if (loc + CT < N) {
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) fn[i] = __ldcg(fin + (int64_t)i * N + loc + CT);
+                        nn = load_cg(rec + loc + CT);
+                    }
+                    batch_collide_node<T, RELAX_FULL>(q.l, rp, step, loc, f, n);
+                }
+            }
+#else
+            for (int64_t loc = tc; loc < N; loc += CT) {
+                T f[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] = __ldcg(fin + (int64_t)i * N + loc);
+                const N4 n = load_cg(rec + loc);
+                batch_collide_node<T, RELAX_FULL>(q.l, rp, step, loc, f, n);
+            }
+#endif
+            cluster_barrier();
+            const T *fst = ((step & 1ull) ? q.l.f0 : q.l.f1) + 19 * rp.node_off;
+            for (int64_t loc = tc; loc < N; loc += CT) {
+                T fl[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) fl[i] = __ldcg(fst + (int64_t)i * N + loc);
+                batch_moments_node(q.l, rp, loc, fl);
+            }
+            ++step;
+            cluster_barrier();
+        }
+        cyc = cyc + 1 == m ? 0 : cyc + 1;
+    }
+    if (tc == 0) q.l.lb_step[r] = step;
+}
+
+constexpr int BATCH_PERSIST_THREADS = 256;
+#ifndef PERSIST_MINB
+#define PERSIST_MINB 4
+#endif
+
+template <typename T, bool RELAX_FULL>
+__global__ void __launch_bounds__(BATCH_PERSIST_THREADS, sizeof(T) == 4 ? PERSIST_MINB : 2)
+    batch_persistent_kernel(BPersist<T> q) {
+    const unsigned C = (unsigned)q.cluster;
+    const int rank = (int)(blockIdx.x % C), cid = (int)(blockIdx.x / C);
+    const int n_clusters = (int)(gridDim.x / C);
+    const int64_t tc = (int64_t)rank * blockDim.x + threadIdx.x;
+    const int64_t CT = (int64_t)C * blockDim.x;
+    const long long t0 = *q.tick0;
+    for (int it = 0;; ++it) {
+        int32_t *slot = q.taken + 2 * cid + (it & 1);
+        if (tc == 0) *slot = (int32_t)atomicAdd(&q.queue[0], 1u);
+        cluster_barrier();
+        // the slot is written again two iterations on, after every thread of
+        // the cluster has passed the next barrier (and so read it)
+        const int qi = __ldcg(slot);
+        if (qi >= q.R) break;
+        persistent_replica<T, RELAX_FULL>(q, q.order[qi], t0, tc, CT);
+    }
+    if (tc == 0) {
+        __threadfence();
+        if (atomicAdd(&q.queue[1], 1u) == (unsigned)n_clusters - 1u) *q.tick0 = t0 + q.ticks;
+    }
 }
 
 template <typename T>
@@ -584,6 +775,22 @@ struct lbmd_batch {
     int64_t ticks = 0;  // MD steps done by every replica
     cudaGraphExec_t graph = nullptr;
     double tune_ms_lb[3] = {0, 0, 0}, tune_ms_part[3] = {0, 0, 0};
+    // persistent schedule: replicas heaviest first, queue counters, the
+    // clusters' taken slots, the device copy of the tick count; graph of one
+    // launch for pticks MD steps
+    int schedule = LBMD_BATCH_PERIOD_GRAPH;
+    int cluster_req = 0;    // blocks per cluster asked for (0: the tuned size)
+    int cluster_tuned = 4;  // the autotuner's choice
+    double tune_ms_cluster[5] = {0, 0, 0, 0, 0};
+    int32_t *order = nullptr;
+    unsigned *queue = nullptr;
+    int32_t *taken = nullptr;
+    int64_t taken_cap = 0;  // clusters the taken array has room for
+    long long *dtick = nullptr;
+    bool dtick_valid = true;  // the device copy equals ticks
+    cudaGraphExec_t pgraph = nullptr;
+    int64_t pgraph_ticks = 0;
+    int pgraph_cluster = 0;
     std::string err;
 };
 
@@ -616,11 +823,13 @@ lbmd_status bcuda(lbmd_batch *b, cudaError_t e, const char *what) {
 size_t real_bytes(const lbmd_batch *b) { return b->precision == LBMD_FP64 ? 8 : 4; }
 
 void free_batch(lbmd_batch *b) {
-    void *bufs[] = {b->f[0], b->f[1], b->node, b->jacc, b->pos4, b->vel4, b->fc4, b->old4, b->prep, b->rep,
-                    b->lb_step, b->unstable, b->items_done, b->kin, b->staging, b->work};
+    void *bufs[] = {b->f[0], b->f[1],  b->node,  b->jacc,  b->pos4,  b->vel4,  b->fc4,  b->old4,
+                    b->prep, b->rep,   b->lb_step, b->unstable, b->items_done, b->kin, b->staging, b->work,
+                    b->order, b->queue, b->taken, b->dtick};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -800,6 +1009,87 @@ cudaError_t launch_tick(lbmd_batch *b, int64_t k) {
     return launch_lb_tables<T>(b, k, true);
 }
 
+// Persistent schedule: replicas by estimated work per MD step, heaviest
+// first (node updates N / m, the particles, and a fixed share for a tick's
+// barriers and latencies), so that the last clusters to start hold the
+// lightest replicas.
+cudaError_t upload_order(lbmd_batch *b) {
+    std::vector<int32_t> o((size_t)b->R);
+    std::iota(o.begin(), o.end(), 0);
+    std::vector<double> w((size_t)b->R);
+    for (int r = 0; r < b->R; ++r)
+        w[(size_t)r] = (double)b->nx[r] * b->ny[r] * b->nz[r] / b->n_sub[r] + 8.0 * b->np[r] + 2048.0;
+    std::stable_sort(o.begin(), o.end(), [&](int32_t x, int32_t y) { return w[(size_t)x] > w[(size_t)y]; });
+    return cudaMemcpyAsync(b->order, o.data(), o.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream);
+}
+
+template <typename T>
+void persistent_config(lbmd_batch *b, int C, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(BATCH_PERSIST_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+}
+
+bool relax_full(const lbmd_batch *b) { return b->co.gamma_bulk == 0.0 && b->co.gamma_ghost == 0.0; }
+
+// clusters of C blocks that fit on the device at once, at most one per
+// replica and the taken array's capacity (0: C does not fit)
+template <typename T>
+int persistent_clusters(lbmd_batch *b, int C) {
+    if (C > 8) {  // 16 blocks: a non-portable cluster size
+        if (cudaFuncSetAttribute(batch_persistent_kernel<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(batch_persistent_kernel<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                 1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+    }
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    persistent_config<T>(b, C, cfg, at);
+    int n = 0;
+    const cudaError_t e = relax_full(b) ? cudaOccupancyMaxActiveClusters(&n, batch_persistent_kernel<T, true>, &cfg)
+                                        : cudaOccupancyMaxActiveClusters(&n, batch_persistent_kernel<T, false>, &cfg);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return (int)std::min<int64_t>({(int64_t)n, (int64_t)b->R, b->taken_cap});
+}
+
+// one launch of the persistent kernel for `ticks` MD steps (after zeroing
+// the queue counters)
+template <typename T>
+cudaError_t launch_persistent(lbmd_batch *b, int ticks, int C, int n_clusters) {
+    BPersist<T> q;
+    q.p = make_bargs<T>(b, 0);
+    q.l = make_lbargs<T>(b, 0);
+    q.order = b->order;
+    q.R = b->R;
+    q.ticks = ticks;
+    q.cluster = C;
+    q.tick0 = b->dtick;
+    q.queue = b->queue;
+    q.taken = b->taken;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    persistent_config<T>(b, C, cfg, at);
+    cfg.gridDim = dim3((unsigned)(n_clusters * C));
+    cudaError_t e = cudaMemsetAsync(b->queue, 0, 2 * sizeof(unsigned), b->stream);
+    if (e != cudaSuccess) return e;
+    return relax_full(b) ? cudaLaunchKernelEx(&cfg, batch_persistent_kernel<T, true>, q)
+                         : cudaLaunchKernelEx(&cfg, batch_persistent_kernel<T, false>, q);
+}
+
 template <typename T>
 cudaError_t init_state(lbmd_batch *b) {
     const unsigned blocks = (unsigned)((b->n_nodes + 255) / 256);
@@ -808,6 +1098,8 @@ cudaError_t init_state(lbmd_batch *b) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->lb_step, 0, b->R * sizeof(unsigned long long), b->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->dtick, 0, sizeof(long long), b->stream)) != cudaSuccess) return e;
+    b->dtick_valid = b->ticks == 0;
     if ((e = cudaMemsetAsync(b->unstable, 0, b->R * sizeof(int), b->stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->jacc, 0, b->n_nodes * 4 * real_bytes(b), b->stream)) != cudaSuccess) return e;
     // node field of the rest state: the moments kernel reads buffer
@@ -923,6 +1215,85 @@ cudaError_t tune_particles(lbmd_batch *b) {
     return e;
 }
 
+// Persistent schedule: time one period on the current state for each
+// cluster size (1, 2, 4, 8 blocks); the state is re-initialised afterwards
+// by the caller.
+template <typename T>
+cudaError_t tune_persistent(lbmd_batch *b) {
+    const int cand[5] = {1, 2, 4, 8, 16};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    int best_c = 4;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
+        b->tune_ms_cluster[c] = 0.0;
+        const int nc = persistent_clusters<T>(b, cand[c]);
+        if (nc < 1) continue;
+        const int k = (int)b->period;
+        e = launch_persistent<T>(b, k, cand[c], nc);
+        cudaEventRecord(e0, b->stream);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = launch_persistent<T>(b, k, cand[c], nc);
+        cudaEventRecord(e1, b->stream);
+        if (e != cudaSuccess) break;
+        const double ms = time_ms(b->stream, e0, e1) / 2.0;
+        b->tune_ms_cluster[c] = ms;
+        if (ms < best) {
+            best = ms;
+            best_c = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cluster_tuned = best_c;
+    return e;
+}
+
+// lbmd_batch_run with the persistent schedule: one graph-replayed launch per
+// call (a graph per distinct md_steps; the launch reads its first tick from
+// the device copy of the tick count, which its last cluster advances)
+template <typename T>
+lbmd_status run_persistent(lbmd_batch *b, int64_t md_steps) {
+    const int C = b->cluster_req ? b->cluster_req : b->cluster_tuned;
+    const int nc = persistent_clusters<T>(b, C);
+    if (nc < 1) return bfail(b, LBMD_ERR_CUDA, "no cluster of the persistent schedule fits on the device");
+    if (!b->dtick_valid) {
+        const long long t = b->ticks;
+        BCK(b, cudaStreamSynchronize(b->stream));
+        BCK(b, cudaMemcpy(b->dtick, &t, sizeof(t), cudaMemcpyHostToDevice));
+        b->dtick_valid = true;
+    }
+    while (md_steps > 0) {
+        const int k = (int)std::min<int64_t>(md_steps, (int64_t)1 << 30);
+        if (!b->pgraph || b->pgraph_ticks != k || b->pgraph_cluster != C) {
+            if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+            b->pgraph = nullptr;
+            cudaGraph_t g = nullptr;
+            BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t e = launch_persistent<T>(b, k, C, nc);
+            const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return bcuda(b, e, "persistent launch capture");
+            }
+            if (e2 != cudaSuccess) return bcuda(b, e2, "cudaStreamEndCapture");
+            const cudaError_t e3 = cudaGraphInstantiate(&b->pgraph, g, 0);
+            cudaGraphDestroy(g);
+            if (e3 != cudaSuccess) {
+                b->pgraph = nullptr;
+                return bcuda(b, e3, "cudaGraphInstantiate");
+            }
+            b->pgraph_ticks = k;
+            b->pgraph_cluster = C;
+        }
+        BCK(b, cudaGraphLaunch(b->pgraph, b->stream));
+        b->ticks += k;
+        md_steps -= k;
+    }
+    return LBMD_OK;
+}
+
 #define LBMD_BATCH_DISPATCH(b, FN, ...) \
     ((b)->precision == LBMD_FP64 ? FN<double>(__VA_ARGS__) : FN<float>(__VA_ARGS__))
 
@@ -1036,6 +1407,9 @@ lbmd_status lbmd_batch_create(const lbmd_batch_params *p, lbmd_batch **out) {
         {(void **)&b->items_done, (size_t)R * sizeof(unsigned)},
         {(void **)&b->kin, (size_t)R * 5 * sizeof(double)},
         {(void **)&b->staging, (size_t)b->staging_len * sizeof(double)},
+        {(void **)&b->order, (size_t)R * sizeof(int32_t)},
+        {(void **)&b->queue, 2 * sizeof(unsigned)},
+        {(void **)&b->dtick, sizeof(long long)},
     };
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.ptr, a.bytes);
@@ -1051,6 +1425,15 @@ lbmd_status lbmd_batch_create(const lbmd_batch_params *p, lbmd_batch **out) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
         if (b->sms < 1) b->sms = 1;
+        // resident clusters of the persistent schedule: at most 32 blocks per SM
+        b->taken_cap = (int64_t)b->sms * 32;
+        const cudaError_t e = cudaMalloc(&b->taken, (size_t)2 * b->taken_cap * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            lbmd_status s = bcuda(nullptr, e, "cudaMalloc");
+            free_batch(b);
+            delete b;
+            return s;
+        }
     }
     std::vector<int32_t> prep((size_t)sl, 0);
     for (int r = 0; r < R; ++r)
@@ -1059,7 +1442,9 @@ lbmd_status lbmd_batch_create(const lbmd_batch_params *p, lbmd_batch **out) {
     if (e == cudaSuccess) e = LBMD_BATCH_DISPATCH(b, upload_reps, b);
     if (e == cudaSuccess) e = build_tables(b);
     if (e == cudaSuccess) e = LBMD_BATCH_DISPATCH(b, init_state, b);
+    if (e == cudaSuccess) e = upload_order(b);
     if (e == cudaSuccess) e = LBMD_BATCH_DISPATCH(b, tune_lb, b);
+    if (e == cudaSuccess) e = LBMD_BATCH_DISPATCH(b, tune_persistent, b);
     if (e == cudaSuccess) e = LBMD_BATCH_DISPATCH(b, init_state, b);  // tuning stepped the populations
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -1108,6 +1493,7 @@ lbmd_status lbmd_batch_add_particles(lbmd_batch *b, int32_t r, int64_t n, const 
     BCK(b, cudaGetLastError());
     b->np[r] += (int)n;
     BCK(b, LBMD_BATCH_DISPATCH(b, upload_reps, b));
+    BCK(b, upload_order(b));
     BCK(b, cudaStreamSynchronize(b->stream));
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
@@ -1120,7 +1506,9 @@ lbmd_status lbmd_batch_add_particles(lbmd_batch *b, int32_t r, int64_t n, const 
 lbmd_status lbmd_batch_run(lbmd_batch *b, int64_t md_steps) {
     LBMD_TRACE("lbmd_batch_run");
     if (!b || md_steps < 0) return LBMD_ERR_ARG;
+    if (b->schedule == LBMD_BATCH_PERSISTENT) return LBMD_BATCH_DISPATCH(b, run_persistent, b, md_steps);
     if (!b->particles_tuned && b->n_slots > 0) BCK(b, LBMD_BATCH_DISPATCH(b, tune_particles, b));
+    if (md_steps > 0) b->dtick_valid = false;  // the device tick copy serves the persistent schedule only
     int64_t left = md_steps;
     // eager ticks up to the next period boundary, whole periods from the
     // captured graph, eager ticks for the rest
@@ -1315,6 +1703,30 @@ lbmd_status lbmd_batch_set_lb_grid(lbmd_batch *b, int32_t max_blocks) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_batch_set_schedule(lbmd_batch *b, int32_t schedule, int32_t cluster_blocks) {
+    if (!b) return LBMD_ERR_ARG;
+    if (schedule != LBMD_BATCH_PERIOD_GRAPH && schedule != LBMD_BATCH_PERSISTENT)
+        return bfail(b, LBMD_ERR_ARG, "unknown schedule");
+    if (cluster_blocks != 0 && cluster_blocks != 1 && cluster_blocks != 2 && cluster_blocks != 4 && cluster_blocks != 8 &&
+        cluster_blocks != 16)
+        return bfail(b, LBMD_ERR_ARG, "cluster_blocks must be 0, 1, 2, 4, 8 or 16");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    if (schedule == LBMD_BATCH_PERSISTENT && cluster_blocks != 0 &&
+        LBMD_BATCH_DISPATCH(b, persistent_clusters, b, cluster_blocks) < 1)
+        return bfail(b, LBMD_ERR_ARG, "a cluster of that many blocks does not fit on the device");
+    b->schedule = schedule;
+    b->cluster_req = cluster_blocks;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_batch_persistent_tuning(lbmd_batch *b, int32_t *cluster_blocks, double *ms) {
+    if (!b) return LBMD_ERR_ARG;
+    if (cluster_blocks) *cluster_blocks = b->cluster_tuned;
+    if (ms)
+        for (int c = 0; c < 5; ++c) ms[c] = b->tune_ms_cluster[c];
     return LBMD_OK;
 }
 

@@ -24,6 +24,9 @@ LBMD_ERR_SEQUENCE = -4
 LBMD_ERR_NONFINITE = -5
 LBMD_ERR_CAPACITY = -6
 LBMD_ERR_RANGE = -7
+LBMD_BATCH_PERIOD_GRAPH = 0
+LBMD_BATCH_PERSISTENT = 1
+BATCH_SCHEDULES = {"period_graph": LBMD_BATCH_PERIOD_GRAPH, "persistent": LBMD_BATCH_PERSISTENT}
 VARIANT_A, VARIANT_B, VARIANT_C = 0, 1, 2
 FP32, FP64, FP16_DEV, BF16_DEV, FP16_DEV_SR, BF16_DEV_SR = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp32": FP32, "fp64": FP64, "fp16dev": FP16_DEV, "bf16dev": BF16_DEV, "fp16dev_sr": FP16_DEV_SR,
@@ -48,7 +51,7 @@ EXPORTS = (
     "lbmd_batch_kinetic_device",
     "lbmd_batch_unstable", "lbmd_batch_get_populations", "lbmd_batch_set_populations", "lbmd_batch_get_particles",
     "lbmd_batch_get_counts", "lbmd_batch_tuning", "lbmd_batch_set_lb_grid", "lbmd_batch_stream",
-    "lbmd_batch_last_error",
+    "lbmd_batch_last_error", "lbmd_batch_set_schedule", "lbmd_batch_persistent_tuning",
     "lbmd_adjoint_create", "lbmd_adjoint_destroy", "lbmd_adjoint_forward", "lbmd_adjoint_backward",
     "lbmd_adjoint_last_error",
 )
@@ -160,6 +163,8 @@ def load():
     L.lbmd_batch_get_counts.argtypes = [P, i32, i64p, i64p, i64p]
     L.lbmd_batch_tuning.argtypes = [P, ct.POINTER(i32), ct.POINTER(i32), P, P]
     L.lbmd_batch_set_lb_grid.argtypes = [P, i32]
+    L.lbmd_batch_set_schedule.argtypes = [P, i32, i32]
+    L.lbmd_batch_persistent_tuning.argtypes = [P, ct.POINTER(i32), P]
     L.lbmd_batch_stream.restype = ct.c_void_p
     L.lbmd_batch_stream.argtypes = [P]
     L.lbmd_batch_last_error.restype = ct.c_char_p
@@ -620,6 +625,21 @@ class Batch:
     def set_lb_grid(self, max_blocks: int):
         """Cap on the blocks of the persistent LB kernels (0: as many as fit)."""
         _bcheck(self._h, load().lbmd_batch_set_lb_grid(self._h, int(max_blocks)), "lbmd_batch_set_lb_grid")
+
+    def set_schedule(self, schedule: str, cluster_blocks: int = 0):
+        """Schedule of run(): "period_graph" (per-tick kernels, a period
+        replayed from a CUDA graph) or "persistent" (one launch per call,
+        thread-block clusters of cluster_blocks blocks each running whole
+        replicas; 0 = the tuned size)."""
+        _bcheck(self._h, load().lbmd_batch_set_schedule(self._h, BATCH_SCHEDULES[schedule], int(cluster_blocks)),
+                "lbmd_batch_set_schedule")
+
+    def persistent_tuning(self) -> dict:
+        c = ct.c_int32()
+        ms = np.zeros(5)
+        _bcheck(self._h, load().lbmd_batch_persistent_tuning(self._h, ct.byref(c), _ptr(ms)),
+                "lbmd_batch_persistent_tuning")
+        return {"cluster_blocks": c.value, "candidates": [1, 2, 4, 8, 16], "period_ms": ms.tolist()}
 
     @property
     def stream(self) -> int:
