@@ -550,29 +550,6 @@ __device__ __forceinline__ void persistent_replica(const BPersist<T> &q, int r, 
         if (due) {
             const T *fin = ((step & 1ull) ? q.l.f1 : q.l.f0) + 19 * rp.node_off;
             const N4 *rec = (B ? q.l.node : q.l.jacc) + rp.node_off;
-#ifdef PERSIST_PREFETCH
-            {
-                T fn[Q];
-                N4 nn;
-                if (tc < N) {
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) fn[i] = __ldcg(fin + (int64_t)i * N + tc);
-                    nn = load_cg(rec + tc);
-                }
-                for (int64_t loc = tc; loc < N; loc += CT) {
-                    T f[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) f[i] = fn[i];
-                    const N4 n = nn;
-                    if (loc + CT < N) {
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) fn[i] = __ldcg(fin + (int64_t)i * N + loc + CT);
-                        nn = load_cg(rec + loc + CT);
-                    }
-                    batch_collide_node<T, RELAX_FULL>(q.l, rp, step, loc, f, n);
-                }
-            }
-#else
             for (int64_t loc = tc; loc < N; loc += CT) {
                 T f[Q];
 #pragma unroll
@@ -580,7 +557,6 @@ __device__ __forceinline__ void persistent_replica(const BPersist<T> &q, int r, 
                 const N4 n = load_cg(rec + loc);
                 batch_collide_node<T, RELAX_FULL>(q.l, rp, step, loc, f, n);
             }
-#endif
             cluster_barrier();
             const T *fst = ((step & 1ull) ? q.l.f0 : q.l.f1) + 19 * rp.node_off;
             for (int64_t loc = tc; loc < N; loc += CT) {
@@ -598,12 +574,9 @@ __device__ __forceinline__ void persistent_replica(const BPersist<T> &q, int r, 
 }
 
 constexpr int BATCH_PERSIST_THREADS = 256;
-#ifndef PERSIST_MINB
-#define PERSIST_MINB 4
-#endif
 
 template <typename T, bool RELAX_FULL>
-__global__ void __launch_bounds__(BATCH_PERSIST_THREADS, sizeof(T) == 4 ? PERSIST_MINB : 2)
+__global__ void __launch_bounds__(BATCH_PERSIST_THREADS, sizeof(T) == 4 ? 4 : 2)
     batch_persistent_kernel(BPersist<T> q) {
     const unsigned C = (unsigned)q.cluster;
     const int rank = (int)(blockIdx.x % C), cid = (int)(blockIdx.x / C);
