@@ -140,3 +140,26 @@ def test_persistent_tuning_and_arguments():
         b.set_schedule("persistent", 3)
     with pytest.raises(lbmd.LbmdError):
         lbmd._bcheck(b._h, lbmd.load().lbmd_batch_set_schedule(b._h, 2, 0), "lbmd_batch_set_schedule")
+
+
+@pytest.mark.parametrize("schedule_first", ["persistent", "period_graph"])
+def test_particles_added_and_populations_replaced_between_runs(schedule_first):
+    # particles added after a run re-order the replicas (heaviest first) under
+    # the same captured launch; populations replaced at a replica's cycle
+    # boundary; both schedules give the same bits
+    def run(schedule):
+        b, _ = _build("fp32")
+        b.set_schedule(schedule)
+        b.run(10)
+        dims = REPLICAS[3][0]  # the replica that had no particles
+        b_pos = inputs.uniform_positions(1, dims, 77)
+        b.add_particles(3, b_pos, inputs.maxwell_velocities(1, 1e-3, 77))
+        b.run(10)
+        f = inputs.perturbed(b.populations(2), 0.02, 78)  # replica 2: m = 10, at its cycle boundary
+        b.set_populations(2, f)
+        b.run(5)
+        return b
+
+    b1 = run(schedule_first)
+    b2 = run("period_graph" if schedule_first == "persistent" else "persistent")
+    _assert_same(b1, b2, len(REPLICAS))
