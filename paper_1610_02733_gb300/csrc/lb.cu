@@ -187,13 +187,15 @@ __device__ __forceinline__ void collide_push_node(const LbArgs<T, S> &a, int x, 
     }
 }
 
-// Resident blocks per SM the compiler plans registers for: 7 (32 registers,
-// 20 bytes spilled) for the FP32 form with full relaxation and uniform noise,
-// measured 0.8 % faster per cycle than 6 (40 registers); the other forms
-// spill 50-300 bytes at 32 registers and keep 6 (3 in FP64).
+// Resident blocks per SM the compiler plans registers for: 7 (32 registers)
+// for the forms with full relaxation, uniform noise and FP32 or
+// rounded-to-nearest 16-bit storage, measured faster than 6 (40 registers)
+// despite their spills: FP32 cycle -0.8 %, FP16 / BF16 LB step -6.5 % /
+// -4.3 %; the stochastic-rounding form measured slower at 7, and it and the
+// Gaussian-noise and partial-relaxation forms keep 6 (3 in FP64).
 template <typename T, typename S, bool RELAX_FULL, bool GAUSS>
 constexpr int collide_min_blocks() {
-    return sizeof(T) == 8 ? 3 : (sizeof(S) == 4 && RELAX_FULL && !GAUSS ? 7 : 6);
+    return sizeof(T) == 8 ? 3 : (RELAX_FULL && !GAUSS && !PopStore<S, T>::stochastic ? 7 : 6);
 }
 
 template <typename T, typename S, bool RELAX_FULL, bool GAUSS>
