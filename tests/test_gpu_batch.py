@@ -188,3 +188,48 @@ def test_kinetic_sums_fp32():
         assert abs(k[i, 0] - e2) <= 1e-12 * max(1e-30, e2)
         for d in range(3):
             assert abs(k[i, 1 + d] - math.fsum(v[:, d])) <= 1e-12 * max(1e-30, math.fsum(np.abs(v[:, d])))
+
+
+@pytest.mark.parametrize("schedule", ["period_graph", "persistent"])
+def test_full_batched_configuration_sampled(schedule):
+    # the benchmark's batch itself (512 replicas, cubic edges {12, 16, 24, 32},
+    # 1-400 particles, zeta in [0.5, 5], m in {1, 5, 10}, variants A / B
+    # alternating, kT = 1e-4, FP32), 12 MD steps; a stable replica of every
+    # edge and every m is checked element by element against an oracle run
+    # of its own box
+    R, seed0 = 512, 1
+    cfg = inputs.replica_configs(R, seed0)
+    seeds = np.arange(R, dtype=np.uint64) + np.uint64(seed0 * 1000)
+    b = lbmd.Batch(cfg["dims"], n_sub=cfg["n_sub"], variant=cfg["variant"], zeta=cfg["zeta"], seed=seeds,
+                   max_particles=cfg["n_particles"], precision="fp32", kT=KT)
+    for r in range(R):
+        n = int(cfg["n_particles"][r])
+        b.add_particles(r, inputs.uniform_positions(n, cfg["dims"][r], seed0 + r),
+                        inputs.maxwell_velocities(n, KT, seed0 + r))
+    b.set_schedule(schedule)
+    steps = 12
+    b.run(steps)
+    unstable = b.unstable()
+    picked = {}
+    for r in range(R):
+        key = (int(cfg["dims"][r][0]), int(cfg["n_sub"][r]))
+        # inside the stable range of the explicit friction (zeta dt / m < 1)
+        if key not in picked and not unstable[r] and cfg["zeta"][r] / cfg["n_sub"][r] < 1.0:
+            picked[key] = r
+    assert len(picked) == 12, sorted(picked)  # 4 edges x 3 values of m
+    for (edge, m), r in sorted(picked.items()):
+        dims = tuple(int(d) for d in cfg["dims"][r])
+        n = int(cfg["n_particles"][r])
+        o = orc.Oracle(*dims, n_sub=m, variant={"A": 0, "B": 1}[cfg["variant"][r]], kT=KT,
+                       zeta=float(cfg["zeta"][r]), seed=int(seeds[r]))
+        o.add_particles(inputs.uniform_positions(n, dims, seed0 + r), inputs.maxwell_velocities(n, KT, seed0 + r))
+        _oracle_steps(o, m, 0, steps)
+        assert b.counts(r)["lb_step"] == steps // m
+        err = np.abs(b.populations(r) - o.populations()) / W[:, None]
+        assert float(err.max()) <= TOL["fp32"], (r, edge, m, float(err.max()))
+        pg, vg = b.particles(r)
+        po, vo = o.particles()
+        assert_vec_close(pg, po, "fp32", "replica %d positions" % r)
+        assert_vec_close(vg, vo, "fp32", "replica %d velocities" % r)
+        o.close()
+    b.close()
