@@ -190,18 +190,19 @@ def test_kinetic_sums_fp32():
             assert abs(k[i, 1 + d] - math.fsum(v[:, d])) <= 1e-12 * max(1e-30, math.fsum(np.abs(v[:, d])))
 
 
-@pytest.mark.parametrize("schedule", ["period_graph", "persistent"])
-def test_full_batched_configuration_sampled(schedule):
+@pytest.mark.parametrize("precision,schedule", [("fp32", "period_graph"), ("fp32", "persistent"),
+                                                ("fp64", "period_graph")])
+def test_full_batched_configuration_sampled(precision, schedule):
     # the benchmark's batch itself (512 replicas, cubic edges {12, 16, 24, 32},
     # 1-400 particles, zeta in [0.5, 5], m in {1, 5, 10}, variants A / B
-    # alternating, kT = 1e-4, FP32), 12 MD steps; a stable replica of every
+    # alternating, kT = 1e-4; FP32 as benchmarked, and FP64), 12 MD steps; a stable replica of every
     # edge and every m is checked element by element against an oracle run
     # of its own box
     R, seed0 = 512, 1
     cfg = inputs.replica_configs(R, seed0)
     seeds = np.arange(R, dtype=np.uint64) + np.uint64(seed0 * 1000)
     b = lbmd.Batch(cfg["dims"], n_sub=cfg["n_sub"], variant=cfg["variant"], zeta=cfg["zeta"], seed=seeds,
-                   max_particles=cfg["n_particles"], precision="fp32", kT=KT)
+                   max_particles=cfg["n_particles"], precision=precision, kT=KT)
     for r in range(R):
         n = int(cfg["n_particles"][r])
         b.add_particles(r, inputs.uniform_positions(n, cfg["dims"][r], seed0 + r),
@@ -226,10 +227,10 @@ def test_full_batched_configuration_sampled(schedule):
         _oracle_steps(o, m, 0, steps)
         assert b.counts(r)["lb_step"] == steps // m
         err = np.abs(b.populations(r) - o.populations()) / W[:, None]
-        assert float(err.max()) <= TOL["fp32"], (r, edge, m, float(err.max()))
+        assert float(err.max()) <= TOL[precision], (r, edge, m, float(err.max()))
         pg, vg = b.particles(r)
         po, vo = o.particles()
-        assert_vec_close(pg, po, "fp32", "replica %d positions" % r)
-        assert_vec_close(vg, vo, "fp32", "replica %d velocities" % r)
+        assert_vec_close(pg, po, precision, "replica %d positions" % r)
+        assert_vec_close(vg, vo, precision, "replica %d velocities" % r)
         o.close()
     b.close()
