@@ -115,3 +115,37 @@ def test_reduced_precision_lb_step_full_size_sampled(states, precision):
     exact = assert_rounded_like_oracle(np.array(got), want, step, dist)
     assert exact > 0.9, exact
     print("%s: %.4f of the sampled populations bit-identical to the oracle's rounding" % (precision, exact))
+
+
+def test_fp64_full_size(states):
+    # the verification precision on the same workload: the MD phase (every
+    # particle, every node's pending transfer) and the LB step on a sample of
+    # nodes, at the FP64 tolerance
+    from gpu_common import D3Q19_C, TOL, W
+    o, _ = states
+    g = lbmd.LBMD(*SHAPE, variant="B", precision="fp64", n_sub=N_SUB, kT=1e-4, zeta=1.0, seed=1, max_particles=NP)
+    g.add_particles(inputs.uniform_positions(NP, SHAPE, 1), inputs.maxwell_velocities(NP, 1e-4, 1))
+    for _ in range(N_SUB):
+        g.md_substep()
+    po, vo = o.particles()
+    pg, vg = g.particles()
+    d = pg - po
+    d -= 256.0 * np.round(d / 256.0)
+    assert np.abs(d).max() < 1e-10
+    assert np.abs(vg - vo).max() <= TOL["fp64"] * np.abs(vo).max()
+    J = o.jacc()
+    assert np.abs(g.transfer() - J).max() <= TOL["fp64"] * np.abs(J).max()
+    g.lb_step()
+    fg = g.populations()
+    g.close()
+    L = np.array(SHAPE)
+    rng = np.random.default_rng(7)
+    sample = np.vstack([rng.integers(0, 256, size=(100, 3)), [[0, 0, 0], [255, 255, 255], [0, 255, 1]]])
+    for r in sample:
+        want = np.zeros(19)
+        for i in range(19):
+            s = (r - D3Q19_C[i]) % L
+            sidx = int(s[0] + 256 * (s[1] + 256 * s[2]))
+            want[i] = o.collide_node(W * 1.0, J[sidx], node=sidx, lb_step=0)[i]
+        got = fg[:, int(r[0] + 256 * (r[1] + 256 * r[2]))]
+        assert (np.abs(got - want) / W).max() <= TOL["fp64"], (r, np.abs(got - want).max())
